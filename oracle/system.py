@@ -1,0 +1,134 @@
+"""ORACLE (test infrastructure).  Total field, energies and the explicit TDGL step.
+
+Eq. 2: F = F_Land + F_Grad + F_Elec + F_Ext; Eq. 7: F_Ext = -int E_ext . P, so the external
+field enters the effective field as +E_ext.  Eq. 1 with L = 1 (Sec. 2), integrated with the
+forward Euler rule (the simplest of the explicit schemes named in Sec. 3):
+    P <- P + dt * L * (h_Land + h_Grad + E_el + E_ext)      on material cells;
+vacuum cells keep P = 0 (Sec. 2: P = 0 outside the sample).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import electrostatics as _es
+from . import gradient as _grad
+from . import landau as _landau
+from . import tensor as _tensor
+from .material import coefficients
+
+TERM_LANDAU, TERM_GRAD, TERM_ELEC, TERM_EXT = 1, 2, 4, 8
+TERM_ALL = 15
+_COEF_KEYS = ("a1x", "a1y", "a1z", "a11", "a12", "a111", "a112", "a123", "G11", "G12", "G44", "G44p")
+
+
+class System:
+    """A finite sample on an (nx, ny, nz) grid of (dx, dy, dz) cells, SI units, float64.
+
+    mat: uint8 (nz, ny, nx) material ids (0 = vacuum); materials: {id: material record}.
+    conv: 'fft' (zero-padded FFT) or 'direct' (O(N^2) sum) for the electrostatic field.
+    """
+
+    def __init__(self, shape, cell, mat, materials, T, eps_b=1.0, E_ext=(0.0, 0.0, 0.0),
+                 terms=TERM_ALL, conv="fft", octant=None, L=1.0):
+        self.shape = tuple(int(v) for v in shape)
+        self.cell = tuple(float(v) for v in cell)
+        nx, ny, nz = self.shape
+        self.mat = np.asarray(mat, dtype=np.uint8).reshape(nz, ny, nx)
+        self.m = self.mat > 0
+        self.materials = dict(materials)
+        self.eps_b = float(eps_b)
+        self.E_ext = np.asarray(E_ext, dtype=np.float64).reshape(3)
+        self.terms = int(terms)
+        self.L = float(L)
+        self.V = self.cell[0] * self.cell[1] * self.cell[2]
+        self.conv = conv
+        self._octant = octant
+        self._convolver = None
+        self._Nfull = None
+        self.set_temperature(T)
+
+    # -- parameters -------------------------------------------------------------------------
+    def set_temperature(self, T):
+        self.T = float(T)
+        self.coef = {k: np.zeros(self.mat.shape) for k in _COEF_KEYS}
+        for mid, rec in self.materials.items():
+            sel = self.mat == mid
+            if not np.any(sel):
+                continue
+            c = coefficients(rec, self.T)
+            for k in _COEF_KEYS:
+                self.coef[k][sel] = c[k]
+
+    def _tensor_octant(self):
+        if self._octant is None:
+            self._octant = _tensor.octant(self.shape, self.cell)
+        return self._octant
+
+    # -- fields -----------------------------------------------------------------------------
+    def electrostatic_field(self, P):
+        P = np.asarray(P, dtype=np.float64)
+        if self.conv == "direct":
+            if self._Nfull is None:
+                self._Nfull = _tensor.full(self.shape, self.cell, self._tensor_octant())
+            return _es.direct(P, self._Nfull, self.eps_b)
+        if self._convolver is None:
+            self._convolver = _es.FFTConvolver(self.shape, self.cell, self._tensor_octant())
+        return self._convolver.apply(P, self.eps_b)
+
+    def fields(self, P):
+        """Dict of the four field contributions and their sum, each (3, nz, ny, nx), V/m."""
+        P = np.asarray(P, dtype=np.float64)
+        z = np.zeros(P.shape)
+        out = {"landau": z, "grad": z, "elec": z, "ext": z}
+        if self.terms & TERM_LANDAU:
+            out["landau"] = np.where(self.m, _landau.field(P, self.coef), 0.0)
+        if self.terms & TERM_GRAD:
+            out["grad"], _ = _grad.field_and_energy(P, self.mat, self.coef, self.cell)
+        if self.terms & TERM_ELEC:
+            out["elec"] = self.electrostatic_field(P)
+        if self.terms & TERM_EXT:
+            out["ext"] = np.where(self.m, self.E_ext[:, None, None, None], 0.0)
+        out["total"] = np.where(self.m, out["landau"] + out["grad"] + out["elec"] + out["ext"], 0.0)
+        return out
+
+    def energy(self, P):
+        """Energy terms of Eq. 2 in joules: land, grad, elec, ext, total."""
+        P = np.asarray(P, dtype=np.float64)
+        e = dict(land=0.0, grad=0.0, elec=0.0, ext=0.0)
+        if self.terms & TERM_LANDAU:
+            e["land"] = self.V * float(np.sum(np.where(self.m, _landau.energy_density(P, self.coef), 0.0)))
+        if self.terms & TERM_GRAD:
+            _, e["grad"] = _grad.field_and_energy(P, self.mat, self.coef, self.cell)
+        if self.terms & TERM_ELEC:
+            e["elec"] = _es.energy(self.electrostatic_field(P), P, self.V)
+        if self.terms & TERM_EXT:
+            e["ext"] = -self.V * float(np.sum(np.where(self.m, np.tensordot(self.E_ext, P, 1), 0.0)))
+        e["total"] = e["land"] + e["grad"] + e["elec"] + e["ext"]
+        return e
+
+    # -- dynamics ---------------------------------------------------------------------------
+    def step(self, P, dt):
+        """One forward Euler step of Eq. 1; returns the new P (float64)."""
+        P = np.asarray(P, dtype=np.float64)
+        Pn = P + dt * self.L * self.fields(P)["total"]
+        return np.where(self.m, Pn, 0.0)
+
+    def run(self, P, dt, n):
+        for _ in range(n):
+            P = self.step(P, dt)
+        return P
+
+    def relax(self, P, dt, tol, P0, max_steps, check_every=16):
+        """Step until max|P_new - P| / P0 < tol on a checked step (every check_every steps).
+
+        Returns (P, steps_taken, converged)."""
+        P = np.asarray(P, dtype=np.float64)
+        steps = 0
+        while steps < max_steps:
+            Pn = self.step(P, dt)
+            steps += 1
+            if steps % check_every == 0 or steps == max_steps:
+                if float(np.max(np.abs(Pn - P))) / P0 < tol:
+                    return Pn, steps, True
+            P = Pn
+        return P, steps, False

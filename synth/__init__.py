@@ -1,0 +1,128 @@
+"""Seeded synthetic inputs for the TDGL ferroelectric hot path.
+
+This module is shared by the FP64 oracle side and the CUDA side of every test and of the
+benchmark. It holds *inputs only*: the raw Table 1 coefficients as printed in the paper, grid
+recipes for the benchmark workloads, seeded initial polarization fields and material maps. It
+holds none of the method's arithmetic: it never evaluates a coefficient at a temperature, never
+computes a field, an energy or a tensor. Each side does that in its own code.
+
+Material records use SI units and the same field names as ``tdgl_material`` in ``include/tdgl.h``:
+
+    alpha1 = a0 * (T - T0)                              (a1_form = 0, linear)
+    alpha1 = coth_A * (coth(coth_Ts/T) - coth(coth_Ts/coth_T1))   (a1_form = 1)
+    alpha1 = a0                                         (a1_form = 2, temperature independent)
+    alpha11  = a11_0  + a11_T  * (T - a11_Tref)
+    alpha111 = a111_0 + a111_T * (T - a111_Tref)
+    alpha12, alpha112, alpha123, G11, G12, G44, G44p constant;
+    r_s scales the z quadratic coefficient (strain form of Sec. 4.4, r_s = 1 means none).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "material", "BTO", "PTO", "STO", "STO_LITERAL", "wall_material",
+    "uniform_P", "layer_map", "cylinder_start", "batch_sizes",
+    "CONFIG1", "CONFIG2", "CONFIG4", "EPS0",
+]
+
+#: vacuum permittivity, F/m (CODATA 2018); a physical constant, not method arithmetic
+EPS0 = 8.8541878128e-12
+
+
+def material(**kw) -> dict:
+    """A material record with every field present (defaults: zero coefficients, r_s = 1)."""
+    m = dict(a1_form=0, a0=0.0, T0=0.0, coth_A=0.0, coth_Ts=0.0, coth_T1=1.0,
+             a11_0=0.0, a11_T=0.0, a11_Tref=0.0, a12=0.0,
+             a111_0=0.0, a111_T=0.0, a111_Tref=0.0, a112=0.0, a123=0.0,
+             G11=0.0, G12=0.0, G44=0.0, G44p=0.0, r_s=1.0)
+    for k, v in kw.items():
+        if k not in m:
+            raise KeyError(f"unknown material field {k!r}")
+        m[k] = v
+    return m
+
+
+# Table 1, BaTiO3 column [46,47]: alpha1 = 3.34e5 (T - 381); alpha11 = 4.69e6 (T - 393) - 2.02e8;
+# alpha12 = 3.23e8; alpha111 = -5.52e7 (T - 393) + 2.76e9; alpha112 = 4.47e9; alpha123 = 4.91e9;
+# G11 = 5.1e-10, G12 = -2.0e-11, G44 = G'44 = 2.0e-11 (G110 = 5.1e-10).
+BTO = material(a0=3.34e5, T0=381.0, a11_0=-2.02e8, a11_T=4.69e6, a11_Tref=393.0, a12=3.23e8,
+               a111_0=2.76e9, a111_T=-5.52e7, a111_Tref=393.0, a112=4.47e9, a123=4.91e9,
+               G11=5.1e-10, G12=-2.0e-11, G44=2.0e-11, G44p=2.0e-11)
+
+# Table 1, PbTiO3 column [48]: alpha1 = 3.85e5 (T - 752); alpha11 = -7.3e7; alpha12 = 7.5e8;
+# alpha111 = 2.6e8; alpha112 = 6.1e8; alpha123 = -3.7e9; G11 = 1.038e-10, G12 = 0,
+# G44 = G'44 = 5.19e-11 (G110 = 1.73e-10).
+PTO = material(a0=3.85e5, T0=752.0, a11_0=-7.3e7, a12=7.5e8, a111_0=2.6e8, a112=6.1e8,
+               a123=-3.7e9, G11=1.038e-10, G12=0.0, G44=5.19e-11, G44p=5.19e-11)
+
+# Table 1, SrTiO3 column [49]: alpha1 printed as 405[coth(54/T) - coth(54/30)] with unit N m^2 C^-2.
+# Read as 4.05e7 (garbled exponent: the literal 405 gives a dielectric constant near 3e7); the
+# literal value is kept as STO_LITERAL. alpha11 = 1.7e9, alpha12 = 1.37e9; the sixth-order and
+# gradient entries are "-" in the table: sixth order set to 0, gradient taken from PbTiO3.
+STO = material(a1_form=1, coth_A=4.05e7, coth_Ts=54.0, coth_T1=30.0, a11_0=1.7e9, a12=1.37e9,
+               G11=1.038e-10, G12=0.0, G44=5.19e-11, G44p=5.19e-11)
+STO_LITERAL = dict(STO, coth_A=405.0)
+
+
+def wall_material(alpha1=-1.7402e8, alpha11=1.7402e8, G11=0.0, G44=1.73e-10, G44p=1.73e-10) -> dict:
+    """The 180-degree wall test material of Sec. 4.1 (alpha1, alpha11 and G44 = G'44 as printed)."""
+    return material(a1_form=2, a0=alpha1, a11_0=alpha11, G11=G11, G44=G44, G44p=G44p)
+
+
+def uniform_P(shape_xyz, amp, seed, dtype=np.float32) -> np.ndarray:
+    """Seeded polarization, uniform in [-amp, amp] C/m^2, shape (3, nz, ny, nx), x fastest.
+
+    Drawn with numpy's Philox bit generator; returned in float32 so that both sides start
+    from exactly the same values.
+    """
+    nx, ny, nz = shape_xyz
+    g = np.random.Generator(np.random.Philox(seed))
+    return g.uniform(-amp, amp, size=(3, nz, ny, nx)).astype(dtype)
+
+
+def layer_map(shape_xyz, layers) -> np.ndarray:
+    """uint8 material map (nz, ny, nx) from [(z0, z1, id), ...] half-open z ranges; rest vacuum."""
+    nx, ny, nz = shape_xyz
+    m = np.zeros((nz, ny, nx), np.uint8)
+    for z0, z1, mid in layers:
+        m[z0:z1] = mid
+    return m
+
+
+def cylinder_start(shape_xyz, radius, p_up, noise, seed, z_range=None) -> np.ndarray:
+    """Uniform +p_up along z with a centred reversed cylinder (axis z) plus uniform noise."""
+    nx, ny, nz = shape_xyz
+    P = uniform_P(shape_xyz, noise, seed, np.float64)
+    y, x = np.mgrid[0:ny, 0:nx]
+    inside = (x - (nx - 1) / 2.0) ** 2 + (y - (ny - 1) / 2.0) ** 2 <= radius ** 2
+    z0, z1 = (0, nz) if z_range is None else z_range
+    P[2, z0:z1] += np.where(inside, -p_up, p_up)[None]
+    return P.astype(np.float32)
+
+
+def batch_sizes(n=48, choices=(32, 48, 64, 96), seed=0) -> list:
+    """Cube edge lengths for the uneven batched sweep: each choice n/len(choices) times, shuffled."""
+    per = n // len(choices)
+    sizes = [c for c in choices for _ in range(per)]
+    g = np.random.Generator(np.random.Philox(seed))
+    g.shuffle(sizes)
+    return [int(s) for s in sizes]
+
+
+#: 32x32x8 BaTiO3 thin film, 1 nm cells, +-0.01 C/m^2 start (seed 1), 300 K, eps_B = 45,
+#: isotropic gradient (G11 = G44 + G'44 = G110, no cross coupling), zero field, 200 steps.
+CONFIG1 = dict(shape=(32, 32, 8), cell=(1e-9, 1e-9, 1e-9), seed=1, amp=0.01, T=300.0, eps_b=45.0,
+               material=dict(BTO, G12=0.0, G44=2.55e-10, G44p=2.55e-10), dt_star=0.004, steps=200)
+
+#: 128^3 BaTiO3 cube, 1 nm cells, +-0.01 start (seed 2), full Table 1 gradient, eps_B = 45,
+#: temperatures 450 -> 200 K in 25 K steps, relaxation to max|dP| < 1e-6 P0 per step.
+CONFIG2 = dict(shape=(128, 128, 128), cell=(1e-9, 1e-9, 1e-9), seed=2, amp=0.01, eps_b=45.0,
+               material=BTO, temperatures=[450.0 - 25.0 * i for i in range(11)], tol=1e-6,
+               dt_star=0.004)
+
+#: 256x256x64 bilayer: PbTiO3 on top (z 32..63), SrTiO3 below (z 0..31), eps_B = 649, 300 K,
+#: reversed cylinder of radius 20 cells, Ez swept +-200 MV/m in 81 points.
+CONFIG4 = dict(shape=(256, 256, 64), cell=(1e-9, 1e-9, 1e-9), seed=4, amp=0.01, eps_b=649.0,
+               T=300.0, layers=[(0, 32, 2), (32, 64, 1)], radius=20,
+               fields=[2e8 - 1e7 * i for i in range(41)] + [-1.9e8 + 1e7 * i for i in range(40)])
