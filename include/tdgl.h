@@ -1,0 +1,184 @@
+/*
+ * tdgl.h - C ABI of libtdgl: one explicit time step of the time-dependent Ginzburg-Landau
+ * (Landau-Khalatnikov) equation for the three-component polarization P of a ferroelectric on a
+ * 3D finite-difference grid, after arxiv 2605.28800 ("A GPU-based Solver for Polarization
+ * Dynamics in Ferroelectric Materials"), on NVIDIA B300 (sm_103a).
+ *
+ * What one step computes (Sec. 2, Eqs. 1-7):
+ *   dP/dt = -L dF/dP,  L = 1 s^-1 m^-2 C^2 N^-1,   F = F_Land + F_Grad + F_Elec + F_Ext,
+ *   h = h_Land (Eq. 3) + h_Grad (Eq. 4) + E_el (Eqs. 5-6, open boundary, P = 0 outside)
+ *       + E_ext (Eq. 7),
+ *   P <- P + dt L h  (forward Euler; vacuum cells keep P = 0).
+ * Units at this boundary are SI: metres, kelvin, seconds, V/m, C/m^2, joules.
+ *
+ * Conventions common to every call:
+ *  - Return value: TDGL_OK (0) or a negative TDGL_E* code; a human-readable message is kept per
+ *    context and returned by tdgl_last_error().
+ *  - Arrays of cells are float32, "SoA", shape [3][nz][ny][nx] for vectors and [nz][ny][nx] for
+ *    scalars, x fastest.  Component order x, y, z.
+ *  - `where` says where a caller buffer lives: TDGL_HOST (ordinary or pinned host memory) or
+ *    TDGL_DEVICE (device memory of the context's GPU, e.g. a torch CUDA tensor's data_ptr()).
+ *    Data are always copied; the library never keeps a pointer to a caller buffer.
+ *  - The library owns every device buffer it allocates.  All work is ordered on the context's
+ *    stream.  Calls that return data to the host synchronize that stream; others do not.
+ *  - Not thread safe: one context (and its sims) must be used from one host thread at a time.
+ */
+#ifndef TDGL_H
+#define TDGL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------- */
+#define TDGL_OK              0
+#define TDGL_EINVAL         -1   /* bad argument: null pointer, size, id, dt, ...               */
+#define TDGL_ENOMEM         -2   /* a device or host allocation failed                           */
+#define TDGL_ECUDA          -3   /* a CUDA runtime call failed (message has the CUDA error)     */
+#define TDGL_EDIVERGED      -4   /* NaN or |P| above the divergence bound after a step          */
+#define TDGL_ENOTCONVERGED  -5   /* relaxation hit its step cap before reaching the tolerance   */
+#define TDGL_ESTATE         -6   /* call not valid in the current state (e.g. no material)      */
+
+#define TDGL_HOST   0
+#define TDGL_DEVICE 1
+
+/* energy terms (Eq. 2); also used as the on/off flags of Sec. 3 ("flags allow users to turn
+ * different contributions on or off") */
+#define TDGL_TERM_LANDAU 1u
+#define TDGL_TERM_GRAD   2u
+#define TDGL_TERM_ELEC   4u
+#define TDGL_TERM_EXT    8u
+#define TDGL_TERM_ALL    15u
+
+#define TDGL_MAX_MATERIALS 16    /* material ids 1..15; id 0 is vacuum (P = 0)                  */
+#define TDGL_MAX_DIM       1024  /* largest nx, ny, nz                                          */
+
+typedef struct tdgl_ctx   tdgl_ctx;
+typedef struct tdgl_sim   tdgl_sim;
+typedef struct tdgl_batch tdgl_batch;
+
+/* Material coefficients, SI (Table 1 forms; the z quadratic coefficient is r_s * alpha1,
+ * the strain form of Sec. 4.4):
+ *   a1_form 0: alpha1 = a0 (T - T0)
+ *   a1_form 1: alpha1 = coth_A (coth(coth_Ts/T) - coth(coth_Ts/coth_T1))   (SrTiO3 form)
+ *   a1_form 2: alpha1 = a0                                                  (constant)
+ *   alpha11  = a11_0  + a11_T  (T - a11_Tref)        alpha12, alpha112, alpha123 constant
+ *   alpha111 = a111_0 + a111_T (T - a111_Tref)       G11, G12, G44, G44p (= G'44) of Eq. 4 */
+typedef struct {
+    int    a1_form;
+    double a0, T0, coth_A, coth_Ts, coth_T1;
+    double a11_0, a11_T, a11_Tref, a12;
+    double a111_0, a111_T, a111_Tref, a112, a123;
+    double G11, G12, G44, G44p;
+    double r_s;
+} tdgl_material;
+
+/* Energy terms of Eq. 2, joules, accumulated in float64 (Eqs. 3, 4 (discrete), 5, 7). */
+typedef struct {
+    double land, grad, elec, ext, total;
+} tdgl_energies;
+
+/* ---- context --------------------------------------------------------------------------------
+ * tdgl_ctx_create: bind to CUDA device `device` and to `stream` (a cudaStream_t, e.g.
+ * torch.cuda.current_stream().cuda_stream; NULL = the library creates and owns a stream).
+ * The caller keeps ownership of a stream it passes.  *out receives the context. */
+int  tdgl_ctx_create(tdgl_ctx **out, int device, void *stream);
+void tdgl_ctx_destroy(tdgl_ctx *ctx);
+/* last error message of the context (never NULL; "" when none); valid until the next call */
+const char *tdgl_last_error(const tdgl_ctx *ctx);
+/* number of libtdgl kernel launches issued on this context so far (graph replays included) */
+long tdgl_launch_count(const tdgl_ctx *ctx);
+
+/* ---- simulation (Sec. 3: P uniform in each cell of a finite-difference grid) -----------------
+ * tdgl_sim_create: grid nx*ny*nz (1..TDGL_MAX_DIM each) of dx*dy*dz cells (metres, > 0).
+ * All cells start as vacuum (id 0) until a map or layers are set; P starts at zero.
+ * The electrostatic field uses a zero-padded FFT of size >= 2n-1 per axis (open boundary). */
+int  tdgl_sim_create(tdgl_ctx *ctx, int nx, int ny, int nz, double dx, double dy, double dz,
+                     tdgl_sim **out);
+void tdgl_sim_destroy(tdgl_sim *sim);
+
+/* Define (or redefine) material `id` (1..15) from Table 1-style coefficients (Sec. 3:
+ * spatially varying material parameters at the cell level). */
+int tdgl_material_define(tdgl_sim *sim, int id, const tdgl_material *m);
+/* Per-cell material ids, uint8 [nz][ny][nx]; 0 = vacuum.  Every non-zero id must be defined
+ * before the first step.  Cells that become vacuum get P = 0. */
+int tdgl_set_material_map(tdgl_sim *sim, const uint8_t *ids, int where);
+/* Layers along z: cells with z0[i] <= z < z1[i] get id[i] (later entries win); others vacuum. */
+int tdgl_set_layers(tdgl_sim *sim, int n, const int *z0, const int *z1, const int *id);
+/* Background permittivity eps_B of Eq. 6 (> 0; a free parameter in the paper). Default 1. */
+int tdgl_set_eps_b(tdgl_sim *sim, double eps_b);
+/* Enabled terms, a mask of TDGL_TERM_*.  Default TDGL_TERM_ALL. */
+int tdgl_set_terms(tdgl_sim *sim, unsigned mask);
+/* Temperature (kelvin, > 0) at which Table 1 coefficients are evaluated.  Default 300. */
+int tdgl_set_temperature(tdgl_sim *sim, double T);
+/* Uniform applied field E_ext of Eq. 7, V/m.  Default 0. */
+int tdgl_set_field(tdgl_sim *sim, double Ex, double Ey, double Ez);
+
+/* Internal normalization (Table 2): P* = P/P0, tau = alpha_ref L t, E* = E/(alpha_ref P0).
+ * Defaults, fixed at the first step unless set here: alpha_ref = |alpha1| of the lowest defined
+ * material id at 300 K; P0 = that material's tetragonal spontaneous polarization at 300 K
+ * (1 C/m^2 if it has none).  Relaxation tolerances are in units of P0.  Setting the scales
+ * keeps the physical P. */
+int tdgl_set_scales(tdgl_sim *sim, double P0, double alpha_ref);
+int tdgl_get_scales(tdgl_sim *sim, double *P0, double *alpha_ref);
+
+/* P in C/m^2, float32 [3][nz][ny][nx].  set_P zeroes vacuum cells. */
+int tdgl_set_P(tdgl_sim *sim, const float *P, int where);
+int tdgl_get_P(tdgl_sim *sim, float *out, int where);
+/* Fill P with independent uniform values in [-amp, amp] C/m^2 from a Philox4x32-10 stream:
+ * value (c, cell) uses counter (cell, c, 0, 0) and key (seed & 0xffffffff, seed >> 32); the
+ * first 32-bit output u maps to amp * (2 (u + 0.5) / 2^32 - 1).  Vacuum cells stay 0. */
+int tdgl_init_random(tdgl_sim *sim, uint64_t seed, double amp);
+
+/* Effective-field contributions of the current P for the terms in `mask` (V/m, float32
+ * [3][nz][ny][nx], zero on vacuum cells): h_Land, h_Grad, E_el, E_ext of Eqs. 3-7. */
+int tdgl_get_field(tdgl_sim *sim, unsigned mask, float *out, int where);
+
+/* n >= 0 forward Euler steps of Eq. 1 with time step dt (seconds, > 0).  Returns
+ * TDGL_EDIVERGED (state left as computed) if any step produced NaN or |P_i| > 1e3 P0. */
+int tdgl_step(tdgl_sim *sim, int n, double dt);
+/* max over cells and components of |P_new - P_old| of the most recent step, in units of P0. */
+int tdgl_last_max_dP(tdgl_sim *sim, double *out);
+/* Relaxation (Sec. 4: equilibrium as the steady state of Eq. 1): step with dt until the
+ * max |dP| of a step, checked every `check_every` steps (>= 1), is below tol * P0, or until
+ * max_steps.  *steps_taken (may be NULL) receives the steps done.  Returns TDGL_OK on
+ * convergence, TDGL_ENOTCONVERGED at the cap, TDGL_EDIVERGED on divergence. */
+int tdgl_relax(tdgl_sim *sim, double dt, double tol, long max_steps, int check_every,
+               long *steps_taken);
+/* Energy terms of Eq. 2 for the current P (joules, float64 accumulation). */
+int tdgl_energy(tdgl_sim *sim, tdgl_energies *out);
+
+/* ---- batches (Sec. 3: many independent simulations run in parallel on one GPU) --------------
+ * A batch groups n sims of one context (any sizes) so that each kernel of a step is one launch
+ * over all of them.  The sims stay usable on their own; a sim may belong to one batch at a time
+ * and must not be destroyed before its batch. */
+int  tdgl_batch_create(tdgl_ctx *ctx, int n, tdgl_sim *const *sims, tdgl_batch **out);
+void tdgl_batch_destroy(tdgl_batch *b);
+/* n steps of every sim; dt[i] (seconds) per sim. */
+int  tdgl_batch_step(tdgl_batch *b, int n, const double *dt);
+/* Relax every sim to its own tolerance (tol in units of each sim's P0, one value for all);
+ * converged sims leave the batch's work list.  steps_taken[i] (may be NULL) per sim.
+ * Returns TDGL_OK when all converged, else TDGL_ENOTCONVERGED / TDGL_EDIVERGED. */
+int  tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_steps,
+                      int check_every, long *steps_taken);
+
+/* ---- measurement -----------------------------------------------------------------------------
+ * tdgl_profile(ctx, 1) records a CUDA event pair around every kernel launch on the context's
+ * stream; tdgl_profile_read(ctx, k, &ms, &n) synchronizes and returns the summed device time and
+ * the launch count of kernel kind k since the last reset (then resets kind k).  Kinds: */
+#define TDGL_K_STEP   0   /* fused x-inverse + Landau + gradient + update + x-forward  */
+#define TDGL_K_YFWD   1   /* y forward FFT of the zero-padded x-spectrum               */
+#define TDGL_K_ZCONV  2   /* z FFT, 3x3 tensor multiply, inverse z FFT                  */
+#define TDGL_K_YINV   3   /* inverse y FFT                                             */
+#define TDGL_K_XFWD   4   /* x forward real FFT of P (prologue)                        */
+#define TDGL_K_OTHER  5   /* energy, field readback, tensor build, copies              */
+#define TDGL_K_COUNT  6
+int tdgl_profile(tdgl_ctx *ctx, int enable);
+int tdgl_profile_read(tdgl_ctx *ctx, int kind, double *total_ms, long *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDGL_H */

@@ -1,0 +1,1125 @@
+// libtdgl host runtime: contexts, simulations, batches and the C ABI declared in include/tdgl.h.
+//
+// One explicit TDGL step (Eq. 1, forward Euler, L = 1) of a sim whose electrostatic term is on is
+//   [k_yfwd, k_zconv, k_yinv]  x-spectrum of P  ->  x-spectrum of E_el  (Eqs. 5-6)
+//   k_rows<STEP>               E_el rows, Landau (Eq. 3), gradient (Eq. 4), E_ext (Eq. 7),
+//                              update, and the x-spectrum of the new P for the next step.
+// A batch issues each of these kernels once over the work items of all of its sims.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tdgl.h"
+#include "kernels.cuh"
+#include "tensor.cuh"
+
+using namespace tdgl;
+
+namespace {
+
+const double kEps0 = 8.8541878128e-12;   // F/m
+const int kMaxSmem = 200 * 1024;
+
+enum { XS_NONE = 0, XS_PHAT = 1, XS_EHAT = 2 };
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct tdgl_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    long launches = 0;
+    bool profiling = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[TDGL_K_COUNT] = {0};
+    long prof_n[TDGL_K_COUNT] = {0};
+};
+
+struct tdgl_sim {
+    tdgl_ctx *ctx = nullptr;
+    int nx = 0, ny = 0, nz = 0;
+    double d[3] = {0, 0, 0};
+    long ncell = 0;
+    int Mx = 0, My = 0, Mz = 0, hx = 0, Kx = 0, kxp = 0, kyh = 0, kzh = 0;
+    tdgl_material mats[TDGL_MAX_MATERIALS];
+    bool defined[TDGL_MAX_MATERIALS] = {false};
+    std::vector<uint8_t> map;
+    double T = 300.0, eps_b = 1.0, E[3] = {0, 0, 0};
+    unsigned terms = TDGL_TERM_ALL;
+    double P0 = 1.0, alpha_ref = 1.0;
+    bool scales_fixed = false;
+    double ell = 1.0;   // length unit: smallest cell edge
+    // device buffers
+    float *dP[2] = {nullptr, nullptr};
+    uint8_t *dmat = nullptr;
+    float2 *dX = nullptr, *dY = nullptr;
+    float *dNhat = nullptr;
+    float2 *dtw = nullptr;
+    float *dcoef = nullptr;
+    unsigned *dmaxdp = nullptr;
+    int *dflag = nullptr;
+    double *denergy = nullptr;
+    float *dout = nullptr;
+    SimDev *ddesc = nullptr;
+    SimDev desc;
+    Plan px, py, pz;
+    int twr = 0;
+    // work items
+    std::vector<int4> it_rows, it_y, it_z;
+    int rows_cnt_max = 1, ky_cnt_max = 1, kz_cnt_max = 1;
+    int4 *d_rows = nullptr, *d_y = nullptr, *d_z = nullptr;
+    int cur = 0;
+    int xstate = XS_NONE;
+    bool spectra_alloc = false, tensor_ready = false;
+    bool has_cross = false;
+    double last_maxdp = 0.0;
+    tdgl_batch *batch = nullptr;
+};
+
+struct tdgl_batch {
+    tdgl_ctx *ctx = nullptr;
+    std::vector<tdgl_sim *> sims;
+    SimDev *ddescs = nullptr;
+    int4 *d_items = nullptr;
+    size_t items_cap = 0;
+};
+
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+int fail(tdgl_ctx *ctx, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    return code;
+}
+
+#define CK(ctx, call)                                                                            \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? TDGL_ENOMEM : TDGL_ECUDA,         \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);   \
+    } while (0)
+
+#define TRY(x)                  \
+    do {                        \
+        int r_ = (x);           \
+        if (r_ != TDGL_OK) return r_; \
+    } while (0)
+
+int smooth_at_least(int m, bool even) {
+    // smallest 2^a 3^b >= m (even when asked)
+    int best = 1 << 30;
+    for (long p2 = 1; p2 < (1L << 30); p2 *= 2)
+        for (long v = p2; v < (1L << 30); v *= 3) {
+            if (v >= m && (!even || v % 2 == 0) && v < best) best = (int)v;
+            if (v >= m) break;
+        }
+    return best;
+}
+
+Plan make_plan(int n, std::vector<float2> &tw) {
+    Plan p;
+    memset(&p, 0, sizeof p);
+    p.n = n;
+    int r = n;
+    const int rads[5] = {16, 8, 4, 3, 2};
+    for (int i = 0; i < 5; ++i)
+        while (r % rads[i] == 0 && r > 1) {
+            p.rad[p.nrad++] = rads[i];
+            r /= rads[i];
+        }
+    p.tw = (int)tw.size();
+    for (int t = 0; t < n; ++t) {
+        const double a = -2.0 * M_PI * (double)t / (double)n;
+        tw.push_back(make_float2((float)cos(a), (float)sin(a)));
+    }
+    return p;
+}
+
+double alpha1_of(const tdgl_material &m, double T) {
+    if (m.a1_form == 1) {
+        auto coth = [](double v) { return cosh(v) / sinh(v); };
+        return m.coth_A * (coth(m.coth_Ts / T) - coth(m.coth_Ts / m.coth_T1));
+    }
+    if (m.a1_form == 2) return m.a0;
+    return m.a0 * (T - m.T0);
+}
+
+// tetragonal spontaneous polarization of a material at T (Eq. 12 along <100>), 0 if none
+double tetragonal_ps(const tdgl_material &m, double T) {
+    const double a1 = alpha1_of(m, T);
+    const double a11 = m.a11_0 + m.a11_T * (T - m.a11_Tref);
+    const double a111 = m.a111_0 + m.a111_T * (T - m.a111_Tref);
+    // 2 a1 + 4 a11 u + 6 a111 u^2 = 0, u = P^2, minimum: 4 a11 + 12 a111 u > 0
+    double best = 0.0, fbest = 0.0;
+    double roots[2];
+    int nr = 0;
+    if (a111 != 0.0) {
+        const double disc = 16.0 * a11 * a11 - 48.0 * a111 * a1;
+        if (disc >= 0) {
+            roots[nr++] = (-4.0 * a11 + sqrt(disc)) / (12.0 * a111);
+            roots[nr++] = (-4.0 * a11 - sqrt(disc)) / (12.0 * a111);
+        }
+    } else if (a11 != 0.0) {
+        roots[nr++] = -a1 / (2.0 * a11);
+    }
+    for (int i = 0; i < nr; ++i) {
+        const double u = roots[i];
+        if (!(u > 0) || 4.0 * a11 + 12.0 * a111 * u <= 0) continue;
+        const double f = a1 * u + a11 * u * u + a111 * u * u * u;
+        if (f < fbest) { fbest = f; best = sqrt(u); }
+    }
+    return best;
+}
+
+void ctx_set(tdgl_ctx *ctx) { cudaSetDevice(ctx->device); }
+
+cudaEvent_t take_event(tdgl_ctx *ctx) {
+    if (!ctx->pool.empty()) {
+        cudaEvent_t e = ctx->pool.back();
+        ctx->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+template <class F>
+int launch(tdgl_ctx *ctx, int kind, F f) {
+    ProfRec r{kind, nullptr, nullptr};
+    if (ctx->profiling) {
+        r.a = take_event(ctx);
+        r.b = take_event(ctx);
+        cudaEventRecord(r.a, ctx->stream);
+    }
+    f();
+    cudaError_t e = cudaGetLastError();
+    if (ctx->profiling) {
+        cudaEventRecord(r.b, ctx->stream);
+        ctx->recs.push_back(r);
+    }
+    ctx->launches++;
+    if (e != cudaSuccess) return fail(ctx, TDGL_ECUDA, "kernel launch (kind %d): %s", kind, cudaGetErrorString(e));
+    return TDGL_OK;
+}
+
+int grid_for(long n) { return (int)std::min<long>(std::max<long>((n + 255) / 256, 1), 148L * 16); }
+
+// -- geometry and plans ------------------------------------------------------------------------
+void build_items(tdgl_sim *s) {
+    s->it_rows.clear();
+    s->it_y.clear();
+    s->it_z.clear();
+    const int RB = std::max(1, std::min(s->ny, std::max(1, 512 / s->nx)));
+    s->rows_cnt_max = RB;
+    for (int z = 0; z < s->nz; ++z)
+        for (int y0 = 0; y0 < s->ny; y0 += RB) s->it_rows.push_back(make_int4(0, z, y0, std::min(RB, s->ny - y0)));
+    const int ky = std::max(1, std::min(16, 73728 / (16 * (s->My + 1))));
+    s->ky_cnt_max = ky;
+    for (int c = 0; c < 3; ++c)
+        for (int z = 0; z < s->nz; ++z)
+            for (int k0 = 0; k0 < s->Kx; k0 += ky)
+                s->it_y.push_back(make_int4(0, c * s->nz + z, k0, std::min(ky, s->Kx - k0)));
+    const int kz = std::max(1, std::min(16, 102400 / (48 * (s->Mz + 1))));
+    s->kz_cnt_max = kz;
+    for (int k = 0; k < s->My; ++k)
+        for (int k0 = 0; k0 < s->Kx; k0 += kz) s->it_z.push_back(make_int4(0, k, k0, std::min(kz, s->Kx - k0)));
+}
+
+size_t smem_rows(const tdgl_sim *s, int cnt) { return 2ull * 3 * cnt * (s->hx + 2) * sizeof(float2); }
+size_t smem_y(const tdgl_sim *s, int cnt) { return 2ull * cnt * (s->My + 1) * sizeof(float2); }
+size_t smem_z(const tdgl_sim *s, int cnt) { return 2ull * 3 * cnt * (s->Mz + 1) * sizeof(float2); }
+
+int upload_items(tdgl_sim *s) {
+    tdgl_ctx *ctx = s->ctx;
+    cudaFree(s->d_rows); cudaFree(s->d_y); cudaFree(s->d_z);
+    s->d_rows = s->d_y = s->d_z = nullptr;
+    CK(ctx, cudaMalloc(&s->d_rows, s->it_rows.size() * sizeof(int4)));
+    CK(ctx, cudaMemcpy(s->d_rows, s->it_rows.data(), s->it_rows.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(ctx, cudaMalloc(&s->d_y, s->it_y.size() * sizeof(int4)));
+    CK(ctx, cudaMemcpy(s->d_y, s->it_y.data(), s->it_y.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(ctx, cudaMalloc(&s->d_z, s->it_z.size() * sizeof(int4)));
+    CK(ctx, cudaMemcpy(s->d_z, s->it_z.data(), s->it_z.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    return TDGL_OK;
+}
+
+// -- normalization and coefficient table --------------------------------------------------------
+int lowest_material(const tdgl_sim *s) {
+    for (int i = 1; i < TDGL_MAX_MATERIALS; ++i)
+        if (s->defined[i]) return i;
+    return 0;
+}
+
+void fix_scales(tdgl_sim *s) {
+    if (s->scales_fixed) return;
+    const int m = lowest_material(s);
+    double a = m ? fabs(alpha1_of(s->mats[m], 300.0)) : 0.0;
+    if (!(a > 0.0) || !std::isfinite(a)) a = 1e8;
+    double p = m ? tetragonal_ps(s->mats[m], 300.0) : 0.0;
+    if (!(p > 0.0) || !std::isfinite(p)) p = 1.0;
+    s->alpha_ref = a;
+    s->P0 = p;
+    s->scales_fixed = true;
+}
+
+void coef_table(const tdgl_sim *s, float *tab) {
+    memset(tab, 0, sizeof(float) * MAXMAT * NCOEF);
+    const double a = s->alpha_ref, P0 = s->P0, l2 = s->ell * s->ell, T = s->T;
+    for (int id = 1; id < TDGL_MAX_MATERIALS; ++id) {
+        if (!s->defined[id]) continue;
+        const tdgl_material &m = s->mats[id];
+        const double a1 = alpha1_of(m, T);
+        const double a11 = m.a11_0 + m.a11_T * (T - m.a11_Tref);
+        const double a111 = m.a111_0 + m.a111_T * (T - m.a111_Tref);
+        float *c = tab + id * NCOEF;
+        c[0] = (float)(a1 / a);
+        c[1] = (float)(a1 / a);
+        c[2] = (float)(m.r_s * a1 / a);
+        c[3] = (float)(a11 * P0 * P0 / a);
+        c[4] = (float)(m.a12 * P0 * P0 / a);
+        c[5] = (float)(a111 * P0 * P0 * P0 * P0 / a);
+        c[6] = (float)(m.a112 * P0 * P0 * P0 * P0 / a);
+        c[7] = (float)(m.a123 * P0 * P0 * P0 * P0 / a);
+        c[8] = (float)(m.G11 / (a * l2));
+        c[9] = (float)((m.G44 + m.G44p) / (a * l2));
+        c[10] = (float)(m.G12 / (a * l2));
+        c[11] = (float)((m.G44 - m.G44p) / (a * l2));
+    }
+}
+
+bool any_cross(const tdgl_sim *s) {
+    for (int id = 1; id < TDGL_MAX_MATERIALS; ++id)
+        if (s->defined[id] && (s->mats[id].G12 != 0.0 || s->mats[id].G44 != s->mats[id].G44p)) return true;
+    return false;
+}
+
+// -- tensor spectrum -----------------------------------------------------------------------------
+void gauss_legendre01(int m, double *tau, double *wt) {
+    // m-point Gauss-Legendre on [0, 1] (Newton on the Legendre recurrence), weights times (1 - tau)
+    for (int i = 0; i < m; ++i) {
+        double x = cos(M_PI * (i + 0.75) / (m + 0.5)), dp = 1.0;
+        for (int it = 0; it < 60; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= m; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = m * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-15) break;
+        }
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= m; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = m * (x * p1 - p0) / (x * x - 1.0);
+        const double w = 2.0 / ((1.0 - x * x) * dp * dp);
+        tau[i] = 0.5 * (1.0 + x);
+        wt[i] = 0.5 * w * (1.0 - tau[i]);
+    }
+}
+
+int build_tensor(tdgl_sim *s) {
+    tdgl_ctx *ctx = s->ctx;
+    const int nx = s->nx, ny = s->ny, nz = s->nz;
+    FarRule rule;
+    memset(&rule, 0, sizeof rule);
+    const int ms[3] = {8, 6, 4};
+    for (int q = 0; q < 3; ++q) {
+        rule.m[q] = ms[q];
+        gauss_legendre01(ms[q], rule.tau[q], rule.wt[q]);
+    }
+    const double l = s->ell;
+    double *dN = nullptr, *dT1 = nullptr, *dT2 = nullptr, *dtrig = nullptr;
+    const long nreal = (long)nx * ny * nz;
+    const long n1 = (long)nz * ny * s->Kx, n2 = (long)nz * s->kyh * s->Kx, n3 = (long)s->kzh * s->kyh * s->Kx;
+    CK(ctx, cudaMalloc(&dN, 6 * nreal * sizeof(double)));
+    CK(ctx, cudaMalloc(&dT1, 6 * std::max(n1, n3) * sizeof(double)));   // passes x and z write here
+    CK(ctx, cudaMalloc(&dT2, 6 * std::max(n2, n3) * sizeof(double)));
+    const int Ms[3] = {s->Mx, s->My, s->Mz};
+    std::vector<double> trig;
+    size_t off[3];
+    for (int a = 0; a < 3; ++a) {
+        off[a] = trig.size();
+        for (int t = 0; t < Ms[a]; ++t) trig.push_back(cos(2.0 * M_PI * t / Ms[a]));
+        for (int t = 0; t < Ms[a]; ++t) trig.push_back(sin(2.0 * M_PI * t / Ms[a]));
+    }
+    CK(ctx, cudaMalloc(&dtrig, trig.size() * sizeof(double)));
+    CK(ctx, cudaMemcpyAsync(dtrig, trig.data(), trig.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    // lengths in units of the smallest cell edge
+    TRY(launch(ctx, TDGL_K_OTHER, [&] {
+        k_tensor_real<<<grid_for(nreal), 256, 0, ctx->stream>>>(dN, nx, ny, nz, s->d[0] / l, s->d[1] / l, s->d[2] / l,
+                                                                  5.0, 16.0, 40.0, rule);
+    }));
+    TRY(launch(ctx, TDGL_K_OTHER, [&] {
+        k_tensor_dft<<<grid_for(6 * n1), 256, 0, ctx->stream>>>(dN, dT1, 0, nx, s->Kx, s->Mx, 1, nz * ny,
+                                                                  dtrig + off[0], dtrig + off[0] + s->Mx);
+    }));
+    TRY(launch(ctx, TDGL_K_OTHER, [&] {
+        k_tensor_dft<<<grid_for(6 * n2), 256, 0, ctx->stream>>>(dT1, dT2, 1, ny, s->kyh, s->My, s->Kx, nz,
+                                                                  dtrig + off[1], dtrig + off[1] + s->My);
+    }));
+    TRY(launch(ctx, TDGL_K_OTHER, [&] {
+        k_tensor_dft<<<grid_for(6 * n3), 256, 0, ctx->stream>>>(dT2, dT1, 2, nz, s->kzh, s->Mz, s->kyh * s->Kx, 1,
+                                                                  dtrig + off[2], dtrig + off[2] + s->Mz);
+    }));
+    TRY(launch(ctx, TDGL_K_OTHER, [&] {
+        k_tensor_store<<<grid_for(6 * n3), 256, 0, ctx->stream>>>(dT1, s->dNhat, n3);
+    }));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(dN);
+    cudaFree(dT1);
+    cudaFree(dT2);
+    cudaFree(dtrig);
+    s->tensor_ready = true;
+    return TDGL_OK;
+}
+
+int alloc_spectra(tdgl_sim *s) {
+    if (s->spectra_alloc) return TDGL_OK;
+    tdgl_ctx *ctx = s->ctx;
+    CK(ctx, cudaMalloc(&s->dX, 3ull * s->nz * s->ny * s->kxp * sizeof(float2)));
+    CK(ctx, cudaMalloc(&s->dY, 3ull * s->nz * s->My * s->kxp * sizeof(float2)));
+    CK(ctx, cudaMalloc(&s->dNhat, 6ull * s->kzh * s->kyh * s->Kx * sizeof(float)));
+    s->spectra_alloc = true;
+    return TDGL_OK;
+}
+
+// rebuild the device descriptor; P[0] is the current buffer
+void fill_desc(tdgl_sim *s, double dt, unsigned terms) {
+    SimDev &D = s->desc;
+    memset(&D, 0, sizeof D);
+    D.nx = s->nx; D.ny = s->ny; D.nz = s->nz; D.ncell = s->ncell;
+    D.hx = s->hx; D.Kx = s->Kx; D.kxp = s->kxp; D.My = s->My; D.Mz = s->Mz; D.kyh = s->kyh; D.kzh = s->kzh;
+    D.px = s->px; D.py = s->py; D.pz = s->pz; D.twr = s->twr; D.tw = s->dtw;
+    D.P[0] = s->dP[s->cur]; D.P[1] = s->dP[s->cur ^ 1];
+    D.mat = s->dmat; D.X = s->dX; D.Y = s->dY; D.Nhat = s->dNhat; D.coef = s->dcoef;
+    for (int a = 0; a < 3; ++a) {
+        const double h = s->d[a] / s->ell;
+        D.inv_d2[a] = (float)(1.0 / (h * h));
+        D.inv_2d[a] = (float)(1.0 / (2.0 * h));
+        D.eext[a] = (float)(s->E[a] / (s->alpha_ref * s->P0));
+    }
+    D.dt = (float)(s->alpha_ref * dt);
+    D.escale = (float)(-1.0 / (kEps0 * s->eps_b * s->alpha_ref) / ((double)s->Mx * s->My * s->Mz));
+    D.pmax = 1e3f;
+    D.terms = terms;
+    D.has_cross = s->has_cross ? 1 : 0;
+    D.maxdp = s->dmaxdp; D.flag = s->dflag; D.energy = s->denergy;
+    D.out = s->dout;
+    D.out_scale = (float)(s->alpha_ref * s->P0);
+}
+
+int prepare(tdgl_sim *s, unsigned need_terms) {
+    tdgl_ctx *ctx = s->ctx;
+    for (size_t i = 0; i < s->map.size(); ++i)
+        if (s->map[i] && !s->defined[s->map[i]])
+            return fail(ctx, TDGL_ESTATE, "material id %d used in the map but not defined", (int)s->map[i]);
+    if (!lowest_material(s)) return fail(ctx, TDGL_ESTATE, "no material defined");
+    fix_scales(s);
+    s->has_cross = any_cross(s);
+    float tab[MAXMAT * NCOEF];
+    coef_table(s, tab);
+    CK(ctx, cudaMemcpyAsync(s->dcoef, tab, sizeof tab, cudaMemcpyHostToDevice, ctx->stream));
+    if (need_terms & TDGL_TERM_ELEC) {
+        TRY(alloc_spectra(s));
+        if (!s->tensor_ready) TRY(build_tensor(s));
+    }
+    return TDGL_OK;
+}
+
+int upload_desc(tdgl_sim *s) {
+    CK(s->ctx, cudaMemcpyAsync(s->ddesc, &s->desc, sizeof(SimDev), cudaMemcpyHostToDevice, s->ctx->stream));
+    return TDGL_OK;
+}
+
+// -- kernel sequences (over a descriptor table and item lists) ---------------------------------------
+struct Work {
+    const SimDev *descs;
+    const int4 *rows, *y, *z;
+    int n_rows, n_y, n_z;
+    size_t sm_rows, sm_y, sm_z;
+};
+
+int launch_rows(tdgl_ctx *ctx, int mode, const Work &w, int parity) {
+    const int kind = (mode == MODE_XFWD) ? TDGL_K_XFWD : (mode == MODE_STEP ? TDGL_K_STEP : TDGL_K_OTHER);
+    if (w.n_rows == 0) return TDGL_OK;
+    return launch(ctx, kind, [&] {
+        switch (mode) {
+            case MODE_STEP: k_rows<MODE_STEP><<<w.n_rows, NTHREADS, w.sm_rows, ctx->stream>>>(w.descs, w.rows, parity); break;
+            case MODE_FIELD: k_rows<MODE_FIELD><<<w.n_rows, NTHREADS, w.sm_rows, ctx->stream>>>(w.descs, w.rows, parity); break;
+            case MODE_ENERGY: k_rows<MODE_ENERGY><<<w.n_rows, NTHREADS, w.sm_rows, ctx->stream>>>(w.descs, w.rows, parity); break;
+            default: k_rows<MODE_XFWD><<<w.n_rows, NTHREADS, w.sm_rows, ctx->stream>>>(w.descs, w.rows, parity); break;
+        }
+    });
+}
+
+int launch_conv(tdgl_ctx *ctx, const Work &w) {
+    if (w.n_y == 0) return TDGL_OK;
+    TRY(launch(ctx, TDGL_K_YFWD, [&] { k_yfwd<<<w.n_y, NTHREADS, w.sm_y, ctx->stream>>>(w.descs, w.y); }));
+    TRY(launch(ctx, TDGL_K_ZCONV, [&] { k_zconv<<<w.n_z, NTHREADS, w.sm_z, ctx->stream>>>(w.descs, w.z); }));
+    TRY(launch(ctx, TDGL_K_YINV, [&] { k_yinv<<<w.n_y, NTHREADS, w.sm_y, ctx->stream>>>(w.descs, w.y); }));
+    return TDGL_OK;
+}
+
+Work sim_work(tdgl_sim *s, bool elec) {
+    Work w;
+    w.descs = s->ddesc;
+    w.rows = s->d_rows; w.y = s->d_y; w.z = s->d_z;
+    w.n_rows = (int)s->it_rows.size();
+    w.n_y = elec ? (int)s->it_y.size() : 0;
+    w.n_z = elec ? (int)s->it_z.size() : 0;
+    w.sm_rows = smem_rows(s, s->rows_cnt_max);
+    w.sm_y = smem_y(s, s->ky_cnt_max);
+    w.sm_z = smem_z(s, s->kz_cnt_max);
+    return w;
+}
+
+// bring X to the E-hat state of the current P (descriptor already uploaded with P[0] = current)
+int ensure_ehat(tdgl_sim *s, const Work &w) {
+    if (s->xstate == XS_NONE) {
+        TRY(launch_rows(s->ctx, MODE_XFWD, w, 0));
+        s->xstate = XS_PHAT;
+    }
+    if (s->xstate == XS_PHAT) {
+        TRY(launch_conv(s->ctx, w));
+        s->xstate = XS_EHAT;
+    }
+    return TDGL_OK;
+}
+
+int read_status(tdgl_sim *s, double *maxdp, int *flag) {
+    unsigned u = 0;
+    int f = 0;
+    CK(s->ctx, cudaMemcpyAsync(&u, s->dmaxdp, sizeof u, cudaMemcpyDeviceToHost, s->ctx->stream));
+    CK(s->ctx, cudaMemcpyAsync(&f, s->dflag, sizeof f, cudaMemcpyDeviceToHost, s->ctx->stream));
+    CK(s->ctx, cudaStreamSynchronize(s->ctx->stream));
+    float v;
+    memcpy(&v, &u, sizeof v);
+    *maxdp = (u >= 0x7f800000u) ? INFINITY : (double)v;
+    *flag = f;
+    s->last_maxdp = *maxdp;
+    return TDGL_OK;
+}
+
+// n steps of one sim without a status read; maxdp reset before the last step
+int steps_nosync(tdgl_sim *s, int n, double dt) {
+    tdgl_ctx *ctx = s->ctx;
+    const bool elec = (s->terms & TDGL_TERM_ELEC) != 0;
+    fill_desc(s, dt, s->terms);
+    TRY(upload_desc(s));
+    Work w = sim_work(s, elec);
+    int parity = 0;
+    if (elec && s->xstate == XS_NONE) {
+        TRY(launch_rows(ctx, MODE_XFWD, w, 0));
+        s->xstate = XS_PHAT;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (elec && s->xstate == XS_PHAT) {
+            TRY(launch_conv(ctx, w));
+            s->xstate = XS_EHAT;
+        }
+        if (i == n - 1) CK(ctx, cudaMemsetAsync(s->dmaxdp, 0, sizeof(unsigned), ctx->stream));
+        TRY(launch_rows(ctx, MODE_STEP, w, parity));
+        parity ^= 1;
+        s->xstate = elec ? XS_PHAT : XS_NONE;
+    }
+    if (n & 1) s->cur ^= 1;
+    return TDGL_OK;
+}
+
+bool valid_where(int w) { return w == TDGL_HOST || w == TDGL_DEVICE; }
+
+int copy_in(tdgl_ctx *ctx, void *dst, const void *src, size_t bytes, int where) {
+    CK(ctx, cudaMemcpyAsync(dst, src, bytes, where == TDGL_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+    return TDGL_OK;
+}
+
+int copy_out(tdgl_ctx *ctx, void *dst, const void *src, size_t bytes, int where) {
+    CK(ctx, cudaMemcpyAsync(dst, src, bytes, where == TDGL_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+    if (where == TDGL_HOST) CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return TDGL_OK;
+}
+
+int ensure_out(tdgl_sim *s) {
+    if (!s->dout) CK(s->ctx, cudaMalloc(&s->dout, 3ull * s->ncell * sizeof(float)));
+    return TDGL_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+extern "C" {
+
+int tdgl_ctx_create(tdgl_ctx **out, int device, void *stream) {
+    if (!out) return TDGL_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return TDGL_ECUDA;
+    tdgl_ctx *ctx = new tdgl_ctx();
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return TDGL_ECUDA; }
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { delete ctx; return TDGL_ECUDA; }
+        ctx->own_stream = true;
+    }
+    cudaFuncSetAttribute(k_rows<MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(k_rows<MODE_FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(k_rows<MODE_ENERGY>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(k_rows<MODE_XFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(k_yfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(k_yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(k_zconv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    if (cudaGetLastError() != cudaSuccess) { delete ctx; return TDGL_ECUDA; }
+    *out = ctx;
+    return TDGL_OK;
+}
+
+void tdgl_ctx_destroy(tdgl_ctx *ctx) {
+    if (!ctx) return;
+    ctx_set(ctx);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : ctx->pool) cudaEventDestroy(e);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char *tdgl_last_error(const tdgl_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+long tdgl_launch_count(const tdgl_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int tdgl_sim_create(tdgl_ctx *ctx, int nx, int ny, int nz, double dx, double dy, double dz, tdgl_sim **out) {
+    if (!ctx || !out) return TDGL_EINVAL;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > TDGL_MAX_DIM || ny > TDGL_MAX_DIM || nz > TDGL_MAX_DIM)
+        return fail(ctx, TDGL_EINVAL, "grid %dx%dx%d outside 1..%d", nx, ny, nz, TDGL_MAX_DIM);
+    if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
+        return fail(ctx, TDGL_EINVAL, "cell sizes must be positive and finite");
+    ctx_set(ctx);
+    tdgl_sim *s = new tdgl_sim();
+    s->ctx = ctx;
+    s->nx = nx; s->ny = ny; s->nz = nz;
+    s->d[0] = dx; s->d[1] = dy; s->d[2] = dz;
+    s->ell = std::min(dx, std::min(dy, dz));
+    s->ncell = (long)nx * ny * nz;
+    memset(s->mats, 0, sizeof s->mats);
+    s->map.assign(s->ncell, 0);
+    s->Mx = smooth_at_least(2 * nx - 1, true);
+    s->My = smooth_at_least(2 * ny - 1, false);
+    s->Mz = smooth_at_least(2 * nz - 1, false);
+    s->hx = s->Mx / 2;
+    s->Kx = s->hx + 1;
+    s->kxp = (s->Kx + 3) & ~3;
+    s->kyh = s->My / 2 + 1;
+    s->kzh = s->Mz / 2 + 1;
+    std::vector<float2> tw;
+    s->px = make_plan(s->hx, tw);
+    s->py = make_plan(s->My, tw);
+    s->pz = make_plan(s->Mz, tw);
+    s->twr = (int)tw.size();
+    for (int k = 0; k <= s->hx; ++k) {
+        const double a = -2.0 * M_PI * (double)k / (double)s->Mx;
+        tw.push_back(make_float2((float)cos(a), (float)sin(a)));
+    }
+    build_items(s);
+    int rc = TDGL_OK;
+    auto al = [&](void **p, size_t b) {
+        if (rc != TDGL_OK) return;
+        cudaError_t e = cudaMalloc(p, b);
+        if (e != cudaSuccess) rc = fail(ctx, TDGL_ENOMEM, "cudaMalloc(%zu): %s", b, cudaGetErrorString(e));
+    };
+    al((void **)&s->dP[0], 3ull * s->ncell * sizeof(float));
+    al((void **)&s->dP[1], 3ull * s->ncell * sizeof(float));
+    al((void **)&s->dmat, s->ncell);
+    al((void **)&s->dtw, tw.size() * sizeof(float2));
+    al((void **)&s->dcoef, MAXMAT * NCOEF * sizeof(float));
+    al((void **)&s->dmaxdp, sizeof(unsigned));
+    al((void **)&s->dflag, sizeof(int));
+    al((void **)&s->denergy, 4 * sizeof(double));
+    al((void **)&s->ddesc, sizeof(SimDev));
+    if (rc == TDGL_OK) {
+        cudaMemsetAsync(s->dP[0], 0, 3ull * s->ncell * sizeof(float), ctx->stream);
+        cudaMemsetAsync(s->dP[1], 0, 3ull * s->ncell * sizeof(float), ctx->stream);
+        cudaMemsetAsync(s->dmat, 0, s->ncell, ctx->stream);
+        cudaMemsetAsync(s->dflag, 0, sizeof(int), ctx->stream);
+        cudaMemsetAsync(s->dmaxdp, 0, sizeof(unsigned), ctx->stream);
+        cudaMemcpyAsync(s->dtw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream);
+        rc = upload_items(s);
+        if (rc == TDGL_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            rc = fail(ctx, TDGL_ECUDA, "sim setup: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    if (rc != TDGL_OK) {
+        tdgl_sim_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return TDGL_OK;
+}
+
+void tdgl_sim_destroy(tdgl_sim *s) {
+    if (!s) return;
+    ctx_set(s->ctx);
+    cudaStreamSynchronize(s->ctx->stream);
+    void *ptrs[] = {s->dP[0], s->dP[1], s->dmat, s->dX, s->dY, s->dNhat, s->dtw, s->dcoef, s->dmaxdp,
+                    s->dflag, s->denergy, s->dout, s->ddesc, s->d_rows, s->d_y, s->d_z};
+    for (void *p : ptrs) cudaFree(p);
+    delete s;
+}
+
+int tdgl_material_define(tdgl_sim *s, int id, const tdgl_material *m) {
+    if (!s || !m) return TDGL_EINVAL;
+    if (id < 1 || id >= TDGL_MAX_MATERIALS) return fail(s->ctx, TDGL_EINVAL, "material id %d outside 1..%d", id, TDGL_MAX_MATERIALS - 1);
+    if (m->a1_form < 0 || m->a1_form > 2) return fail(s->ctx, TDGL_EINVAL, "a1_form %d", m->a1_form);
+    if (m->a1_form == 1 && (m->coth_Ts == 0.0 || m->coth_T1 <= 0.0)) return fail(s->ctx, TDGL_EINVAL, "coth form needs Ts != 0, T1 > 0");
+    s->mats[id] = *m;
+    s->defined[id] = true;
+    return TDGL_OK;
+}
+
+static int apply_map(tdgl_sim *s) {
+    tdgl_ctx *ctx = s->ctx;
+    ctx_set(ctx);
+    CK(ctx, cudaMemcpyAsync(s->dmat, s->map.data(), s->ncell, cudaMemcpyHostToDevice, ctx->stream));
+    TRY(launch(ctx, TDGL_K_OTHER, [&] { k_mask<<<grid_for(3 * s->ncell), 256, 0, ctx->stream>>>(s->dP[s->cur], s->dmat, s->ncell); }));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    s->xstate = XS_NONE;
+    return TDGL_OK;
+}
+
+int tdgl_set_material_map(tdgl_sim *s, const uint8_t *ids, int where) {
+    if (!s || !ids || !valid_where(where)) return TDGL_EINVAL;
+    ctx_set(s->ctx);
+    if (where == TDGL_HOST) {
+        memcpy(s->map.data(), ids, s->ncell);
+    } else {
+        CK(s->ctx, cudaMemcpy(s->map.data(), ids, s->ncell, cudaMemcpyDeviceToHost));
+    }
+    for (long i = 0; i < s->ncell; ++i)
+        if (s->map[i] >= TDGL_MAX_MATERIALS) return fail(s->ctx, TDGL_EINVAL, "material id %d >= %d", (int)s->map[i], TDGL_MAX_MATERIALS);
+    return apply_map(s);
+}
+
+int tdgl_set_layers(tdgl_sim *s, int n, const int *z0, const int *z1, const int *id) {
+    if (!s || n < 0 || (n > 0 && (!z0 || !z1 || !id))) return TDGL_EINVAL;
+    std::fill(s->map.begin(), s->map.end(), 0);
+    const long plane = (long)s->nx * s->ny;
+    for (int i = 0; i < n; ++i) {
+        if (id[i] < 0 || id[i] >= TDGL_MAX_MATERIALS) return fail(s->ctx, TDGL_EINVAL, "layer id %d", id[i]);
+        const int a = std::max(0, z0[i]), b = std::min(s->nz, z1[i]);
+        for (int z = a; z < b; ++z) std::fill(s->map.begin() + z * plane, s->map.begin() + (z + 1) * plane, (uint8_t)id[i]);
+    }
+    return apply_map(s);
+}
+
+int tdgl_set_eps_b(tdgl_sim *s, double eps_b) {
+    if (!s || !(eps_b > 0) || !std::isfinite(eps_b)) return s ? fail(s->ctx, TDGL_EINVAL, "eps_b must be > 0") : TDGL_EINVAL;
+    if (eps_b != s->eps_b) s->xstate = (s->xstate == XS_EHAT) ? XS_NONE : s->xstate;
+    s->eps_b = eps_b;
+    return TDGL_OK;
+}
+
+int tdgl_set_terms(tdgl_sim *s, unsigned mask) {
+    if (!s || (mask & ~TDGL_TERM_ALL)) return TDGL_EINVAL;
+    s->terms = mask;
+    return TDGL_OK;
+}
+
+int tdgl_set_temperature(tdgl_sim *s, double T) {
+    if (!s || !(T > 0) || !std::isfinite(T)) return s ? fail(s->ctx, TDGL_EINVAL, "T must be > 0") : TDGL_EINVAL;
+    s->T = T;
+    return TDGL_OK;
+}
+
+int tdgl_set_field(tdgl_sim *s, double Ex, double Ey, double Ez) {
+    if (!s || !std::isfinite(Ex) || !std::isfinite(Ey) || !std::isfinite(Ez)) return TDGL_EINVAL;
+    s->E[0] = Ex; s->E[1] = Ey; s->E[2] = Ez;
+    return TDGL_OK;
+}
+
+int tdgl_set_scales(tdgl_sim *s, double P0, double alpha_ref) {
+    if (!s || !(P0 > 0) || !(alpha_ref > 0) || !std::isfinite(P0) || !std::isfinite(alpha_ref)) return TDGL_EINVAL;
+    ctx_set(s->ctx);
+    const double old = s->scales_fixed ? s->P0 : 0.0;
+    s->P0 = P0;
+    s->alpha_ref = alpha_ref;
+    if (old > 0 && old != P0) {
+        const float f = (float)(old / P0);
+        TRY(launch(s->ctx, TDGL_K_OTHER, [&] {
+            k_scale_out<<<grid_for(3 * s->ncell), 256, 0, s->ctx->stream>>>(s->dP[s->cur], s->dP[s->cur], 3 * s->ncell, f);
+        }));
+        s->xstate = XS_NONE;
+    }
+    s->scales_fixed = true;
+    return TDGL_OK;
+}
+
+int tdgl_get_scales(tdgl_sim *s, double *P0, double *alpha_ref) {
+    if (!s) return TDGL_EINVAL;
+    if (!s->scales_fixed && lowest_material(s)) fix_scales(s);
+    if (P0) *P0 = s->P0;
+    if (alpha_ref) *alpha_ref = s->alpha_ref;
+    return TDGL_OK;
+}
+
+int tdgl_set_P(tdgl_sim *s, const float *P, int where) {
+    if (!s || !P || !valid_where(where)) return TDGL_EINVAL;
+    tdgl_ctx *ctx = s->ctx;
+    ctx_set(ctx);
+    if (lowest_material(s)) fix_scales(s);
+    TRY(ensure_out(s));
+    TRY(copy_in(ctx, s->dout, P, 3ull * s->ncell * sizeof(float), where));
+    const float f = (float)(1.0 / s->P0);
+    TRY(launch(ctx, TDGL_K_OTHER, [&] {
+        k_scale_in<<<grid_for(3 * s->ncell), 256, 0, ctx->stream>>>(s->dP[s->cur], s->dout, s->dmat, s->ncell, f);
+    }));
+    if (where == TDGL_HOST) CK(ctx, cudaStreamSynchronize(ctx->stream));
+    s->xstate = XS_NONE;
+    return TDGL_OK;
+}
+
+int tdgl_get_P(tdgl_sim *s, float *out, int where) {
+    if (!s || !out || !valid_where(where)) return TDGL_EINVAL;
+    tdgl_ctx *ctx = s->ctx;
+    ctx_set(ctx);
+    if (lowest_material(s)) fix_scales(s);
+    TRY(ensure_out(s));
+    const float f = (float)s->P0;
+    TRY(launch(ctx, TDGL_K_OTHER, [&] {
+        k_scale_out<<<grid_for(3 * s->ncell), 256, 0, ctx->stream>>>(s->dout, s->dP[s->cur], 3 * s->ncell, f);
+    }));
+    return copy_out(ctx, out, s->dout, 3ull * s->ncell * sizeof(float), where);
+}
+
+int tdgl_init_random(tdgl_sim *s, uint64_t seed, double amp) {
+    if (!s || !(amp >= 0) || !std::isfinite(amp)) return TDGL_EINVAL;
+    tdgl_ctx *ctx = s->ctx;
+    ctx_set(ctx);
+    if (lowest_material(s)) fix_scales(s);
+    const float a = (float)(amp / s->P0);
+    TRY(launch(ctx, TDGL_K_OTHER, [&] {
+        k_init_random<<<grid_for(3 * s->ncell), 256, 0, ctx->stream>>>(s->dP[s->cur], s->dmat, s->ncell,
+                                                                         (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), a);
+    }));
+    s->xstate = XS_NONE;
+    return TDGL_OK;
+}
+
+int tdgl_get_field(tdgl_sim *s, unsigned mask, float *out, int where) {
+    if (!s || !out || !valid_where(where) || (mask & ~TDGL_TERM_ALL)) return TDGL_EINVAL;
+    tdgl_ctx *ctx = s->ctx;
+    ctx_set(ctx);
+    TRY(prepare(s, mask));
+    TRY(ensure_out(s));
+    fill_desc(s, 0.0, mask);
+    TRY(upload_desc(s));
+    const bool elec = (mask & TDGL_TERM_ELEC) != 0;
+    Work w = sim_work(s, elec);
+    if (elec) TRY(ensure_ehat(s, w));
+    TRY(launch_rows(ctx, MODE_FIELD, w, 0));
+    return copy_out(ctx, out, s->dout, 3ull * s->ncell * sizeof(float), where);
+}
+
+int tdgl_step(tdgl_sim *s, int n, double dt) {
+    if (!s || n < 0 || !(dt > 0) || !std::isfinite(dt)) return s ? fail(s->ctx, TDGL_EINVAL, "bad n or dt") : TDGL_EINVAL;
+    ctx_set(s->ctx);
+    if (n == 0) return TDGL_OK;
+    TRY(prepare(s, s->terms));
+    TRY(steps_nosync(s, n, dt));
+    double m;
+    int f;
+    TRY(read_status(s, &m, &f));
+    if (f) {
+        CK(s->ctx, cudaMemsetAsync(s->dflag, 0, sizeof(int), s->ctx->stream));
+        return fail(s->ctx, TDGL_EDIVERGED, "P diverged (NaN or |P| > 1e3 P0)");
+    }
+    return TDGL_OK;
+}
+
+int tdgl_last_max_dP(tdgl_sim *s, double *out) {
+    if (!s || !out) return TDGL_EINVAL;
+    *out = s->last_maxdp;
+    return TDGL_OK;
+}
+
+int tdgl_relax(tdgl_sim *s, double dt, double tol, long max_steps, int check_every, long *steps_taken) {
+    if (steps_taken) *steps_taken = 0;
+    if (!s || !(dt > 0) || !(tol > 0) || max_steps < 0 || check_every < 1) return TDGL_EINVAL;
+    ctx_set(s->ctx);
+    TRY(prepare(s, s->terms));
+    long done = 0;
+    while (done < max_steps) {
+        const int k = (int)std::min<long>(check_every, max_steps - done);
+        TRY(steps_nosync(s, k, dt));
+        done += k;
+        double m;
+        int f;
+        TRY(read_status(s, &m, &f));
+        if (steps_taken) *steps_taken = done;
+        if (f) {
+            CK(s->ctx, cudaMemsetAsync(s->dflag, 0, sizeof(int), s->ctx->stream));
+            return fail(s->ctx, TDGL_EDIVERGED, "P diverged after %ld steps", done);
+        }
+        if (m < tol) return TDGL_OK;
+    }
+    return fail(s->ctx, TDGL_ENOTCONVERGED, "not converged after %ld steps (last max|dP| = %g P0)", done, s->last_maxdp);
+}
+
+int tdgl_energy(tdgl_sim *s, tdgl_energies *out) {
+    if (!s || !out) return TDGL_EINVAL;
+    tdgl_ctx *ctx = s->ctx;
+    ctx_set(ctx);
+    TRY(prepare(s, s->terms));
+    fill_desc(s, 0.0, s->terms);
+    TRY(upload_desc(s));
+    const bool elec = (s->terms & TDGL_TERM_ELEC) != 0;
+    Work w = sim_work(s, elec);
+    if (elec) TRY(ensure_ehat(s, w));
+    CK(ctx, cudaMemsetAsync(s->denergy, 0, 4 * sizeof(double), ctx->stream));
+    TRY(launch_rows(ctx, MODE_ENERGY, w, 0));
+    double e[4];
+    CK(ctx, cudaMemcpyAsync(e, s->denergy, sizeof e, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    const double scale = s->alpha_ref * s->P0 * s->P0 * s->d[0] * s->d[1] * s->d[2];
+    out->land = e[0] * scale;
+    out->grad = e[1] * scale;
+    out->elec = e[2] * scale;
+    out->ext = e[3] * scale;
+    out->total = out->land + out->grad + out->elec + out->ext;
+    return TDGL_OK;
+}
+
+// ---- batches ---------------------------------------------------------------------------------------
+int tdgl_batch_create(tdgl_ctx *ctx, int n, tdgl_sim *const *sims, tdgl_batch **out) {
+    if (!ctx || !out || n < 1 || !sims) return TDGL_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!sims[i] || sims[i]->ctx != ctx) return fail(ctx, TDGL_EINVAL, "sim %d missing or of another context", i);
+        if (sims[i]->batch) return fail(ctx, TDGL_ESTATE, "sim %d already in a batch", i);
+        for (int j = 0; j < i; ++j)
+            if (sims[j] == sims[i]) return fail(ctx, TDGL_EINVAL, "sim %d listed twice", i);
+    }
+    ctx_set(ctx);
+    tdgl_batch *b = new tdgl_batch();
+    b->ctx = ctx;
+    b->sims.assign(sims, sims + n);
+    if (cudaMalloc(&b->ddescs, n * sizeof(SimDev)) != cudaSuccess) {
+        delete b;
+        return fail(ctx, TDGL_ENOMEM, "batch descriptors");
+    }
+    for (auto s : b->sims) s->batch = b;
+    *out = b;
+    return TDGL_OK;
+}
+
+void tdgl_batch_destroy(tdgl_batch *b) {
+    if (!b) return;
+    ctx_set(b->ctx);
+    cudaStreamSynchronize(b->ctx->stream);
+    for (auto s : b->sims) s->batch = nullptr;
+    cudaFree(b->ddescs);
+    cudaFree(b->d_items);
+    delete b;
+}
+
+namespace {
+
+// build concatenated work lists over the active sims and run n steps of all of them
+int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const double *dt) {
+    tdgl_ctx *ctx = b->ctx;
+    std::vector<SimDev> descs(b->sims.size());
+    std::vector<int4> rows, ys, zs;
+    Work w;
+    memset(&w, 0, sizeof w);
+    bool any_elec = false;
+    for (int idx : active) {
+        tdgl_sim *s = b->sims[idx];
+        const bool elec = (s->terms & TDGL_TERM_ELEC) != 0;
+        any_elec |= elec;
+        fill_desc(s, dt[idx], s->terms);
+        descs[idx] = s->desc;
+        for (auto it : s->it_rows) rows.push_back(make_int4(idx, it.y, it.z, it.w));
+        if (elec) {
+            for (auto it : s->it_y) ys.push_back(make_int4(idx, it.y, it.z, it.w));
+            for (auto it : s->it_z) zs.push_back(make_int4(idx, it.y, it.z, it.w));
+        }
+        w.sm_rows = std::max(w.sm_rows, smem_rows(s, s->rows_cnt_max));
+        w.sm_y = std::max(w.sm_y, smem_y(s, s->ky_cnt_max));
+        w.sm_z = std::max(w.sm_z, smem_z(s, s->kz_cnt_max));
+    }
+    const size_t tot = rows.size() + ys.size() + zs.size();
+    if (tot > b->items_cap) {
+        cudaFree(b->d_items);
+        b->d_items = nullptr;
+        CK(ctx, cudaMalloc(&b->d_items, tot * sizeof(int4)));
+        b->items_cap = tot;
+    }
+    std::vector<int4> all;
+    all.reserve(tot);
+    all.insert(all.end(), rows.begin(), rows.end());
+    all.insert(all.end(), ys.begin(), ys.end());
+    all.insert(all.end(), zs.begin(), zs.end());
+    CK(ctx, cudaMemcpyAsync(b->d_items, all.data(), tot * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(b->ddescs, descs.data(), descs.size() * sizeof(SimDev), cudaMemcpyHostToDevice, ctx->stream));
+    w.descs = b->ddescs;
+    w.rows = b->d_items;
+    w.y = b->d_items + rows.size();
+    w.z = b->d_items + rows.size() + ys.size();
+    w.n_rows = (int)rows.size();
+    w.n_y = (int)ys.size();
+    w.n_z = (int)zs.size();
+    // prologue: sims whose x-spectrum is not P-hat of the current P get the x forward pass
+    {
+        std::vector<int4> pro;
+        for (int idx : active) {
+            tdgl_sim *s = b->sims[idx];
+            if ((s->terms & TDGL_TERM_ELEC) && s->xstate != XS_PHAT)
+                for (auto it : s->it_rows) pro.push_back(make_int4(idx, it.y, it.z, it.w));
+        }
+        if (!pro.empty()) {
+            int4 *dpro = nullptr;
+            CK(ctx, cudaMalloc(&dpro, pro.size() * sizeof(int4)));
+            CK(ctx, cudaMemcpyAsync(dpro, pro.data(), pro.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+            Work wp = w;
+            wp.rows = dpro;
+            wp.n_rows = (int)pro.size();
+            TRY(launch_rows(ctx, MODE_XFWD, wp, 0));
+            CK(ctx, cudaStreamSynchronize(ctx->stream));
+            cudaFree(dpro);
+        }
+    }
+    for (int idx : active) CK(ctx, cudaMemsetAsync(b->sims[idx]->dflag, 0, sizeof(int), ctx->stream));
+    int parity = 0;
+    for (int i = 0; i < n; ++i) {
+        if (any_elec) TRY(launch_conv(ctx, w));
+        if (i == n - 1)
+            for (int idx : active) CK(ctx, cudaMemsetAsync(b->sims[idx]->dmaxdp, 0, sizeof(unsigned), ctx->stream));
+        TRY(launch_rows(ctx, MODE_STEP, w, parity));
+        parity ^= 1;
+    }
+    for (int idx : active) {
+        tdgl_sim *s = b->sims[idx];
+        if (n & 1) s->cur ^= 1;
+        s->xstate = (s->terms & TDGL_TERM_ELEC) ? XS_PHAT : XS_NONE;
+    }
+    return TDGL_OK;
+}
+
+}  // namespace
+
+int tdgl_batch_step(tdgl_batch *b, int n, const double *dt) {
+    if (!b || n < 0 || !dt) return TDGL_EINVAL;
+    tdgl_ctx *ctx = b->ctx;
+    ctx_set(ctx);
+    std::vector<int> active;
+    for (size_t i = 0; i < b->sims.size(); ++i) {
+        if (!(dt[i] > 0) || !std::isfinite(dt[i])) return fail(ctx, TDGL_EINVAL, "dt[%zu]", i);
+        TRY(prepare(b->sims[i], b->sims[i]->terms));
+        active.push_back((int)i);
+    }
+    if (n == 0) return TDGL_OK;
+    TRY(batch_steps(b, active, n, dt));
+    int rc = TDGL_OK;
+    for (int idx : active) {
+        double m;
+        int f;
+        TRY(read_status(b->sims[idx], &m, &f));
+        if (f) rc = fail(ctx, TDGL_EDIVERGED, "sim %d diverged", idx);
+    }
+    return rc;
+}
+
+int tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_steps, int check_every,
+                     long *steps_taken) {
+    if (!b || !dt || !(tol > 0) || max_steps < 0 || check_every < 1) return TDGL_EINVAL;
+    tdgl_ctx *ctx = b->ctx;
+    ctx_set(ctx);
+    const int n = (int)b->sims.size();
+    std::vector<int> active;
+    std::vector<long> taken(n, 0);
+    for (int i = 0; i < n; ++i) {
+        if (!(dt[i] > 0) || !std::isfinite(dt[i])) return fail(ctx, TDGL_EINVAL, "dt[%d]", i);
+        TRY(prepare(b->sims[i], b->sims[i]->terms));
+        active.push_back(i);
+    }
+    long done = 0;
+    int rc = TDGL_OK;
+    while (!active.empty() && done < max_steps) {
+        const int k = (int)std::min<long>(check_every, max_steps - done);
+        TRY(batch_steps(b, active, k, dt));
+        done += k;
+        std::vector<int> keep;
+        for (int idx : active) {
+            double m;
+            int f;
+            TRY(read_status(b->sims[idx], &m, &f));
+            taken[idx] = done;
+            if (f) {
+                rc = fail(ctx, TDGL_EDIVERGED, "sim %d diverged", idx);
+                continue;
+            }
+            if (!(m < tol)) keep.push_back(idx);
+        }
+        active.swap(keep);
+    }
+    if (steps_taken)
+        for (int i = 0; i < n; ++i) steps_taken[i] = taken[i];
+    if (rc != TDGL_OK) return rc;
+    if (!active.empty()) return fail(ctx, TDGL_ENOTCONVERGED, "%zu sims not converged after %ld steps", active.size(), done);
+    return TDGL_OK;
+}
+
+// ---- measurement -------------------------------------------------------------------------------------
+int tdgl_profile(tdgl_ctx *ctx, int enable) {
+    if (!ctx) return TDGL_EINVAL;
+    ctx->profiling = enable != 0;
+    return TDGL_OK;
+}
+
+int tdgl_profile_read(tdgl_ctx *ctx, int kind, double *total_ms, long *launches) {
+    if (!ctx || kind < 0 || kind >= TDGL_K_COUNT) return TDGL_EINVAL;
+    ctx_set(ctx);
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto &r : ctx->recs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        ctx->prof_ms[r.kind] += ms;
+        ctx->prof_n[r.kind] += 1;
+        ctx->pool.push_back(r.a);
+        ctx->pool.push_back(r.b);
+    }
+    ctx->recs.clear();
+    if (total_ms) *total_ms = ctx->prof_ms[kind];
+    if (launches) *launches = ctx->prof_n[kind];
+    ctx->prof_ms[kind] = 0.0;
+    ctx->prof_n[kind] = 0;
+    return TDGL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,292 @@
+"""Python binding of libtdgl (include/tdgl.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels of libtdgl.so; this module converts numpy arrays or
+torch CUDA tensors to pointers and raises on error codes.  There is no CPU fallback: importing
+works without a GPU, but creating a Context needs the built library and a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtdgl.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ENOTCONVERGED, ESTATE = 0, -1, -2, -3, -4, -5, -6
+HOST, DEVICE = 0, 1
+TERM_LANDAU, TERM_GRAD, TERM_ELEC, TERM_EXT, TERM_ALL = 1, 2, 4, 8, 15
+K_STEP, K_YFWD, K_ZCONV, K_YINV, K_XFWD, K_OTHER = range(6)
+KERNEL_NAMES = {K_STEP: "k_rows<STEP>", K_YFWD: "k_yfwd", K_ZCONV: "k_zconv", K_YINV: "k_yinv",
+                K_XFWD: "k_rows<XFWD>", K_OTHER: "other"}
+MAX_MATERIALS, MAX_DIM = 16, 1024
+
+_CODES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EDIVERGED: "EDIVERGED",
+          ENOTCONVERGED: "ENOTCONVERGED", ESTATE: "ESTATE"}
+
+
+class TdglError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("a1_form", ctypes.c_int)] + [(n, ctypes.c_double) for n in (
+        "a0", "T0", "coth_A", "coth_Ts", "coth_T1", "a11_0", "a11_T", "a11_Tref", "a12",
+        "a111_0", "a111_T", "a111_Tref", "a112", "a123", "G11", "G12", "G44", "G44p", "r_s")]
+
+
+class Energies(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("land", "grad", "elec", "ext", "total")]
+
+
+_lib = None
+_VP, _D, _I, _U, _L = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_uint, ctypes.c_long
+
+_SIGS = {
+    "tdgl_ctx_create": (_I, [ctypes.POINTER(_VP), _I, _VP]),
+    "tdgl_ctx_destroy": (None, [_VP]),
+    "tdgl_last_error": (ctypes.c_char_p, [_VP]),
+    "tdgl_launch_count": (_L, [_VP]),
+    "tdgl_sim_create": (_I, [_VP, _I, _I, _I, _D, _D, _D, ctypes.POINTER(_VP)]),
+    "tdgl_sim_destroy": (None, [_VP]),
+    "tdgl_material_define": (_I, [_VP, _I, ctypes.POINTER(Material)]),
+    "tdgl_set_material_map": (_I, [_VP, _VP, _I]),
+    "tdgl_set_layers": (_I, [_VP, _I, _VP, _VP, _VP]),
+    "tdgl_set_eps_b": (_I, [_VP, _D]),
+    "tdgl_set_terms": (_I, [_VP, _U]),
+    "tdgl_set_temperature": (_I, [_VP, _D]),
+    "tdgl_set_field": (_I, [_VP, _D, _D, _D]),
+    "tdgl_set_scales": (_I, [_VP, _D, _D]),
+    "tdgl_get_scales": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "tdgl_set_P": (_I, [_VP, _VP, _I]),
+    "tdgl_get_P": (_I, [_VP, _VP, _I]),
+    "tdgl_init_random": (_I, [_VP, ctypes.c_uint64, _D]),
+    "tdgl_get_field": (_I, [_VP, _U, _VP, _I]),
+    "tdgl_step": (_I, [_VP, _I, _D]),
+    "tdgl_last_max_dP": (_I, [_VP, ctypes.POINTER(_D)]),
+    "tdgl_relax": (_I, [_VP, _D, _D, _L, _I, ctypes.POINTER(_L)]),
+    "tdgl_energy": (_I, [_VP, ctypes.POINTER(Energies)]),
+    "tdgl_batch_create": (_I, [_VP, _I, ctypes.POINTER(_VP), ctypes.POINTER(_VP)]),
+    "tdgl_batch_destroy": (None, [_VP]),
+    "tdgl_batch_step": (_I, [_VP, _I, ctypes.POINTER(_D)]),
+    "tdgl_batch_relax": (_I, [_VP, ctypes.POINTER(_D), _D, _L, _I, ctypes.POINTER(_L)]),
+    "tdgl_profile": (_I, [_VP, _I]),
+    "tdgl_profile_read": (_I, [_VP, _I, ctypes.POINTER(_D), ctypes.POINTER(_L)]),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def library(path: str = LIB_PATH):
+    """Load libtdgl.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise OSError(f"{path} not built; run paper_2605_28800_b300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    """(pointer, where) of a numpy array (host) or a torch tensor (host or CUDA)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, HOST
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), DEVICE if a.is_cuda else HOST
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def material_struct(rec: dict) -> Material:
+    m = Material()
+    for name, _ in Material._fields_:
+        setattr(m, name, rec.get(name, 1.0 if name == "r_s" else 0))
+    return m
+
+
+class Context:
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = library()
+        h = _VP()
+        s = None if stream is None else _VP(int(stream))
+        rc = self.lib.tdgl_ctx_create(ctypes.byref(h), device, s)
+        if rc != OK:
+            raise TdglError(rc, f"tdgl_ctx_create(device={device}) failed")
+        self.h = h
+
+    def check(self, rc):
+        if rc != OK:
+            raise TdglError(rc, self.lib.tdgl_last_error(self.h).decode())
+        return rc
+
+    @property
+    def launch_count(self) -> int:
+        return int(self.lib.tdgl_launch_count(self.h))
+
+    def profile(self, enable: bool = True):
+        self.check(self.lib.tdgl_profile(self.h, int(enable)))
+
+    def profile_read(self, kind: int):
+        ms, n = _D(), _L()
+        self.check(self.lib.tdgl_profile_read(self.h, kind, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tdgl_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Sim:
+    """One finite sample: grid (nx, ny, nz) of (dx, dy, dz)-metre cells."""
+
+    def __init__(self, ctx: Context, shape, cell):
+        self.ctx, self.lib = ctx, ctx.lib
+        self.shape = tuple(int(v) for v in shape)
+        nx, ny, nz = self.shape
+        h = _VP()
+        ctx.check(self.lib.tdgl_sim_create(ctx.h, nx, ny, nz, *map(float, cell), ctypes.byref(h)))
+        self.h = h
+        self.ncell = nx * ny * nz
+
+    def _c(self, rc):
+        return self.ctx.check(rc)
+
+    def define_material(self, mid: int, rec: dict):
+        m = material_struct(rec)
+        self._c(self.lib.tdgl_material_define(self.h, mid, ctypes.byref(m)))
+
+    def set_material_map(self, ids):
+        if isinstance(ids, np.ndarray):
+            ids = np.ascontiguousarray(ids, dtype=np.uint8)
+        p, where = _ptr(ids)
+        self._c(self.lib.tdgl_set_material_map(self.h, p, where))
+
+    def set_layers(self, layers):
+        z0 = np.array([l[0] for l in layers], np.int32)
+        z1 = np.array([l[1] for l in layers], np.int32)
+        ids = np.array([l[2] for l in layers], np.int32)
+        self._c(self.lib.tdgl_set_layers(self.h, len(layers), z0.ctypes.data, z1.ctypes.data, ids.ctypes.data))
+
+    def set_eps_b(self, v): self._c(self.lib.tdgl_set_eps_b(self.h, float(v)))
+    def set_terms(self, mask): self._c(self.lib.tdgl_set_terms(self.h, int(mask)))
+    def set_temperature(self, T): self._c(self.lib.tdgl_set_temperature(self.h, float(T)))
+    def set_field(self, E): self._c(self.lib.tdgl_set_field(self.h, *map(float, E)))
+    def set_scales(self, P0, alpha_ref): self._c(self.lib.tdgl_set_scales(self.h, float(P0), float(alpha_ref)))
+
+    def scales(self):
+        a, b = _D(), _D()
+        self._c(self.lib.tdgl_get_scales(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def set_P(self, P):
+        if isinstance(P, np.ndarray):
+            P = np.ascontiguousarray(P, dtype=np.float32)
+        if P.size != 3 * self.ncell:
+            raise ValueError("P must have 3*nx*ny*nz elements")
+        p, where = _ptr(P)
+        self._c(self.lib.tdgl_set_P(self.h, p, where))
+
+    def get_P(self, out=None):
+        nx, ny, nz = self.shape
+        if out is None:
+            out = np.empty((3, nz, ny, nx), np.float32)
+        p, where = _ptr(out)
+        self._c(self.lib.tdgl_get_P(self.h, p, where))
+        return out
+
+    def init_random(self, seed: int, amp: float):
+        self._c(self.lib.tdgl_init_random(self.h, ctypes.c_uint64(seed), float(amp)))
+
+    def get_field(self, mask=TERM_ALL, out=None):
+        nx, ny, nz = self.shape
+        if out is None:
+            out = np.empty((3, nz, ny, nx), np.float32)
+        p, where = _ptr(out)
+        self._c(self.lib.tdgl_get_field(self.h, int(mask), p, where))
+        return out
+
+    def step(self, n: int, dt: float):
+        self._c(self.lib.tdgl_step(self.h, int(n), float(dt)))
+
+    def last_max_dP(self) -> float:
+        v = _D()
+        self._c(self.lib.tdgl_last_max_dP(self.h, ctypes.byref(v)))
+        return v.value
+
+    def relax(self, dt, tol, max_steps, check_every=16, raise_on_cap=True):
+        n = _L()
+        rc = self.lib.tdgl_relax(self.h, float(dt), float(tol), int(max_steps), int(check_every), ctypes.byref(n))
+        if rc == ENOTCONVERGED and not raise_on_cap:
+            return n.value, False
+        self._c(rc)
+        return n.value, True
+
+    def energy(self) -> dict:
+        e = Energies()
+        self._c(self.lib.tdgl_energy(self.h, ctypes.byref(e)))
+        return {k: getattr(e, k) for k, _ in Energies._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tdgl_sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent sims of one context stepped with one launch per kernel."""
+
+    def __init__(self, ctx: Context, sims):
+        self.ctx, self.lib, self.sims = ctx, ctx.lib, list(sims)
+        arr = (_VP * len(self.sims))(*[s.h for s in self.sims])
+        h = _VP()
+        ctx.check(self.lib.tdgl_batch_create(ctx.h, len(self.sims), arr, ctypes.byref(h)))
+        self.h = h
+
+    def _dts(self, dt):
+        dts = [float(dt)] * len(self.sims) if np.isscalar(dt) else [float(v) for v in dt]
+        return (_D * len(self.sims))(*dts)
+
+    def step(self, n, dt):
+        self.ctx.check(self.lib.tdgl_batch_step(self.h, int(n), self._dts(dt)))
+
+    def relax(self, dt, tol, max_steps, check_every=16, raise_on_cap=True):
+        steps = (_L * len(self.sims))()
+        rc = self.lib.tdgl_batch_relax(self.h, self._dts(dt), float(tol), int(max_steps), int(check_every), steps)
+        if not (rc == ENOTCONVERGED and not raise_on_cap):
+            self.ctx.check(rc)
+        return [int(v) for v in steps], rc == OK
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tdgl_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

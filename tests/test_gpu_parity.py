@@ -1,0 +1,185 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: the fields are compared relative to the largest magnitude of the same field
+(float32 arithmetic, FFT round-off grows like log N: 2e-5); trajectories use the stated bar
+max|P_gpu - P_oracle| / P0 <= 1e-5 after 100 and 200 steps and |dF| / sum|F_terms| <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import coefficients
+from oracle import tensor as otensor
+from tests.helpers import gpu_sim, mixed_case, oracle_sys, rel_err
+
+pytestmark = pytest.mark.gpu
+
+CELL = (1e-9, 1.1e-9, 0.9e-9)
+MATS = {1: synth.BTO, 2: dict(synth.PTO, G12=3e-11, G44=7e-11, G44p=2e-11, r_s=1.3)}
+SHAPES = [(1, 1, 1), (1, 1, 6), (5, 1, 1), (3, 5, 7), (8, 8, 4), (17, 9, 5), (32, 32, 8), (24, 12, 20)]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2605_28800_b300 import tdgl
+    c = tdgl.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("term,tol", [(1, 2e-6), (2, 2e-6), (4, 2e-5), (8, 1e-7)])
+def test_each_field_term_matches_oracle(ctx, shape, term, tol):
+    mat, P = mixed_case(shape, seed=sum(shape))
+    E = (2e7, -1e7, 3e7)
+    g = gpu_sim(ctx, shape, CELL, mat, MATS, 280.0, 30.0, E=E, P=P)
+    o = oracle_sys(shape, CELL, mat, MATS, 280.0, 30.0, E=E)
+    key = {1: "landau", 2: "grad", 4: "elec", 8: "ext"}[term]
+    want = o.fields(P.astype(np.float64))[key]
+    got = g.get_field(term)
+    if np.abs(want).max() == 0:
+        assert np.abs(got).max() == 0
+        return
+    assert rel_err(got, want) <= tol
+    assert np.all(got[:, mat == 0] == 0)
+
+
+def test_electrostatic_field_of_uniform_slab(ctx):
+    # closed form as well: uniform Pz film -> E_z ~ -Pz/(eps0 epsB) in the middle
+    shape = (64, 64, 2)
+    mat = np.ones((2, 64, 64), np.uint8)
+    P = np.zeros((3, 2, 64, 64), np.float32); P[2] = 0.25
+    g = gpu_sim(ctx, shape, (1e-9,) * 3, mat, {1: synth.BTO}, 300.0, 45.0, P=P)
+    o = oracle_sys(shape, (1e-9,) * 3, mat, {1: synth.BTO}, 300.0, 45.0)
+    got = g.get_field(4)
+    assert rel_err(got, o.fields(P.astype(np.float64))["elec"]) <= 2e-5
+    assert got[2, :, 32, 32].mean() == pytest.approx(-0.25 / (synth.EPS0 * 45.0), rel=0.05)
+
+
+@pytest.mark.parametrize("shape", [(3, 5, 7), (16, 8, 6)])
+def test_energy_terms_match_oracle(ctx, shape):
+    mat, P = mixed_case(shape, seed=7)
+    E = (1e7, 2e7, -3e7)
+    g = gpu_sim(ctx, shape, CELL, mat, MATS, 300.0, 45.0, E=E, P=P)
+    o = oracle_sys(shape, CELL, mat, MATS, 300.0, 45.0, E=E)
+    eg, eo = g.energy(), o.energy(P.astype(np.float64))
+    scale = sum(abs(eo[k]) for k in ("land", "grad", "elec", "ext"))
+    for k in ("land", "grad", "elec", "ext", "total"):
+        assert abs(eg[k] - eo[k]) <= 1e-6 * scale, k
+
+
+def _config1():
+    c = synth.CONFIG1
+    shape = c["shape"]
+    nx, ny, nz = shape
+    mat = np.ones((nz, ny, nx), np.uint8)
+    P = synth.uniform_P(shape, c["amp"], c["seed"])
+    dt = c["dt_star"] / abs(coefficients(c["material"], c["T"])["a1x"])
+    return c, shape, mat, P, dt
+
+
+def test_config1_trajectory_parity_100_and_200_steps(ctx):
+    c, shape, mat, P, dt = _config1()
+    mats = {1: c["material"]}
+    g = gpu_sim(ctx, shape, c["cell"], mat, mats, c["T"], c["eps_b"], P=P)
+    o = oracle_sys(shape, c["cell"], mat, mats, c["T"], c["eps_b"])
+    P0 = g.scales()[0]
+    Po = P.astype(np.float64)
+    for _ in range(2):
+        g.step(100, dt)
+        Po = o.run(Po, dt, 100)
+        Pg = g.get_P()
+        assert np.abs(Pg - Po).max() / P0 <= 1e-5
+    eg, eo = g.energy(), o.energy(Po)
+    scale = sum(abs(eo[k]) for k in ("land", "grad", "elec", "ext"))
+    assert abs(eg["total"] - eo["total"]) <= 1e-6 * scale
+
+
+def test_mixed_materials_trajectory_parity(ctx):
+    shape = (12, 10, 8)
+    mat, P = mixed_case(shape, seed=3)
+    P *= 0.2
+    E = (0.0, 0.0, 5e7)
+    g = gpu_sim(ctx, shape, CELL, mat, MATS, 300.0, 45.0, E=E, P=P)
+    o = oracle_sys(shape, CELL, mat, MATS, 300.0, 45.0, E=E)
+    dt = 0.003 / abs(coefficients(synth.PTO, 300.0)["a1x"])
+    g.step(50, dt)
+    Po = o.run(P.astype(np.float64), dt, 50)
+    assert np.abs(g.get_P() - Po).max() / g.scales()[0] <= 1e-5
+
+
+# ---- full-size workloads: sampled cells, oracle one cell at a time -----------------------------
+def _oracle_field_at(shape, cell, mat, mats, T, eps_b, P, octant, cells):
+    """Total field at selected cells: local terms on a 5x5x5 block, E_el by the direct sum."""
+    from oracle import System, TERM_GRAD, TERM_LANDAU
+    nx, ny, nz = shape
+    kappa = 1.0 / (synth.EPS0 * eps_b)
+    Pd = P.astype(np.float64)
+    out = []
+    for (x, y, z) in cells:
+        x0, x1 = max(0, x - 2), min(nx, x + 3)
+        y0, y1 = max(0, y - 2), min(ny, y + 3)
+        z0, z1 = max(0, z - 2), min(nz, z + 3)
+        sub = System((x1 - x0, y1 - y0, z1 - z0), cell, mat[z0:z1, y0:y1, x0:x1], mats, T,
+                     terms=TERM_LANDAU | TERM_GRAD)
+        h = sub.fields(Pd[:, z0:z1, y0:y1, x0:x1])["total"][:, z - z0, y - y0, x - x0].copy()
+        dz = np.abs(z - np.arange(nz))[:, None, None]
+        dy = np.abs(y - np.arange(ny))[None, :, None]
+        dx = np.abs(x - np.arange(nx))[None, None, :]
+        sx = np.sign(x - np.arange(nx))[None, None, :]
+        sy = np.sign(y - np.arange(ny))[None, :, None]
+        sz = np.sign(z - np.arange(nz))[:, None, None]
+        N = [octant[c][dz, dy, dx] for c in range(6)]
+        Nxy, Nxz, Nyz = N[3] * sx * sy, N[4] * sx * sz, N[5] * sy * sz
+        E = np.array([np.sum(N[0] * Pd[0] + Nxy * Pd[1] + Nxz * Pd[2]),
+                      np.sum(Nxy * Pd[0] + N[1] * Pd[1] + Nyz * Pd[2]),
+                      np.sum(Nxz * Pd[0] + Nyz * Pd[1] + N[2] * Pd[2])])
+        if mat[z, y, x]:
+            h += -kappa * E
+        out.append(h)
+    return np.array(out)
+
+
+def _sample_cells(shape, n, seed):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    corners = [(0, 0, 0), (nx - 1, ny - 1, nz - 1), (0, ny - 1, nz // 2), (nx // 2, 0, 0), (nx - 1, ny // 2, nz - 1)]
+    rand = [tuple(int(v) for v in (rng.integers(nx), rng.integers(ny), rng.integers(nz))) for _ in range(n)]
+    return corners + rand
+
+
+@pytest.mark.parametrize("workload", ["bto_cube_128", "pto_sto_bilayer_256x256x64"])
+def test_full_size_field_and_step_at_sampled_cells(ctx, workload):
+    if workload == "bto_cube_128":
+        c = synth.CONFIG2
+        shape = c["shape"]
+        nx, ny, nz = shape
+        mat = np.ones((nz, ny, nx), np.uint8)
+        mats = {1: c["material"]}
+        T, eps_b = 300.0, c["eps_b"]
+        P = synth.uniform_P(shape, c["amp"], c["seed"])
+        a1 = abs(coefficients(c["material"], T)["a1x"])
+    else:
+        c = synth.CONFIG4
+        shape = c["shape"]
+        mat = synth.layer_map(shape, c["layers"])
+        mats = {1: synth.PTO, 2: synth.STO}
+        T, eps_b = c["T"], c["eps_b"]
+        P = synth.cylinder_start(shape, c["radius"], 0.7, c["amp"], c["seed"], z_range=(32, 64))
+        a1 = abs(coefficients(synth.PTO, T)["a1x"])
+    cell = c["cell"]
+    E = (0.0, 0.0, 1e8)
+    g = gpu_sim(ctx, shape, cell, mat, mats, T, eps_b, E=E, P=P)
+    octant = otensor.octant(shape, cell)
+    cells = _sample_cells(shape, 20, 5)
+    h_o = _oracle_field_at(shape, cell, mat, mats, T, eps_b, P, octant, cells) + np.array(E)[None, :]
+    h_g = g.get_field(15)
+    got = np.array([h_g[:, z, y, x] for (x, y, z) in cells])
+    assert rel_err(got, h_o) <= 3e-5
+    dt = 0.004 / a1
+    g.step(1, dt)
+    Pn = g.get_P()
+    want = np.array([P[:, z, y, x].astype(np.float64) + dt * h_o[i] for i, (x, y, z) in enumerate(cells)])
+    gotp = np.array([Pn[:, z, y, x] for (x, y, z) in cells])
+    dP = np.abs(want - np.array([P[:, z, y, x] for (x, y, z) in cells])).max()
+    assert np.abs(gotp - want).max() <= 3e-5 * dP + 1e-7 * g.scales()[0]

@@ -1,0 +1,197 @@
+"""Runtime behaviour of the CUDA path through the C ABI: batches, relaxation, random start,
+edge cases and error codes (no GPU fault is provoked: every bad input is rejected on the host)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import coefficients
+from tests.helpers import gpu_sim, oracle_sys
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2605_28800_b300 import tdgl
+    c = tdgl.Context(0)
+    yield c
+    c.close()
+
+
+def _bto(ctx, shape, T=300.0, seed=1, eps_b=45.0):
+    nx, ny, nz = shape
+    mat = np.ones((nz, ny, nx), np.uint8)
+    P = synth.uniform_P(shape, 0.01, seed)
+    return gpu_sim(ctx, shape, (1e-9,) * 3, mat, {1: synth.BTO}, T, eps_b, P=P), P
+
+
+def test_batch_equals_single_runs_bitwise(ctx):
+    from paper_2605_28800_b300 import tdgl
+    shapes = [(16, 16, 16), (12, 20, 8), (9, 7, 5), (32, 8, 4)]
+    temps = [300.0, 250.0, 350.0, 200.0]
+    dt = [0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"]) * f for f in (1.0, 0.8, 1.2, 0.5)]
+    singles, batched = [], []
+    for i, (sh, T) in enumerate(zip(shapes, temps)):
+        a, _ = _bto(ctx, sh, T, seed=10 + i)
+        b, _ = _bto(ctx, sh, T, seed=10 + i)
+        singles.append(a)
+        batched.append(b)
+    for a, d in zip(singles, dt):
+        a.step(7, d)
+    B = tdgl.Batch(ctx, batched)
+    B.step(7, dt)
+    for a, b in zip(singles, batched):
+        assert np.array_equal(a.get_P(), b.get_P())
+    B.close()
+
+
+def test_batch_relax_converged_sims_leave_the_work_list(ctx):
+    from paper_2605_28800_b300 import tdgl
+    sims = []
+    for i, T in enumerate((300.0, 420.0)):
+        s, _ = _bto(ctx, (8, 8, 8), T, seed=20 + i)
+        sims.append(s)
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    B = tdgl.Batch(ctx, sims)
+    steps, ok = B.relax(dt, 1e-6, 200000, check_every=16)
+    assert ok
+    assert steps[0] != steps[1]
+    for s in sims:
+        # each sim satisfies the criterion on its own after the batch stopped it
+        s.step(1, dt)
+        assert s.last_max_dP() < 1.5e-6
+    B.close()
+
+
+def test_relax_reaches_oracle_state(ctx):
+    shape = (6, 6, 4)
+    nx, ny, nz = shape
+    mat = np.ones((nz, ny, nx), np.uint8)
+    P = synth.uniform_P(shape, 0.01, 4)
+    P[2] += 0.05
+    # eps_B = 649 and a 50 MV/m field along z give a polarized, non-uniform relaxed state
+    g = gpu_sim(ctx, shape, (1e-9,) * 3, mat, {1: synth.BTO}, 300.0, 649.0, E=(0.0, 0.0, 5e7), P=P)
+    o = oracle_sys(shape, (1e-9,) * 3, mat, {1: synth.BTO}, 300.0, 649.0, E=(0.0, 0.0, 5e7))
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    n, ok = g.relax(dt, 1e-7, 400000, check_every=16)
+    assert ok
+    Po, no, oko = o.relax(P.astype(np.float64), dt, 1e-7, g.scales()[0], 400000, check_every=16)
+    assert oko
+    eg, eo = g.energy(), o.energy(Po)
+    assert abs(eg["total"] - eo["total"]) <= 1e-5 * sum(abs(eo[k]) for k in ("land", "grad", "elec", "ext"))
+    assert np.abs(g.get_P() - Po).max() / g.scales()[0] <= 1e-3
+
+
+def _philox_first(c, k):
+    M0, M1, W0, W1 = 0xD2511F53, 0xCD9E8D57, 0x9E3779B9, 0xBB67AE85
+    c, k = list(c), list(k)
+    for _ in range(10):
+        p0, p1 = M0 * c[0], M1 * c[2]
+        c = [((p1 >> 32) ^ c[1] ^ k[0]) & 0xFFFFFFFF, p1 & 0xFFFFFFFF, ((p0 >> 32) ^ c[3] ^ k[1]) & 0xFFFFFFFF,
+             p0 & 0xFFFFFFFF]
+        k = [(k[0] + W0) & 0xFFFFFFFF, (k[1] + W1) & 0xFFFFFFFF]
+    return c[0]
+
+
+def test_philox_reference_known_answers():
+    # known-answer vectors of Philox4x32-10 (Random123 distribution, kat_vectors): first word
+    assert _philox_first([0, 0, 0, 0], [0, 0]) == 0x6627E8D5
+    assert _philox_first([0xFFFFFFFF] * 4, [0xFFFFFFFF] * 2) == 0x408F276D
+    assert _philox_first([0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344], [0xA4093822, 0x299F31D0]) == 0xD16CFE09
+
+
+def test_init_random_is_the_documented_philox_stream(ctx):
+    shape = (7, 5, 3)
+    s, _ = _bto(ctx, shape)
+    seed, amp = 0x1234_5678_9ABC, 0.02
+    s.init_random(seed, amp)
+    P = s.get_P()
+    ncell = 7 * 5 * 3
+    want = np.empty(3 * ncell)
+    for i in range(3 * ncell):
+        u = _philox_first([i % ncell, i // ncell, 0, 0], [seed & 0xFFFFFFFF, seed >> 32])
+        want[i] = amp * (2.0 * ((u + 0.5) / 2 ** 32) - 1.0)
+    assert np.allclose(P.ravel(), want, rtol=1e-6, atol=1e-9)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 9), (9, 1, 1), (1, 7, 1), (3, 5, 7), (2, 2, 2)])
+def test_degenerate_grids_step(ctx, shape):
+    s, P = _bto(ctx, shape)
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    nx, ny, nz = shape
+    o = oracle_sys(shape, (1e-9,) * 3, np.ones((nz, ny, nx), np.uint8), {1: synth.BTO}, 300.0, 45.0)
+    s.step(20, dt)
+    Po = o.run(P.astype(np.float64), dt, 20)
+    assert np.abs(s.get_P() - Po).max() / s.scales()[0] <= 1e-5
+
+
+def test_all_vacuum_map_keeps_zero(ctx):
+    from paper_2605_28800_b300 import tdgl
+    s = tdgl.Sim(ctx, (4, 4, 4), (1e-9,) * 3)
+    s.define_material(1, synth.BTO)
+    s.set_material_map(np.zeros((4, 4, 4), np.uint8))
+    s.set_P(np.ones((3, 4, 4, 4), np.float32))
+    s.step(3, 1e-12)
+    assert np.all(s.get_P() == 0)
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    from paper_2605_28800_b300 import tdgl
+    with pytest.raises(tdgl.TdglError) as e:
+        tdgl.Sim(ctx, (0, 4, 4), (1e-9,) * 3)
+    assert e.value.code == tdgl.EINVAL
+    with pytest.raises(tdgl.TdglError):
+        tdgl.Sim(ctx, (tdgl.MAX_DIM + 1, 1, 1), (1e-9,) * 3)
+    with pytest.raises(tdgl.TdglError):
+        tdgl.Sim(ctx, (4, 4, 4), (1e-9, -1.0, 1e-9))
+    s = tdgl.Sim(ctx, (4, 4, 4), (1e-9,) * 3)
+    with pytest.raises(tdgl.TdglError):
+        s.define_material(16, synth.BTO)
+    with pytest.raises(tdgl.TdglError) as e:
+        s.step(1, 1e-12)                       # no material defined
+    assert e.value.code == tdgl.ESTATE
+    s.define_material(1, synth.BTO)
+    with pytest.raises(tdgl.TdglError):
+        s.set_material_map(np.full((4, 4, 4), 20, np.uint8))
+    m = np.ones((4, 4, 4), np.uint8); m[0, 0, 0] = 3   # undefined id
+    s.set_material_map(m)
+    with pytest.raises(tdgl.TdglError) as e:
+        s.step(1, 1e-12)
+    assert e.value.code == tdgl.ESTATE
+    s.set_material_map(np.ones((4, 4, 4), np.uint8))
+    with pytest.raises(tdgl.TdglError):
+        s.step(1, -1.0)
+    with pytest.raises(tdgl.TdglError):
+        s.set_eps_b(0.0)
+    with pytest.raises(tdgl.TdglError):
+        s.set_temperature(-5.0)
+
+
+def test_divergence_is_reported(ctx):
+    from paper_2605_28800_b300 import tdgl
+    s, _ = _bto(ctx, (6, 6, 6))
+    with pytest.raises(tdgl.TdglError) as e:
+        s.step(50, 1e-6)                       # far beyond the explicit stability bound
+    assert e.value.code == tdgl.EDIVERGED
+
+
+def test_device_buffers_round_trip(ctx):
+    import torch
+    shape = (10, 6, 4)
+    s, P = _bto(ctx, shape)
+    Pt = torch.from_numpy(P).cuda()
+    torch.cuda.synchronize()          # device buffers are read and written on the library's stream
+    s.set_P(Pt)
+    out = torch.empty_like(Pt)
+    s.get_P(out)
+    torch.cuda.synchronize()
+    assert np.allclose(out.cpu().numpy(), P, rtol=2e-7, atol=1e-12)
+
+
+def test_launch_counter_counts_kernels(ctx):
+    s, _ = _bto(ctx, (8, 8, 8))
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    s.step(1, dt)
+    n0 = ctx.launch_count
+    s.step(10, dt)
+    assert ctx.launch_count - n0 == 10 * 4
