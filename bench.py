@@ -1,0 +1,340 @@
+"""Benchmark of the explicit TDGL step on one B300 (or N replicas under torchrun).
+
+Workload (default): the 128^3 BaTiO3 cube with 1 nm cells, seeded +-0.01 C/m^2 start, full
+Table 1 gradient coefficients, eps_B = 45, T = 300 K, dt* = 0.004, open-boundary electrostatics
+through a zero-padded 256^3 FFT convolution.  One bench step = one explicit TDGL step (Landau,
+gradient, electrostatic and applied field, forward Euler update, max|dP| reduction); the steps
+run as the relaxation driver does: a convergence check every 16 steps and the four energy terms
+(float64) recorded every 16 steps.  value = cell-updates/s over the timed region (inputs resident
+in HBM); e2e = the same metric through the C ABI with host buffers (P copied in from pinned host
+memory and the step's max|dP| read back, every step).
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "TDGL cell-updates/s (% HBM roofline); time-to-relax vs plain at equal tol"
+UNIT = "cell-updates/s"
+B_ALG_FUSED = 144.0   # bytes/cell/step of the fused two-pass design (algorithmic floor)
+CHECK_EVERY = 16
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ---- workload ---------------------------------------------------------------------------------
+def workload(name):
+    if name == "bto_cube_128":
+        c = synth.CONFIG2
+        shape = c["shape"]
+        nx, ny, nz = shape
+        return dict(name=name, shape=shape, cell=c["cell"], mat=np.ones((nz, ny, nx), np.uint8),
+                    mats={1: c["material"]}, T=300.0, eps_b=c["eps_b"], E=(0.0, 0.0, 0.0),
+                    P=synth.uniform_P(shape, c["amp"], c["seed"]), dt_star=c["dt_star"])
+    if name == "pto_sto_bilayer_256x256x64":
+        c = synth.CONFIG4
+        shape = c["shape"]
+        return dict(name=name, shape=shape, cell=c["cell"], mat=synth.layer_map(shape, c["layers"]),
+                    mats={1: synth.PTO, 2: synth.STO}, T=c["T"], eps_b=c["eps_b"], E=(0.0, 0.0, c["fields"][0]),
+                    P=synth.cylinder_start(shape, c["radius"], 0.7, c["amp"], c["seed"], z_range=(32, 64)),
+                    dt_star=0.004)
+    raise ValueError(name)
+
+
+def padded(n, even):
+    best = None
+    p2 = 1
+    while p2 < 1 << 20:
+        v = p2
+        while v < 1 << 20:
+            if v >= n and (not even or v % 2 == 0):
+                best = v if best is None else min(best, v)
+            v *= 3
+        p2 *= 2
+    return best
+
+
+def kernel_bytes(shape):
+    """Algorithmic bytes per launch of each kernel of one step ('Roofline')."""
+    nx, ny, nz = shape
+    Mx, My, Mz = padded(2 * nx - 1, True), padded(2 * ny - 1, False), padded(2 * nz - 1, False)
+    Kx = Mx // 2 + 1
+    ncell = nx * ny * nz
+    xs = 3 * Kx * ny * nz * 8          # x-spectrum, complex64, 3 components
+    ys = 3 * Kx * My * nz * 8          # y-padded spectrum
+    nhat = 6 * (Mz // 2 + 1) * (My // 2 + 1) * Kx * 4
+    return {
+        "k_rows<STEP>": 12 * ncell + ncell + xs + 12 * ncell + xs,
+        "k_yfwd": xs + ys,
+        "k_zconv": 2 * ys + nhat,
+        "k_yinv": ys + xs,
+    }, (Mx, My, Mz)
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    for f in ("fft.cuh", "kernels.cuh", "tdgl.cu"):
+        with open(os.path.join(ROOT, "paper_2605_28800_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, wl):
+    """DRAM bytes per launch from the committed ncu summary, or None when absent or stale."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            t = json.load(f)
+        rec = t[wl][kernel]
+        if rec.get("sources_sha") != kernel_sources_sha():
+            return None
+        return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ---- clocks during the timed region ------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        for line in out.strip().splitlines():
+            parts = [v.strip() for v in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ---- GPU arm -------------------------------------------------------------------------------------
+def make_sim(ctx, wl):
+    from paper_2605_28800_b300 import tdgl
+    s = tdgl.Sim(ctx, wl["shape"], wl["cell"])
+    for mid, rec in wl["mats"].items():
+        s.define_material(mid, rec)
+    s.set_material_map(wl["mat"])
+    s.set_temperature(wl["T"])
+    s.set_eps_b(wl["eps_b"])
+    s.set_field(wl["E"])
+    s.set_P(wl["P"])
+    P0, a = s.scales()
+    return s, wl["dt_star"] / a
+
+
+def run_steps(s, n, dt):
+    """n steps the way the relaxation driver runs them: check every 16, energies every 16."""
+    done = 0
+    while done < n:
+        k = min(CHECK_EVERY, n - done)
+        s.relax(dt, 1e-30, k, check_every=k, raise_on_cap=False)
+        s.energy()
+        done += k
+
+
+def gpu_arm(args, rank, world):
+    import torch
+    from paper_2605_28800_b300 import tdgl
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    ctx = tdgl.Context(dev, stream=stream.cuda_stream)
+    wl = workload(args.workload)
+    s, dt = make_sim(ctx, wl)
+    ncell = int(np.prod(wl["shape"]))
+    # warm-up (includes the one-off FP64 tensor build)
+    run_steps(s, max(args.warmup, 3), dt)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    for k in range(6):
+        ctx.profile_read(k)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        time.sleep(0.3)
+        e0.record(stream)
+        run_steps(s, args.steps, dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = ctx.launch_count - l0
+    prof = {tdgl.KERNEL_NAMES[k]: ctx.profile_read(k) for k in range(6)}
+    ctx.profile(False)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    # end to end through the C ABI with host buffers
+    Ph = torch.from_numpy(np.ascontiguousarray(wl["P"])).pin_memory()
+    e2e_steps = max(4, min(args.steps, 64))
+    s.set_P(Ph)
+    s.step(1, dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_P(Ph)
+        s.step(1, dt)       # returns after reading the step's max|dP| and divergence flag
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    return dict(ms=ms, launches=launches, prof=prof, clocks=clk.summary(), ncell=ncell, wl=wl,
+                e2e=ncell * e2e_steps / e2e_s * world, e2e_h2d=Ph.numel() * 4)
+
+
+# ---- CPU oracle ----------------------------------------------------------------------------------
+def oracle_time(wl, sample_steps):
+    from oracle import System, coefficients
+    o = System(wl["shape"], wl["cell"], wl["mat"], wl["mats"], wl["T"], wl["eps_b"], E_ext=wl["E"])
+    P = wl["P"].astype(np.float64)
+    a = abs(coefficients(list(wl["mats"].values())[0], 300.0)["a1x"])
+    dt = wl["dt_star"] / a
+    P = o.step(P, dt)            # builds the tensor and its spectrum (set-up, not timed)
+    t0 = time.perf_counter()
+    for _ in range(sample_steps):
+        P = o.step(P, dt)
+    el = time.perf_counter() - t0
+    ncell = int(np.prod(wl["shape"]))
+    return ncell * sample_steps / el, el
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=640)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bto_cube_128", choices=["bto_cube_128", "pto_sto_bilayer_256x256x64"])
+    ap.add_argument("--oracle-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    wl = workload(args.workload)
+    ncell = int(np.prod(wl["shape"]))
+    config = {"workload": args.workload, "grid": list(wl["shape"]), "cell_nm": [c * 1e9 for c in wl["cell"]],
+              "T_K": wl["T"], "eps_b": wl["eps_b"], "dt_star": wl["dt_star"], "check_every": CHECK_EVERY,
+              "energy_every": CHECK_EVERY, "global_batch": world, "parallelism": f"replicas{world}",
+              "l2": "working set > 126 MB L2 (no flush)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        v, el = oracle_time(wl, args.oracle_steps)
+        import multiprocessing
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.oracle_steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"{args.oracle_steps} FP64 oracle steps of the full grid "
+                                           f"(numpy, single thread; host has {multiprocessing.cpu_count()} cores)"},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    r = gpu_arm(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    hbm, peak_kind = peaks()
+    value = ncell * args.steps * world / (r["ms"] * 1e-3)
+    kb, M = kernel_bytes(wl["shape"])
+    prof = {k: v for k, v in r["prof"].items() if k in kb and v[1] > 0}
+    dom = max(prof, key=lambda k: prof[k][0]) if prof else None
+    total_prof = sum(v[0] for v in r["prof"].values()) or 1.0
+    roof = None
+    if dom:
+        avg_ms = prof[dom][0] / prof[dom][1]
+        ach = kb[dom] / (avg_ms * 1e-3) / 1e9
+        tr = ncu_traffic(dom, args.workload)
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "peak_kind": peak_kind, "traffic": tr, "alg_bytes_per_launch": kb[dom],
+                "avg_launch_ms": avg_ms}
+    kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / total_prof,
+                   "GBps": (kb[k] / (v[0] / v[1] * 1e-3) / 1e9) if (k in kb and v[1]) else None}
+               for k, v in r["prof"].items() if v[1]}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+            "hbm_frac_of_fused_floor": value / world * B_ALG_FUSED / (hbm * 1e9),
+            "fft_pad": list(M), "roofline": roof, "kernels": kernels, "clocks": r["clocks"],
+            "gpu_launches": r["launches"],
+            "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": r["e2e_h2d"], "d2h_bytes_per_step": 8}}
+    if world == 1 and not args.no_cpu_baseline:
+        import multiprocessing
+        v, el = oracle_time(wl, args.oracle_steps)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{args.oracle_steps} FP64 oracle steps of the full grid (numpy, "
+                                          f"single thread; host has {multiprocessing.cpu_count()} cores), {el:.1f} s"}
+    print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

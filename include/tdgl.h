@@ -83,7 +83,10 @@ typedef struct {
 /* ---- context --------------------------------------------------------------------------------
  * tdgl_ctx_create: bind to CUDA device `device` and to `stream` (a cudaStream_t, e.g.
  * torch.cuda.current_stream().cuda_stream; NULL = the library creates and owns a stream).
- * The caller keeps ownership of a stream it passes.  *out receives the context. */
+ * The caller keeps ownership of a stream it passes.  *out receives the context.
+ * tdgl_ctx_destroy also destroys the context's remaining batches and sims (their handles become
+ * invalid).  DEVICE-side results are ordered on the context's stream: synchronize it (or pass
+ * your own stream here) before reading them on another stream. */
 int  tdgl_ctx_create(tdgl_ctx **out, int device, void *stream);
 void tdgl_ctx_destroy(tdgl_ctx *ctx);
 /* last error message of the context (never NULL; "" when none); valid until the next call */
@@ -152,8 +155,8 @@ int tdgl_energy(tdgl_sim *sim, tdgl_energies *out);
 
 /* ---- batches (Sec. 3: many independent simulations run in parallel on one GPU) --------------
  * A batch groups n sims of one context (any sizes) so that each kernel of a step is one launch
- * over all of them.  The sims stay usable on their own; a sim may belong to one batch at a time
- * and must not be destroyed before its batch. */
+ * over all of them.  The sims stay usable on their own; a sim may belong to one batch at a time;
+ * destroying a sim removes it from its batch (per-sim arrays then follow the remaining order). */
 int  tdgl_batch_create(tdgl_ctx *ctx, int n, tdgl_sim *const *sims, tdgl_batch **out);
 void tdgl_batch_destroy(tdgl_batch *b);
 /* n steps of every sim; dt[i] (seconds) per sim. */

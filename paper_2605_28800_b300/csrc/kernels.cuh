@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(NTHREADS) k_rows(const SimDev *__restrict__ si
                 if (S.terms & TERM_GRAD) e_grad += gradient_energy(S, Pc, s_coef, x, y, z, m, p);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    if (elec) e_elec += -0.5 * (double)(Erow[(c * cnt + r) * 2 * ld + x] * S.escale) * p[c];
+                    if (elec) e_elec += -0.5 * (double)Erow[(c * cnt + r) * 2 * ld + x] * p[c];
                     if (S.terms & TERM_EXT) e_ext += -(double)S.eext[c] * p[c];
                 }
                 continue;
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(NTHREADS) k_rows(const SimDev *__restrict__ si
             if (S.terms & TERM_GRAD) gradient_field(S, Pc, s_coef, x, y, z, m, p, h);
             if (elec) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) h[c] = fmaf(Erow[(c * cnt + r) * 2 * ld + x], S.escale, h[c]);
+                for (int c = 0; c < 3; ++c) h[c] += Erow[(c * cnt + r) * 2 * ld + x];   // scaled in k_zconv
             }
             if (S.terms & TERM_EXT) {
 #pragma unroll

@@ -46,6 +46,8 @@ struct tdgl_ctx {
     std::vector<cudaEvent_t> pool;
     double prof_ms[TDGL_K_COUNT] = {0};
     long prof_n[TDGL_K_COUNT] = {0};
+    std::vector<tdgl_sim *> sims;       // owned: freed by tdgl_ctx_destroy if still alive
+    std::vector<tdgl_batch *> batches;
 };
 
 struct tdgl_sim {
@@ -606,6 +608,10 @@ void tdgl_ctx_destroy(tdgl_ctx *ctx) {
     if (!ctx) return;
     ctx_set(ctx);
     cudaStreamSynchronize(ctx->stream);
+    const std::vector<tdgl_batch *> bs = ctx->batches;
+    for (auto b : bs) tdgl_batch_destroy(b);
+    const std::vector<tdgl_sim *> ss = ctx->sims;
+    for (auto sm : ss) tdgl_sim_destroy(sm);
     for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -679,6 +685,7 @@ int tdgl_sim_create(tdgl_ctx *ctx, int nx, int ny, int nz, double dx, double dy,
         tdgl_sim_destroy(s);
         return rc;
     }
+    ctx->sims.push_back(s);
     *out = s;
     return TDGL_OK;
 }
@@ -687,6 +694,12 @@ void tdgl_sim_destroy(tdgl_sim *s) {
     if (!s) return;
     ctx_set(s->ctx);
     cudaStreamSynchronize(s->ctx->stream);
+    auto &v = s->ctx->sims;
+    v.erase(std::remove(v.begin(), v.end(), s), v.end());
+    if (s->batch) {   // leave the batch rather than dangle in it
+        auto &bv = s->batch->sims;
+        bv.erase(std::remove(bv.begin(), bv.end(), s), bv.end());
+    }
     void *ptrs[] = {s->dP[0], s->dP[1], s->dmat, s->dX, s->dY, s->dNhat, s->dtw, s->dcoef, s->dmaxdp,
                     s->dflag, s->denergy, s->dout, s->ddesc, s->d_rows, s->d_y, s->d_z};
     for (void *p : ptrs) cudaFree(p);
@@ -934,6 +947,7 @@ int tdgl_batch_create(tdgl_ctx *ctx, int n, tdgl_sim *const *sims, tdgl_batch **
         return fail(ctx, TDGL_ENOMEM, "batch descriptors");
     }
     for (auto s : b->sims) s->batch = b;
+    ctx->batches.push_back(b);
     *out = b;
     return TDGL_OK;
 }
@@ -943,6 +957,8 @@ void tdgl_batch_destroy(tdgl_batch *b) {
     ctx_set(b->ctx);
     cudaStreamSynchronize(b->ctx->stream);
     for (auto s : b->sims) s->batch = nullptr;
+    auto &v = b->ctx->batches;
+    v.erase(std::remove(v.begin(), v.end(), b), v.end());
     cudaFree(b->ddescs);
     cudaFree(b->d_items);
     delete b;

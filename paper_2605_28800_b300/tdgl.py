@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -124,6 +125,10 @@ class Context:
         if rc != OK:
             raise TdglError(rc, f"tdgl_ctx_create(device={device}) failed")
         self.h = h
+        self._children = weakref.WeakSet()
+
+    def _adopt(self, obj):
+        self._children.add(obj)
 
     def check(self, rc):
         if rc != OK:
@@ -143,7 +148,14 @@ class Context:
         return ms.value, n.value
 
     def close(self):
+        """Destroy the context; its batches and sims are closed first (their handles die with it)."""
         if getattr(self, "h", None):
+            kids = list(self._children)
+            for k in kids:
+                if isinstance(k, Batch):
+                    k.close()
+            for k in kids:
+                k.close()
             self.lib.tdgl_ctx_destroy(self.h)
             self.h = None
 
@@ -165,6 +177,7 @@ class Sim:
         ctx.check(self.lib.tdgl_sim_create(ctx.h, nx, ny, nz, *map(float, cell), ctypes.byref(h)))
         self.h = h
         self.ncell = nx * ny * nz
+        ctx._adopt(self)
 
     def _c(self, rc):
         return self.ctx.check(rc)
@@ -199,7 +212,7 @@ class Sim:
     def set_P(self, P):
         if isinstance(P, np.ndarray):
             P = np.ascontiguousarray(P, dtype=np.float32)
-        if P.size != 3 * self.ncell:
+        if (P.numel() if hasattr(P, "numel") else P.size) != 3 * self.ncell:
             raise ValueError("P must have 3*nx*ny*nz elements")
         p, where = _ptr(P)
         self._c(self.lib.tdgl_set_P(self.h, p, where))
@@ -246,7 +259,8 @@ class Sim:
 
     def close(self):
         if getattr(self, "h", None):
-            self.lib.tdgl_sim_destroy(self.h)
+            if getattr(self.ctx, "h", None):      # a destroyed context already freed its sims
+                self.lib.tdgl_sim_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -265,6 +279,7 @@ class Batch:
         h = _VP()
         ctx.check(self.lib.tdgl_batch_create(ctx.h, len(self.sims), arr, ctypes.byref(h)))
         self.h = h
+        ctx._adopt(self)
 
     def _dts(self, dt):
         dts = [float(dt)] * len(self.sims) if np.isscalar(dt) else [float(v) for v in dt]
@@ -282,7 +297,8 @@ class Batch:
 
     def close(self):
         if getattr(self, "h", None):
-            self.lib.tdgl_batch_destroy(self.h)
+            if getattr(self.ctx, "h", None):
+                self.lib.tdgl_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
