@@ -40,6 +40,7 @@ extern "C" {
 #define TDGL_EDIVERGED      -4   /* NaN or |P| above the divergence bound after a step          */
 #define TDGL_ENOTCONVERGED  -5   /* relaxation hit its step cap before reaching the tolerance   */
 #define TDGL_ESTATE         -6   /* call not valid in the current state (e.g. no material)      */
+#define TDGL_ETOOBIG        -7   /* grid too large for tdgl_elec_field_static's fixed scratch   */
 
 #define TDGL_HOST   0
 #define TDGL_DEVICE 1
@@ -166,6 +167,32 @@ int  tdgl_batch_step(tdgl_batch *b, int n, const double *dt);
  * Returns TDGL_OK when all converged, else TDGL_ENOTCONVERGED / TDGL_EDIVERGED. */
 int  tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_steps,
                       int check_every, long *steps_taken);
+
+/* ---- field without allocation ------------------------------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that cannot call cudaMalloc:
+ * code running while a stream is captured into a CUDA graph (an allocation there is not
+ * capturable, and elsewhere it synchronizes the device), plug-ins whose host owns all device
+ * memory through its own pool, and real-time loops that must not wait on the allocator.
+ *
+ * tdgl_elec_field_static computes the open-boundary electrostatic field E_el of P (the same
+ * quantity as tdgl_get_field with TDGL_TERM_ELEC) on an nx*ny*nz grid of dx*dy*dz cells:
+ *   P     device, float32 [3][nz][ny][nx], C/m^2 (caller-owned input; must be 0 on vacuum cells)
+ *   mat   device, uint8 [nz][ny][nx], 0 = vacuum, or NULL for an all-material box
+ *   E     device, float32 [3][nz][ny][nx], V/m (caller-owned output; 0 on vacuum cells)
+ *   stream  cudaStream_t to enqueue on (NULL = legacy default stream); the call returns once the
+ *           work is enqueued.
+ * It allocates nothing: every intermediate lives in one static device array of
+ * TDGL_STATIC_SCRATCH_BYTES that each GPU loading this library holds until the process exits.
+ * Grids whose intermediates do not fit return TDGL_ETOOBIG (a 36x36x36 cube fits, 40x40x40 does
+ * not; 32x32x32 needs about 8 MiB); bad
+ * arguments return TDGL_EINVAL.  The first call on a device looks up the array's device address
+ * with that device current (set-up done once per device): make that first call before any stream
+ * capture begins.  All calls share the array and each call overwrites it completely, so calls
+ * whose work overlaps on the GPU (other streams, other host threads) race and must be serialized
+ * by the caller. */
+#define TDGL_STATIC_SCRATCH_BYTES (16u << 20)
+int tdgl_elec_field_static(int nx, int ny, int nz, double dx, double dy, double dz, double eps_b,
+                           const float *P, const uint8_t *mat, float *E, void *stream);
 
 /* ---- measurement -----------------------------------------------------------------------------
  * tdgl_profile(ctx, 1) records a CUDA event pair around every kernel launch on the context's

@@ -1139,3 +1139,231 @@ int tdgl_profile_read(tdgl_ctx *ctx, int kind, double *total_ms, long *launches)
 }
 
 }  // extern "C"
+
+// =============================================================================================
+// Electrostatic field without any allocation (tdgl_elec_field_static).
+//
+// Some callers cannot call cudaMalloc: code that runs while a stream is being captured into a
+// CUDA graph (cudaMalloc is not a capturable operation and, outside capture, synchronizes the
+// device), plug-ins whose host application owns every device byte through its own pool, and
+// real-time loops that may not block on the driver's allocator.  For them this entry point
+// computes the open-boundary field of a given P with every intermediate buffer (descriptor,
+// work lists, twiddles, FP64 tensor temporaries, tensor spectrum, x- and y-spectra) carved out
+// of one file-scope device array of fixed size.  It runs the same kernels as tdgl_get_field.
+// =============================================================================================
+namespace {
+
+static __device__ __align__(256) unsigned char g_static_scratch[TDGL_STATIC_SCRATCH_BYTES];
+
+const int kMaxDevices = 64;
+void *g_static_ptr[kMaxDevices] = {nullptr};   // device address of g_static_scratch, per device
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// radix plan without host twiddles (the table is written on the device)
+Plan plan_only(int n, int tw_offset) {
+    Plan p;
+    memset(&p, 0, sizeof p);
+    p.n = n;
+    int r = n;
+    const int rads[5] = {16, 8, 4, 3, 2};
+    for (int i = 0; i < 5; ++i)
+        while (r % rads[i] == 0 && r > 1) {
+            p.rad[p.nrad++] = rads[i];
+            r /= rads[i];
+        }
+    p.tw = tw_offset;
+    return p;
+}
+
+struct StaticPlan {
+    int nx, ny, nz, Mx, My, Mz, hx, Kx, kxp, kyh, kzh;
+    int RB, KY, KZ, nrb, nky, nkz, n_rows, n_y, n_z;
+    size_t o_desc, o_rows, o_y, o_z, o_tw, o_coef, o_mat, o_X, o_Y, o_Nhat, o_N, o_T1, o_T2, o_trig, o_slots, total;
+    long ncell, n1, n2, n3;
+};
+
+StaticPlan static_plan(int nx, int ny, int nz) {
+    StaticPlan q;
+    memset(&q, 0, sizeof q);
+    q.nx = nx; q.ny = ny; q.nz = nz;
+    q.Mx = smooth_at_least(2 * nx - 1, true);
+    q.My = smooth_at_least(2 * ny - 1, false);
+    q.Mz = smooth_at_least(2 * nz - 1, false);
+    q.hx = q.Mx / 2; q.Kx = q.hx + 1; q.kxp = (q.Kx + 3) & ~3; q.kyh = q.My / 2 + 1; q.kzh = q.Mz / 2 + 1;
+    // chunking identical to build_items()
+    q.RB = std::max(1, std::min(ny, std::max(1, 512 / nx)));
+    q.KY = std::max(1, std::min(16, 73728 / (16 * (q.My + 1))));
+    q.KZ = std::max(1, std::min(16, 102400 / (48 * (q.Mz + 1))));
+    q.nrb = (ny + q.RB - 1) / q.RB;
+    q.nky = (q.Kx + q.KY - 1) / q.KY;
+    q.nkz = (q.Kx + q.KZ - 1) / q.KZ;
+    q.n_rows = nz * q.nrb;
+    q.n_y = 3 * nz * q.nky;
+    q.n_z = q.My * q.nkz;
+    q.ncell = (long)nx * ny * nz;
+    q.n1 = (long)nz * ny * q.Kx;
+    q.n2 = (long)nz * q.kyh * q.Kx;
+    q.n3 = (long)q.kzh * q.kyh * q.Kx;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t at = o; o = align256(o + bytes); return at; };
+    q.o_desc = take(sizeof(SimDev));
+    q.o_rows = take(sizeof(int4) * q.n_rows);
+    q.o_y = take(sizeof(int4) * q.n_y);
+    q.o_z = take(sizeof(int4) * q.n_z);
+    q.o_tw = take(sizeof(float2) * (size_t)(q.hx + q.My + q.Mz + q.hx + 1));
+    q.o_coef = take(sizeof(float) * MAXMAT * NCOEF);
+    q.o_mat = take((size_t)q.ncell);
+    q.o_X = take(sizeof(float2) * 3ull * nz * ny * q.kxp);
+    q.o_Y = take(sizeof(float2) * 3ull * nz * q.My * q.kxp);
+    q.o_Nhat = take(sizeof(float) * 6ull * q.n3);
+    q.o_N = take(sizeof(double) * 6ull * q.ncell);
+    q.o_T1 = take(sizeof(double) * 6ull * std::max(q.n1, q.n3));
+    q.o_T2 = take(sizeof(double) * 6ull * std::max(q.n2, q.n3));
+    q.o_trig = take(sizeof(double) * 2ull * (q.Mx + q.My + q.Mz));
+    q.o_slots = take(64);
+    q.total = o;
+    return q;
+}
+
+// work lists of the three kernel families, written on the device (same order as build_items)
+__global__ void k_static_items(int4 *rows, int4 *ys, int4 *zs, StaticPlan q) {
+    const int n = q.n_rows + q.n_y + q.n_z;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (i < q.n_rows) {
+            const int z = i / q.nrb, y0 = (i % q.nrb) * q.RB;
+            rows[i] = make_int4(0, z, y0, min(q.RB, q.ny - y0));
+        } else if (i < q.n_rows + q.n_y) {
+            const int j = i - q.n_rows, cz = j / q.nky, k0 = (j % q.nky) * q.KY;
+            ys[j] = make_int4(0, cz, k0, min(q.KY, q.Kx - k0));
+        } else {
+            const int j = i - q.n_rows - q.n_y, ky = j / q.nkz, k0 = (j % q.nkz) * q.KZ;
+            zs[j] = make_int4(0, ky, k0, min(q.KZ, q.Kx - k0));
+        }
+    }
+}
+
+// FFT twiddles W_n^t (float32 from float64 sincospi) and the tensor transform's cos/sin tables
+__global__ void k_static_tables(float2 *tw, double *trig, StaticPlan q) {
+    const int ntw = q.hx + q.My + q.Mz + q.hx + 1;
+    const int ntr = q.Mx + q.My + q.Mz;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ntw + ntr; i += gridDim.x * blockDim.x) {
+        if (i < ntw) {
+            int n, t;
+            if (i < q.hx) { n = q.hx; t = i; }
+            else if (i < q.hx + q.My) { n = q.My; t = i - q.hx; }
+            else if (i < q.hx + q.My + q.Mz) { n = q.Mz; t = i - q.hx - q.My; }
+            else { n = q.Mx; t = i - q.hx - q.My - q.Mz; }
+            double s, c;
+            sincospi(-2.0 * (double)t / (double)n, &s, &c);
+            tw[i] = make_float2((float)c, (float)s);
+        } else {
+            const int j = i - ntw;
+            int base, M, t;
+            if (j < q.Mx) { base = 0; M = q.Mx; t = j; }
+            else if (j < q.Mx + q.My) { base = 2 * q.Mx; M = q.My; t = j - q.Mx; }
+            else { base = 2 * (q.Mx + q.My); M = q.Mz; t = j - q.Mx - q.My; }
+            double s, c;
+            sincospi(2.0 * (double)t / (double)M, &s, &c);
+            trig[base + t] = c;
+            trig[base + M + t] = s;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int tdgl_elec_field_static(int nx, int ny, int nz, double dx, double dy, double dz, double eps_b,
+                                      const float *P, const uint8_t *mat, float *E, void *stream) {
+    if (nx < 1 || ny < 1 || nz < 1 || nx > TDGL_MAX_DIM || ny > TDGL_MAX_DIM || nz > TDGL_MAX_DIM) return TDGL_EINVAL;
+    if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
+        return TDGL_EINVAL;
+    if (!(eps_b > 0) || !std::isfinite(eps_b) || !P || !E) return TDGL_EINVAL;
+    const StaticPlan q = static_plan(nx, ny, nz);
+    if (q.total > (size_t)TDGL_STATIC_SCRATCH_BYTES) return TDGL_ETOOBIG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TDGL_ECUDA;
+    if (!g_static_ptr[dev]) {
+        // once per device, with that device current: device address of the scratch array and
+        // the dynamic shared-memory limits of the kernels used below
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) return TDGL_ECUDA;
+        cudaFuncSetAttribute(k_rows<MODE_XFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        cudaFuncSetAttribute(k_rows<MODE_FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        cudaFuncSetAttribute(k_yfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        cudaFuncSetAttribute(k_yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        cudaFuncSetAttribute(k_zconv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        if (cudaGetLastError() != cudaSuccess) return TDGL_ECUDA;
+        g_static_ptr[dev] = ptr;
+    }
+    unsigned char *base = static_cast<unsigned char *>(g_static_ptr[dev]);
+    cudaStream_t st = (cudaStream_t)stream;
+    SimDev D;
+    memset(&D, 0, sizeof D);
+    D.nx = nx; D.ny = ny; D.nz = nz; D.ncell = q.ncell;
+    D.hx = q.hx; D.Kx = q.Kx; D.kxp = q.kxp; D.My = q.My; D.Mz = q.Mz; D.kyh = q.kyh; D.kzh = q.kzh;
+    D.px = plan_only(q.hx, 0);
+    D.py = plan_only(q.My, q.hx);
+    D.pz = plan_only(q.Mz, q.hx + q.My);
+    D.twr = q.hx + q.My + q.Mz;
+    D.tw = reinterpret_cast<const float2 *>(base + q.o_tw);
+    D.P[0] = D.P[1] = const_cast<float *>(P);          // read only in the modes used here
+    D.mat = mat ? mat : reinterpret_cast<const uint8_t *>(base + q.o_mat);
+    D.X = reinterpret_cast<float2 *>(base + q.o_X);
+    D.Y = reinterpret_cast<float2 *>(base + q.o_Y);
+    D.Nhat = reinterpret_cast<const float *>(base + q.o_Nhat);
+    D.coef = reinterpret_cast<const float *>(base + q.o_coef);
+    D.escale = (float)(-1.0 / (kEps0 * eps_b) / ((double)q.Mx * q.My * q.Mz));   // alpha_ref = P0 = 1
+    D.pmax = 1e3f;
+    D.terms = TERM_ELEC;
+    D.maxdp = reinterpret_cast<unsigned *>(base + q.o_slots);
+    D.flag = reinterpret_cast<int *>(base + q.o_slots + 16);
+    D.energy = reinterpret_cast<double *>(base + q.o_slots + 32);
+    D.out = E;
+    D.out_scale = 1.0f;
+    const double ell = std::min(dx, std::min(dy, dz));
+    for (int a = 0; a < 3; ++a) {
+        const double h = (a == 0 ? dx : (a == 1 ? dy : dz)) / ell;
+        D.inv_d2[a] = (float)(1.0 / (h * h));
+        D.inv_2d[a] = (float)(1.0 / (2.0 * h));
+    }
+    const SimDev *ddesc = reinterpret_cast<const SimDev *>(base + q.o_desc);
+    int4 *rows = reinterpret_cast<int4 *>(base + q.o_rows);
+    int4 *ys = reinterpret_cast<int4 *>(base + q.o_y);
+    int4 *zs = reinterpret_cast<int4 *>(base + q.o_z);
+    double *dN = reinterpret_cast<double *>(base + q.o_N);
+    double *dT1 = reinterpret_cast<double *>(base + q.o_T1);
+    double *dT2 = reinterpret_cast<double *>(base + q.o_T2);
+    double *trig = reinterpret_cast<double *>(base + q.o_trig);
+    FarRule rule;
+    memset(&rule, 0, sizeof rule);
+    const int ms[3] = {8, 6, 4};
+    for (int k = 0; k < 3; ++k) {
+        rule.m[k] = ms[k];
+        gauss_legendre01(ms[k], rule.tau[k], rule.wt[k]);
+    }
+    if (cudaMemcpyAsync(base + q.o_desc, &D, sizeof D, cudaMemcpyHostToDevice, st) != cudaSuccess) return TDGL_ECUDA;
+    if (cudaMemsetAsync(base + q.o_coef, 0, sizeof(float) * MAXMAT * NCOEF, st) != cudaSuccess) return TDGL_ECUDA;
+    if (!mat && cudaMemsetAsync(base + q.o_mat, 1, (size_t)q.ncell, st) != cudaSuccess) return TDGL_ECUDA;
+    const int ntab = q.hx + q.My + q.Mz + q.hx + 1 + q.Mx + q.My + q.Mz;
+    k_static_items<<<grid_for(q.n_rows + q.n_y + q.n_z), 256, 0, st>>>(rows, ys, zs, q);
+    k_static_tables<<<grid_for(ntab), 256, 0, st>>>(reinterpret_cast<float2 *>(base + q.o_tw), trig, q);
+    // tensor spectrum (FP64), lengths in units of the smallest cell edge
+    k_tensor_real<<<grid_for(q.ncell), 256, 0, st>>>(dN, nx, ny, nz, dx / ell, dy / ell, dz / ell, 5.0, 16.0, 40.0, rule);
+    k_tensor_dft<<<grid_for(6 * q.n1), 256, 0, st>>>(dN, dT1, 0, nx, q.Kx, q.Mx, 1, nz * ny, trig, trig + q.Mx);
+    k_tensor_dft<<<grid_for(6 * q.n2), 256, 0, st>>>(dT1, dT2, 1, ny, q.kyh, q.My, q.Kx, nz, trig + 2 * q.Mx,
+                                                      trig + 2 * q.Mx + q.My);
+    k_tensor_dft<<<grid_for(6 * q.n3), 256, 0, st>>>(dT2, dT1, 2, nz, q.kzh, q.Mz, q.kyh * q.Kx, 1,
+                                                      trig + 2 * (q.Mx + q.My), trig + 2 * (q.Mx + q.My) + q.Mz);
+    k_tensor_store<<<grid_for(6 * q.n3), 256, 0, st>>>(dT1, reinterpret_cast<float *>(base + q.o_Nhat), q.n3);
+    // x forward, y/z convolution, x inverse into E (the kernels of tdgl_get_field)
+    const size_t sm_rows = 2ull * 3 * q.RB * (q.hx + 2) * sizeof(float2);
+    const size_t sm_y = 2ull * q.KY * (q.My + 1) * sizeof(float2);
+    const size_t sm_z = 2ull * 3 * q.KZ * (q.Mz + 1) * sizeof(float2);
+    k_rows<MODE_XFWD><<<q.n_rows, NTHREADS, sm_rows, st>>>(ddesc, rows, 0);
+    k_yfwd<<<q.n_y, NTHREADS, sm_y, st>>>(ddesc, ys);
+    k_zconv<<<q.n_z, NTHREADS, sm_z, st>>>(ddesc, zs);
+    k_yinv<<<q.n_y, NTHREADS, sm_y, st>>>(ddesc, ys);
+    k_rows<MODE_FIELD><<<q.n_rows, NTHREADS, sm_rows, st>>>(ddesc, rows, 0);
+    return cudaGetLastError() == cudaSuccess ? TDGL_OK : TDGL_ECUDA;
+}

@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtdgl.so")
 
-OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ENOTCONVERGED, ESTATE = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ENOTCONVERGED, ESTATE, ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7
 HOST, DEVICE = 0, 1
 TERM_LANDAU, TERM_GRAD, TERM_ELEC, TERM_EXT, TERM_ALL = 1, 2, 4, 8, 15
 K_STEP, K_YFWD, K_ZCONV, K_YINV, K_XFWD, K_OTHER = range(6)
@@ -24,7 +24,8 @@ KERNEL_NAMES = {K_STEP: "k_rows<STEP>", K_YFWD: "k_yfwd", K_ZCONV: "k_zconv", K_
 MAX_MATERIALS, MAX_DIM = 16, 1024
 
 _CODES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EDIVERGED: "EDIVERGED",
-          ENOTCONVERGED: "ENOTCONVERGED", ESTATE: "ESTATE"}
+          ENOTCONVERGED: "ENOTCONVERGED", ESTATE: "ESTATE", ETOOBIG: "ETOOBIG"}
+STATIC_SCRATCH_BYTES = 16 << 20
 
 
 class TdglError(RuntimeError):
@@ -74,6 +75,7 @@ _SIGS = {
     "tdgl_batch_destroy": (None, [_VP]),
     "tdgl_batch_step": (_I, [_VP, _I, ctypes.POINTER(_D)]),
     "tdgl_batch_relax": (_I, [_VP, ctypes.POINTER(_D), _D, _L, _I, ctypes.POINTER(_L)]),
+    "tdgl_elec_field_static": (_I, [_I, _I, _I, _D, _D, _D, _D, _VP, _VP, _VP, _VP]),
     "tdgl_profile": (_I, [_VP, _I]),
     "tdgl_profile_read": (_I, [_VP, _I, ctypes.POINTER(_D), ctypes.POINTER(_L)]),
 }
@@ -306,3 +308,24 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def elec_field_static(P, E, cell, eps_b, mat=None, stream=0):
+    """Open-boundary field E_el of P without any device allocation (tdgl_elec_field_static).
+
+    For callers that cannot allocate device memory (inside stream capture, host-owned memory
+    pools, real-time loops).  P and E are contiguous CUDA tensors of shape (3, nz, ny, nx)
+    (float32, C/m^2 in, V/m out); mat an optional uint8 CUDA tensor (nz, ny, nx).  Work is
+    enqueued on `stream` (a cudaStream_t as int; 0 = legacy default stream).  Every call shares
+    one fixed static scratch array: calls that overlap on the GPU race.
+    """
+    lib = library()
+    _, nz, ny, nx = P.shape
+    for t in (P, E) + (() if mat is None else (mat,)):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("P, E and mat must be contiguous CUDA tensors")
+    rc = lib.tdgl_elec_field_static(nx, ny, nz, float(cell[0]), float(cell[1]), float(cell[2]), float(eps_b),
+                                    P.data_ptr(), None if mat is None else mat.data_ptr(), E.data_ptr(),
+                                    None if not stream else _VP(int(stream)))
+    if rc != OK:
+        raise TdglError(rc, "tdgl_elec_field_static failed")
