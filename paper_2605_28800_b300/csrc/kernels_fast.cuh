@@ -1,0 +1,129 @@
+// Length-specialized y and z passes of the zero-padded convolution (Eqs. 5-6), built on the
+// register FFT of fft_reg.cuh.  Thread (t, l) of a block owns position t of line l (kx0 + l):
+// for every register the 16 (or 8) lanes of a half-warp touch consecutive kx of one row, so all
+// global loads and stores are full 64/128-byte segments and every shared-memory exchange
+// (layout [pos][l]) is conflict-free.
+#pragma once
+#include "fft_reg.cuh"
+#include "kernels.cuh"
+
+namespace tdgl {
+
+template <int N> __host__ __device__ constexpr int lines_per_block() {
+    return (256 / rf::threads_per_line<N>()) < 16 ? (256 / rf::threads_per_line<N>()) : 16;
+}
+template <int N> __host__ __device__ constexpr int zlines_per_block() {
+    return (128 / rf::threads_per_line<N>()) < 16 ? (128 / rf::threads_per_line<N>()) : 16;
+}
+
+// y transform of the x-spectrum: forward (ny -> My, zero padded) or inverse (My -> first ny)
+template <int N, bool INV>
+__global__ void __launch_bounds__(256) k_ypass(const SimDev *__restrict__ sims, const int4 *__restrict__ items) {
+    constexpr int E = rf::Cfg<N>::E, T = N / E, KX = lines_per_block<N>();
+    __shared__ float2 S[N * KX];
+    __shared__ float2 tw[N];
+    const int4 it = items[blockIdx.x];
+    const SimDev &D = sims[it.x];
+    const int cz = it.y, kx0 = it.z, cnt = it.w;
+    const int l = threadIdx.x % KX, t = threadIdx.x / KX;
+    const bool ok = l < cnt;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = D.tw[D.py.tw + i];
+    const int ny = D.ny, kxp = D.kxp;
+    float2 v[E];
+    if (!INV) {
+        const float2 *src = D.X + (long)cz * ny * kxp + kx0 + l;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int y = t + T * m;
+            v[m] = (ok && y < ny) ? src[(long)y * kxp] : make_float2(0.f, 0.f);
+        }
+    } else {
+        const float2 *src = D.Y + (long)cz * N * kxp + kx0 + l;
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = ok ? src[(long)(t + T * m) * kxp] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    rf::fft<N, INV>(v, t, S, [&](int pos) { return pos * KX + l; }, tw);
+    if (!ok) return;
+    if (!INV) {
+        float2 *dst = D.Y + (long)cz * N * kxp + kx0 + l;
+#pragma unroll
+        for (int i = 0; i < E; ++i) dst[(long)rf::final_pos<N>(t, i) * kxp] = v[i];
+    } else {
+        float2 *dst = D.X + (long)cz * ny * kxp + kx0 + l;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int y = rf::final_pos<N>(t, i);
+            if (y < ny) dst[(long)y * kxp] = v[i];
+        }
+    }
+}
+
+// z transform, per-k 3x3 tensor multiply, inverse z transform (first nz outputs kept)
+template <int N>
+__global__ void __launch_bounds__(128) k_zpass(const SimDev *__restrict__ sims, const int4 *__restrict__ items) {
+    constexpr int E = rf::Cfg<N>::E, T = N / E, KX = zlines_per_block<N>();
+    __shared__ float2 S[N * KX];
+    __shared__ float2 tw[N];
+    const int4 it = items[blockIdx.x];
+    const SimDev &D = sims[it.x];
+    const int ky = it.y, kx0 = it.z, cnt = it.w;
+    const int l = threadIdx.x % KX, t = threadIdx.x / KX;
+    const bool ok = l < cnt;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = D.tw[D.pz.tw + i];
+    const int nz = D.nz, My = D.My, kxp = D.kxp;
+    const long zs = (long)My * kxp, cs = (long)nz * zs;
+    const float2 *src = D.Y + (long)ky * kxp + kx0 + l;
+    float2 a[3][E];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int z = t + T * m;
+            a[c][m] = (ok && z < nz) ? src[c * cs + z * zs] : make_float2(0.f, 0.f);
+        }
+    __syncthreads();
+    auto idx = [&](int pos) { return pos * KX + l; };
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rf::fft<N, false>(a[c], t, S, idx, tw);
+    // E-hat(k) = escale * N-hat(k) P-hat(k); N-hat from the reduced table with reflection signs
+    const int kyr = (ky <= My / 2) ? ky : My - ky;
+    const float sy = (ky <= My / 2) ? 1.f : -1.f;
+    const long ns = (long)D.kzh * D.kyh * D.Kx;
+    const float es = D.escale;
+    const float *Nb = D.Nhat + (long)kyr * D.Kx + kx0 + l;
+    const long rowN = (long)D.kyh * D.Kx;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int kz = rf::final_pos<N>(t, i);
+        const int kzr = (kz <= N / 2) ? kz : N - kz;
+        const float sz = (kz <= N / 2) ? 1.f : -1.f;
+        const float *Np = Nb + kzr * rowN;
+        float nxx = 0.f, nyy = 0.f, nzz = 0.f, nxy = 0.f, nxz = 0.f, nyz = 0.f;
+        if (ok) {
+            nxx = __ldg(Np); nyy = __ldg(Np + ns); nzz = __ldg(Np + 2 * ns);
+            nxy = sy * __ldg(Np + 3 * ns); nxz = sz * __ldg(Np + 4 * ns); nyz = sy * sz * __ldg(Np + 5 * ns);
+        }
+        const float2 px = a[0][i], py = a[1][i], pz = a[2][i];
+        a[0][i] = make_float2(es * (nxx * px.x + nxy * py.x + nxz * pz.x), es * (nxx * px.y + nxy * py.y + nxz * pz.y));
+        a[1][i] = make_float2(es * (nxy * px.x + nyy * py.x + nyz * pz.x), es * (nxy * px.y + nyy * py.y + nyz * pz.y));
+        a[2][i] = make_float2(es * (nxz * px.x + nyz * py.x + nzz * pz.x), es * (nxz * px.y + nyz * py.y + nzz * pz.y));
+    }
+    float2 *dst = D.Y + (long)ky * kxp + kx0 + l;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = a[c][rf::final_reg<N>(m)];
+        rf::fft<N, true>(v, t, S, idx, tw);
+        if (ok) {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int z = rf::final_pos<N>(t, i);
+                if (z < nz) dst[c * cs + z * zs] = v[i];
+            }
+        }
+    }
+}
+
+}  // namespace tdgl

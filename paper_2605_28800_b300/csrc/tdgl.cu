@@ -17,6 +17,7 @@
 
 #include "../../include/tdgl.h"
 #include "kernels.cuh"
+#include "kernels_fast.cuh"
 #include "tensor.cuh"
 
 using namespace tdgl;
@@ -82,6 +83,7 @@ struct tdgl_sim {
     // work items
     std::vector<int4> it_rows, it_y, it_z;
     int rows_cnt_max = 1, ky_cnt_max = 1, kz_cnt_max = 1;
+    int yN = 0, zN = 0;   // specialized y / z transform length (0 = generic kernels)
     int4 *d_rows = nullptr, *d_y = nullptr, *d_z = nullptr;
     int cur = 0;
     int xstate = XS_NONE;
@@ -227,6 +229,14 @@ int launch(tdgl_ctx *ctx, int kind, F f) {
 int grid_for(long n) { return (int)std::min<long>(std::max<long>((n + 255) / 256, 1), 148L * 16); }
 
 // -- geometry and plans ------------------------------------------------------------------------
+// lengths with a register-FFT specialization (fft_reg.cuh) and its geometry
+bool fast_len(int n) {
+    return n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 512 || n == 48 || n == 96 || n == 192;
+}
+int fast_tpl(int n) { return n / (n == 48 ? 12 : ((n == 96 || n == 192) ? 24 : 16)); }   // threads per line
+int fast_ylines(int n) { return std::min(256 / fast_tpl(n), 16); }
+int fast_zlines(int n) { return std::min(128 / fast_tpl(n), 16); }
+
 void build_items(tdgl_sim *s) {
     s->it_rows.clear();
     s->it_y.clear();
@@ -235,15 +245,23 @@ void build_items(tdgl_sim *s) {
     s->rows_cnt_max = RB;
     for (int z = 0; z < s->nz; ++z)
         for (int y0 = 0; y0 < s->ny; y0 += RB) s->it_rows.push_back(make_int4(0, z, y0, std::min(RB, s->ny - y0)));
-    const int ky = std::max(1, std::min(16, 73728 / (16 * (s->My + 1))));
+    s->yN = fast_len(s->My) ? s->My : 0;
+    s->zN = fast_len(s->Mz) ? s->Mz : 0;
+    const int ky = s->yN ? fast_ylines(s->My) : std::max(1, std::min(16, 73728 / (16 * (s->My + 1))));
     s->ky_cnt_max = ky;
     for (int c = 0; c < 3; ++c)
         for (int z = 0; z < s->nz; ++z)
             for (int k0 = 0; k0 < s->Kx; k0 += ky)
                 s->it_y.push_back(make_int4(0, c * s->nz + z, k0, std::min(ky, s->Kx - k0)));
-    const int kz = std::max(1, std::min(16, 102400 / (48 * (s->Mz + 1))));
+    const int kz = s->zN ? fast_zlines(s->Mz) : std::max(1, std::min(16, 102400 / (48 * (s->Mz + 1))));
     s->kz_cnt_max = kz;
-    for (int k = 0; k < s->My; ++k)
+    // rows ky and My - ky read the same tensor row: issue them back to back so the second read hits L2
+    std::vector<int> order;
+    for (int k = 0; k <= s->My / 2; ++k) {
+        order.push_back(k);
+        if (k != 0 && s->My - k != k) order.push_back(s->My - k);
+    }
+    for (int k : order)
         for (int k0 = 0; k0 < s->Kx; k0 += kz) s->it_z.push_back(make_int4(0, k, k0, std::min(kz, s->Kx - k0)));
 }
 
@@ -459,11 +477,19 @@ int upload_desc(tdgl_sim *s) {
 }
 
 // -- kernel sequences (over a descriptor table and item lists) ---------------------------------------
+struct Group {
+    int N;              // specialized transform length, 0 = generic kernel
+    const int4 *items;
+    int n;
+    size_t smem;        // dynamic shared memory (generic kernels only)
+};
+
 struct Work {
     const SimDev *descs;
-    const int4 *rows, *y, *z;
-    int n_rows, n_y, n_z;
-    size_t sm_rows, sm_y, sm_z;
+    const int4 *rows;
+    int n_rows;
+    size_t sm_rows;
+    std::vector<Group> yg, zg;
 };
 
 int launch_rows(tdgl_ctx *ctx, int mode, const Work &w, int parity) {
@@ -479,24 +505,53 @@ int launch_rows(tdgl_ctx *ctx, int mode, const Work &w, int parity) {
     });
 }
 
+#define TDGL_FAST_LENGTHS(X) X(16) X(32) X(64) X(128) X(256) X(512) X(48) X(96) X(192)
+
+template <bool INV>
+void ypass(const Group &g, const SimDev *d, cudaStream_t st) {
+    if (g.N == 0) {
+        if (INV) k_yinv<<<g.n, NTHREADS, g.smem, st>>>(d, g.items);
+        else k_yfwd<<<g.n, NTHREADS, g.smem, st>>>(d, g.items);
+        return;
+    }
+    switch (g.N) {
+#define TDGL_Y(LEN) \
+    case LEN: k_ypass<LEN, INV><<<g.n, rf::threads_per_line<LEN>() * lines_per_block<LEN>(), 0, st>>>(d, g.items); break;
+        TDGL_FAST_LENGTHS(TDGL_Y)
+#undef TDGL_Y
+    }
+}
+
+void zpass(const Group &g, const SimDev *d, cudaStream_t st) {
+    if (g.N == 0) {
+        k_zconv<<<g.n, NTHREADS, g.smem, st>>>(d, g.items);
+        return;
+    }
+    switch (g.N) {
+#define TDGL_Z(LEN) \
+    case LEN: k_zpass<LEN><<<g.n, rf::threads_per_line<LEN>() * zlines_per_block<LEN>(), 0, st>>>(d, g.items); break;
+        TDGL_FAST_LENGTHS(TDGL_Z)
+#undef TDGL_Z
+    }
+}
+
 int launch_conv(tdgl_ctx *ctx, const Work &w) {
-    if (w.n_y == 0) return TDGL_OK;
-    TRY(launch(ctx, TDGL_K_YFWD, [&] { k_yfwd<<<w.n_y, NTHREADS, w.sm_y, ctx->stream>>>(w.descs, w.y); }));
-    TRY(launch(ctx, TDGL_K_ZCONV, [&] { k_zconv<<<w.n_z, NTHREADS, w.sm_z, ctx->stream>>>(w.descs, w.z); }));
-    TRY(launch(ctx, TDGL_K_YINV, [&] { k_yinv<<<w.n_y, NTHREADS, w.sm_y, ctx->stream>>>(w.descs, w.y); }));
+    for (const Group &g : w.yg) TRY(launch(ctx, TDGL_K_YFWD, [&] { ypass<false>(g, w.descs, ctx->stream); }));
+    for (const Group &g : w.zg) TRY(launch(ctx, TDGL_K_ZCONV, [&] { zpass(g, w.descs, ctx->stream); }));
+    for (const Group &g : w.yg) TRY(launch(ctx, TDGL_K_YINV, [&] { ypass<true>(g, w.descs, ctx->stream); }));
     return TDGL_OK;
 }
 
 Work sim_work(tdgl_sim *s, bool elec) {
     Work w;
     w.descs = s->ddesc;
-    w.rows = s->d_rows; w.y = s->d_y; w.z = s->d_z;
+    w.rows = s->d_rows;
     w.n_rows = (int)s->it_rows.size();
-    w.n_y = elec ? (int)s->it_y.size() : 0;
-    w.n_z = elec ? (int)s->it_z.size() : 0;
     w.sm_rows = smem_rows(s, s->rows_cnt_max);
-    w.sm_y = smem_y(s, s->ky_cnt_max);
-    w.sm_z = smem_z(s, s->kz_cnt_max);
+    if (elec) {
+        w.yg.push_back(Group{s->yN, s->d_y, (int)s->it_y.size(), s->yN ? 0 : smem_y(s, s->ky_cnt_max)});
+        w.zg.push_back(Group{s->zN, s->d_z, (int)s->it_z.size(), s->zN ? 0 : smem_z(s, s->kz_cnt_max)});
+    }
     return w;
 }
 
@@ -970,26 +1025,37 @@ namespace {
 int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const double *dt) {
     tdgl_ctx *ctx = b->ctx;
     std::vector<SimDev> descs(b->sims.size());
-    std::vector<int4> rows, ys, zs;
+    std::vector<int4> rows;
+    // y and z work grouped by transform length (one launch per length class)
+    std::vector<std::pair<int, std::vector<int4>>> ygr, zgr;
+    std::vector<size_t> ysm, zsm;
+    auto group_of = [](std::vector<std::pair<int, std::vector<int4>>> &g, std::vector<size_t> &sm, int N) -> size_t {
+        for (size_t i = 0; i < g.size(); ++i)
+            if (g[i].first == N) return i;
+        g.push_back({N, {}});
+        sm.push_back(0);
+        return g.size() - 1;
+    };
     Work w;
-    memset(&w, 0, sizeof w);
-    bool any_elec = false;
+    w.sm_rows = 0;
     for (int idx : active) {
         tdgl_sim *s = b->sims[idx];
         const bool elec = (s->terms & TDGL_TERM_ELEC) != 0;
-        any_elec |= elec;
         fill_desc(s, dt[idx], s->terms);
         descs[idx] = s->desc;
         for (auto it : s->it_rows) rows.push_back(make_int4(idx, it.y, it.z, it.w));
         if (elec) {
-            for (auto it : s->it_y) ys.push_back(make_int4(idx, it.y, it.z, it.w));
-            for (auto it : s->it_z) zs.push_back(make_int4(idx, it.y, it.z, it.w));
+            const size_t gy = group_of(ygr, ysm, s->yN), gz = group_of(zgr, zsm, s->zN);
+            for (auto it : s->it_y) ygr[gy].second.push_back(make_int4(idx, it.y, it.z, it.w));
+            for (auto it : s->it_z) zgr[gz].second.push_back(make_int4(idx, it.y, it.z, it.w));
+            if (!s->yN) ysm[gy] = std::max(ysm[gy], smem_y(s, s->ky_cnt_max));
+            if (!s->zN) zsm[gz] = std::max(zsm[gz], smem_z(s, s->kz_cnt_max));
         }
         w.sm_rows = std::max(w.sm_rows, smem_rows(s, s->rows_cnt_max));
-        w.sm_y = std::max(w.sm_y, smem_y(s, s->ky_cnt_max));
-        w.sm_z = std::max(w.sm_z, smem_z(s, s->kz_cnt_max));
     }
-    const size_t tot = rows.size() + ys.size() + zs.size();
+    size_t tot = rows.size();
+    for (auto &g : ygr) tot += g.second.size();
+    for (auto &g : zgr) tot += g.second.size();
     if (tot > b->items_cap) {
         cudaFree(b->d_items);
         b->d_items = nullptr;
@@ -999,17 +1065,19 @@ int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const doub
     std::vector<int4> all;
     all.reserve(tot);
     all.insert(all.end(), rows.begin(), rows.end());
-    all.insert(all.end(), ys.begin(), ys.end());
-    all.insert(all.end(), zs.begin(), zs.end());
-    CK(ctx, cudaMemcpyAsync(b->d_items, all.data(), tot * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
-    CK(ctx, cudaMemcpyAsync(b->ddescs, descs.data(), descs.size() * sizeof(SimDev), cudaMemcpyHostToDevice, ctx->stream));
     w.descs = b->ddescs;
     w.rows = b->d_items;
-    w.y = b->d_items + rows.size();
-    w.z = b->d_items + rows.size() + ys.size();
     w.n_rows = (int)rows.size();
-    w.n_y = (int)ys.size();
-    w.n_z = (int)zs.size();
+    for (size_t i = 0; i < ygr.size(); ++i) {
+        w.yg.push_back(Group{ygr[i].first, b->d_items + all.size(), (int)ygr[i].second.size(), ysm[i]});
+        all.insert(all.end(), ygr[i].second.begin(), ygr[i].second.end());
+    }
+    for (size_t i = 0; i < zgr.size(); ++i) {
+        w.zg.push_back(Group{zgr[i].first, b->d_items + all.size(), (int)zgr[i].second.size(), zsm[i]});
+        all.insert(all.end(), zgr[i].second.begin(), zgr[i].second.end());
+    }
+    CK(ctx, cudaMemcpyAsync(b->d_items, all.data(), tot * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(b->ddescs, descs.data(), descs.size() * sizeof(SimDev), cudaMemcpyHostToDevice, ctx->stream));
     // prologue: sims whose x-spectrum is not P-hat of the current P get the x forward pass
     {
         std::vector<int4> pro;
@@ -1033,7 +1101,7 @@ int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const doub
     for (int idx : active) CK(ctx, cudaMemsetAsync(b->sims[idx]->dflag, 0, sizeof(int), ctx->stream));
     int parity = 0;
     for (int i = 0; i < n; ++i) {
-        if (any_elec) TRY(launch_conv(ctx, w));
+        TRY(launch_conv(ctx, w));
         if (i == n - 1)
             for (int idx : active) CK(ctx, cudaMemsetAsync(b->sims[idx]->dmaxdp, 0, sizeof(unsigned), ctx->stream));
         TRY(launch_rows(ctx, MODE_STEP, w, parity));
