@@ -1,0 +1,343 @@
+// Row kernel with a shared-memory tile and register x-transforms (x complex length HX).
+//
+// A block owns TY consecutive x-rows (y0 .. y0+TY-1) of one plane z.  It stages P and the
+// material ids of planes z-1, z, z+1, rows y0-1 .. y0+TY, all x, in shared memory: that covers
+// every neighbour the discrete Eq. 4 needs (faces, and the edge cells of the cross terms), with
+// cells outside the grid stored as vacuum.  Per mode:
+//   STEP    x-inverse of the field spectrum (C2R) -> E_el rows; Landau (Eq. 3), gradient (Eq. 4),
+//           E_ext (Eq. 7); forward Euler update (Eq. 1); x-forward (R2C) of the new rows.
+//   FIELD   the same field, written out instead of the update.
+//   ENERGY  energy densities (float32 per cell, float64 sums) of Eqs. 3-7.
+//   XFWD    x-forward of the current rows only.
+// Line (c, r) of the x-transforms is held by T = HX/E threads, thread t holding elements
+// t + T m; the exchange buffer is [line][pos] padded by one slot in 16.
+#pragma once
+#include "fft_reg.cuh"
+#include "kernels.cuh"
+
+namespace tdgl {
+
+template <int HX> __host__ __device__ constexpr int xrows_tile(int ny) {
+    // rows per block so that 3 * TY lines of T threads fill at most 192 threads
+    return (192 / (3 * rf::threads_per_line<HX>())) < ny ? (192 / (3 * rf::threads_per_line<HX>())) : ny;
+}
+template <int HX> __host__ __device__ constexpr int xrows_ldp() { return HX + HX / 16 + 1; }
+
+struct TileView {
+    const float *P;       // [3 comps][3 planes][TYH rows][nx]
+    const uint8_t *M;     // [3 planes][TYH][nx]
+    int nx, TYH;
+    __device__ __forceinline__ int m(int pz, int py, int x) const {
+        return (unsigned)x < (unsigned)nx ? (int)M[(pz * TYH + py) * nx + x] : 0;
+    }
+    __device__ __forceinline__ float p(int c, int pz, int py, int x) const {
+        return P[((c * 3 + pz) * TYH + py) * nx + x];
+    }
+};
+
+__device__ __forceinline__ void nbr(int d, int s, int &pz, int &py, int &x) {
+    if (d == 0) x += s; else if (d == 1) py += s; else pz += s;
+}
+
+// D_d P_f at a material tile cell, mirror ghosts at non-material neighbours
+__device__ __forceinline__ float tcentral(const TileView &V, const SimDev &S, int pz, int py, int x, int d, int f) {
+    const float q0 = V.p(f, pz, py, x);
+    int az = pz, ay = py, ax = x, bz = pz, by = py, bx = x;
+    nbr(d, 1, az, ay, ax);
+    nbr(d, -1, bz, by, bx);
+    const float qp = V.m(az, ay, ax) ? V.p(f, az, ay, ax) : q0;
+    const float qm = V.m(bz, by, bx) ? V.p(f, bz, by, bx) : q0;
+    return (qp - qm) * S.inv_2d[d];
+}
+
+// cross-term fluxes attached to direction d at a material tile cell (see cross_fluxes)
+__device__ __forceinline__ void tfluxes(const TileView &V, const SimDev &S, const float *coef, int pz, int py, int x,
+                                        int m, int d, float &Sd, float *T) {
+    const float *c = coef + m * NCOEF;
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        if (j != d) s += tcentral(V, S, pz, py, x, j, j);
+    Sd = c[10] * s;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) T[i] = (i != d) ? c[11] * tcentral(V, S, pz, py, x, i, d) : 0.f;
+}
+
+// gradient field of the discrete Eq. 4 at centre-plane tile cell (1, py, x) of material ma
+__device__ __forceinline__ void tgrad_field(const TileView &V, const SimDev &S, const float *coef, int py, int x,
+                                            int ma, const float *pa, float *h) {
+    const float *ca = coef + ma * NCOEF;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+        for (int s = -1; s <= 1; s += 2) {
+            int nz_ = 1, ny_ = py, nx_ = x;
+            nbr(d, s, nz_, ny_, nx_);
+            const int mb = V.m(nz_, ny_, nx_);
+            if (!mb) continue;
+            const float *cb = coef + mb * NCOEF;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float g = 0.5f * ((i == d) ? ca[8] + cb[8] : ca[9] + cb[9]) * S.inv_d2[d];
+                h[i] = fmaf(g, V.p(i, nz_, ny_, nx_) - pa[i], h[i]);
+            }
+        }
+    }
+    if (!S.has_cross) return;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float Sa, Ta[3], Sp, Tp[3], Sm, Tm[3];
+        tfluxes(V, S, coef, 1, py, x, ma, d, Sa, Ta);
+        int az = 1, ay = py, ax = x, bz = 1, by = py, bx = x;
+        nbr(d, 1, az, ay, ax);
+        nbr(d, -1, bz, by, bx);
+        const int mp = V.m(az, ay, ax), mm = V.m(bz, by, bx);
+        if (mp) tfluxes(V, S, coef, az, ay, ax, mp, d, Sp, Tp);
+        else { Sp = -Sa; Tp[0] = -Ta[0]; Tp[1] = -Ta[1]; Tp[2] = -Ta[2]; }
+        if (mm) tfluxes(V, S, coef, bz, by, bx, mm, d, Sm, Tm);
+        else { Sm = -Sa; Tm[0] = -Ta[0]; Tm[1] = -Ta[1]; Tm[2] = -Ta[2]; }
+        const float w = S.inv_2d[d];
+        h[d] = fmaf(Sp - Sm, w, h[d]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            if (i != d) h[i] = fmaf(Tp[i] - Tm[i], w, h[i]);
+    }
+}
+
+// gradient energy density at centre-plane cell: faces towards +x, +y, +z and the cross terms
+__device__ __forceinline__ float tgrad_energy(const TileView &V, const SimDev &S, const float *coef, int py, int x,
+                                              int ma, const float *pa) {
+    const float *ca = coef + ma * NCOEF;
+    float e = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int nz_ = 1, ny_ = py, nx_ = x;
+        nbr(d, 1, nz_, ny_, nx_);
+        const int mb = V.m(nz_, ny_, nx_);
+        if (!mb) continue;
+        const float *cb = coef + mb * NCOEF;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float g = 0.5f * ((i == d) ? ca[8] + cb[8] : ca[9] + cb[9]) * S.inv_d2[d];
+            const float df = V.p(i, nz_, ny_, nx_) - pa[i];
+            e = fmaf(0.5f * g * df, df, e);
+        }
+    }
+    if (S.has_cross) {
+        float D[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) D[i][d] = tcentral(V, S, 1, py, x, d, i);
+        e += ca[10] * (D[0][0] * D[1][1] + D[1][1] * D[2][2] + D[2][2] * D[0][0]) +
+             ca[11] * (D[0][1] * D[1][0] + D[1][2] * D[2][1] + D[0][2] * D[2][0]);
+    }
+    return e;
+}
+
+template <int MODE, int HX>
+__global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, const int4 *__restrict__ items,
+                                               int parity) {
+    constexpr int E = rf::Cfg<HX>::E, T = HX / E, LDP = xrows_ldp<HX>();
+    extern __shared__ float4 smem4[];
+    __shared__ float s_coef[MAXMAT * NCOEF];
+    __shared__ float2 s_tw[HX];          // W_HX^t for the complex transform
+    __shared__ float2 s_twr[HX + 1];     // W_Mx^k for the real pre/post-processing
+    __shared__ double s_red[8];
+    __shared__ unsigned s_max;
+    const int4 it = items[blockIdx.x];
+    const SimDev &S = sims[it.x];
+    const int z = it.y, y0 = it.z, TY = it.w;     // TY rows of this block (<= tile)
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const int TYmax = xrows_tile<HX>(ny);
+    const int TYH = TYmax + 2;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    // layout (xrows_smem): P tile, E / new-P rows, x-transform exchange (one line per T threads),
+    // material tile
+    float *Pt = reinterpret_cast<float *>(smem4);                 // [3][3][TYH][nx]
+    float *Eb = Pt + 9 * TYH * nx;                                // [3][TYmax][nx]
+    const int nf = 9 * TYH * nx + 3 * TYmax * nx;
+    float2 *X2 = reinterpret_cast<float2 *>(Pt + nf + (nf & 1));  // [nthr / T][LDP]
+    uint8_t *Mt = reinterpret_cast<uint8_t *>(X2 + (nthr / T) * LDP);   // [3][TYH][nx]
+    const float *Pc = S.P[parity];
+    float *Pn = S.P[parity ^ 1];
+    const bool elec = (S.terms & TERM_ELEC) != 0;
+    for (int i = tid; i < MAXMAT * NCOEF; i += nthr) s_coef[i] = S.coef[i];
+    for (int i = tid; i < HX; i += nthr) s_tw[i] = S.tw[S.px.tw + i];
+    for (int i = tid; i <= HX; i += nthr) s_twr[i] = S.tw[S.twr + i];
+    if (tid == 0) s_max = 0u;
+    // ---- stage the P / material tile (cells outside the grid: vacuum, P = 0)
+    const int planes = (MODE == MODE_XFWD) ? 1 : 3;
+    for (int w = tid; w < planes * TYH * nx; w += nthr) {
+        const int x = w % nx, rr = w / nx;
+        const int py = rr % TYH, pzi = rr / TYH;
+        const int pz = (MODE == MODE_XFWD) ? 1 : pzi;
+        const int gy = y0 - 1 + py, gz = z - 1 + pz;
+        const bool in = (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && py <= TY + 1;
+        const long id = ((long)gz * ny + gy) * nx + x;
+        Mt[(pz * TYH + py) * nx + x] = in ? __ldg(&S.mat[id]) : (uint8_t)0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Pt[((c * 3 + pz) * TYH + py) * nx + x] = in ? __ldg(&Pc[c * S.ncell + id]) : 0.f;
+    }
+    // ---- x-inverse of the field spectrum: line l = c*TY + r held by T threads
+    const int line = tid / T, t = tid % T;
+    const int nlines = 3 * TYmax;
+    const int lc = line / TYmax, lr = line % TYmax;
+    const bool lok = line < nlines && lr < TY;
+    auto xidx = [&](int pos) { return line * LDP + pos + (pos >> 4); };
+    __syncthreads();
+    if (MODE != MODE_XFWD && elec) {
+        float2 v[E];
+        const float2 *row = S.X + (((long)lc * nz + z) * ny + y0 + lr) * S.kxp;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int k = t + T * m;
+            float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+            if (lok) { a = row[k]; b = cconj(row[HX - k]); }
+            const float2 w = cconj(s_twr[k]);               // W^{-k}
+            const float2 d = cmul(csub(a, b), w);
+            v[m] = make_float2(a.x + b.x - d.y, a.y + b.y + d.x);
+        }
+        rf::fft<HX, true>(v, t, X2, xidx, s_tw);
+        if (lok) {
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int j = rf::final_pos<HX>(t, i);
+                const int x0 = 2 * j;
+                float *er = Eb + (lc * TYmax + lr) * nx;
+                if (x0 < nx) er[x0] = v[i].x;
+                if (x0 + 1 < nx) er[x0 + 1] = v[i].y;
+            }
+        }
+        __syncthreads();
+    }
+    // ---- cells
+    const TileView V{Pt, Mt, nx, TYH};
+    float lmax = 0.f;
+    bool bad = false;
+    double e_land = 0.0, e_grad = 0.0, e_elec = 0.0, e_ext = 0.0;
+    if (MODE != MODE_XFWD) {
+        for (int w = tid; w < TY * nx; w += nthr) {
+            const int r = w / nx, x = w - r * nx;
+            const int py = r + 1;
+            const long id = ((long)z * ny + y0 + r) * nx + x;
+            const int m = V.m(1, py, x);
+            if (m == 0) {
+                if (MODE == MODE_STEP) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) { Pn[c * S.ncell + id] = 0.f; Eb[(c * TYmax + r) * nx + x] = 0.f; }
+                } else if (MODE == MODE_FIELD) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) S.out[c * S.ncell + id] = 0.f;
+                }
+                continue;
+            }
+            float p[3], h[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) p[c] = V.p(c, 1, py, x);
+            const float *cm = s_coef + m * NCOEF;
+            if (MODE == MODE_ENERGY) {
+                if (S.terms & TERM_LANDAU) {
+                    const float x2 = p[0] * p[0], y2 = p[1] * p[1], z2 = p[2] * p[2];
+                    const float f = cm[0] * x2 + cm[1] * y2 + cm[2] * z2 + cm[3] * (x2 * x2 + y2 * y2 + z2 * z2) +
+                                    cm[4] * (x2 * y2 + y2 * z2 + z2 * x2) +
+                                    cm[5] * (x2 * x2 * x2 + y2 * y2 * y2 + z2 * z2 * z2) +
+                                    cm[6] * (x2 * x2 * (y2 + z2) + y2 * y2 * (x2 + z2) + z2 * z2 * (x2 + y2)) +
+                                    cm[7] * x2 * y2 * z2;
+                    e_land += (double)f;
+                }
+                if (S.terms & TERM_GRAD) e_grad += (double)tgrad_energy(V, S, s_coef, py, x, m, p);
+                float el = 0.f, ex = 0.f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (elec) el = fmaf(-0.5f * Eb[(c * TYmax + r) * nx + x], p[c], el);
+                    if (S.terms & TERM_EXT) ex = fmaf(-S.eext[c], p[c], ex);
+                }
+                e_elec += (double)el;
+                e_ext += (double)ex;
+                continue;
+            }
+            if (S.terms & TERM_LANDAU) landau_field(p, cm, h);
+            if (S.terms & TERM_GRAD) tgrad_field(V, S, s_coef, py, x, m, p, h);
+            if (elec) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) h[c] += Eb[(c * TYmax + r) * nx + x];
+            }
+            if (S.terms & TERM_EXT) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) h[c] += S.eext[c];
+            }
+            if (MODE == MODE_FIELD) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) S.out[c * S.ncell + id] = h[c] * S.out_scale;
+                continue;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float pn = fmaf(S.dt, h[c], p[c]);
+                lmax = fmaxf(lmax, fabsf(pn - p[c]));
+                bad |= !(fabsf(pn) <= S.pmax);
+                Pn[c * S.ncell + id] = pn;
+                Eb[(c * TYmax + r) * nx + x] = pn;      // the cell's own slot: E read above, new P kept
+            }
+        }
+    }
+    if (MODE == MODE_ENERGY) {
+        double v;
+        v = block_sum(e_land, s_red); if (tid == 0) atomicAdd(&S.energy[0], v);
+        v = block_sum(e_grad, s_red); if (tid == 0) atomicAdd(&S.energy[1], v);
+        v = block_sum(e_elec, s_red); if (tid == 0) atomicAdd(&S.energy[2], v);
+        v = block_sum(e_ext, s_red); if (tid == 0) atomicAdd(&S.energy[3], v);
+        return;
+    }
+    if (MODE == MODE_FIELD) return;
+    if (MODE == MODE_STEP) {
+        for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        if ((tid & 31) == 0) atomicMax(&s_max, __float_as_uint(lmax));
+        if (bad) atomicOr(S.flag, 1);
+        __syncthreads();
+        if (tid == 0) atomicMax(S.maxdp, s_max);
+    }
+    if (!elec) return;
+    __syncthreads();
+    // ---- x-forward of the new (STEP) or current (XFWD) rows: z_j = (x_2j, x_2j+1), zero padded
+    {
+        float2 v[E];
+        const float *src = (MODE == MODE_XFWD) ? Pt + ((lc * 3 + 1) * TYH + lr + 1) * nx : Eb + (lc * TYmax + lr) * nx;
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int j = t + T * m;
+            const int x0 = 2 * j;
+            v[m] = make_float2((lok && x0 < nx) ? src[x0] : 0.f, (lok && x0 + 1 < nx) ? src[x0 + 1] : 0.f);
+        }
+        rf::fft<HX, false>(v, t, X2, xidx, s_tw);
+        // Hermitian half-spectrum from the packed transform: needs Z_k and Z_{HX-k}
+#pragma unroll
+        for (int i = 0; i < E; ++i) X2[xidx(rf::final_pos<HX>(t, i))] = v[i];
+        __syncthreads();
+        if (lok) {
+            float2 *row = S.X + (((long)lc * nz + z) * ny + y0 + lr) * S.kxp;
+            for (int k = t; k <= HX; k += T) {
+                const float2 a = X2[xidx(k == HX ? 0 : k)];
+                const float2 b = cconj(X2[xidx(k == 0 ? 0 : HX - k)]);
+                const float2 d = cmul(csub(a, b), s_twr[k]);
+                row[k] = make_float2(0.5f * (a.x + b.x + d.y), 0.5f * (a.y + b.y - d.x));
+            }
+        }
+    }
+}
+
+// k_xrows is always launched with XROWS_THREADS threads (idle lines when 3 TY T is smaller)
+constexpr int XROWS_THREADS = 192;
+
+// dynamic shared memory of k_xrows for a sim (bytes); must match the kernel's layout
+template <int HX> __host__ size_t xrows_smem(int nx, int ny) {
+    const int TY = xrows_tile<HX>(ny), TYH = TY + 2;
+    const size_t nf = 9ull * TYH * nx + 3ull * TY * nx;
+    size_t b = sizeof(float) * (nf + (nf & 1));
+    b += sizeof(float2) * (size_t)(XROWS_THREADS / rf::threads_per_line<HX>()) * xrows_ldp<HX>();
+    b += 3ull * TYH * nx;
+    return (b + 15) & ~(size_t)15;
+}
+
+}  // namespace tdgl

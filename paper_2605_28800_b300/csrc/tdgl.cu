@@ -18,6 +18,7 @@
 #include "../../include/tdgl.h"
 #include "kernels.cuh"
 #include "kernels_fast.cuh"
+#include "kernels_rows.cuh"
 #include "tensor.cuh"
 
 using namespace tdgl;
@@ -83,7 +84,7 @@ struct tdgl_sim {
     // work items
     std::vector<int4> it_rows, it_y, it_z;
     int rows_cnt_max = 1, ky_cnt_max = 1, kz_cnt_max = 1;
-    int yN = 0, zN = 0;   // specialized y / z transform length (0 = generic kernels)
+    int xN = 0, yN = 0, zN = 0;   // specialized x / y / z transform length (0 = generic kernels)
     int4 *d_rows = nullptr, *d_y = nullptr, *d_z = nullptr;
     int cur = 0;
     int xstate = XS_NONE;
@@ -241,7 +242,9 @@ void build_items(tdgl_sim *s) {
     s->it_rows.clear();
     s->it_y.clear();
     s->it_z.clear();
-    const int RB = std::max(1, std::min(s->ny, std::max(1, 512 / s->nx)));
+    s->xN = fast_len(s->hx) ? s->hx : 0;
+    const int RB = s->xN ? std::min(192 / (3 * fast_tpl(s->hx)), s->ny)
+                         : std::max(1, std::min(s->ny, std::max(1, 512 / s->nx)));
     s->rows_cnt_max = RB;
     for (int z = 0; z < s->nz; ++z)
         for (int y0 = 0; y0 < s->ny; y0 += RB) s->it_rows.push_back(make_int4(0, z, y0, std::min(RB, s->ny - y0)));
@@ -265,7 +268,17 @@ void build_items(tdgl_sim *s) {
         for (int k0 = 0; k0 < s->Kx; k0 += kz) s->it_z.push_back(make_int4(0, k, k0, std::min(kz, s->Kx - k0)));
 }
 
-size_t smem_rows(const tdgl_sim *s, int cnt) { return 2ull * 3 * cnt * (s->hx + 2) * sizeof(float2); }
+size_t xrows_smem_for(int hx, int nx, int ny) {
+    switch (hx) {
+#define TDGL_XS(LEN) case LEN: return xrows_smem<LEN>(nx, ny);
+        TDGL_XS(16) TDGL_XS(32) TDGL_XS(64) TDGL_XS(128) TDGL_XS(256) TDGL_XS(512) TDGL_XS(48) TDGL_XS(96) TDGL_XS(192)
+#undef TDGL_XS
+    }
+    return 0;
+}
+size_t smem_rows(const tdgl_sim *s, int cnt) {
+    return s->xN ? xrows_smem_for(s->xN, s->nx, s->ny) : 2ull * 3 * cnt * (s->hx + 2) * sizeof(float2);
+}
 size_t smem_y(const tdgl_sim *s, int cnt) { return 2ull * cnt * (s->My + 1) * sizeof(float2); }
 size_t smem_z(const tdgl_sim *s, int cnt) { return 2ull * 3 * cnt * (s->Mz + 1) * sizeof(float2); }
 
@@ -486,26 +499,39 @@ struct Group {
 
 struct Work {
     const SimDev *descs;
-    const int4 *rows;
-    int n_rows;
-    size_t sm_rows;
-    std::vector<Group> yg, zg;
+    std::vector<Group> rg, yg, zg;   // row, y and z work by transform length
 };
+
+#define TDGL_FAST_LENGTHS(X) X(16) X(32) X(64) X(128) X(256) X(512) X(48) X(96) X(192)
+
+template <int MODE>
+void rows_launch(const Group &g, const SimDev *d, cudaStream_t st, int parity) {
+    if (g.N == 0) {
+        k_rows<MODE><<<g.n, NTHREADS, g.smem, st>>>(d, g.items, parity);
+        return;
+    }
+    switch (g.N) {
+#define TDGL_R(LEN) case LEN: k_xrows<MODE, LEN><<<g.n, XROWS_THREADS, g.smem, st>>>(d, g.items, parity); break;
+        TDGL_FAST_LENGTHS(TDGL_R)
+#undef TDGL_R
+    }
+}
 
 int launch_rows(tdgl_ctx *ctx, int mode, const Work &w, int parity) {
     const int kind = (mode == MODE_XFWD) ? TDGL_K_XFWD : (mode == MODE_STEP ? TDGL_K_STEP : TDGL_K_OTHER);
-    if (w.n_rows == 0) return TDGL_OK;
-    return launch(ctx, kind, [&] {
-        switch (mode) {
-            case MODE_STEP: k_rows<MODE_STEP><<<w.n_rows, NTHREADS, w.sm_rows, ctx->stream>>>(w.descs, w.rows, parity); break;
-            case MODE_FIELD: k_rows<MODE_FIELD><<<w.n_rows, NTHREADS, w.sm_rows, ctx->stream>>>(w.descs, w.rows, parity); break;
-            case MODE_ENERGY: k_rows<MODE_ENERGY><<<w.n_rows, NTHREADS, w.sm_rows, ctx->stream>>>(w.descs, w.rows, parity); break;
-            default: k_rows<MODE_XFWD><<<w.n_rows, NTHREADS, w.sm_rows, ctx->stream>>>(w.descs, w.rows, parity); break;
-        }
-    });
+    for (const Group &g : w.rg) {
+        if (g.n == 0) continue;
+        TRY(launch(ctx, kind, [&] {
+            switch (mode) {
+                case MODE_STEP: rows_launch<MODE_STEP>(g, w.descs, ctx->stream, parity); break;
+                case MODE_FIELD: rows_launch<MODE_FIELD>(g, w.descs, ctx->stream, parity); break;
+                case MODE_ENERGY: rows_launch<MODE_ENERGY>(g, w.descs, ctx->stream, parity); break;
+                default: rows_launch<MODE_XFWD>(g, w.descs, ctx->stream, parity); break;
+            }
+        }));
+    }
+    return TDGL_OK;
 }
-
-#define TDGL_FAST_LENGTHS(X) X(16) X(32) X(64) X(128) X(256) X(512) X(48) X(96) X(192)
 
 template <bool INV>
 void ypass(const Group &g, const SimDev *d, cudaStream_t st) {
@@ -545,9 +571,7 @@ int launch_conv(tdgl_ctx *ctx, const Work &w) {
 Work sim_work(tdgl_sim *s, bool elec) {
     Work w;
     w.descs = s->ddesc;
-    w.rows = s->d_rows;
-    w.n_rows = (int)s->it_rows.size();
-    w.sm_rows = smem_rows(s, s->rows_cnt_max);
+    w.rg.push_back(Group{s->xN, s->d_rows, (int)s->it_rows.size(), smem_rows(s, s->rows_cnt_max)});
     if (elec) {
         w.yg.push_back(Group{s->yN, s->d_y, (int)s->it_y.size(), s->yN ? 0 : smem_y(s, s->ky_cnt_max)});
         w.zg.push_back(Group{s->zN, s->d_z, (int)s->it_z.size(), s->zN ? 0 : smem_z(s, s->kz_cnt_max)});
@@ -654,6 +678,13 @@ int tdgl_ctx_create(tdgl_ctx **out, int device, void *stream) {
     cudaFuncSetAttribute(k_yfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     cudaFuncSetAttribute(k_yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     cudaFuncSetAttribute(k_zconv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+#define TDGL_XA(LEN)                                                                                    \
+    cudaFuncSetAttribute(k_xrows<MODE_STEP, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);   \
+    cudaFuncSetAttribute(k_xrows<MODE_FIELD, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);  \
+    cudaFuncSetAttribute(k_xrows<MODE_ENERGY, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem); \
+    cudaFuncSetAttribute(k_xrows<MODE_XFWD, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    TDGL_FAST_LENGTHS(TDGL_XA)
+#undef TDGL_XA
     if (cudaGetLastError() != cudaSuccess) { delete ctx; return TDGL_ECUDA; }
     *out = ctx;
     return TDGL_OK;
@@ -1025,10 +1056,9 @@ namespace {
 int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const double *dt) {
     tdgl_ctx *ctx = b->ctx;
     std::vector<SimDev> descs(b->sims.size());
-    std::vector<int4> rows;
-    // y and z work grouped by transform length (one launch per length class)
-    std::vector<std::pair<int, std::vector<int4>>> ygr, zgr;
-    std::vector<size_t> ysm, zsm;
+    // row, y and z work grouped by transform length (one launch per length class)
+    std::vector<std::pair<int, std::vector<int4>>> rgr, ygr, zgr;
+    std::vector<size_t> rsm, ysm, zsm;
     auto group_of = [](std::vector<std::pair<int, std::vector<int4>>> &g, std::vector<size_t> &sm, int N) -> size_t {
         for (size_t i = 0; i < g.size(); ++i)
             if (g[i].first == N) return i;
@@ -1037,13 +1067,14 @@ int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const doub
         return g.size() - 1;
     };
     Work w;
-    w.sm_rows = 0;
     for (int idx : active) {
         tdgl_sim *s = b->sims[idx];
         const bool elec = (s->terms & TDGL_TERM_ELEC) != 0;
         fill_desc(s, dt[idx], s->terms);
         descs[idx] = s->desc;
-        for (auto it : s->it_rows) rows.push_back(make_int4(idx, it.y, it.z, it.w));
+        const size_t gr = group_of(rgr, rsm, s->xN);
+        for (auto it : s->it_rows) rgr[gr].second.push_back(make_int4(idx, it.y, it.z, it.w));
+        rsm[gr] = std::max(rsm[gr], smem_rows(s, s->rows_cnt_max));
         if (elec) {
             const size_t gy = group_of(ygr, ysm, s->yN), gz = group_of(zgr, zsm, s->zN);
             for (auto it : s->it_y) ygr[gy].second.push_back(make_int4(idx, it.y, it.z, it.w));
@@ -1051,9 +1082,9 @@ int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const doub
             if (!s->yN) ysm[gy] = std::max(ysm[gy], smem_y(s, s->ky_cnt_max));
             if (!s->zN) zsm[gz] = std::max(zsm[gz], smem_z(s, s->kz_cnt_max));
         }
-        w.sm_rows = std::max(w.sm_rows, smem_rows(s, s->rows_cnt_max));
     }
-    size_t tot = rows.size();
+    size_t tot = 0;
+    for (auto &g : rgr) tot += g.second.size();
     for (auto &g : ygr) tot += g.second.size();
     for (auto &g : zgr) tot += g.second.size();
     if (tot > b->items_cap) {
@@ -1064,10 +1095,11 @@ int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const doub
     }
     std::vector<int4> all;
     all.reserve(tot);
-    all.insert(all.end(), rows.begin(), rows.end());
     w.descs = b->ddescs;
-    w.rows = b->d_items;
-    w.n_rows = (int)rows.size();
+    for (size_t i = 0; i < rgr.size(); ++i) {
+        w.rg.push_back(Group{rgr[i].first, b->d_items + all.size(), (int)rgr[i].second.size(), rsm[i]});
+        all.insert(all.end(), rgr[i].second.begin(), rgr[i].second.end());
+    }
     for (size_t i = 0; i < ygr.size(); ++i) {
         w.yg.push_back(Group{ygr[i].first, b->d_items + all.size(), (int)ygr[i].second.size(), ysm[i]});
         all.insert(all.end(), ygr[i].second.begin(), ygr[i].second.end());
@@ -1080,19 +1112,30 @@ int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const doub
     CK(ctx, cudaMemcpyAsync(b->ddescs, descs.data(), descs.size() * sizeof(SimDev), cudaMemcpyHostToDevice, ctx->stream));
     // prologue: sims whose x-spectrum is not P-hat of the current P get the x forward pass
     {
-        std::vector<int4> pro;
+        std::vector<std::pair<int, std::vector<int4>>> pgr;
+        std::vector<size_t> psm;
+        size_t npro = 0;
         for (int idx : active) {
             tdgl_sim *s = b->sims[idx];
-            if ((s->terms & TDGL_TERM_ELEC) && s->xstate != XS_PHAT)
-                for (auto it : s->it_rows) pro.push_back(make_int4(idx, it.y, it.z, it.w));
+            if ((s->terms & TDGL_TERM_ELEC) && s->xstate != XS_PHAT) {
+                const size_t g = group_of(pgr, psm, s->xN);
+                for (auto it : s->it_rows) pgr[g].second.push_back(make_int4(idx, it.y, it.z, it.w));
+                psm[g] = std::max(psm[g], smem_rows(s, s->rows_cnt_max));
+                npro += s->it_rows.size();
+            }
         }
-        if (!pro.empty()) {
+        if (npro) {
+            std::vector<int4> pro;
+            pro.reserve(npro);
             int4 *dpro = nullptr;
-            CK(ctx, cudaMalloc(&dpro, pro.size() * sizeof(int4)));
-            CK(ctx, cudaMemcpyAsync(dpro, pro.data(), pro.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
-            Work wp = w;
-            wp.rows = dpro;
-            wp.n_rows = (int)pro.size();
+            CK(ctx, cudaMalloc(&dpro, npro * sizeof(int4)));
+            Work wp;
+            wp.descs = w.descs;
+            for (size_t i = 0; i < pgr.size(); ++i) {
+                wp.rg.push_back(Group{pgr[i].first, dpro + pro.size(), (int)pgr[i].second.size(), psm[i]});
+                pro.insert(pro.end(), pgr[i].second.begin(), pgr[i].second.end());
+            }
+            CK(ctx, cudaMemcpyAsync(dpro, pro.data(), npro * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
             TRY(launch_rows(ctx, MODE_XFWD, wp, 0));
             CK(ctx, cudaStreamSynchronize(ctx->stream));
             cudaFree(dpro);
