@@ -59,12 +59,20 @@ __global__ void __launch_bounds__(256) k_ypass(const SimDev *__restrict__ sims, 
     }
 }
 
-// z transform, per-k 3x3 tensor multiply, inverse z transform (first nz outputs kept)
+// dynamic shared memory of k_zpass: three component spectra [3][N][KX] and the twiddles
+template <int N> __host__ __device__ constexpr size_t zpass_smem() {
+    return (3 * N * zlines_per_block<N>() + N) * sizeof(float2);
+}
+
+// z transform, per-k 3x3 tensor multiply, inverse z transform (first nz outputs kept).
+// The three forward spectra are parked in shared memory (each thread's own slots) so that the
+// block needs few registers and several blocks share an SM.
 template <int N>
-__global__ void __launch_bounds__(128) k_zpass(const SimDev *__restrict__ sims, const int4 *__restrict__ items) {
+__global__ void __launch_bounds__(128, 4) k_zpass(const SimDev *__restrict__ sims, const int4 *__restrict__ items) {
     constexpr int E = rf::Cfg<N>::E, T = N / E, KX = zlines_per_block<N>();
-    __shared__ float2 S[N * KX];
-    __shared__ float2 tw[N];
+    extern __shared__ float4 smem4[];
+    float2 *A = reinterpret_cast<float2 *>(smem4);      // [3][N][KX]
+    float2 *tw = A + 3 * N * KX;                          // [N]
     const int4 it = items[blockIdx.x];
     const SimDev &D = sims[it.x];
     const int ky = it.y, kx0 = it.z, cnt = it.w;
@@ -74,26 +82,30 @@ __global__ void __launch_bounds__(128) k_zpass(const SimDev *__restrict__ sims, 
     const int nz = D.nz, My = D.My, kxp = D.kxp;
     const long zs = (long)My * kxp, cs = (long)nz * zs;
     const float2 *src = D.Y + (long)ky * kxp + kx0 + l;
-    float2 a[3][E];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
+    auto idx = [&](int pos) { return pos * KX + l; };
+    __syncthreads();
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        float2 *Ac = A + c * N * KX;
+        float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int z = t + T * m;
-            a[c][m] = (ok && z < nz) ? src[c * cs + z * zs] : make_float2(0.f, 0.f);
+            v[m] = (ok && z < nz) ? src[c * cs + z * zs] : make_float2(0.f, 0.f);
         }
-    __syncthreads();
-    auto idx = [&](int pos) { return pos * KX + l; };
+        rf::fft<N, false>(v, t, Ac, idx, tw);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) rf::fft<N, false>(a[c], t, S, idx, tw);
-    // E-hat(k) = escale * N-hat(k) P-hat(k); N-hat from the reduced table with reflection signs
+        for (int i = 0; i < E; ++i) Ac[idx(rf::final_pos<N>(t, i))] = v[i];
+    }
+    // E-hat(k) = escale * N-hat(k) P-hat(k) on this thread's own slots; N-hat from the reduced
+    // table with reflection signs
     const int kyr = (ky <= My / 2) ? ky : My - ky;
     const float sy = (ky <= My / 2) ? 1.f : -1.f;
     const long ns = (long)D.kzh * D.kyh * D.Kx;
     const float es = D.escale;
     const float *Nb = D.Nhat + (long)kyr * D.Kx + kx0 + l;
     const long rowN = (long)D.kyh * D.Kx;
-#pragma unroll
+#pragma unroll 4
     for (int i = 0; i < E; ++i) {
         const int kz = rf::final_pos<N>(t, i);
         const int kzr = (kz <= N / 2) ? kz : N - kz;
@@ -104,18 +116,22 @@ __global__ void __launch_bounds__(128) k_zpass(const SimDev *__restrict__ sims, 
             nxx = __ldg(Np); nyy = __ldg(Np + ns); nzz = __ldg(Np + 2 * ns);
             nxy = sy * __ldg(Np + 3 * ns); nxz = sz * __ldg(Np + 4 * ns); nyz = sy * sz * __ldg(Np + 5 * ns);
         }
-        const float2 px = a[0][i], py = a[1][i], pz = a[2][i];
-        a[0][i] = make_float2(es * (nxx * px.x + nxy * py.x + nxz * pz.x), es * (nxx * px.y + nxy * py.y + nxz * pz.y));
-        a[1][i] = make_float2(es * (nxy * px.x + nyy * py.x + nyz * pz.x), es * (nxy * px.y + nyy * py.y + nyz * pz.y));
-        a[2][i] = make_float2(es * (nxz * px.x + nyz * py.x + nzz * pz.x), es * (nxz * px.y + nyz * py.y + nzz * pz.y));
+        const int p = idx(kz);
+        const float2 px = A[p], py = A[N * KX + p], pz = A[2 * N * KX + p];
+        A[p] = make_float2(es * (nxx * px.x + nxy * py.x + nxz * pz.x), es * (nxx * px.y + nxy * py.y + nxz * pz.y));
+        A[N * KX + p] = make_float2(es * (nxy * px.x + nyy * py.x + nyz * pz.x), es * (nxy * px.y + nyy * py.y + nyz * pz.y));
+        A[2 * N * KX + p] = make_float2(es * (nxz * px.x + nyz * py.x + nzz * pz.x), es * (nxz * px.y + nyz * py.y + nzz * pz.y));
     }
     float2 *dst = D.Y + (long)ky * kxp + kx0 + l;
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < 3; ++c) {
+        float2 *Ac = A + c * N * KX;
         float2 v[E];
+        __syncthreads();   // every slot of Ac read by its owner before the exchanges overwrite it
 #pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = a[c][rf::final_reg<N>(m)];
-        rf::fft<N, true>(v, t, S, idx, tw);
+        for (int m = 0; m < E; ++m) v[m] = Ac[idx(t + T * m)];
+        __syncthreads();
+        rf::fft<N, true>(v, t, Ac, idx, tw);
         if (ok) {
 #pragma unroll
             for (int i = 0; i < E; ++i) {

@@ -22,6 +22,12 @@ template <int HX> __host__ __device__ constexpr int xrows_tile(int ny) {
     return (192 / (3 * rf::threads_per_line<HX>())) < ny ? (192 / (3 * rf::threads_per_line<HX>())) : ny;
 }
 template <int HX> __host__ __device__ constexpr int xrows_ldp() { return HX + HX / 16 + 1; }
+// floats of the region shared by the P tile and the x-transform exchange (multiple of 4)
+template <int HX> __host__ __device__ constexpr int xrows_region(int nx, int TYH, int nthr) {
+    return (((9 * TYH * nx) > (2 * (nthr / rf::threads_per_line<HX>()) * xrows_ldp<HX>())
+                 ? (9 * TYH * nx)
+                 : (2 * (nthr / rf::threads_per_line<HX>()) * xrows_ldp<HX>())) + 3) & ~3;
+}
 
 struct TileView {
     const float *P;       // [3 comps][3 planes][TYH rows][nx]
@@ -67,6 +73,46 @@ __device__ __forceinline__ void tfluxes(const TileView &V, const SimDev &S, cons
 __device__ __forceinline__ void tgrad_field(const TileView &V, const SimDev &S, const float *coef, int py, int x,
                                             int ma, const float *pa, float *h) {
     const float *ca = coef + ma * NCOEF;
+    // Bulk cells (the 6 face and, with cross terms, the 12 edge neighbours all of material ma):
+    // no ghost rule applies and the coefficients are uniform, so the discrete field below reduces
+    // exactly to G (P(+) + P(-) - 2P) / dx^2 per face pair plus (G12 + G44 - G'44) times the
+    // four-corner mixed differences d_e d_f P_f.
+    bool bulk = V.m(1, py, x - 1) == ma && V.m(1, py, x + 1) == ma && V.m(1, py - 1, x) == ma &&
+                V.m(1, py + 1, x) == ma && V.m(0, py, x) == ma && V.m(2, py, x) == ma;
+    if (bulk && S.has_cross)
+        bulk = V.m(1, py - 1, x - 1) == ma && V.m(1, py - 1, x + 1) == ma && V.m(1, py + 1, x - 1) == ma &&
+               V.m(1, py + 1, x + 1) == ma && V.m(0, py, x - 1) == ma && V.m(0, py, x + 1) == ma &&
+               V.m(2, py, x - 1) == ma && V.m(2, py, x + 1) == ma && V.m(0, py - 1, x) == ma &&
+               V.m(0, py + 1, x) == ma && V.m(2, py - 1, x) == ma && V.m(2, py + 1, x) == ma;
+    if (bulk) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float lx = V.p(i, 1, py, x - 1) + V.p(i, 1, py, x + 1) - 2.f * pa[i];
+            const float ly = V.p(i, 1, py - 1, x) + V.p(i, 1, py + 1, x) - 2.f * pa[i];
+            const float lz = V.p(i, 0, py, x) + V.p(i, 2, py, x) - 2.f * pa[i];
+            const float gx = (i == 0) ? ca[8] : ca[9], gy = (i == 1) ? ca[8] : ca[9], gz = (i == 2) ? ca[8] : ca[9];
+            h[i] = fmaf(gx * S.inv_d2[0], lx, fmaf(gy * S.inv_d2[1], ly, fmaf(gz * S.inv_d2[2], lz, h[i])));
+        }
+        if (S.has_cross) {
+            const float C = ca[10] + ca[11];
+            const float wxy = C * S.inv_2d[0] * S.inv_2d[1], wxz = C * S.inv_2d[0] * S.inv_2d[2],
+                        wyz = C * S.inv_2d[1] * S.inv_2d[2];
+            auto cxy = [&](int f) {   // (x+,y+) - (x+,y-) - (x-,y+) + (x-,y-)
+                return V.p(f, 1, py + 1, x + 1) - V.p(f, 1, py - 1, x + 1) - V.p(f, 1, py + 1, x - 1) +
+                       V.p(f, 1, py - 1, x - 1);
+            };
+            auto cxz = [&](int f) {
+                return V.p(f, 2, py, x + 1) - V.p(f, 0, py, x + 1) - V.p(f, 2, py, x - 1) + V.p(f, 0, py, x - 1);
+            };
+            auto cyz = [&](int f) {
+                return V.p(f, 2, py + 1, x) - V.p(f, 0, py + 1, x) - V.p(f, 2, py - 1, x) + V.p(f, 0, py - 1, x);
+            };
+            h[0] = fmaf(wxy, cxy(1), fmaf(wxz, cxz(2), h[0]));
+            h[1] = fmaf(wxy, cxy(0), fmaf(wyz, cyz(2), h[1]));
+            h[2] = fmaf(wxz, cxz(0), fmaf(wyz, cyz(1), h[2]));
+        }
+        return;
+    }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
 #pragma unroll
@@ -152,13 +198,14 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
     const int TYmax = xrows_tile<HX>(ny);
     const int TYH = TYmax + 2;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    // layout (xrows_smem): P tile, E / new-P rows, x-transform exchange (one line per T threads),
-    // material tile
-    float *Pt = reinterpret_cast<float *>(smem4);                 // [3][3][TYH][nx]
-    float *Eb = Pt + 9 * TYH * nx;                                // [3][TYmax][nx]
-    const int nf = 9 * TYH * nx + 3 * TYmax * nx;
-    float2 *X2 = reinterpret_cast<float2 *>(Pt + nf + (nf & 1));  // [nthr / T][LDP]
-    uint8_t *Mt = reinterpret_cast<uint8_t *>(X2 + (nthr / T) * LDP);   // [3][TYH][nx]
+    // layout (xrows_smem): region R = max(P tile [3][3][TYH][nx] floats, x-transform exchange
+    // [nthr/T][LDP] float2; the exchange is only live while the tile is not), then the E / new-P
+    // rows [3][TYmax][nx] and the material tile [3][TYH][nx]
+    float *Pt = reinterpret_cast<float *>(smem4);
+    float2 *X2 = reinterpret_cast<float2 *>(smem4);
+    const int rf_ = xrows_region<HX>(nx, TYH, nthr);           // floats, multiple of 4
+    float *Eb = Pt + rf_;
+    uint8_t *Mt = reinterpret_cast<uint8_t *>(Eb + 3 * TYmax * nx);
     const float *Pc = S.P[parity];
     float *Pn = S.P[parity ^ 1];
     const bool elec = (S.terms & TERM_ELEC) != 0;
@@ -166,26 +213,13 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
     for (int i = tid; i < HX; i += nthr) s_tw[i] = S.tw[S.px.tw + i];
     for (int i = tid; i <= HX; i += nthr) s_twr[i] = S.tw[S.twr + i];
     if (tid == 0) s_max = 0u;
-    // ---- stage the P / material tile (cells outside the grid: vacuum, P = 0)
-    const int planes = (MODE == MODE_XFWD) ? 1 : 3;
-    for (int w = tid; w < planes * TYH * nx; w += nthr) {
-        const int x = w % nx, rr = w / nx;
-        const int py = rr % TYH, pzi = rr / TYH;
-        const int pz = (MODE == MODE_XFWD) ? 1 : pzi;
-        const int gy = y0 - 1 + py, gz = z - 1 + pz;
-        const bool in = (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && py <= TY + 1;
-        const long id = ((long)gz * ny + gy) * nx + x;
-        Mt[(pz * TYH + py) * nx + x] = in ? __ldg(&S.mat[id]) : (uint8_t)0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) Pt[((c * 3 + pz) * TYH + py) * nx + x] = in ? __ldg(&Pc[c * S.ncell + id]) : 0.f;
-    }
     // ---- x-inverse of the field spectrum: line l = c*TY + r held by T threads
     const int line = tid / T, t = tid % T;
     const int nlines = 3 * TYmax;
     const int lc = line / TYmax, lr = line % TYmax;
     const bool lok = line < nlines && lr < TY;
     auto xidx = [&](int pos) { return line * LDP + pos + (pos >> 4); };
-    __syncthreads();
+    __syncthreads();   // twiddle and coefficient tables
     if (MODE != MODE_XFWD && elec) {
         float2 v[E];
         const float2 *row = S.X + (((long)lc * nz + z) * ny + y0 + lr) * S.kxp;
@@ -211,6 +245,42 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
         }
         __syncthreads();
     }
+    // ---- stage the P / material tile (cells outside the grid: vacuum, P = 0)
+    {
+        const int planes = (MODE == MODE_XFWD) ? 1 : 3;
+        const int nrow = planes * TYH;
+        for (int w = tid; w < nrow * nx; w += nthr) {
+            const int x = w % nx, rr = w / nx;
+            const int py = rr % TYH;
+            const int pz = (MODE == MODE_XFWD) ? 1 : rr / TYH;
+            const int gy = y0 - 1 + py, gz = z - 1 + pz;
+            const bool in = (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && py <= TY + 1;
+            Mt[(pz * TYH + py) * nx + x] = in ? __ldg(&S.mat[((long)gz * ny + gy) * nx + x]) : (uint8_t)0;
+        }
+        if ((nx & 3) == 0) {   // rows of nx floats: 16-byte vector copies
+            const int nq = nx >> 2;
+            for (int w = tid; w < 3 * nrow * nq; w += nthr) {
+                const int q = w % nq, rr = w / nq;
+                const int py = rr % TYH, pc = rr / TYH;
+                const int c = pc / planes, pz = (MODE == MODE_XFWD) ? 1 : pc % planes;
+                const int gy = y0 - 1 + py, gz = z - 1 + pz;
+                const bool in = (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && py <= TY + 1;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (in) v = __ldg(reinterpret_cast<const float4 *>(Pc + c * S.ncell + ((long)gz * ny + gy) * nx) + q);
+                reinterpret_cast<float4 *>(Pt + ((c * 3 + pz) * TYH + py) * nx)[q] = v;
+            }
+        } else {
+            for (int w = tid; w < 3 * nrow * nx; w += nthr) {
+                const int x = w % nx, rr = w / nx;
+                const int py = rr % TYH, pc = rr / TYH;
+                const int c = pc / planes, pz = (MODE == MODE_XFWD) ? 1 : pc % planes;
+                const int gy = y0 - 1 + py, gz = z - 1 + pz;
+                const bool in = (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && py <= TY + 1;
+                Pt[((c * 3 + pz) * TYH + py) * nx + x] = in ? __ldg(&Pc[c * S.ncell + ((long)gz * ny + gy) * nx + x]) : 0.f;
+            }
+        }
+    }
+    __syncthreads();
     // ---- cells
     const TileView V{Pt, Mt, nx, TYH};
     float lmax = 0.f;
@@ -310,6 +380,7 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
             const int x0 = 2 * j;
             v[m] = make_float2((lok && x0 < nx) ? src[x0] : 0.f, (lok && x0 + 1 < nx) ? src[x0 + 1] : 0.f);
         }
+        __syncthreads();   // the exchange below reuses the tile's memory
         rf::fft<HX, false>(v, t, X2, xidx, s_tw);
         // Hermitian half-spectrum from the packed transform: needs Z_k and Z_{HX-k}
 #pragma unroll
@@ -333,9 +404,7 @@ constexpr int XROWS_THREADS = 192;
 // dynamic shared memory of k_xrows for a sim (bytes); must match the kernel's layout
 template <int HX> __host__ size_t xrows_smem(int nx, int ny) {
     const int TY = xrows_tile<HX>(ny), TYH = TY + 2;
-    const size_t nf = 9ull * TYH * nx + 3ull * TY * nx;
-    size_t b = sizeof(float) * (nf + (nf & 1));
-    b += sizeof(float2) * (size_t)(XROWS_THREADS / rf::threads_per_line<HX>()) * xrows_ldp<HX>();
+    size_t b = sizeof(float) * ((size_t)xrows_region<HX>(nx, TYH, XROWS_THREADS) + 3ull * TY * nx);
     b += 3ull * TYH * nx;
     return (b + 15) & ~(size_t)15;
 }

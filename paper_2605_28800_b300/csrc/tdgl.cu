@@ -90,6 +90,7 @@ struct tdgl_sim {
     int xstate = XS_NONE;
     bool spectra_alloc = false, tensor_ready = false;
     bool has_cross = false;
+    bool dirty = true;      // map, materials, T or scales changed since the last prepare()
     double last_maxdp = 0.0;
     tdgl_batch *batch = nullptr;
 };
@@ -468,15 +469,18 @@ void fill_desc(tdgl_sim *s, double dt, unsigned terms) {
 
 int prepare(tdgl_sim *s, unsigned need_terms) {
     tdgl_ctx *ctx = s->ctx;
-    for (size_t i = 0; i < s->map.size(); ++i)
-        if (s->map[i] && !s->defined[s->map[i]])
-            return fail(ctx, TDGL_ESTATE, "material id %d used in the map but not defined", (int)s->map[i]);
-    if (!lowest_material(s)) return fail(ctx, TDGL_ESTATE, "no material defined");
-    fix_scales(s);
-    s->has_cross = any_cross(s);
-    float tab[MAXMAT * NCOEF];
-    coef_table(s, tab);
-    CK(ctx, cudaMemcpyAsync(s->dcoef, tab, sizeof tab, cudaMemcpyHostToDevice, ctx->stream));
+    if (s->dirty) {   // validation and coefficient upload only after a change
+        for (size_t i = 0; i < s->map.size(); ++i)
+            if (s->map[i] && !s->defined[s->map[i]])
+                return fail(ctx, TDGL_ESTATE, "material id %d used in the map but not defined", (int)s->map[i]);
+        if (!lowest_material(s)) return fail(ctx, TDGL_ESTATE, "no material defined");
+        fix_scales(s);
+        s->has_cross = any_cross(s);
+        float tab[MAXMAT * NCOEF];
+        coef_table(s, tab);
+        CK(ctx, cudaMemcpyAsync(s->dcoef, tab, sizeof tab, cudaMemcpyHostToDevice, ctx->stream));
+        s->dirty = false;
+    }
     if (need_terms & TDGL_TERM_ELEC) {
         TRY(alloc_spectra(s));
         if (!s->tensor_ready) TRY(build_tensor(s));
@@ -555,7 +559,7 @@ void zpass(const Group &g, const SimDev *d, cudaStream_t st) {
     }
     switch (g.N) {
 #define TDGL_Z(LEN) \
-    case LEN: k_zpass<LEN><<<g.n, rf::threads_per_line<LEN>() * zlines_per_block<LEN>(), 0, st>>>(d, g.items); break;
+    case LEN: k_zpass<LEN><<<g.n, rf::threads_per_line<LEN>() * zlines_per_block<LEN>(), zpass_smem<LEN>(), st>>>(d, g.items); break;
         TDGL_FAST_LENGTHS(TDGL_Z)
 #undef TDGL_Z
     }
@@ -685,6 +689,9 @@ int tdgl_ctx_create(tdgl_ctx **out, int device, void *stream) {
     cudaFuncSetAttribute(k_xrows<MODE_XFWD, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     TDGL_FAST_LENGTHS(TDGL_XA)
 #undef TDGL_XA
+#define TDGL_ZA(LEN) cudaFuncSetAttribute(k_zpass<LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    TDGL_FAST_LENGTHS(TDGL_ZA)
+#undef TDGL_ZA
     if (cudaGetLastError() != cudaSuccess) { delete ctx; return TDGL_ECUDA; }
     *out = ctx;
     return TDGL_OK;
@@ -799,11 +806,13 @@ int tdgl_material_define(tdgl_sim *s, int id, const tdgl_material *m) {
     if (m->a1_form == 1 && (m->coth_Ts == 0.0 || m->coth_T1 <= 0.0)) return fail(s->ctx, TDGL_EINVAL, "coth form needs Ts != 0, T1 > 0");
     s->mats[id] = *m;
     s->defined[id] = true;
+    s->dirty = true;
     return TDGL_OK;
 }
 
 static int apply_map(tdgl_sim *s) {
     tdgl_ctx *ctx = s->ctx;
+    s->dirty = true;
     ctx_set(ctx);
     CK(ctx, cudaMemcpyAsync(s->dmat, s->map.data(), s->ncell, cudaMemcpyHostToDevice, ctx->stream));
     TRY(launch(ctx, TDGL_K_OTHER, [&] { k_mask<<<grid_for(3 * s->ncell), 256, 0, ctx->stream>>>(s->dP[s->cur], s->dmat, s->ncell); }));
@@ -853,6 +862,7 @@ int tdgl_set_terms(tdgl_sim *s, unsigned mask) {
 int tdgl_set_temperature(tdgl_sim *s, double T) {
     if (!s || !(T > 0) || !std::isfinite(T)) return s ? fail(s->ctx, TDGL_EINVAL, "T must be > 0") : TDGL_EINVAL;
     s->T = T;
+    s->dirty = true;
     return TDGL_OK;
 }
 
@@ -868,6 +878,7 @@ int tdgl_set_scales(tdgl_sim *s, double P0, double alpha_ref) {
     const double old = s->scales_fixed ? s->P0 : 0.0;
     s->P0 = P0;
     s->alpha_ref = alpha_ref;
+    s->dirty = true;
     if (old > 0 && old != P0) {
         const float f = (float)(old / P0);
         TRY(launch(s->ctx, TDGL_K_OTHER, [&] {
