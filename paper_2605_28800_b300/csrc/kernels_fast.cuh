@@ -83,6 +83,22 @@ __global__ void __launch_bounds__(128, 4) k_zpass(const SimDev *__restrict__ sim
     const long zs = (long)My * kxp, cs = (long)nz * zs;
     const float2 *src = D.Y + (long)ky * kxp + kx0 + l;
     auto idx = [&](int pos) { return pos * KX + l; };
+    // all three components' inputs in flight at once: asynchronous 8-byte copies into this
+    // thread's own slots of the spectra buffers
+    if (ok) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int z = t + T * m;
+                if (z < nz) {
+                    const unsigned dst = (unsigned)__cvta_generic_to_shared(A + c * N * KX + idx(z));
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src + c * cs + z * zs));
+                }
+            }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::);
     __syncthreads();
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
@@ -91,8 +107,9 @@ __global__ void __launch_bounds__(128, 4) k_zpass(const SimDev *__restrict__ sim
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int z = t + T * m;
-            v[m] = (ok && z < nz) ? src[c * cs + z * zs] : make_float2(0.f, 0.f);
+            v[m] = (ok && z < nz) ? Ac[idx(z)] : make_float2(0.f, 0.f);
         }
+        __syncthreads();   // own slots read before the exchanges overwrite them
         rf::fft<N, false>(v, t, Ac, idx, tw);
 #pragma unroll
         for (int i = 0; i < E; ++i) Ac[idx(rf::final_pos<N>(t, i))] = v[i];
@@ -105,7 +122,7 @@ __global__ void __launch_bounds__(128, 4) k_zpass(const SimDev *__restrict__ sim
     const float es = D.escale;
     const float *Nb = D.Nhat + (long)kyr * D.Kx + kx0 + l;
     const long rowN = (long)D.kyh * D.Kx;
-#pragma unroll 4
+#pragma unroll 8
     for (int i = 0; i < E; ++i) {
         const int kz = rf::final_pos<N>(t, i);
         const int kzr = (kz <= N / 2) ? kz : N - kz;

@@ -17,27 +17,35 @@
 
 namespace tdgl {
 
-template <int HX> __host__ __device__ constexpr int xrows_tile(int ny) {
-    // rows per block so that 3 * TY lines of T threads fill at most 192 threads
-    return (192 / (3 * rf::threads_per_line<HX>())) < ny ? (192 / (3 * rf::threads_per_line<HX>())) : ny;
+// rows per block (TYC) and threads per block for the x-transform length HX (row length NX = HX)
+template <int HX> __host__ __device__ constexpr int xrows_tile() {
+    return (192 / (3 * rf::threads_per_line<HX>())) < 16 ? (192 / (3 * rf::threads_per_line<HX>())) : 16;
+}
+template <int HX> __host__ __device__ constexpr int xrows_threads() {
+    return ((3 * xrows_tile<HX>() * rf::threads_per_line<HX>()) + 31) / 32 * 32;
 }
 template <int HX> __host__ __device__ constexpr int xrows_ldp() { return HX + HX / 16 + 1; }
 // floats of the region shared by the P tile and the x-transform exchange (multiple of 4)
-template <int HX> __host__ __device__ constexpr int xrows_region(int nx, int TYH, int nthr) {
-    return (((9 * TYH * nx) > (2 * (nthr / rf::threads_per_line<HX>()) * xrows_ldp<HX>())
-                 ? (9 * TYH * nx)
-                 : (2 * (nthr / rf::threads_per_line<HX>()) * xrows_ldp<HX>())) + 3) & ~3;
+template <int HX> __host__ __device__ constexpr int xrows_region() {
+    constexpr int tile = 9 * (xrows_tile<HX>() + 2) * HX;
+    constexpr int exch = 2 * (xrows_threads<HX>() / rf::threads_per_line<HX>()) * xrows_ldp<HX>();
+    return ((tile > exch ? tile : exch) + 3) & ~3;
+}
+// dynamic shared memory of k_xrows (bytes): shared region, E / new-P rows, material tile
+template <int HX> __host__ __device__ constexpr size_t xrows_smem() {
+    return ((sizeof(float) * ((size_t)xrows_region<HX>() + 3ull * xrows_tile<HX>() * HX) +
+             3ull * (xrows_tile<HX>() + 2) * HX) + 15) & ~(size_t)15;
 }
 
+template <int NX, int TYH>
 struct TileView {
-    const float *P;       // [3 comps][3 planes][TYH rows][nx]
-    const uint8_t *M;     // [3 planes][TYH][nx]
-    int nx, TYH;
+    const float *P;       // [3 comps][3 planes][TYH rows][NX]
+    const uint8_t *M;     // [3 planes][TYH][NX]
     __device__ __forceinline__ int m(int pz, int py, int x) const {
-        return (unsigned)x < (unsigned)nx ? (int)M[(pz * TYH + py) * nx + x] : 0;
+        return (unsigned)x < (unsigned)NX ? (int)M[(pz * TYH + py) * NX + x] : 0;
     }
     __device__ __forceinline__ float p(int c, int pz, int py, int x) const {
-        return P[((c * 3 + pz) * TYH + py) * nx + x];
+        return P[((c * 3 + pz) * TYH + py) * NX + x];
     }
 };
 
@@ -46,7 +54,8 @@ __device__ __forceinline__ void nbr(int d, int s, int &pz, int &py, int &x) {
 }
 
 // D_d P_f at a material tile cell, mirror ghosts at non-material neighbours
-__device__ __forceinline__ float tcentral(const TileView &V, const SimDev &S, int pz, int py, int x, int d, int f) {
+template <class TV>
+__device__ __forceinline__ float tcentral(const TV &V, const SimDev &S, int pz, int py, int x, int d, int f) {
     const float q0 = V.p(f, pz, py, x);
     int az = pz, ay = py, ax = x, bz = pz, by = py, bx = x;
     nbr(d, 1, az, ay, ax);
@@ -57,7 +66,8 @@ __device__ __forceinline__ float tcentral(const TileView &V, const SimDev &S, in
 }
 
 // cross-term fluxes attached to direction d at a material tile cell (see cross_fluxes)
-__device__ __forceinline__ void tfluxes(const TileView &V, const SimDev &S, const float *coef, int pz, int py, int x,
+template <class TV>
+__device__ __forceinline__ void tfluxes(const TV &V, const SimDev &S, const float *coef, int pz, int py, int x,
                                         int m, int d, float &Sd, float *T) {
     const float *c = coef + m * NCOEF;
     float s = 0.f;
@@ -70,7 +80,8 @@ __device__ __forceinline__ void tfluxes(const TileView &V, const SimDev &S, cons
 }
 
 // gradient field of the discrete Eq. 4 at centre-plane tile cell (1, py, x) of material ma
-__device__ __forceinline__ void tgrad_field(const TileView &V, const SimDev &S, const float *coef, int py, int x,
+template <class TV>
+__device__ __forceinline__ void tgrad_field(const TV &V, const SimDev &S, const float *coef, int py, int x,
                                             int ma, const float *pa, float *h) {
     const float *ca = coef + ma * NCOEF;
     // Bulk cells (the 6 face and, with cross terms, the 12 edge neighbours all of material ma):
@@ -151,7 +162,8 @@ __device__ __forceinline__ void tgrad_field(const TileView &V, const SimDev &S, 
 }
 
 // gradient energy density at centre-plane cell: faces towards +x, +y, +z and the cross terms
-__device__ __forceinline__ float tgrad_energy(const TileView &V, const SimDev &S, const float *coef, int py, int x,
+template <class TV>
+__device__ __forceinline__ float tgrad_energy(const TV &V, const SimDev &S, const float *coef, int py, int x,
                                               int ma, const float *pa) {
     const float *ca = coef + ma * NCOEF;
     float e = 0.f;
@@ -185,6 +197,7 @@ template <int MODE, int HX>
 __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, const int4 *__restrict__ items,
                                                int parity) {
     constexpr int E = rf::Cfg<HX>::E, T = HX / E, LDP = xrows_ldp<HX>();
+    constexpr int nx = HX, TYmax = xrows_tile<HX>(), TYH = TYmax + 2, nthr = xrows_threads<HX>();
     extern __shared__ float4 smem4[];
     __shared__ float s_coef[MAXMAT * NCOEF];
     __shared__ float2 s_tw[HX];          // W_HX^t for the complex transform
@@ -194,16 +207,14 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
     const int4 it = items[blockIdx.x];
     const SimDev &S = sims[it.x];
     const int z = it.y, y0 = it.z, TY = it.w;     // TY rows of this block (<= tile)
-    const int nx = S.nx, ny = S.ny, nz = S.nz;
-    const int TYmax = xrows_tile<HX>(ny);
-    const int TYH = TYmax + 2;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int ny = S.ny, nz = S.nz;
+    const int tid = threadIdx.x;
     // layout (xrows_smem): region R = max(P tile [3][3][TYH][nx] floats, x-transform exchange
     // [nthr/T][LDP] float2; the exchange is only live while the tile is not), then the E / new-P
     // rows [3][TYmax][nx] and the material tile [3][TYH][nx]
     float *Pt = reinterpret_cast<float *>(smem4);
     float2 *X2 = reinterpret_cast<float2 *>(smem4);
-    const int rf_ = xrows_region<HX>(nx, TYH, nthr);           // floats, multiple of 4
+    constexpr int rf_ = xrows_region<HX>();                     // floats, multiple of 4
     float *Eb = Pt + rf_;
     uint8_t *Mt = reinterpret_cast<uint8_t *>(Eb + 3 * TYmax * nx);
     const float *Pc = S.P[parity];
@@ -249,13 +260,15 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
     {
         const int planes = (MODE == MODE_XFWD) ? 1 : 3;
         const int nrow = planes * TYH;
-        for (int w = tid; w < nrow * nx; w += nthr) {
-            const int x = w % nx, rr = w / nx;
+        static_assert(nx % 4 == 0, "row length must be a multiple of 4");
+        for (int w = tid; w < nrow * (nx / 4); w += nthr) {
+            const int q = w % (nx / 4), rr = w / (nx / 4);
             const int py = rr % TYH;
             const int pz = (MODE == MODE_XFWD) ? 1 : rr / TYH;
             const int gy = y0 - 1 + py, gz = z - 1 + pz;
             const bool in = (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && py <= TY + 1;
-            Mt[(pz * TYH + py) * nx + x] = in ? __ldg(&S.mat[((long)gz * ny + gy) * nx + x]) : (uint8_t)0;
+            const unsigned v = in ? __ldg(reinterpret_cast<const unsigned *>(S.mat + ((long)gz * ny + gy) * nx) + q) : 0u;
+            reinterpret_cast<unsigned *>(Mt + (pz * TYH + py) * nx)[q] = v;
         }
         if ((nx & 3) == 0) {   // rows of nx floats: 16-byte vector copies
             const int nq = nx >> 2;
@@ -282,7 +295,7 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
     }
     __syncthreads();
     // ---- cells
-    const TileView V{Pt, Mt, nx, TYH};
+    const TileView<nx, TYH> V{Pt, Mt};
     float lmax = 0.f;
     bool bad = false;
     double e_land = 0.0, e_grad = 0.0, e_elec = 0.0, e_ext = 0.0;
@@ -396,17 +409,6 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
             }
         }
     }
-}
-
-// k_xrows is always launched with XROWS_THREADS threads (idle lines when 3 TY T is smaller)
-constexpr int XROWS_THREADS = 192;
-
-// dynamic shared memory of k_xrows for a sim (bytes); must match the kernel's layout
-template <int HX> __host__ size_t xrows_smem(int nx, int ny) {
-    const int TY = xrows_tile<HX>(ny), TYH = TY + 2;
-    size_t b = sizeof(float) * ((size_t)xrows_region<HX>(nx, TYH, XROWS_THREADS) + 3ull * TY * nx);
-    b += 3ull * TYH * nx;
-    return (b + 15) & ~(size_t)15;
 }
 
 }  // namespace tdgl

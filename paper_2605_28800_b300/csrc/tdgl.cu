@@ -243,8 +243,9 @@ void build_items(tdgl_sim *s) {
     s->it_rows.clear();
     s->it_y.clear();
     s->it_z.clear();
-    s->xN = fast_len(s->hx) ? s->hx : 0;
-    const int RB = s->xN ? std::min(192 / (3 * fast_tpl(s->hx)), s->ny)
+    // the tiled row kernel needs the row length to equal the x half-length (2 nx smooth)
+    s->xN = (fast_len(s->hx) && s->nx == s->hx) ? s->hx : 0;
+    const int RB = s->xN ? std::min(192 / (3 * fast_tpl(s->hx)), 16)
                          : std::max(1, std::min(s->ny, std::max(1, 512 / s->nx)));
     s->rows_cnt_max = RB;
     for (int z = 0; z < s->nz; ++z)
@@ -269,16 +270,16 @@ void build_items(tdgl_sim *s) {
         for (int k0 = 0; k0 < s->Kx; k0 += kz) s->it_z.push_back(make_int4(0, k, k0, std::min(kz, s->Kx - k0)));
 }
 
-size_t xrows_smem_for(int hx, int nx, int ny) {
+size_t xrows_smem_for(int hx) {
     switch (hx) {
-#define TDGL_XS(LEN) case LEN: return xrows_smem<LEN>(nx, ny);
+#define TDGL_XS(LEN) case LEN: return xrows_smem<LEN>();
         TDGL_XS(16) TDGL_XS(32) TDGL_XS(64) TDGL_XS(128) TDGL_XS(256) TDGL_XS(512) TDGL_XS(48) TDGL_XS(96) TDGL_XS(192)
 #undef TDGL_XS
     }
     return 0;
 }
 size_t smem_rows(const tdgl_sim *s, int cnt) {
-    return s->xN ? xrows_smem_for(s->xN, s->nx, s->ny) : 2ull * 3 * cnt * (s->hx + 2) * sizeof(float2);
+    return s->xN ? xrows_smem_for(s->xN) : 2ull * 3 * cnt * (s->hx + 2) * sizeof(float2);
 }
 size_t smem_y(const tdgl_sim *s, int cnt) { return 2ull * cnt * (s->My + 1) * sizeof(float2); }
 size_t smem_z(const tdgl_sim *s, int cnt) { return 2ull * 3 * cnt * (s->Mz + 1) * sizeof(float2); }
@@ -515,7 +516,7 @@ void rows_launch(const Group &g, const SimDev *d, cudaStream_t st, int parity) {
         return;
     }
     switch (g.N) {
-#define TDGL_R(LEN) case LEN: k_xrows<MODE, LEN><<<g.n, XROWS_THREADS, g.smem, st>>>(d, g.items, parity); break;
+#define TDGL_R(LEN) case LEN: k_xrows<MODE, LEN><<<g.n, xrows_threads<LEN>(), g.smem, st>>>(d, g.items, parity); break;
         TDGL_FAST_LENGTHS(TDGL_R)
 #undef TDGL_R
     }
