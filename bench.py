@@ -95,7 +95,7 @@ def kernel_bytes(shape):
 
 def kernel_sources_sha():
     h = hashlib.sha256()
-    for f in ("fft.cuh", "fft_reg.cuh", "kernels.cuh", "kernels_fast.cuh", "tensor.cuh", "tdgl.cu"):
+    for f in ("fft.cuh", "fft_reg.cuh", "kernels.cuh", "kernels_fast.cuh", "kernels_rows.cuh", "tensor.cuh", "tdgl.cu"):
         with open(os.path.join(ROOT, "paper_2605_28800_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
