@@ -95,7 +95,8 @@ def kernel_bytes(shape):
 
 def kernel_sources_sha():
     h = hashlib.sha256()
-    for f in ("fft.cuh", "fft_reg.cuh", "kernels.cuh", "kernels_fast.cuh", "kernels_rows.cuh", "tensor.cuh", "tdgl.cu"):
+    # device code of the step kernels (host runtime changes do not invalidate the counters)
+    for f in ("fft.cuh", "fft_reg.cuh", "kernels.cuh", "kernels_fast.cuh", "kernels_rows.cuh"):
         with open(os.path.join(ROOT, "paper_2605_28800_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -254,6 +255,62 @@ def oracle_time(wl, sample_steps):
     return ncell * sample_steps / el, el
 
 
+def relax_compare(args):
+    """Time to relax the uneven BaTiO3 sweep to one tolerance: each sim alone vs one batch."""
+    import torch
+    from paper_2605_28800_b300 import tdgl
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    ctx = tdgl.Context(dev)
+    members = synth.sweep_members(args.sweep_sims)
+    cell = (1e-9, 1e-9, 1e-9)
+
+    def make(m):
+        L = m["L"]
+        s = tdgl.Sim(ctx, (L, L, L), cell)
+        s.define_material(1, synth.BTO)
+        s.set_material_map(np.ones((L, L, L), np.uint8))
+        s.set_temperature(m["T"])
+        s.set_eps_b(45.0)
+        P = (synth.uniform_P((L, L, L), 0.01, m["seed"]) if m["branch"] == "cooling"
+             else synth.rhombohedral_start((L, L, L), 0.2, 0.01, m["seed"]))
+        s.set_P(P)
+        s.energy()                      # one-off tensor build, outside the timed region
+        return s, 0.004 / s.scales()[1]
+
+    res = {}
+    for mode in ("plain", "batched"):
+        sims = [make(m) for m in members]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if mode == "plain":
+            steps = [s.relax(dt, args.tol, args.max_relax_steps, CHECK_EVERY, raise_on_cap=False) for s, dt in sims]
+            steps, conv = [v[0] for v in steps], [v[1] for v in steps]
+        else:
+            B = tdgl.Batch(ctx, [s for s, _ in sims])
+            steps, allconv = B.relax([dt for _, dt in sims], args.tol, args.max_relax_steps, CHECK_EVERY,
+                                     raise_on_cap=False)
+            conv = [st < args.max_relax_steps for st in steps]
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        energies = [s.energy()["total"] for s, _ in sims]
+        res[mode] = dict(seconds=el, steps=steps, converged=sum(conv), energies=energies)
+        for s, _ in sims:
+            s.close()
+    cells = sum(m["L"] ** 3 for m in members)
+    same = all(abs(a - b) <= 1e-6 * max(abs(a), 1e-30) for a, b in zip(res["plain"]["energies"], res["batched"]["energies"]))
+    line = {"metric": "time-to-relax, batched vs plain at equal tol", "unit": "s",
+            "workload": f"bto_sweep_{len(members)}", "sims": len(members), "cells": cells, "tol": args.tol,
+            "check_every": CHECK_EVERY, "max_steps": args.max_relax_steps,
+            "plain_s": res["plain"]["seconds"], "batched_s": res["batched"]["seconds"],
+            "speedup": res["plain"]["seconds"] / res["batched"]["seconds"],
+            "converged": [res["plain"]["converged"], res["batched"]["converged"]],
+            "total_steps": sum(res["plain"]["steps"]), "same_final_energies": same,
+            "sizes": [m["L"] for m in members], "temperatures": [m["T"] for m in members],
+            "steps_per_sim": res["plain"]["steps"]}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -263,7 +320,14 @@ def main():
     ap.add_argument("--workload", default="bto_cube_128", choices=["bto_cube_128", "pto_sto_bilayer_256x256x64"])
     ap.add_argument("--oracle-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--relax-compare", action="store_true",
+                    help="time-to-relax of the uneven sweep, each sim alone vs one batch")
+    ap.add_argument("--sweep-sims", type=int, default=48)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--max-relax-steps", type=int, default=20000)
     args = ap.parse_args()
+    if args.relax_compare:
+        return relax_compare(args)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     wl = workload(args.workload)

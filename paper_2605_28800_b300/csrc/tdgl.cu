@@ -91,6 +91,8 @@ struct tdgl_sim {
     bool spectra_alloc = false, tensor_ready = false;
     bool has_cross = false;
     bool dirty = true;      // map, materials, T or scales changed since the last prepare()
+    struct GraphRec { int n; bool elec; int p0; cudaGraphExec_t exec; long kernels; };
+    std::vector<GraphRec> graphs;   // captured steady step sequences
     double last_maxdp = 0.0;
     tdgl_batch *batch = nullptr;
 };
@@ -101,6 +103,10 @@ struct tdgl_batch {
     SimDev *ddescs = nullptr;
     int4 *d_items = nullptr;
     size_t items_cap = 0;
+    // work lists and captured step sequences for the current active set
+    std::vector<int> w_active;
+    struct Cached;
+    Cached *cache = nullptr;
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -225,6 +231,28 @@ int launch(tdgl_ctx *ctx, int kind, F f) {
     }
     ctx->launches++;
     if (e != cudaSuccess) return fail(ctx, TDGL_ECUDA, "kernel launch (kind %d): %s", kind, cudaGetErrorString(e));
+    return TDGL_OK;
+}
+
+// Record the launches issued by record() into a CUDA graph and instantiate it.  The launches are
+// not counted at capture time; *kernels receives how many each replay issues.
+template <class F>
+int capture_graph(tdgl_ctx *ctx, F record, cudaGraphExec_t *out, long *kernels) {
+    const long l0 = ctx->launches;
+    CK(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = record();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    *kernels = ctx->launches - l0;
+    ctx->launches = l0;
+    if (rc != TDGL_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    CK(ctx, e);
+    const cudaError_t e2 = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    CK(ctx, e2);
     return TDGL_OK;
 }
 
@@ -618,22 +646,45 @@ int steps_nosync(tdgl_sim *s, int n, double dt) {
     fill_desc(s, dt, s->terms);
     TRY(upload_desc(s));
     Work w = sim_work(s, elec);
-    int parity = 0;
     if (elec && s->xstate == XS_NONE) {
         TRY(launch_rows(ctx, MODE_XFWD, w, 0));
         s->xstate = XS_PHAT;
     }
-    for (int i = 0; i < n; ++i) {
-        if (elec && s->xstate == XS_PHAT) {
-            TRY(launch_conv(ctx, w));
-            s->xstate = XS_EHAT;
+    int i0 = 0;
+    if (elec && s->xstate == XS_EHAT) {   // the first step reuses the field spectrum already in X
+        if (n == 1) CK(ctx, cudaMemsetAsync(s->dmaxdp, 0, sizeof(unsigned), ctx->stream));
+        TRY(launch_rows(ctx, MODE_STEP, w, 0));
+        i0 = 1;
+    }
+    // steps i0..n-1 start from P-hat in X: convolution, then the row kernel with parity i & 1
+    auto record = [&]() -> int {
+        for (int i = i0; i < n; ++i) {
+            if (elec) TRY(launch_conv(ctx, w));
+            if (i == n - 1) CK(ctx, cudaMemsetAsync(s->dmaxdp, 0, sizeof(unsigned), ctx->stream));
+            TRY(launch_rows(ctx, MODE_STEP, w, i & 1));
         }
-        if (i == n - 1) CK(ctx, cudaMemsetAsync(s->dmaxdp, 0, sizeof(unsigned), ctx->stream));
-        TRY(launch_rows(ctx, MODE_STEP, w, parity));
-        parity ^= 1;
-        s->xstate = elec ? XS_PHAT : XS_NONE;
+        return TDGL_OK;
+    };
+    const int m = n - i0;
+    // repeated sequences replay a captured graph (the descriptor, read by the kernels from device
+    // memory, carries dt and the current P buffer); not while profiling
+    if (m >= 2 && !ctx->profiling && ctx->stream) {
+        tdgl_sim::GraphRec *G = nullptr;
+        for (auto &g : s->graphs)
+            if (g.n == m && g.elec == elec && g.p0 == (i0 & 1)) G = &g;
+        if (!G) {
+            tdgl_sim::GraphRec r{m, elec, i0 & 1, nullptr, 0};
+            TRY(capture_graph(ctx, record, &r.exec, &r.kernels));
+            s->graphs.push_back(r);
+            G = &s->graphs.back();
+        }
+        CK(ctx, cudaGraphLaunch(G->exec, ctx->stream));
+        ctx->launches += G->kernels;
+    } else if (m > 0) {
+        TRY(record());
     }
     if (n & 1) s->cur ^= 1;
+    s->xstate = elec ? XS_PHAT : XS_NONE;
     return TDGL_OK;
 }
 
@@ -793,7 +844,10 @@ void tdgl_sim_destroy(tdgl_sim *s) {
     if (s->batch) {   // leave the batch rather than dangle in it
         auto &bv = s->batch->sims;
         bv.erase(std::remove(bv.begin(), bv.end(), s), bv.end());
+        delete s->batch->cache;            // indices in the cached work lists changed
+        s->batch->cache = nullptr;
     }
+    for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
     void *ptrs[] = {s->dP[0], s->dP[1], s->dmat, s->dX, s->dY, s->dNhat, s->dtw, s->dcoef, s->dmaxdp,
                     s->dflag, s->denergy, s->dout, s->ddesc, s->d_rows, s->d_y, s->d_z};
     for (void *p : ptrs) cudaFree(p);
@@ -1057,6 +1111,7 @@ void tdgl_batch_destroy(tdgl_batch *b) {
     for (auto s : b->sims) s->batch = nullptr;
     auto &v = b->ctx->batches;
     v.erase(std::remove(v.begin(), v.end(), b), v.end());
+    delete b->cache;
     cudaFree(b->ddescs);
     cudaFree(b->d_items);
     delete b;
@@ -1065,25 +1120,42 @@ void tdgl_batch_destroy(tdgl_batch *b) {
 namespace {
 
 // build concatenated work lists over the active sims and run n steps of all of them
-int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const double *dt) {
-    tdgl_ctx *ctx = b->ctx;
-    std::vector<SimDev> descs(b->sims.size());
-    // row, y and z work grouped by transform length (one launch per length class)
-    std::vector<std::pair<int, std::vector<int4>>> rgr, ygr, zgr;
-    std::vector<size_t> rsm, ysm, zsm;
-    auto group_of = [](std::vector<std::pair<int, std::vector<int4>>> &g, std::vector<size_t> &sm, int N) -> size_t {
-        for (size_t i = 0; i < g.size(); ++i)
-            if (g[i].first == N) return i;
-        g.push_back({N, {}});
-        sm.push_back(0);
-        return g.size() - 1;
-    };
+}  // namespace
+
+// work lists and captured step sequences of a batch for one active set
+struct tdgl_batch::Cached {
     Work w;
+    struct G {
+        int n;
+        cudaGraphExec_t exec;
+        long kernels;
+    };
+    std::vector<G> graphs;
+    ~Cached() {
+        for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
+    }
+};
+
+namespace {
+
+using GroupList = std::vector<std::pair<int, std::vector<int4>>>;
+
+size_t group_of(GroupList &g, std::vector<size_t> &sm, int N) {
+    for (size_t i = 0; i < g.size(); ++i)
+        if (g[i].first == N) return i;
+    g.push_back({N, {}});
+    sm.push_back(0);
+    return g.size() - 1;
+}
+
+// concatenated work lists (row, y, z by transform length) of the active sims of a batch
+int build_batch_work(tdgl_batch *b, const std::vector<int> &active, Work &w) {
+    tdgl_ctx *ctx = b->ctx;
+    GroupList rgr, ygr, zgr;
+    std::vector<size_t> rsm, ysm, zsm;
     for (int idx : active) {
         tdgl_sim *s = b->sims[idx];
         const bool elec = (s->terms & TDGL_TERM_ELEC) != 0;
-        fill_desc(s, dt[idx], s->terms);
-        descs[idx] = s->desc;
         const size_t gr = group_of(rgr, rsm, s->xN);
         for (auto it : s->it_rows) rgr[gr].second.push_back(make_int4(idx, it.y, it.z, it.w));
         rsm[gr] = std::max(rsm[gr], smem_rows(s, s->rows_cnt_max));
@@ -1100,6 +1172,7 @@ int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const doub
     for (auto &g : ygr) tot += g.second.size();
     for (auto &g : zgr) tot += g.second.size();
     if (tot > b->items_cap) {
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
         cudaFree(b->d_items);
         b->d_items = nullptr;
         CK(ctx, cudaMalloc(&b->d_items, tot * sizeof(int4)));
@@ -1108,23 +1181,40 @@ int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const doub
     std::vector<int4> all;
     all.reserve(tot);
     w.descs = b->ddescs;
-    for (size_t i = 0; i < rgr.size(); ++i) {
-        w.rg.push_back(Group{rgr[i].first, b->d_items + all.size(), (int)rgr[i].second.size(), rsm[i]});
-        all.insert(all.end(), rgr[i].second.begin(), rgr[i].second.end());
-    }
-    for (size_t i = 0; i < ygr.size(); ++i) {
-        w.yg.push_back(Group{ygr[i].first, b->d_items + all.size(), (int)ygr[i].second.size(), ysm[i]});
-        all.insert(all.end(), ygr[i].second.begin(), ygr[i].second.end());
-    }
-    for (size_t i = 0; i < zgr.size(); ++i) {
-        w.zg.push_back(Group{zgr[i].first, b->d_items + all.size(), (int)zgr[i].second.size(), zsm[i]});
-        all.insert(all.end(), zgr[i].second.begin(), zgr[i].second.end());
-    }
+    auto emit = [&](GroupList &gl, std::vector<size_t> &sm, std::vector<Group> &out) {
+        for (size_t i = 0; i < gl.size(); ++i) {
+            out.push_back(Group{gl[i].first, b->d_items + all.size(), (int)gl[i].second.size(), sm[i]});
+            all.insert(all.end(), gl[i].second.begin(), gl[i].second.end());
+        }
+    };
+    emit(rgr, rsm, w.rg);
+    emit(ygr, ysm, w.yg);
+    emit(zgr, zsm, w.zg);
     CK(ctx, cudaMemcpyAsync(b->d_items, all.data(), tot * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));   // the host vector goes out of scope
+    return TDGL_OK;
+}
+
+// n steps of every active sim of a batch (one launch per kernel family and length class)
+int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const double *dt) {
+    tdgl_ctx *ctx = b->ctx;
+    std::vector<SimDev> descs(b->sims.size());
+    memset(descs.data(), 0, descs.size() * sizeof(SimDev));
+    for (int idx : active) {
+        fill_desc(b->sims[idx], dt[idx], b->sims[idx]->terms);
+        descs[idx] = b->sims[idx]->desc;
+    }
     CK(ctx, cudaMemcpyAsync(b->ddescs, descs.data(), descs.size() * sizeof(SimDev), cudaMemcpyHostToDevice, ctx->stream));
+    if (!b->cache || b->w_active != active) {
+        delete b->cache;
+        b->cache = new tdgl_batch::Cached();
+        b->w_active = active;
+        TRY(build_batch_work(b, active, b->cache->w));
+    }
+    const Work &w = b->cache->w;
     // prologue: sims whose x-spectrum is not P-hat of the current P get the x forward pass
     {
-        std::vector<std::pair<int, std::vector<int4>>> pgr;
+        GroupList pgr;
         std::vector<size_t> psm;
         size_t npro = 0;
         for (int idx : active) {
@@ -1154,13 +1244,29 @@ int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const doub
         }
     }
     for (int idx : active) CK(ctx, cudaMemsetAsync(b->sims[idx]->dflag, 0, sizeof(int), ctx->stream));
-    int parity = 0;
-    for (int i = 0; i < n; ++i) {
-        TRY(launch_conv(ctx, w));
-        if (i == n - 1)
-            for (int idx : active) CK(ctx, cudaMemsetAsync(b->sims[idx]->dmaxdp, 0, sizeof(unsigned), ctx->stream));
-        TRY(launch_rows(ctx, MODE_STEP, w, parity));
-        parity ^= 1;
+    auto record = [&]() -> int {
+        for (int i = 0; i < n; ++i) {
+            TRY(launch_conv(ctx, w));
+            if (i == n - 1)
+                for (int idx : active) CK(ctx, cudaMemsetAsync(b->sims[idx]->dmaxdp, 0, sizeof(unsigned), ctx->stream));
+            TRY(launch_rows(ctx, MODE_STEP, w, i & 1));
+        }
+        return TDGL_OK;
+    };
+    if (n >= 2 && !(n & 1) && !ctx->profiling && ctx->stream) {
+        tdgl_batch::Cached::G *G = nullptr;
+        for (auto &g : b->cache->graphs)
+            if (g.n == n) G = &g;
+        if (!G) {
+            tdgl_batch::Cached::G r{n, nullptr, 0};
+            TRY(capture_graph(ctx, record, &r.exec, &r.kernels));
+            b->cache->graphs.push_back(r);
+            G = &b->cache->graphs.back();
+        }
+        CK(ctx, cudaGraphLaunch(G->exec, ctx->stream));
+        ctx->launches += G->kernels;
+    } else {
+        TRY(record());
     }
     for (int idx : active) {
         tdgl_sim *s = b->sims[idx];

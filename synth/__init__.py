@@ -126,3 +126,25 @@ CONFIG2 = dict(shape=(128, 128, 128), cell=(1e-9, 1e-9, 1e-9), seed=2, amp=0.01,
 CONFIG4 = dict(shape=(256, 256, 64), cell=(1e-9, 1e-9, 1e-9), seed=4, amp=0.01, eps_b=649.0,
                T=300.0, layers=[(0, 32, 2), (32, 64, 1)], radius=20,
                fields=[2e8 - 1e7 * i for i in range(41)] + [-1.9e8 + 1e7 * i for i in range(40)])
+
+
+def rhombohedral_start(shape_xyz, p, noise, seed) -> np.ndarray:
+    """Uniform P along [111] with magnitude p plus uniform noise in [-noise, noise] (heating branch)."""
+    P = uniform_P(shape_xyz, noise, seed, np.float64)
+    P += p / np.sqrt(3.0)
+    return P.astype(np.float32)
+
+
+def sweep_members(n=48, tmin=180.0, tmax=450.0, seed=0) -> list:
+    """Members of the uneven temperature sweep: n/2 temperatures evenly spread in [tmin, tmax],
+    a cooling branch (random start) and a heating branch ([111] start), cube edges from
+    batch_sizes(n, seed=seed)."""
+    sizes = batch_sizes(n, seed=seed)
+    half = n // 2
+    temps = [tmin + (tmax - tmin) * i / max(half - 1, 1) for i in range(half)]
+    out = []
+    for b, branch in enumerate(("cooling", "heating")):
+        for i, T in enumerate(temps):
+            k = b * half + i
+            out.append(dict(L=sizes[k], T=T, branch=branch, seed=100 + k))
+    return out

@@ -183,3 +183,24 @@ def test_full_size_field_and_step_at_sampled_cells(ctx, workload):
     gotp = np.array([Pn[:, z, y, x] for (x, y, z) in cells])
     dP = np.abs(want - np.array([P[:, z, y, x] for (x, y, z) in cells])).max()
     assert np.abs(gotp - want).max() <= 3e-5 * dP + 1e-7 * g.scales()[0]
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 8), (24, 12, 20), (16, 16, 16)])
+def test_steps_interleaved_with_energy_and_field_reads(ctx, shape):
+    # energy() and get_field() leave the field spectrum in place; the next step must reuse it
+    # and chunks of any length (graph replays included) must follow the oracle trajectory
+    nx, ny, nz = shape
+    mat = np.ones((nz, ny, nx), np.uint8)
+    P = synth.uniform_P(shape, 0.05, 21)
+    g = gpu_sim(ctx, shape, (1e-9,) * 3, mat, {1: synth.BTO}, 300.0, 45.0, P=P)
+    o = oracle_sys(shape, (1e-9,) * 3, mat, {1: synth.BTO}, 300.0, 45.0)
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    Po = P.astype(np.float64)
+    for n, probe in [(8, "energy"), (5, "field"), (16, "energy"), (1, "energy"), (2, None), (16, None)]:
+        g.step(n, dt)
+        Po = o.run(Po, dt, n)
+        if probe == "energy":
+            g.energy()
+        elif probe == "field":
+            g.get_field(15)
+    assert np.abs(g.get_P() - Po).max() / g.scales()[0] <= 1e-5

@@ -25,7 +25,9 @@ def _bto(ctx, shape, T=300.0, seed=1, eps_b=45.0):
     return gpu_sim(ctx, shape, (1e-9,) * 3, mat, {1: synth.BTO}, T, eps_b, P=P), P
 
 
-def test_batch_equals_single_runs_bitwise(ctx):
+@pytest.mark.parametrize("nsteps", [7, 16])
+def test_batch_equals_single_runs_bitwise(ctx, nsteps):
+    # odd counts run launch by launch, even counts replay captured graphs
     from paper_2605_28800_b300 import tdgl
     shapes = [(16, 16, 16), (12, 20, 8), (9, 7, 5), (32, 8, 4)]
     temps = [300.0, 250.0, 350.0, 200.0]
@@ -37,9 +39,14 @@ def test_batch_equals_single_runs_bitwise(ctx):
         singles.append(a)
         batched.append(b)
     for a, d in zip(singles, dt):
-        a.step(7, d)
+        a.step(nsteps, d)
+        a.energy()
+        a.step(nsteps, d)
     B = tdgl.Batch(ctx, batched)
-    B.step(7, dt)
+    B.step(nsteps, dt)
+    for b in batched:
+        b.energy()
+    B.step(nsteps, dt)
     for a, b in zip(singles, batched):
         assert np.array_equal(a.get_P(), b.get_P())
     B.close()
