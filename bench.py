@@ -115,6 +115,23 @@ def ncu_traffic(kernel, wl):
         return None
 
 
+# ---- multi-rank bookkeeping (one independent replica per rank) ---------------------------------
+def max_over_ranks(x, device):
+    """Max of a per-rank float over all ranks of the default process group (x if none)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, world, seconds_max):
+    """Whole-job throughput: units processed by all ranks over the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 # ---- clocks during the timed region ------------------------------------------------------------
 class ClockSampler:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -218,11 +235,7 @@ def gpu_arm(args, rank, world):
     launches = ctx.launch_count - l0
     prof = {tdgl.KERNEL_NAMES[k]: ctx.profile_read(k) for k in range(6)}
     ctx.profile(False)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, "cuda")
     # end to end through the C ABI with host buffers
     Ph = torch.from_numpy(np.ascontiguousarray(wl["P"])).pin_memory()
     e2e_steps = max(4, min(args.steps, 64))
@@ -234,9 +247,9 @@ def gpu_arm(args, rank, world):
         s.set_P(Ph)
         s.step(1, dt)       # returns after reading the step's max|dP| and divergence flag
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
     return dict(ms=ms, launches=launches, prof=prof, clocks=clk.summary(), ncell=ncell, wl=wl,
-                e2e=ncell * e2e_steps / e2e_s * world, e2e_h2d=Ph.numel() * 4)
+                e2e=aggregate_rate(ncell * e2e_steps, world, e2e_s), e2e_h2d=Ph.numel() * 4)
 
 
 # ---- CPU oracle ----------------------------------------------------------------------------------
@@ -365,7 +378,7 @@ def main():
             dist.destroy_process_group()
         return
     hbm, peak_kind = peaks()
-    value = ncell * args.steps * world / (r["ms"] * 1e-3)
+    value = aggregate_rate(ncell * args.steps, world, r["ms"] * 1e-3)
     kb, M = kernel_bytes(wl["shape"])
     prof = {k: v for k, v in r["prof"].items() if k in kb and v[1] > 0}
     dom = max(prof, key=lambda k: prof[k][0]) if prof else None
