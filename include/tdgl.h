@@ -120,6 +120,23 @@ int tdgl_set_temperature(tdgl_sim *sim, double T);
 /* Uniform applied field E_ext of Eq. 7, V/m.  Default 0. */
 int tdgl_set_field(tdgl_sim *sim, double Ex, double Ey, double Ez);
 
+/* Time-dependent excitation (Sec. 3 "time-dependent external excitations"; Sec. 4.4 AC loops):
+ * the applied field becomes E_ext(t) = (Ex, Ey, Ez) + (Ax, Ay, Az) sin(2 pi freq_hz t + phase), V/m,
+ * evaluated at the time of each step (t advances by dt per step; explicit Euler uses E_ext(t_n)).
+ * Amplitude 0 (the default) turns it off. */
+int tdgl_set_field_ac(tdgl_sim *sim, double Ax, double Ay, double Az, double freq_hz, double phase);
+/* Time integrator of Eq. 1 (Sec. 3 lists Heun, RK45 and AB3M2):
+ *   TDGL_EULER (default)  P <- P + dt h(P, t)
+ *   TDGL_HEUN             P~ = P + dt h(P, t);  P <- P + dt/2 (h(P, t) + h(P~, t + dt))
+ * Heun costs two field evaluations per step and 12 bytes per cell of device memory.  The sims of
+ * a batch must use one integrator. */
+#define TDGL_EULER 0
+#define TDGL_HEUN  1
+int tdgl_set_integrator(tdgl_sim *sim, int method);
+/* Simulated time t (s) of the sim: 0 at creation, advanced by n dt by every step call. */
+int tdgl_set_time(tdgl_sim *sim, double t);
+int tdgl_get_time(tdgl_sim *sim, double *t);
+
 /* Internal normalization (Table 2): P* = P/P0, tau = alpha_ref L t, E* = E/(alpha_ref P0).
  * Defaults, fixed at the first step unless set here: alpha_ref = |alpha1| of the lowest defined
  * material id at 300 K; P0 = that material's tetragonal spontaneous polarization at 300 K
@@ -140,7 +157,8 @@ int tdgl_init_random(tdgl_sim *sim, uint64_t seed, double amp);
  * [3][nz][ny][nx], zero on vacuum cells): h_Land, h_Grad, E_el, E_ext of Eqs. 3-7. */
 int tdgl_get_field(tdgl_sim *sim, unsigned mask, float *out, int where);
 
-/* n >= 0 forward Euler steps of Eq. 1 with time step dt (seconds, > 0).  Returns
+/* n >= 0 steps of Eq. 1 (forward Euler unless tdgl_set_integrator chose Heun) with time step dt
+ * (seconds, > 0).  Returns
  * TDGL_EDIVERGED (state left as computed) if any step produced NaN or |P_i| > 1e3 P0. */
 int tdgl_step(tdgl_sim *sim, int n, double dt);
 /* max over cells and components of |P_new - P_old| of the most recent step, in units of P0. */

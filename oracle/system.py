@@ -1,7 +1,8 @@
 """ORACLE (test infrastructure).  Total field, energies and the explicit TDGL step.
 
 Eq. 2: F = F_Land + F_Grad + F_Elec + F_Ext; Eq. 7: F_Ext = -int E_ext . P, so the external
-field enters the effective field as +E_ext.  Eq. 1 with L = 1 (Sec. 2), integrated with the
+field enters the effective field as +E_ext.  A time-dependent excitation (Sec. 3; the AC loops of
+Sec. 4.4) is E_ext(t) = E_ext + E_ac sin(2 pi f t + phase), taken at the time of each step.  Eq. 1 with L = 1 (Sec. 2), integrated with the
 forward Euler rule (the simplest of the explicit schemes named in Sec. 3):
     P <- P + dt * L * (h_Land + h_Grad + E_el + E_ext)      on material cells;
 vacuum cells keep P = 0 (Sec. 2: P = 0 outside the sample).
@@ -29,7 +30,8 @@ class System:
     """
 
     def __init__(self, shape, cell, mat, materials, T, eps_b=1.0, E_ext=(0.0, 0.0, 0.0),
-                 terms=TERM_ALL, conv="fft", octant=None, L=1.0):
+                 terms=TERM_ALL, conv="fft", octant=None, L=1.0, E_ac=(0.0, 0.0, 0.0), freq=0.0,
+                 phase=0.0):
         self.shape = tuple(int(v) for v in shape)
         self.cell = tuple(float(v) for v in cell)
         nx, ny, nz = self.shape
@@ -38,6 +40,8 @@ class System:
         self.materials = dict(materials)
         self.eps_b = float(eps_b)
         self.E_ext = np.asarray(E_ext, dtype=np.float64).reshape(3)
+        self.E_ac = np.asarray(E_ac, dtype=np.float64).reshape(3)
+        self.freq, self.phase = float(freq), float(phase)
         self.terms = int(terms)
         self.L = float(L)
         self.V = self.cell[0] * self.cell[1] * self.cell[2]
@@ -64,6 +68,10 @@ class System:
             self._octant = _tensor.octant(self.shape, self.cell)
         return self._octant
 
+    def applied_field(self, t=0.0):
+        """E_ext(t), V/m (3,)."""
+        return self.E_ext + self.E_ac * np.sin(2.0 * np.pi * self.freq * t + self.phase)
+
     # -- fields -----------------------------------------------------------------------------
     def electrostatic_field(self, P):
         P = np.asarray(P, dtype=np.float64)
@@ -75,8 +83,8 @@ class System:
             self._convolver = _es.FFTConvolver(self.shape, self.cell, self._tensor_octant())
         return self._convolver.apply(P, self.eps_b)
 
-    def fields(self, P):
-        """Dict of the four field contributions and their sum, each (3, nz, ny, nx), V/m."""
+    def fields(self, P, t=0.0):
+        """Dict of the four field contributions and their sum at time t, each (3, nz, ny, nx), V/m."""
         P = np.asarray(P, dtype=np.float64)
         z = np.zeros(P.shape)
         out = {"landau": z, "grad": z, "elec": z, "ext": z}
@@ -87,12 +95,12 @@ class System:
         if self.terms & TERM_ELEC:
             out["elec"] = self.electrostatic_field(P)
         if self.terms & TERM_EXT:
-            out["ext"] = np.where(self.m, self.E_ext[:, None, None, None], 0.0)
+            out["ext"] = np.where(self.m, self.applied_field(t)[:, None, None, None], 0.0)
         out["total"] = np.where(self.m, out["landau"] + out["grad"] + out["elec"] + out["ext"], 0.0)
         return out
 
-    def energy(self, P):
-        """Energy terms of Eq. 2 in joules: land, grad, elec, ext, total."""
+    def energy(self, P, t=0.0):
+        """Energy terms of Eq. 2 in joules at time t: land, grad, elec, ext, total."""
         P = np.asarray(P, dtype=np.float64)
         e = dict(land=0.0, grad=0.0, elec=0.0, ext=0.0)
         if self.terms & TERM_LANDAU:
@@ -102,20 +110,30 @@ class System:
         if self.terms & TERM_ELEC:
             e["elec"] = _es.energy(self.electrostatic_field(P), P, self.V)
         if self.terms & TERM_EXT:
-            e["ext"] = -self.V * float(np.sum(np.where(self.m, np.tensordot(self.E_ext, P, 1), 0.0)))
+            e["ext"] = -self.V * float(np.sum(np.where(self.m, np.tensordot(self.applied_field(t), P, 1), 0.0)))
         e["total"] = e["land"] + e["grad"] + e["elec"] + e["ext"]
         return e
 
     # -- dynamics ---------------------------------------------------------------------------
-    def step(self, P, dt):
-        """One forward Euler step of Eq. 1; returns the new P (float64)."""
+    def step(self, P, dt, t=0.0):
+        """One forward Euler step of Eq. 1 from time t; returns the new P (float64)."""
         P = np.asarray(P, dtype=np.float64)
-        Pn = P + dt * self.L * self.fields(P)["total"]
+        Pn = P + dt * self.L * self.fields(P, t)["total"]
         return np.where(self.m, Pn, 0.0)
 
-    def run(self, P, dt, n):
-        for _ in range(n):
-            P = self.step(P, dt)
+    def heun_step(self, P, dt, t=0.0):
+        """One step of Heun's method (Sec. 3): predictor P~ = P + dt h(P, t), then
+        P + dt/2 (h(P, t) + h(P~, t + dt))."""
+        P = np.asarray(P, dtype=np.float64)
+        h0 = self.fields(P, t)["total"]
+        Pt = np.where(self.m, P + dt * self.L * h0, 0.0)
+        h1 = self.fields(Pt, t + dt)["total"]
+        return np.where(self.m, P + 0.5 * dt * self.L * (h0 + h1), 0.0)
+
+    def run(self, P, dt, n, t0=0.0, method="euler"):
+        f = self.heun_step if method == "heun" else self.step
+        for i in range(n):
+            P = f(P, dt, t0 + i * dt)
         return P
 
     def relax(self, P, dt, tol, P0, max_steps, check_every=16):

@@ -43,7 +43,9 @@ struct SimDev {
     float inv_d2[3];          // 1/dx*^2
     float inv_2d[3];          // 1/(2 dx*)
     float dt;                 // alpha_ref L dt
-    float eext[3];            // E_ext / (alpha_ref P0)
+    float eext[3];            // E_ext / (alpha_ref P0), static part
+    float eac[3];             // amplitude of the sinusoidal part, normalized like eext
+    double ac_ph0, ac_dph;    // its phase at the first step of the call and per step
     float escale;             // -1/(eps0 epsB alpha_ref) / (Mx My Mz)
     float pmax;               // divergence bound on |P*_i|
     unsigned terms;
@@ -52,6 +54,7 @@ struct SimDev {
     int *flag;                // bit 0: divergence
     double *energy;           // [4] land grad elec ext, normalized (times alpha_ref P0^2 V -> J)
     float *out;               // field readback [3][ncell]
+    float *hbuf;              // Heun: field of the predictor's starting point [3][ncell]
     float out_scale;          // alpha_ref P0
 };
 
@@ -60,7 +63,11 @@ struct SimDev {
 //   y kernels:    y = c*nz + z, z = kx0, w = kx count
 //   z kernel:     y = ky, z = kx0, w = kx count
 
-enum { MODE_STEP = 0, MODE_FIELD = 1, MODE_ENERGY = 2, MODE_XFWD = 3 };
+// STEP: forward Euler.  HEUN1 / HEUN2: predictor and corrector of Heun's method (Sec. 3):
+//   HEUN1  P~ = P + dt h(P), keeps h(P) in S.hbuf, writes P~ to the other buffer;
+//   HEUN2  P <- P + dt/2 (h(P) + h(P~)) in place, with the field evaluated on P~.
+enum { MODE_STEP = 0, MODE_FIELD = 1, MODE_ENERGY = 2, MODE_XFWD = 3, MODE_HEUN1 = 4, MODE_HEUN2 = 5 };
+__host__ __device__ constexpr bool mode_updates(int m) { return m == MODE_STEP || m == MODE_HEUN1 || m == MODE_HEUN2; }
 
 __device__ __forceinline__ int row_ld(const SimDev &S) { return S.hx + 2; }
 
@@ -91,6 +98,14 @@ __device__ __forceinline__ double landau_energy(const float *pf, const float *c)
          + (double)c[5] * (x2 * x2 * x2 + y2 * y2 * y2 + z2 * z2 * z2)
          + (double)c[6] * (x2 * x2 * (y2 + z2) + y2 * y2 * (x2 + z2) + z2 * z2 * (x2 + y2))
          + (double)c[7] * x2 * y2 * z2;
+}
+
+// applied field of Eq. 7 at step istep of the call: static part plus A sin(phase)
+__device__ __forceinline__ void ext_field(const SimDev &S, int istep, float *e) {
+    float s = 0.f;
+    if (S.eac[0] != 0.f || S.eac[1] != 0.f || S.eac[2] != 0.f) s = (float)sin(S.ac_ph0 + istep * S.ac_dph);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) e[c] = fmaf(S.eac[c], s, S.eext[c]);
 }
 
 // ---- neighbourhood access with the free-surface rules of the discrete Eq. 4 ----------------
@@ -234,7 +249,7 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 // smem: bufA, bufB each [3][cnt][ld] float2 with ld = hx + 2; coefficient table; reduction.
 template <int MODE>
 __global__ void __launch_bounds__(NTHREADS) k_rows(const SimDev *__restrict__ sims, const int4 *__restrict__ items,
-                                                   int parity) {
+                                                   int istep) {
     extern __shared__ float4 smem4[];
     __shared__ float s_coef[MAXMAT * NCOEF];
     __shared__ double s_red[NTHREADS / 32];
@@ -249,10 +264,14 @@ __global__ void __launch_bounds__(NTHREADS) k_rows(const SimDev *__restrict__ si
     float2 *bufB = bufA + nl * ld;
     for (int i = tid; i < MAXMAT * NCOEF; i += nthr) s_coef[i] = S.coef[i];
     if (tid == 0) s_max = 0.f;
-    const float *Pc = S.P[parity];
-    float *Pn = S.P[parity ^ 1];
+    const int parity = istep & 1;      // istep: step index within the call
+    // HEUN2 evaluates the field on the predictor (other buffer) and updates P in place
+    const float *Pc = (MODE == MODE_HEUN2) ? S.P[parity ^ 1] : S.P[parity];
+    float *Pn = (MODE == MODE_HEUN2) ? S.P[parity] : S.P[parity ^ 1];
     const bool elec = (S.terms & TERM_ELEC) != 0;
     const int nx = S.nx, hx = S.hx;
+    float eext[3];
+    ext_field(S, istep, eext);
     const float2 *twr = S.tw + S.twr;
 
     float *Erow = nullptr;   // float view: line l holds E*_c of row r at [l*2*ld + x]
@@ -301,7 +320,7 @@ __global__ void __launch_bounds__(NTHREADS) k_rows(const SimDev *__restrict__ si
             const long id = cidx(S, x, y, z);
             const int m = __ldg(&S.mat[id]);
             if (m == 0) {
-                if (MODE == MODE_STEP) {
+                if (mode_updates(MODE)) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) { Pn[c * S.ncell + id] = 0.f; Q[(c * cnt + r) * 2 * ld + x] = 0.f; }
                 } else if (MODE == MODE_FIELD) {
@@ -320,7 +339,7 @@ __global__ void __launch_bounds__(NTHREADS) k_rows(const SimDev *__restrict__ si
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     if (elec) e_elec += -0.5 * (double)Erow[(c * cnt + r) * 2 * ld + x] * p[c];
-                    if (S.terms & TERM_EXT) e_ext += -(double)S.eext[c] * p[c];
+                    if (S.terms & TERM_EXT) e_ext += -(double)eext[c] * p[c];
                 }
                 continue;
             }
@@ -332,7 +351,7 @@ __global__ void __launch_bounds__(NTHREADS) k_rows(const SimDev *__restrict__ si
             }
             if (S.terms & TERM_EXT) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) h[c] += S.eext[c];
+                for (int c = 0; c < 3; ++c) h[c] += eext[c];
             }
             if (MODE == MODE_FIELD) {
 #pragma unroll
@@ -341,8 +360,15 @@ __global__ void __launch_bounds__(NTHREADS) k_rows(const SimDev *__restrict__ si
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float pn = fmaf(S.dt, h[c], p[c]);
-                lmax = fmaxf(lmax, fabsf(pn - p[c]));
+                float pn, p0 = p[c];
+                if (MODE == MODE_HEUN2) {
+                    p0 = Pn[c * S.ncell + id];
+                    pn = fmaf(0.5f * S.dt, S.hbuf[c * S.ncell + id] + h[c], p0);
+                } else {
+                    pn = fmaf(S.dt, h[c], p0);
+                    if (MODE == MODE_HEUN1) S.hbuf[c * S.ncell + id] = h[c];
+                }
+                if (MODE != MODE_HEUN1) lmax = fmaxf(lmax, fabsf(pn - p0));
                 bad |= !(fabsf(pn) <= S.pmax);
                 Pn[c * S.ncell + id] = pn;
                 Q[(c * cnt + r) * 2 * ld + x] = pn;
@@ -358,13 +384,13 @@ __global__ void __launch_bounds__(NTHREADS) k_rows(const SimDev *__restrict__ si
         return;
     }
     if (MODE == MODE_FIELD) return;
-    if (MODE == MODE_STEP) {
+    if (mode_updates(MODE)) {
         for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
         if ((tid & 31) == 0) atomicMax(reinterpret_cast<unsigned *>(&s_max), __float_as_uint(lmax));
         if (bad) atomicOr(S.flag, 1);
     }
     if (!elec) {
-        if (MODE == MODE_STEP) {
+        if (mode_updates(MODE)) {
             __syncthreads();
             if (tid == 0) atomicMax(S.maxdp, __float_as_uint(s_max));
         }
@@ -377,7 +403,7 @@ __global__ void __launch_bounds__(NTHREADS) k_rows(const SimDev *__restrict__ si
         Q[l * 2 * ld + x] = 0.f;
     }
     __syncthreads();
-    if (MODE == MODE_STEP && tid == 0) atomicMax(S.maxdp, __float_as_uint(s_max));
+    if (mode_updates(MODE) && tid == 0) atomicMax(S.maxdp, __float_as_uint(s_max));
     float2 *res = fft_lines<false>(Qbuf, Wbuf, S.px, nl, ld, S.tw, tid, nthr);
     for (int w = tid; w < nl * S.Kx; w += nthr) {
         const int l = w / S.Kx, k = w - l * S.Kx;

@@ -195,7 +195,7 @@ __device__ __forceinline__ float tgrad_energy(const TV &V, const SimDev &S, cons
 
 template <int MODE, int HX>
 __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, const int4 *__restrict__ items,
-                                               int parity) {
+                                               int istep) {
     constexpr int E = rf::Cfg<HX>::E, T = HX / E, LDP = xrows_ldp<HX>();
     constexpr int nx = HX, TYmax = xrows_tile<HX>(), TYH = TYmax + 2, nthr = xrows_threads<HX>();
     extern __shared__ float4 smem4[];
@@ -217,9 +217,13 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
     constexpr int rf_ = xrows_region<HX>();                     // floats, multiple of 4
     float *Eb = Pt + rf_;
     uint8_t *Mt = reinterpret_cast<uint8_t *>(Eb + 3 * TYmax * nx);
-    const float *Pc = S.P[parity];
-    float *Pn = S.P[parity ^ 1];
+    const int parity = istep & 1;      // istep: step index within the call
+    // HEUN2 evaluates the field on the predictor (other buffer) and updates P in place
+    const float *Pc = (MODE == MODE_HEUN2) ? S.P[parity ^ 1] : S.P[parity];
+    float *Pn = (MODE == MODE_HEUN2) ? S.P[parity] : S.P[parity ^ 1];
     const bool elec = (S.terms & TERM_ELEC) != 0;
+    float eext[3];
+    ext_field(S, istep, eext);
     for (int i = tid; i < MAXMAT * NCOEF; i += nthr) s_coef[i] = S.coef[i];
     for (int i = tid; i < HX; i += nthr) s_tw[i] = S.tw[S.px.tw + i];
     for (int i = tid; i <= HX; i += nthr) s_twr[i] = S.tw[S.twr + i];
@@ -306,7 +310,7 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
             const long id = ((long)z * ny + y0 + r) * nx + x;
             const int m = V.m(1, py, x);
             if (m == 0) {
-                if (MODE == MODE_STEP) {
+                if (mode_updates(MODE)) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) { Pn[c * S.ncell + id] = 0.f; Eb[(c * TYmax + r) * nx + x] = 0.f; }
                 } else if (MODE == MODE_FIELD) {
@@ -334,7 +338,7 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     if (elec) el = fmaf(-0.5f * Eb[(c * TYmax + r) * nx + x], p[c], el);
-                    if (S.terms & TERM_EXT) ex = fmaf(-S.eext[c], p[c], ex);
+                    if (S.terms & TERM_EXT) ex = fmaf(-eext[c], p[c], ex);
                 }
                 e_elec += (double)el;
                 e_ext += (double)ex;
@@ -348,7 +352,7 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
             }
             if (S.terms & TERM_EXT) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) h[c] += S.eext[c];
+                for (int c = 0; c < 3; ++c) h[c] += eext[c];
             }
             if (MODE == MODE_FIELD) {
 #pragma unroll
@@ -357,8 +361,15 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float pn = fmaf(S.dt, h[c], p[c]);
-                lmax = fmaxf(lmax, fabsf(pn - p[c]));
+                float pn, p0 = p[c];
+                if (MODE == MODE_HEUN2) {
+                    p0 = Pn[c * S.ncell + id];
+                    pn = fmaf(0.5f * S.dt, S.hbuf[c * S.ncell + id] + h[c], p0);
+                } else {
+                    pn = fmaf(S.dt, h[c], p0);
+                    if (MODE == MODE_HEUN1) S.hbuf[c * S.ncell + id] = h[c];
+                }
+                if (MODE != MODE_HEUN1) lmax = fmaxf(lmax, fabsf(pn - p0));
                 bad |= !(fabsf(pn) <= S.pmax);
                 Pn[c * S.ncell + id] = pn;
                 Eb[(c * TYmax + r) * nx + x] = pn;      // the cell's own slot: E read above, new P kept
@@ -374,7 +385,7 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
         return;
     }
     if (MODE == MODE_FIELD) return;
-    if (MODE == MODE_STEP) {
+    if (mode_updates(MODE)) {
         for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
         if ((tid & 31) == 0) atomicMax(&s_max, __float_as_uint(lmax));
         if (bad) atomicOr(S.flag, 1);

@@ -62,6 +62,10 @@ struct tdgl_sim {
     bool defined[TDGL_MAX_MATERIALS] = {false};
     std::vector<uint8_t> map;
     double T = 300.0, eps_b = 1.0, E[3] = {0, 0, 0};
+    double Eac[3] = {0, 0, 0}, ac_freq = 0.0, ac_phase = 0.0;   // E_ext(t) = E + Eac sin(2 pi f t + phase)
+    double time = 0.0;                                          // simulated time, s
+    int integrator = TDGL_EULER;
+    float *dhbuf = nullptr;                                     // Heun: first field evaluation
     unsigned terms = TDGL_TERM_ALL;
     double P0 = 1.0, alpha_ref = 1.0;
     bool scales_fixed = false;
@@ -91,7 +95,7 @@ struct tdgl_sim {
     bool spectra_alloc = false, tensor_ready = false;
     bool has_cross = false;
     bool dirty = true;      // map, materials, T or scales changed since the last prepare()
-    struct GraphRec { int n; bool elec; int p0; cudaGraphExec_t exec; long kernels; };
+    struct GraphRec { int n; bool elec; int p0; int integ; cudaGraphExec_t exec; long kernels; };
     std::vector<GraphRec> graphs;   // captured steady step sequences
     double last_maxdp = 0.0;
     tdgl_batch *batch = nullptr;
@@ -485,7 +489,13 @@ void fill_desc(tdgl_sim *s, double dt, unsigned terms) {
         D.inv_d2[a] = (float)(1.0 / (h * h));
         D.inv_2d[a] = (float)(1.0 / (2.0 * h));
         D.eext[a] = (float)(s->E[a] / (s->alpha_ref * s->P0));
+        D.eac[a] = (float)(s->Eac[a] / (s->alpha_ref * s->P0));
     }
+    D.ac_ph0 = 2.0 * M_PI * s->ac_freq * s->time + s->ac_phase;
+    // phase per unit of the launch index: Euler step i uses index i; Heun's predictor and
+    // corrector of step i use 2i and 2i + 2 (times t_i and t_i + dt)
+    D.ac_dph = 2.0 * M_PI * s->ac_freq * dt / (s->integrator == TDGL_HEUN ? 2.0 : 1.0);
+    D.hbuf = s->dhbuf;
     D.dt = (float)(s->alpha_ref * dt);
     D.escale = (float)(-1.0 / (kEps0 * s->eps_b * s->alpha_ref) / ((double)s->Mx * s->My * s->Mz));
     D.pmax = 1e3f;
@@ -551,12 +561,14 @@ void rows_launch(const Group &g, const SimDev *d, cudaStream_t st, int parity) {
 }
 
 int launch_rows(tdgl_ctx *ctx, int mode, const Work &w, int parity) {
-    const int kind = (mode == MODE_XFWD) ? TDGL_K_XFWD : (mode == MODE_STEP ? TDGL_K_STEP : TDGL_K_OTHER);
+    const int kind = (mode == MODE_XFWD) ? TDGL_K_XFWD : (mode_updates(mode) ? TDGL_K_STEP : TDGL_K_OTHER);
     for (const Group &g : w.rg) {
         if (g.n == 0) continue;
         TRY(launch(ctx, kind, [&] {
             switch (mode) {
                 case MODE_STEP: rows_launch<MODE_STEP>(g, w.descs, ctx->stream, parity); break;
+                case MODE_HEUN1: rows_launch<MODE_HEUN1>(g, w.descs, ctx->stream, parity); break;
+                case MODE_HEUN2: rows_launch<MODE_HEUN2>(g, w.descs, ctx->stream, parity); break;
                 case MODE_FIELD: rows_launch<MODE_FIELD>(g, w.descs, ctx->stream, parity); break;
                 case MODE_ENERGY: rows_launch<MODE_ENERGY>(g, w.descs, ctx->stream, parity); break;
                 default: rows_launch<MODE_XFWD>(g, w.descs, ctx->stream, parity); break;
@@ -650,18 +662,34 @@ int steps_nosync(tdgl_sim *s, int n, double dt) {
         TRY(launch_rows(ctx, MODE_XFWD, w, 0));
         s->xstate = XS_PHAT;
     }
+    const bool heun = s->integrator == TDGL_HEUN;
     int i0 = 0;
     if (elec && s->xstate == XS_EHAT) {   // the first step reuses the field spectrum already in X
         if (n == 1) CK(ctx, cudaMemsetAsync(s->dmaxdp, 0, sizeof(unsigned), ctx->stream));
-        TRY(launch_rows(ctx, MODE_STEP, w, 0));
+        if (heun) {
+            TRY(launch_rows(ctx, MODE_HEUN1, w, 0));
+            TRY(launch_conv(ctx, w));
+            TRY(launch_rows(ctx, MODE_HEUN2, w, 2));
+        } else {
+            TRY(launch_rows(ctx, MODE_STEP, w, 0));
+        }
         i0 = 1;
     }
-    // steps i0..n-1 start from P-hat in X: convolution, then the row kernel with parity i & 1
+    // steps i0..n-1 start from P-hat in X.  Euler: convolution, row kernel (launch index i,
+    // parity i & 1).  Heun: predictor on P (index 2i), convolution of the predictor, corrector
+    // (index 2i + 2); P stays in the same buffer.
     auto record = [&]() -> int {
         for (int i = i0; i < n; ++i) {
             if (elec) TRY(launch_conv(ctx, w));
-            if (i == n - 1) CK(ctx, cudaMemsetAsync(s->dmaxdp, 0, sizeof(unsigned), ctx->stream));
-            TRY(launch_rows(ctx, MODE_STEP, w, i & 1));
+            if (heun) {
+                TRY(launch_rows(ctx, MODE_HEUN1, w, 2 * i));
+                if (elec) TRY(launch_conv(ctx, w));
+                if (i == n - 1) CK(ctx, cudaMemsetAsync(s->dmaxdp, 0, sizeof(unsigned), ctx->stream));
+                TRY(launch_rows(ctx, MODE_HEUN2, w, 2 * i + 2));
+            } else {
+                if (i == n - 1) CK(ctx, cudaMemsetAsync(s->dmaxdp, 0, sizeof(unsigned), ctx->stream));
+                TRY(launch_rows(ctx, MODE_STEP, w, i));
+            }
         }
         return TDGL_OK;
     };
@@ -670,10 +698,11 @@ int steps_nosync(tdgl_sim *s, int n, double dt) {
     // memory, carries dt and the current P buffer); not while profiling
     if (m >= 2 && !ctx->profiling && ctx->stream) {
         tdgl_sim::GraphRec *G = nullptr;
+        const int p0 = heun ? 0 : (i0 & 1);
         for (auto &g : s->graphs)
-            if (g.n == m && g.elec == elec && g.p0 == (i0 & 1)) G = &g;
+            if (g.n == m && g.elec == elec && g.p0 == p0 && g.integ == s->integrator) G = &g;
         if (!G) {
-            tdgl_sim::GraphRec r{m, elec, i0 & 1, nullptr, 0};
+            tdgl_sim::GraphRec r{m, elec, p0, s->integrator, nullptr, 0};
             TRY(capture_graph(ctx, record, &r.exec, &r.kernels));
             s->graphs.push_back(r);
             G = &s->graphs.back();
@@ -683,8 +712,9 @@ int steps_nosync(tdgl_sim *s, int n, double dt) {
     } else if (m > 0) {
         TRY(record());
     }
-    if (n & 1) s->cur ^= 1;
+    if ((n & 1) && !heun) s->cur ^= 1;
     s->xstate = elec ? XS_PHAT : XS_NONE;
+    s->time += n * dt;
     return TDGL_OK;
 }
 
@@ -731,6 +761,8 @@ int tdgl_ctx_create(tdgl_ctx **out, int device, void *stream) {
     cudaFuncSetAttribute(k_rows<MODE_FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     cudaFuncSetAttribute(k_rows<MODE_ENERGY>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     cudaFuncSetAttribute(k_rows<MODE_XFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(k_rows<MODE_HEUN1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(k_rows<MODE_HEUN2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     cudaFuncSetAttribute(k_yfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     cudaFuncSetAttribute(k_yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     cudaFuncSetAttribute(k_zconv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
@@ -738,7 +770,9 @@ int tdgl_ctx_create(tdgl_ctx **out, int device, void *stream) {
     cudaFuncSetAttribute(k_xrows<MODE_STEP, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);   \
     cudaFuncSetAttribute(k_xrows<MODE_FIELD, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);  \
     cudaFuncSetAttribute(k_xrows<MODE_ENERGY, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem); \
-    cudaFuncSetAttribute(k_xrows<MODE_XFWD, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(k_xrows<MODE_XFWD, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);   \
+    cudaFuncSetAttribute(k_xrows<MODE_HEUN1, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);  \
+    cudaFuncSetAttribute(k_xrows<MODE_HEUN2, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     TDGL_FAST_LENGTHS(TDGL_XA)
 #undef TDGL_XA
 #define TDGL_ZA(LEN) cudaFuncSetAttribute(k_zpass<LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
@@ -849,7 +883,7 @@ void tdgl_sim_destroy(tdgl_sim *s) {
     }
     for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
     void *ptrs[] = {s->dP[0], s->dP[1], s->dmat, s->dX, s->dY, s->dNhat, s->dtw, s->dcoef, s->dmaxdp,
-                    s->dflag, s->denergy, s->dout, s->ddesc, s->d_rows, s->d_y, s->d_z};
+                    s->dflag, s->denergy, s->dout, s->ddesc, s->d_rows, s->d_y, s->d_z, s->dhbuf};
     for (void *p : ptrs) cudaFree(p);
     delete s;
 }
@@ -924,6 +958,38 @@ int tdgl_set_temperature(tdgl_sim *s, double T) {
 int tdgl_set_field(tdgl_sim *s, double Ex, double Ey, double Ez) {
     if (!s || !std::isfinite(Ex) || !std::isfinite(Ey) || !std::isfinite(Ez)) return TDGL_EINVAL;
     s->E[0] = Ex; s->E[1] = Ey; s->E[2] = Ez;
+    return TDGL_OK;
+}
+
+int tdgl_set_field_ac(tdgl_sim *s, double Ax, double Ay, double Az, double freq_hz, double phase) {
+    if (!s || !std::isfinite(Ax) || !std::isfinite(Ay) || !std::isfinite(Az) || !std::isfinite(freq_hz) ||
+        !std::isfinite(phase) || freq_hz < 0)
+        return s ? fail(s->ctx, TDGL_EINVAL, "bad AC field") : TDGL_EINVAL;
+    s->Eac[0] = Ax; s->Eac[1] = Ay; s->Eac[2] = Az;
+    s->ac_freq = freq_hz;
+    s->ac_phase = phase;
+    return TDGL_OK;
+}
+
+int tdgl_set_integrator(tdgl_sim *s, int method) {
+    if (!s || (method != TDGL_EULER && method != TDGL_HEUN)) return s ? fail(s->ctx, TDGL_EINVAL, "integrator %d", method) : TDGL_EINVAL;
+    if (method == TDGL_HEUN && !s->dhbuf) {
+        ctx_set(s->ctx);
+        CK(s->ctx, cudaMalloc(&s->dhbuf, 3ull * s->ncell * sizeof(float)));
+    }
+    s->integrator = method;
+    return TDGL_OK;
+}
+
+int tdgl_set_time(tdgl_sim *s, double t) {
+    if (!s || !std::isfinite(t)) return TDGL_EINVAL;
+    s->time = t;
+    return TDGL_OK;
+}
+
+int tdgl_get_time(tdgl_sim *s, double *t) {
+    if (!s || !t) return TDGL_EINVAL;
+    *t = s->time;
     return TDGL_OK;
 }
 
@@ -1127,6 +1193,7 @@ struct tdgl_batch::Cached {
     Work w;
     struct G {
         int n;
+        bool heun;
         cudaGraphExec_t exec;
         long kernels;
     };
@@ -1244,21 +1311,26 @@ int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const doub
         }
     }
     for (int idx : active) CK(ctx, cudaMemsetAsync(b->sims[idx]->dflag, 0, sizeof(int), ctx->stream));
+    const bool heun = b->sims[active[0]]->integrator == TDGL_HEUN;
     auto record = [&]() -> int {
         for (int i = 0; i < n; ++i) {
             TRY(launch_conv(ctx, w));
+            if (heun) {
+                TRY(launch_rows(ctx, MODE_HEUN1, w, 2 * i));
+                TRY(launch_conv(ctx, w));
+            }
             if (i == n - 1)
                 for (int idx : active) CK(ctx, cudaMemsetAsync(b->sims[idx]->dmaxdp, 0, sizeof(unsigned), ctx->stream));
-            TRY(launch_rows(ctx, MODE_STEP, w, i & 1));
+            TRY(launch_rows(ctx, heun ? MODE_HEUN2 : MODE_STEP, w, heun ? 2 * i + 2 : i));
         }
         return TDGL_OK;
     };
     if (n >= 2 && !(n & 1) && !ctx->profiling && ctx->stream) {
         tdgl_batch::Cached::G *G = nullptr;
         for (auto &g : b->cache->graphs)
-            if (g.n == n) G = &g;
+            if (g.n == n && g.heun == heun) G = &g;
         if (!G) {
-            tdgl_batch::Cached::G r{n, nullptr, 0};
+            tdgl_batch::Cached::G r{n, heun, nullptr, 0};
             TRY(capture_graph(ctx, record, &r.exec, &r.kernels));
             b->cache->graphs.push_back(r);
             G = &b->cache->graphs.back();
@@ -1270,18 +1342,28 @@ int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const doub
     }
     for (int idx : active) {
         tdgl_sim *s = b->sims[idx];
-        if (n & 1) s->cur ^= 1;
+        if ((n & 1) && !heun) s->cur ^= 1;
         s->xstate = (s->terms & TDGL_TERM_ELEC) ? XS_PHAT : XS_NONE;
+        s->time += n * dt[idx];
     }
     return TDGL_OK;
 }
 
 }  // namespace
 
+static int batch_check_integrator(tdgl_batch *b) {
+    for (auto s : b->sims)
+        if (s->integrator != b->sims[0]->integrator)
+            return fail(b->ctx, TDGL_EINVAL, "sims of a batch must use one integrator");
+    return TDGL_OK;
+}
+
 int tdgl_batch_step(tdgl_batch *b, int n, const double *dt) {
     if (!b || n < 0 || !dt) return TDGL_EINVAL;
     tdgl_ctx *ctx = b->ctx;
     ctx_set(ctx);
+    if (b->sims.empty()) return TDGL_OK;
+    TRY(batch_check_integrator(b));
     std::vector<int> active;
     for (size_t i = 0; i < b->sims.size(); ++i) {
         if (!(dt[i] > 0) || !std::isfinite(dt[i])) return fail(ctx, TDGL_EINVAL, "dt[%zu]", i);
@@ -1306,6 +1388,8 @@ int tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_steps
     tdgl_ctx *ctx = b->ctx;
     ctx_set(ctx);
     const int n = (int)b->sims.size();
+    if (n == 0) return TDGL_OK;
+    TRY(batch_check_integrator(b));
     std::vector<int> active;
     std::vector<long> taken(n, 0);
     for (int i = 0; i < n; ++i) {

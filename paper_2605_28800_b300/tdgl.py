@@ -22,6 +22,7 @@ K_STEP, K_YFWD, K_ZCONV, K_YINV, K_XFWD, K_OTHER = range(6)
 KERNEL_NAMES = {K_STEP: "k_rows<STEP>", K_YFWD: "k_yfwd", K_ZCONV: "k_zconv", K_YINV: "k_yinv",
                 K_XFWD: "k_rows<XFWD>", K_OTHER: "other"}
 MAX_MATERIALS, MAX_DIM = 16, 1024
+EULER, HEUN = 0, 1
 
 _CODES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EDIVERGED: "EDIVERGED",
           ENOTCONVERGED: "ENOTCONVERGED", ESTATE: "ESTATE", ETOOBIG: "ETOOBIG"}
@@ -61,6 +62,10 @@ _SIGS = {
     "tdgl_set_terms": (_I, [_VP, _U]),
     "tdgl_set_temperature": (_I, [_VP, _D]),
     "tdgl_set_field": (_I, [_VP, _D, _D, _D]),
+    "tdgl_set_field_ac": (_I, [_VP, _D, _D, _D, _D, _D]),
+    "tdgl_set_integrator": (_I, [_VP, _I]),
+    "tdgl_set_time": (_I, [_VP, _D]),
+    "tdgl_get_time": (_I, [_VP, ctypes.POINTER(_D)]),
     "tdgl_set_scales": (_I, [_VP, _D, _D]),
     "tdgl_get_scales": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "tdgl_set_P": (_I, [_VP, _VP, _I]),
@@ -205,6 +210,18 @@ class Sim:
     def set_temperature(self, T): self._c(self.lib.tdgl_set_temperature(self.h, float(T)))
     def set_field(self, E): self._c(self.lib.tdgl_set_field(self.h, *map(float, E)))
     def set_scales(self, P0, alpha_ref): self._c(self.lib.tdgl_set_scales(self.h, float(P0), float(alpha_ref)))
+
+    def set_field_ac(self, A, freq_hz, phase=0.0):
+        self._c(self.lib.tdgl_set_field_ac(self.h, *map(float, A), float(freq_hz), float(phase)))
+
+    def set_time(self, t): self._c(self.lib.tdgl_set_time(self.h, float(t)))
+
+    def set_integrator(self, method): self._c(self.lib.tdgl_set_integrator(self.h, int(method)))
+
+    def time(self):
+        v = _D()
+        self._c(self.lib.tdgl_get_time(self.h, ctypes.byref(v)))
+        return v.value
 
     def scales(self):
         a, b = _D(), _D()

@@ -204,3 +204,74 @@ def test_steps_interleaved_with_energy_and_field_reads(ctx, shape):
         elif probe == "field":
             g.get_field(15)
     assert np.abs(g.get_P() - Po).max() / g.scales()[0] <= 1e-5
+
+
+def test_ac_applied_field_trajectory(ctx):
+    # E_ext(t) = E + A sin(2 pi f t + phase), sampled at each step's time, vs the oracle
+    shape = (16, 12, 8)
+    mat, P = mixed_case(shape, seed=9)
+    P *= 0.3
+    E, A, f, ph = (0.0, 0.0, 2e7), (5e7, 0.0, 1.5e8), 3.0e8, 0.4
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    g = gpu_sim(ctx, shape, CELL, mat, MATS, 300.0, 45.0, E=E, P=P)
+    g.set_field_ac(A, f, ph)
+    g.set_time(1e-9)
+    o = oracle_sys(shape, CELL, mat, MATS, 300.0, 45.0, E=E)
+    o.E_ac, o.freq, o.phase = np.array(A), f, ph
+    Po = P.astype(np.float64)
+    t = 1e-9
+    for n in (7, 16, 9):
+        g.step(n, dt)
+        Po = o.run(Po, dt, n, t0=t)
+        t += n * dt
+    assert g.time() == pytest.approx(t, rel=1e-12)
+    assert np.abs(g.get_P() - Po).max() / g.scales()[0] <= 1e-5
+    eg, eo = g.energy(), o.energy(Po, t)
+    assert abs(eg["ext"] - eo["ext"]) <= 1e-6 * sum(abs(eo[k]) for k in ("land", "grad", "elec", "ext"))
+
+
+@pytest.mark.parametrize("ac", [False, True])
+def test_heun_trajectory_matches_oracle(ctx, ac):
+    from paper_2605_28800_b300 import tdgl
+    shape = (16, 12, 8)
+    mat, P = mixed_case(shape, seed=13)
+    P *= 0.3
+    E, A, f, ph = (0.0, 0.0, 2e7), (0.0, 4e7, 1e8), 3.0e8, 0.2
+    dt = 0.006 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    g = gpu_sim(ctx, shape, CELL, mat, MATS, 300.0, 45.0, E=E, P=P)
+    g.set_integrator(tdgl.HEUN)
+    o = oracle_sys(shape, CELL, mat, MATS, 300.0, 45.0, E=E)
+    if ac:
+        g.set_field_ac(A, f, ph)
+        o.E_ac, o.freq, o.phase = np.array(A), f, ph
+    Po = P.astype(np.float64)
+    t = 0.0
+    for n in (5, 16, 1):
+        g.step(n, dt)
+        g.energy()
+        Po = o.run(Po, dt, n, t0=t, method="heun")
+        t += n * dt
+    assert np.abs(g.get_P() - Po).max() / g.scales()[0] <= 1e-5
+
+
+def test_heun_batch_equals_single(ctx):
+    from paper_2605_28800_b300 import tdgl
+    sims = []
+    for rep in range(2):
+        row = []
+        for i, sh in enumerate([(16, 16, 8), (12, 10, 6)]):
+            mat, P = mixed_case(sh, seed=30 + i)
+            s = gpu_sim(ctx, sh, CELL, mat, MATS, 280.0, 45.0, P=P * 0.3)
+            s.set_integrator(tdgl.HEUN)
+            row.append(s)
+        sims.append(row)
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    for s in sims[0]:
+        s.step(16, dt)
+        s.step(3, dt)
+    B = tdgl.Batch(ctx, sims[1])
+    B.step(16, dt)
+    B.step(3, dt)
+    for a, b in zip(*sims):
+        assert np.array_equal(a.get_P(), b.get_P())
+    B.close()

@@ -44,3 +44,29 @@ def test_relaxed_state_has_small_field():
     h = s.fields(P)["total"]
     # per-step change below 1e-9 P0 means |h| dt < 1e-9 P0
     assert np.abs(h).max() * 0.004 / a < 1.01e-9 * 0.2649
+
+
+def test_ac_field_enters_at_step_time():
+    # one cell, applied field only: dP/dt = E_ext(t) exactly, so Euler sums E_ext(t_i) dt
+    s = System((1, 1, 1), (1e-9,) * 3, np.ones((1, 1, 1), np.uint8), {1: synth.BTO}, 300.0, terms=8,
+               E_ext=(1e7, 0.0, 0.0), E_ac=(0.0, 0.0, 2e8), freq=1e9, phase=0.3)
+    dt, n = 1e-11, 37
+    P = s.run(np.zeros((3, 1, 1, 1)), dt, n, t0=2e-10)
+    t = 2e-10 + dt * np.arange(n)
+    assert P[0, 0, 0, 0] == pytest.approx(n * dt * 1e7, rel=1e-12)
+    assert P[2, 0, 0, 0] == pytest.approx(np.sum(2e8 * np.sin(2 * np.pi * 1e9 * t + 0.3)) * dt, rel=1e-12)
+
+
+@pytest.mark.parametrize("method,order", [("euler", 1), ("heun", 2)])
+def test_integrator_convergence_order(method, order):
+    # one BaTiO3 cell, Landau term only: halving dt divides the error at a fixed time by 2^order
+    from oracle import TERM_LANDAU
+    s = System((1, 1, 1), (1e-9,) * 3, np.ones((1, 1, 1), np.uint8), {1: synth.BTO}, 300.0, terms=TERM_LANDAU)
+    a = abs(coefficients(synth.BTO, 300.0)["a1x"])
+    P0 = np.array([0.02, 0.05, 0.11]).reshape(3, 1, 1, 1)
+    t_end = 0.5 / a
+    ref = s.run(P0, t_end / 4096, 4096, method="heun")
+    err = [np.abs(s.run(P0, t_end / n, n, method=method) - ref).max() for n in (32, 64, 128)]
+    r1, r2 = err[0] / err[1], err[1] / err[2]
+    assert 0.8 * 2 ** order < r1 < 1.25 * 2 ** order
+    assert 0.8 * 2 ** order < r2 < 1.25 * 2 ** order
