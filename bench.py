@@ -324,6 +324,36 @@ def relax_compare(args):
     print(json.dumps(line))
 
 
+def temperature_sweep(args):
+    """Relaxation sweep of the 128^3 cube, 450 -> 200 K in 25 K steps (adiabatic continuation:
+    each temperature starts from the previous relaxed state), relaxed to args.tol per step."""
+    import torch
+    from paper_2605_28800_b300 import tdgl
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    ctx = tdgl.Context(dev)
+    wl = workload("bto_cube_128")
+    s, dt = make_sim(ctx, wl)
+    rows = []
+    for T in synth.CONFIG2["temperatures"]:
+        s.set_temperature(T)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n, ok = s.relax(dt, args.tol, args.max_relax_steps, CHECK_EVERY, raise_on_cap=False)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        P = s.get_P()
+        a = np.sort(np.abs(P.reshape(3, -1).mean(axis=1)))[::-1]
+        mag = float(np.sqrt((P.astype(np.float64) ** 2).sum(axis=0)).mean())
+        e = s.energy()
+        rows.append(dict(T=T, steps=n, converged=ok, seconds=el, mean_abs_P=mag,
+                         mean_P_sorted=[float(v) for v in a], F_total=e["total"],
+                         cell_updates_per_s=n * wl["P"][0].size / el if el > 0 else None))
+    print(json.dumps({"metric": "time-to-relax per temperature", "workload": "bto_cube_128_T_sweep",
+                      "tol": args.tol, "max_steps": args.max_relax_steps, "dt_star": wl["dt_star"],
+                      "points": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,12 +365,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--relax-compare", action="store_true",
                     help="time-to-relax of the uneven sweep, each sim alone vs one batch")
+    ap.add_argument("--temperature-sweep", action="store_true",
+                    help="relaxation sweep of the 128^3 cube from 450 to 200 K")
     ap.add_argument("--sweep-sims", type=int, default=48)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--max-relax-steps", type=int, default=20000)
     args = ap.parse_args()
     if args.relax_compare:
         return relax_compare(args)
+    if args.temperature_sweep:
+        return temperature_sweep(args)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     wl = workload(args.workload)
