@@ -38,7 +38,7 @@ struct SimDev {
     const uint8_t *mat;       // [ncell]
     float2 *X;                // [3][nz][ny][kxp]  x-spectrum (P-hat or E-hat)
     float2 *Y;                // [3][nz][My][kxp]  y-padded spectrum
-    const float *Nhat;        // [6][kzh][kyh][Kx] reduced real tensor spectrum
+    const float2 *Nhat;       // [3][kzh][kyh][kxp] reduced real tensor spectrum, (xx,yy) (zz,xy) (xz,yz)
     const float *coef;        // [MAXMAT][NCOEF]
     float inv_d2[3];          // 1/dx*^2
     float inv_2d[3];          // 1/(2 dx*)
@@ -486,15 +486,15 @@ __global__ void __launch_bounds__(NTHREADS) k_zconv(const SimDev *__restrict__ s
     // E-hat = escale * N-hat(k) P-hat(k), N-hat from the reduced table with reflection signs
     const int kyr = (ky <= S.My / 2) ? ky : S.My - ky;
     const float sy = (ky <= S.My / 2) ? 1.f : -1.f;
-    const long nstride = (long)S.kzh * S.kyh * S.Kx;
+    const long nstride = (long)S.kzh * S.kyh * S.kxp;
     for (int w = tid; w < S.Mz * cnt; w += nthr) {
         const int kz = w / cnt, q = w - kz * cnt;
         const int kzr = (kz <= S.Mz / 2) ? kz : S.Mz - kz;
         const float sz = (kz <= S.Mz / 2) ? 1.f : -1.f;
-        const float *N = S.Nhat + ((long)kzr * S.kyh + kyr) * S.Kx + kx0 + q;
-        const float nxx = __ldg(N), nyy = __ldg(N + nstride), nzz = __ldg(N + 2 * nstride);
-        const float nxy = sy * __ldg(N + 3 * nstride), nxz = sz * __ldg(N + 4 * nstride);
-        const float nyz = sy * sz * __ldg(N + 5 * nstride);
+        const float2 *N = S.Nhat + ((long)kzr * S.kyh + kyr) * S.kxp + kx0 + q;
+        const float2 n0 = __ldg(N), n1 = __ldg(N + nstride), n2 = __ldg(N + 2 * nstride);
+        const float nxx = n0.x, nyy = n0.y, nzz = n1.x;
+        const float nxy = sy * n1.y, nxz = sz * n2.x, nyz = sy * sz * n2.y;
         const float2 px = res[(0 * cnt + q) * ld + kz], py = res[(1 * cnt + q) * ld + kz],
                      pz = res[(2 * cnt + q) * ld + kz];
         float2 ex, ey, ez;

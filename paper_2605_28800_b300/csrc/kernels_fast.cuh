@@ -12,8 +12,16 @@ namespace tdgl {
 template <int N> __host__ __device__ constexpr int lines_per_block() {
     return (256 / rf::threads_per_line<N>()) < 16 ? (256 / rf::threads_per_line<N>()) : 16;
 }
+
+// Shapes of the z pass.  For 256 and 512 points, 8 elements per thread (radices 8 8 4 and
+// 8 8 8): half the registers of the 16-element shapes, so a block of 256 threads keeps the
+// shared memory of a 128-thread block of those and an SM holds twice the warps.
+template <int N> struct ZCfg : rf::Cfg<N> {};
+template <> struct ZCfg<256> : rf::Shape<256, 8, 8, 8, 4> {};
+template <> struct ZCfg<512> : rf::Shape<512, 8, 8, 8, 8> {};
+template <int N> __host__ __device__ constexpr int zthreads() { return ZCfg<N>::E == 8 ? 256 : 128; }
 template <int N> __host__ __device__ constexpr int zlines_per_block() {
-    return (128 / rf::threads_per_line<N>()) < 16 ? (128 / rf::threads_per_line<N>()) : 16;
+    return (zthreads<N>() / ZCfg<N>::T) < 16 ? (zthreads<N>() / ZCfg<N>::T) : 16;
 }
 
 // y transform of the x-spectrum: forward (ny -> My, zero padded) or inverse (My -> first ny)
@@ -43,17 +51,17 @@ __global__ void __launch_bounds__(256) k_ypass(const SimDev *__restrict__ sims, 
         for (int m = 0; m < E; ++m) v[m] = ok ? src[(long)(t + T * m) * kxp] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    rf::fft<N, INV>(v, t, S, [&](int pos) { return pos * KX + l; }, tw);
+    rf::fft<rf::Cfg<N>, INV>(v, t, S, [&](int pos) { return pos * KX + l; }, tw);
     if (!ok) return;
     if (!INV) {
         float2 *dst = D.Y + (long)cz * N * kxp + kx0 + l;
 #pragma unroll
-        for (int i = 0; i < E; ++i) dst[(long)rf::final_pos<N>(t, i) * kxp] = v[i];
+        for (int i = 0; i < E; ++i) dst[(long)rf::final_pos<rf::Cfg<N>>(t, i) * kxp] = v[i];
     } else {
         float2 *dst = D.X + (long)cz * ny * kxp + kx0 + l;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
-            const int y = rf::final_pos<N>(t, i);
+            const int y = rf::final_pos<rf::Cfg<N>>(t, i);
             if (y < ny) dst[(long)y * kxp] = v[i];
         }
     }
@@ -64,12 +72,27 @@ template <int N> __host__ __device__ constexpr size_t zpass_smem() {
     return (3 * N * zlines_per_block<N>() + N) * sizeof(float2);
 }
 
+// Row of position pos in a [N][KX] exchange buffer.  With KX < 16 lines a half-warp covers
+// G = 16/KX positions; the first pass writes positions R0 apart, which would all start in the
+// same bank.  Rows inside each aligned group of G are permuted by (pos / R0) mod G, which
+// spreads those writes over G different bank groups and keeps consecutive positions (every
+// other access) in distinct bank groups too.
+template <int N, int KX> __device__ __forceinline__ int zrow(int pos) {
+    constexpr int G = KX >= 16 ? 1 : 16 / KX, R0 = ZCfg<N>::R0;
+    static_assert(G == 1 || (R0 % G == 0 && (G & (G - 1)) == 0), "swizzle group must divide the first radix");
+    if constexpr (G == 1) return pos;
+    else return pos ^ ((pos / R0) & (G - 1));
+}
+
 // z transform, per-k 3x3 tensor multiply, inverse z transform (first nz outputs kept).
-// The three forward spectra are parked in shared memory (each thread's own slots) so that the
-// block needs few registers and several blocks share an SM.
+// The three components' inputs are copied asynchronously into shared memory, one commit group
+// each, so the x transform starts while y and z are still in flight.  The forward spectra of x
+// and y are parked in shared memory (each thread's own slots); z stays in registers through the
+// multiply and its inverse runs first, straight from registers.
 template <int N>
-__global__ void __launch_bounds__(128, 4) k_zpass(const SimDev *__restrict__ sims, const int4 *__restrict__ items) {
-    constexpr int E = rf::Cfg<N>::E, T = N / E, KX = zlines_per_block<N>();
+__global__ void __launch_bounds__(zthreads<N>(), 4) k_zpass(const SimDev *__restrict__ sims, const int4 *__restrict__ items) {
+    using S = ZCfg<N>;
+    constexpr int E = S::E, T = S::T, KX = zlines_per_block<N>();
     extern __shared__ float4 smem4[];
     float2 *A = reinterpret_cast<float2 *>(smem4);      // [3][N][KX]
     float2 *tw = A + 3 * N * KX;                          // [N]
@@ -78,16 +101,15 @@ __global__ void __launch_bounds__(128, 4) k_zpass(const SimDev *__restrict__ sim
     const int ky = it.y, kx0 = it.z, cnt = it.w;
     const int l = threadIdx.x % KX, t = threadIdx.x / KX;
     const bool ok = l < cnt;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = D.tw[D.pz.tw + i];
     const int nz = D.nz, My = D.My, kxp = D.kxp;
     const long zs = (long)My * kxp, cs = (long)nz * zs;
     const float2 *src = D.Y + (long)ky * kxp + kx0 + l;
-    auto idx = [&](int pos) { return pos * KX + l; };
-    // all three components' inputs in flight at once: asynchronous 8-byte copies into this
-    // thread's own slots of the spectra buffers
-    if (ok) {
+    auto idx = [&](int pos) { return zrow<N, KX>(pos) * KX + l; };
+    // inputs of all three components in flight at once: asynchronous 8-byte copies into this
+    // thread's own slots, component c in commit group c
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
+    for (int c = 0; c < 3; ++c) {
+        if (ok) {
 #pragma unroll
             for (int m = 0; m < E; ++m) {
                 const int z = t + T * m;
@@ -96,66 +118,92 @@ __global__ void __launch_bounds__(128, 4) k_zpass(const SimDev *__restrict__ sim
                     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src + c * cs + z * zs));
                 }
             }
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
     }
-    asm volatile("cp.async.commit_group;\n" ::);
-    asm volatile("cp.async.wait_group 0;\n" ::);
-    __syncthreads();
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = D.tw[D.pz.tw + i];
+    // forward transform of component c from this thread's own input slots; Ac is its exchange buffer
+    auto forward = [&](int c, float2(&v)[E]) {
         float2 *Ac = A + c * N * KX;
-        float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int z = t + T * m;
             v[m] = (ok && z < nz) ? Ac[idx(z)] : make_float2(0.f, 0.f);
         }
-        __syncthreads();   // own slots read before the exchanges overwrite them
-        rf::fft<N, false>(v, t, Ac, idx, tw);
+        __syncthreads();   // own slots (and the twiddles) read before the exchanges overwrite them
+        rf::fft<S, false>(v, t, Ac, idx, tw);
+    };
+    {
+        asm volatile("cp.async.wait_group 2;\n" ::);
+        float2 v[E];
+        forward(0, v);
 #pragma unroll
-        for (int i = 0; i < E; ++i) Ac[idx(rf::final_pos<N>(t, i))] = v[i];
+        for (int i = 0; i < E; ++i) A[idx(rf::final_pos<S>(t, i))] = v[i];
     }
-    // E-hat(k) = escale * N-hat(k) P-hat(k) on this thread's own slots; N-hat from the reduced
-    // table with reflection signs
+    {
+        asm volatile("cp.async.wait_group 1;\n" ::);
+        float2 v[E];
+        forward(1, v);
+#pragma unroll
+        for (int i = 0; i < E; ++i) A[N * KX + idx(rf::final_pos<S>(t, i))] = v[i];
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    float2 w[E];
+    forward(2, w);
+    // E-hat(k) = escale * N-hat(k) P-hat(k); N-hat from the reduced table with reflection signs.
+    // x and y results go back to their owner's slots, z stays in w.
     const int kyr = (ky <= My / 2) ? ky : My - ky;
     const float sy = (ky <= My / 2) ? 1.f : -1.f;
-    const long ns = (long)D.kzh * D.kyh * D.Kx;
+    const long ns = (long)D.kzh * D.kyh * kxp;
     const float es = D.escale;
-    const float *Nb = D.Nhat + (long)kyr * D.Kx + kx0 + l;
-    const long rowN = (long)D.kyh * D.Kx;
-#pragma unroll 8
+    const float2 *Nb = D.Nhat + (long)kyr * kxp + kx0 + l;
+    const long rowN = (long)D.kyh * kxp;
+#pragma unroll
     for (int i = 0; i < E; ++i) {
-        const int kz = rf::final_pos<N>(t, i);
+        const int kz = rf::final_pos<S>(t, i);
         const int kzr = (kz <= N / 2) ? kz : N - kz;
         const float sz = (kz <= N / 2) ? 1.f : -1.f;
-        const float *Np = Nb + kzr * rowN;
+        const float2 *Np = Nb + kzr * rowN;
         float nxx = 0.f, nyy = 0.f, nzz = 0.f, nxy = 0.f, nxz = 0.f, nyz = 0.f;
         if (ok) {
-            nxx = __ldg(Np); nyy = __ldg(Np + ns); nzz = __ldg(Np + 2 * ns);
-            nxy = sy * __ldg(Np + 3 * ns); nxz = sz * __ldg(Np + 4 * ns); nyz = sy * sz * __ldg(Np + 5 * ns);
+            const float2 n0 = __ldg(Np), n1 = __ldg(Np + ns), n2 = __ldg(Np + 2 * ns);
+            nxx = n0.x; nyy = n0.y; nzz = n1.x;
+            nxy = sy * n1.y; nxz = sz * n2.x; nyz = sy * sz * n2.y;
         }
         const int p = idx(kz);
-        const float2 px = A[p], py = A[N * KX + p], pz = A[2 * N * KX + p];
+        const float2 px = A[p], py = A[N * KX + p], pz = w[i];
         A[p] = make_float2(es * (nxx * px.x + nxy * py.x + nxz * pz.x), es * (nxx * px.y + nxy * py.y + nxz * pz.y));
         A[N * KX + p] = make_float2(es * (nxy * px.x + nyy * py.x + nyz * pz.x), es * (nxy * px.y + nyy * py.y + nyz * pz.y));
-        A[2 * N * KX + p] = make_float2(es * (nxz * px.x + nyz * py.x + nzz * pz.x), es * (nxz * px.y + nyz * py.y + nzz * pz.y));
+        w[i] = make_float2(es * (nxz * px.x + nyz * py.x + nzz * pz.x), es * (nxz * px.y + nyz * py.y + nzz * pz.y));
     }
     float2 *dst = D.Y + (long)ky * kxp + kx0 + l;
-#pragma unroll 1
-    for (int c = 0; c < 3; ++c) {
-        float2 *Ac = A + c * N * KX;
-        float2 v[E];
-        __syncthreads();   // every slot of Ac read by its owner before the exchanges overwrite it
-#pragma unroll
-        for (int m = 0; m < E; ++m) v[m] = Ac[idx(t + T * m)];
-        __syncthreads();
-        rf::fft<N, true>(v, t, Ac, idx, tw);
+    auto store = [&](int c, const float2(&v)[E]) {
         if (ok) {
 #pragma unroll
             for (int i = 0; i < E; ++i) {
-                const int z = rf::final_pos<N>(t, i);
+                const int z = rf::final_pos<S>(t, i);
                 if (z < nz) dst[c * cs + z * zs] = v[i];
             }
         }
+    };
+    {
+        // z first: inverse input order is the forward output order after the register permutation;
+        // its exchange buffer is the z region, which nothing reads any more
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = w[rf::final_reg<S>(m)];
+        rf::fft<S, true>(v, t, A + 2 * N * KX, idx, tw);
+        store(2, v);
+    }
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+        float2 *Ac = A + c * N * KX;
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = Ac[idx(t + T * m)];
+        __syncthreads();   // every slot of Ac read by its owner before the exchanges overwrite it
+        rf::fft<S, true>(v, t, Ac, idx, tw);
+        store(c, v);
     }
 }
 

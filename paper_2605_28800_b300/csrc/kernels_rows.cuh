@@ -247,11 +247,11 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
             const float2 d = cmul(csub(a, b), w);
             v[m] = make_float2(a.x + b.x - d.y, a.y + b.y + d.x);
         }
-        rf::fft<HX, true>(v, t, X2, xidx, s_tw);
+        rf::fft<rf::Cfg<HX>, true>(v, t, X2, xidx, s_tw);
         if (lok) {
 #pragma unroll
             for (int i = 0; i < E; ++i) {
-                const int j = rf::final_pos<HX>(t, i);
+                const int j = rf::final_pos<rf::Cfg<HX>>(t, i);
                 const int x0 = 2 * j;
                 float *er = Eb + (lc * TYmax + lr) * nx;
                 if (x0 < nx) er[x0] = v[i].x;
@@ -405,10 +405,10 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
             v[m] = make_float2((lok && x0 < nx) ? src[x0] : 0.f, (lok && x0 + 1 < nx) ? src[x0 + 1] : 0.f);
         }
         __syncthreads();   // the exchange below reuses the tile's memory
-        rf::fft<HX, false>(v, t, X2, xidx, s_tw);
+        rf::fft<rf::Cfg<HX>, false>(v, t, X2, xidx, s_tw);
         // Hermitian half-spectrum from the packed transform: needs Z_k and Z_{HX-k}
 #pragma unroll
-        for (int i = 0; i < E; ++i) X2[xidx(rf::final_pos<HX>(t, i))] = v[i];
+        for (int i = 0; i < E; ++i) X2[xidx(rf::final_pos<rf::Cfg<HX>>(t, i))] = v[i];
         __syncthreads();
         if (lok) {
             float2 *row = S.X + (((long)lc * nz + z) * ny + y0 + lr) * S.kxp;

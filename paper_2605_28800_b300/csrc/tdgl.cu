@@ -74,7 +74,7 @@ struct tdgl_sim {
     float *dP[2] = {nullptr, nullptr};
     uint8_t *dmat = nullptr;
     float2 *dX = nullptr, *dY = nullptr;
-    float *dNhat = nullptr;
+    float2 *dNhat = nullptr;
     float2 *dtw = nullptr;
     float *dcoef = nullptr;
     unsigned *dmaxdp = nullptr;
@@ -112,6 +112,9 @@ struct tdgl_batch {
     struct Cached;
     Cached *cache = nullptr;
 };
+
+// frees a batch's cached work lists and graphs (defined once the cache type is complete)
+static void drop_cache(tdgl_batch *b);
 
 // ---------------------------------------------------------------------------------------------
 namespace {
@@ -263,13 +266,42 @@ int capture_graph(tdgl_ctx *ctx, F record, cudaGraphExec_t *out, long *kernels) 
 int grid_for(long n) { return (int)std::min<long>(std::max<long>((n + 255) / 256, 1), 148L * 16); }
 
 // -- geometry and plans ------------------------------------------------------------------------
-// lengths with a register-FFT specialization (fft_reg.cuh) and its geometry
+// lengths with a register-FFT specialization (fft_reg.cuh); the host reads each kernel's
+// geometry from the same constexpr functions the kernels are compiled with
+#define TDGL_FAST_LENGTHS(X) X(16) X(32) X(64) X(128) X(256) X(512) X(48) X(96) X(192)
 bool fast_len(int n) {
-    return n == 16 || n == 32 || n == 64 || n == 128 || n == 256 || n == 512 || n == 48 || n == 96 || n == 192;
+    switch (n) {
+#define TDGL_C(LEN) case LEN:
+        TDGL_FAST_LENGTHS(TDGL_C)
+#undef TDGL_C
+        return true;
+    }
+    return false;
 }
-int fast_tpl(int n) { return n / (n == 48 ? 12 : ((n == 96 || n == 192) ? 24 : 16)); }   // threads per line
-int fast_ylines(int n) { return std::min(256 / fast_tpl(n), 16); }
-int fast_zlines(int n) { return std::min(128 / fast_tpl(n), 16); }
+int fast_rowtile(int n) {   // rows per block of the tiled row kernel
+    switch (n) {
+#define TDGL_C(LEN) case LEN: return xrows_tile<LEN>();
+        TDGL_FAST_LENGTHS(TDGL_C)
+#undef TDGL_C
+    }
+    return 0;
+}
+int fast_ylines(int n) {    // lines per block of the y pass
+    switch (n) {
+#define TDGL_C(LEN) case LEN: return lines_per_block<LEN>();
+        TDGL_FAST_LENGTHS(TDGL_C)
+#undef TDGL_C
+    }
+    return 0;
+}
+int fast_zlines(int n) {    // lines per block of the z pass
+    switch (n) {
+#define TDGL_C(LEN) case LEN: return zlines_per_block<LEN>();
+        TDGL_FAST_LENGTHS(TDGL_C)
+#undef TDGL_C
+    }
+    return 0;
+}
 
 void build_items(tdgl_sim *s) {
     s->it_rows.clear();
@@ -277,7 +309,7 @@ void build_items(tdgl_sim *s) {
     s->it_z.clear();
     // the tiled row kernel needs the row length to equal the x half-length (2 nx smooth)
     s->xN = (fast_len(s->hx) && s->nx == s->hx) ? s->hx : 0;
-    const int RB = s->xN ? std::min(192 / (3 * fast_tpl(s->hx)), 16)
+    const int RB = s->xN ? fast_rowtile(s->hx)
                          : std::max(1, std::min(s->ny, std::max(1, 512 / s->nx)));
     s->rows_cnt_max = RB;
     for (int z = 0; z < s->nz; ++z)
@@ -454,7 +486,8 @@ int build_tensor(tdgl_sim *s) {
                                                                   dtrig + off[2], dtrig + off[2] + s->Mz);
     }));
     TRY(launch(ctx, TDGL_K_OTHER, [&] {
-        k_tensor_store<<<grid_for(6 * n3), 256, 0, ctx->stream>>>(dT1, s->dNhat, n3);
+        k_tensor_store<<<grid_for(3L * s->kzh * s->kyh * s->kxp), 256, 0, ctx->stream>>>(dT1, s->dNhat, (long)s->kzh * s->kyh,
+                                                                                         s->Kx, s->kxp);
     }));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     cudaFree(dN);
@@ -470,7 +503,7 @@ int alloc_spectra(tdgl_sim *s) {
     tdgl_ctx *ctx = s->ctx;
     CK(ctx, cudaMalloc(&s->dX, 3ull * s->nz * s->ny * s->kxp * sizeof(float2)));
     CK(ctx, cudaMalloc(&s->dY, 3ull * s->nz * s->My * s->kxp * sizeof(float2)));
-    CK(ctx, cudaMalloc(&s->dNhat, 6ull * s->kzh * s->kyh * s->Kx * sizeof(float)));
+    CK(ctx, cudaMalloc(&s->dNhat, 3ull * s->kzh * s->kyh * s->kxp * sizeof(float2)));
     s->spectra_alloc = true;
     return TDGL_OK;
 }
@@ -545,8 +578,6 @@ struct Work {
     std::vector<Group> rg, yg, zg;   // row, y and z work by transform length
 };
 
-#define TDGL_FAST_LENGTHS(X) X(16) X(32) X(64) X(128) X(256) X(512) X(48) X(96) X(192)
-
 template <int MODE>
 void rows_launch(const Group &g, const SimDev *d, cudaStream_t st, int parity) {
     if (g.N == 0) {
@@ -600,7 +631,7 @@ void zpass(const Group &g, const SimDev *d, cudaStream_t st) {
     }
     switch (g.N) {
 #define TDGL_Z(LEN) \
-    case LEN: k_zpass<LEN><<<g.n, rf::threads_per_line<LEN>() * zlines_per_block<LEN>(), zpass_smem<LEN>(), st>>>(d, g.items); break;
+    case LEN: k_zpass<LEN><<<g.n, ZCfg<LEN>::T * zlines_per_block<LEN>(), zpass_smem<LEN>(), st>>>(d, g.items); break;
         TDGL_FAST_LENGTHS(TDGL_Z)
 #undef TDGL_Z
     }
@@ -878,8 +909,7 @@ void tdgl_sim_destroy(tdgl_sim *s) {
     if (s->batch) {   // leave the batch rather than dangle in it
         auto &bv = s->batch->sims;
         bv.erase(std::remove(bv.begin(), bv.end(), s), bv.end());
-        delete s->batch->cache;            // indices in the cached work lists changed
-        s->batch->cache = nullptr;
+        drop_cache(s->batch);              // indices in the cached work lists changed
     }
     for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
     void *ptrs[] = {s->dP[0], s->dP[1], s->dmat, s->dX, s->dY, s->dNhat, s->dtw, s->dcoef, s->dmaxdp,
@@ -1170,24 +1200,6 @@ int tdgl_batch_create(tdgl_ctx *ctx, int n, tdgl_sim *const *sims, tdgl_batch **
     return TDGL_OK;
 }
 
-void tdgl_batch_destroy(tdgl_batch *b) {
-    if (!b) return;
-    ctx_set(b->ctx);
-    cudaStreamSynchronize(b->ctx->stream);
-    for (auto s : b->sims) s->batch = nullptr;
-    auto &v = b->ctx->batches;
-    v.erase(std::remove(v.begin(), v.end(), b), v.end());
-    delete b->cache;
-    cudaFree(b->ddescs);
-    cudaFree(b->d_items);
-    delete b;
-}
-
-namespace {
-
-// build concatenated work lists over the active sims and run n steps of all of them
-}  // namespace
-
 // work lists and captured step sequences of a batch for one active set
 struct tdgl_batch::Cached {
     Work w;
@@ -1202,6 +1214,27 @@ struct tdgl_batch::Cached {
         for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
     }
 };
+
+extern "C++" {
+static void drop_cache(tdgl_batch *b) {
+    delete b->cache;
+    b->cache = nullptr;
+}
+}
+
+void tdgl_batch_destroy(tdgl_batch *b) {
+    if (!b) return;
+    ctx_set(b->ctx);
+    cudaStreamSynchronize(b->ctx->stream);
+    for (auto s : b->sims) s->batch = nullptr;
+    auto &v = b->ctx->batches;
+    v.erase(std::remove(v.begin(), v.end(), b), v.end());
+    drop_cache(b);
+    cudaFree(b->ddescs);
+    cudaFree(b->d_items);
+    delete b;
+}
+
 
 namespace {
 
@@ -1529,7 +1562,7 @@ StaticPlan static_plan(int nx, int ny, int nz) {
     q.o_mat = take((size_t)q.ncell);
     q.o_X = take(sizeof(float2) * 3ull * nz * ny * q.kxp);
     q.o_Y = take(sizeof(float2) * 3ull * nz * q.My * q.kxp);
-    q.o_Nhat = take(sizeof(float) * 6ull * q.n3);
+    q.o_Nhat = take(sizeof(float2) * 3ull * q.kzh * q.kyh * q.kxp);
     q.o_N = take(sizeof(double) * 6ull * q.ncell);
     q.o_T1 = take(sizeof(double) * 6ull * std::max(q.n1, q.n3));
     q.o_T2 = take(sizeof(double) * 6ull * std::max(q.n2, q.n3));
@@ -1624,7 +1657,7 @@ extern "C" int tdgl_elec_field_static(int nx, int ny, int nz, double dx, double 
     D.mat = mat ? mat : reinterpret_cast<const uint8_t *>(base + q.o_mat);
     D.X = reinterpret_cast<float2 *>(base + q.o_X);
     D.Y = reinterpret_cast<float2 *>(base + q.o_Y);
-    D.Nhat = reinterpret_cast<const float *>(base + q.o_Nhat);
+    D.Nhat = reinterpret_cast<const float2 *>(base + q.o_Nhat);
     D.coef = reinterpret_cast<const float *>(base + q.o_coef);
     D.escale = (float)(-1.0 / (kEps0 * eps_b) / ((double)q.Mx * q.My * q.Mz));   // alpha_ref = P0 = 1
     D.pmax = 1e3f;
@@ -1668,7 +1701,8 @@ extern "C" int tdgl_elec_field_static(int nx, int ny, int nz, double dx, double 
                                                       trig + 2 * q.Mx + q.My);
     k_tensor_dft<<<grid_for(6 * q.n3), 256, 0, st>>>(dT2, dT1, 2, nz, q.kzh, q.Mz, q.kyh * q.Kx, 1,
                                                       trig + 2 * (q.Mx + q.My), trig + 2 * (q.Mx + q.My) + q.Mz);
-    k_tensor_store<<<grid_for(6 * q.n3), 256, 0, st>>>(dT1, reinterpret_cast<float *>(base + q.o_Nhat), q.n3);
+    k_tensor_store<<<grid_for(3L * q.kzh * q.kyh * q.kxp), 256, 0, st>>>(dT1, reinterpret_cast<float2 *>(base + q.o_Nhat),
+                                                                         (long)q.kzh * q.kyh, q.Kx, q.kxp);
     // x forward, y/z convolution, x inverse into E (the kernels of tdgl_get_field)
     const size_t sm_rows = 2ull * 3 * q.RB * (q.hx + 2) * sizeof(float2);
     const size_t sm_y = 2ull * q.KY * (q.My + 1) * sizeof(float2);

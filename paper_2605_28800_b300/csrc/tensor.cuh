@@ -154,11 +154,23 @@ __global__ void k_tensor_dft(const double *__restrict__ in, double *__restrict__
     }
 }
 
-// final conversion: sign (-i)^(number of odd axes) -> -1 for off-diagonal components
-__global__ void k_tensor_store(const double *__restrict__ in, float *__restrict__ out, long per) {
-    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < 6 * per; id += (long)gridDim.x * blockDim.x) {
-        const int c = (int)(id / per);
-        out[id] = (float)((c >= 3 ? -1.0 : 1.0) * in[id]);
+// final conversion to the float table the convolution reads: sign (-i)^(number of odd axes)
+// -> -1 for the off-diagonal components; components paired as float2 planes (xx, yy), (zz, xy),
+// (xz, yz), rows of kxp entries (kxp >= Kx, the row pitch of the spectra, padding zero).
+// in: [6][rows][Kx] float64; out: [3][rows][kxp] float2
+__global__ void k_tensor_store(const double *__restrict__ in, float2 *__restrict__ out, long rows, int Kx, int kxp) {
+    const long per = rows * kxp, per_in = rows * Kx;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < 3 * per; id += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(id / per);
+        const long rk = id - j * per, r = rk / kxp;
+        const int kx = (int)(rk - r * kxp);
+        float2 v = make_float2(0.f, 0.f);
+        if (kx < Kx) {
+            const long a = (2 * j) * per_in + r * Kx + kx, b = a + per_in;
+            v.x = (float)((2 * j >= 3 ? -1.0 : 1.0) * in[a]);
+            v.y = (float)((2 * j + 1 >= 3 ? -1.0 : 1.0) * in[b]);
+        }
+        out[id] = v;
     }
 }
 
