@@ -59,6 +59,7 @@ extern "C" {
 typedef struct tdgl_ctx   tdgl_ctx;
 typedef struct tdgl_sim   tdgl_sim;
 typedef struct tdgl_batch tdgl_batch;
+typedef struct tdgl_unet  tdgl_unet;
 
 /* Material coefficients, SI (Table 1 forms; the z quadratic coefficient is r_s * alpha1,
  * the strain form of Sec. 4.4):
@@ -222,9 +223,60 @@ int tdgl_elec_field_static(int nx, int ny, int nz, double dx, double dy, double 
 #define TDGL_K_YINV   3   /* inverse y FFT                                             */
 #define TDGL_K_XFWD   4   /* x forward real FFT of P (prologue)                        */
 #define TDGL_K_OTHER  5   /* energy, field readback, tensor build, copies              */
-#define TDGL_K_COUNT  6
+#define TDGL_K_UNET   6   /* learned warm start: convolutions, their gradients, Adam     */
+#define TDGL_K_COUNT  7
 int tdgl_profile(tdgl_ctx *ctx, int enable);
 int tdgl_profile_read(tdgl_ctx *ctx, int kind, double *total_ms, long *launches);
+
+/* ---- learned warm start ----------------------------------------------------------------------
+ * The relaxation starts from a proposal instead of a random state (the learned initial guess the
+ * paper's outlook, Sec. 5, motivates): a 3D U-Net maps per-cell inputs (material indicators,
+ * temperature, applied field) to a polarization texture, and the plain relaxation to the same
+ * tolerance then judges it.  The network: `levels` resolution levels with chans[l] channels,
+ * two 3x3x3 convolutions + ReLU per level, 2x2x2 average pooling down, nearest-neighbour
+ * upsampling + skip concatenation up, a 1x1x1 output convolution.  BF16 weights and activations
+ * on the tensor cores (tcgen05, FP32 accumulation in tensor memory), FP32 master weights, Adam.
+ *
+ * Tensors at this boundary are float32 [B][C][nz][ny][nx] (x fastest), the layout of P.
+ * Parameters travel as one float32 vector in the order of the layers (encoder level 0 a, b, ...,
+ * decoder level levels-2 a, b, ..., level 0 a, b, head); per layer the weights w[o][i][dz][dy][dx]
+ * (offsets -1..1, or a single tap for the head) then the biases b[o].
+ *
+ * tdgl_unet_create: cin input channels (1..8), cout outputs (1..16), 2 <= levels <= 5, chans[l]
+ *   multiples of 16 up to 128, grid nx, ny multiples of 8 * 2^(levels-1) ... precisely: every
+ *   level's x extent a multiple of 8 and every extent divisible by 2^(levels-1); max_batch >= 1
+ *   samples per call.  Weights He-normal from a counter-based generator (Philox4x32-10) keyed by
+ *   seed, biases 0.  Returns TDGL_EINVAL on bad shapes, TDGL_ENOMEM if buffers do not fit.
+ * tdgl_unet_param_count: number of floats of the parameter vector.
+ * tdgl_unet_set_params / tdgl_unet_get_params: host float32 vector (caller-owned), resets Adam.
+ * tdgl_unet_forward: x (B*cin*N floats) -> y (B*cout*N), where = TDGL_HOST or TDGL_DEVICE for both.
+ * tdgl_unet_loss_grad: mean-squared loss of forward(x) against target t and its gradient with
+ *   respect to every parameter (grads: caller-owned, param_count floats, same order), no update.
+ * tdgl_unet_train_step: forward, loss, backward and one Adam step (lr; beta1 0.9, beta2 0.999,
+ *   eps 1e-8, bias-corrected with the net's own step counter).  *loss receives the loss before the
+ *   update.  Returns TDGL_ECUDA if a tensor-core pipeline wait timed out (the device stays usable).
+ * All calls are ordered on the context's stream and return after the results are in place. */
+int  tdgl_unet_create(tdgl_ctx *ctx, int cin, int cout, int levels, const int *chans, int nx, int ny, int nz,
+                      int max_batch, uint64_t seed, tdgl_unet **out);
+void tdgl_unet_destroy(tdgl_unet *net);
+long tdgl_unet_param_count(const tdgl_unet *net);
+int  tdgl_unet_set_params(tdgl_unet *net, const float *params);
+int  tdgl_unet_get_params(tdgl_unet *net, float *params);
+int  tdgl_unet_forward(tdgl_unet *net, const float *x, float *y, int batch, int where);
+int  tdgl_unet_loss_grad(tdgl_unet *net, const float *x, const float *t, int batch, double *loss, float *grads,
+                         int where);
+int  tdgl_unet_train_step(tdgl_unet *net, const float *x, const float *t, int batch, double lr, double *loss,
+                          int where);
+
+/* The convolution primitives of the network, for checking them one by one.  x [B][ci][nz][ny][nx],
+ * w [co][ci][k][k][k] (k = 3 or 1), b [co], all host float32; operands are rounded to BF16, sums
+ * are FP32.  tdgl_conv3d: y [B][co][...] = conv(x, w) + b (relu != 0: max(., 0)).
+ * tdgl_conv3d_backward: for upstream gradient dy [B][co][...] returns dx [B][ci][...], dw, db.
+ * Channel counts: ci a multiple of 8 up to 192 (forward) and up to 128 for co; nx a multiple of 8. */
+int tdgl_conv3d(tdgl_ctx *ctx, const float *x, const float *w, const float *b, float *y, int batch, int ci, int co,
+                int k, int nx, int ny, int nz, int relu);
+int tdgl_conv3d_backward(tdgl_ctx *ctx, const float *x, const float *w, const float *dy, float *dx, float *dw,
+                         float *db, int batch, int ci, int co, int k, int nx, int ny, int nz);
 
 #ifdef __cplusplus
 }

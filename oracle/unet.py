@@ -17,12 +17,26 @@ skip concatenation, a 1x1x1 output head).  Every operation is written from its d
 
 Arrays are (batch, channels, z, y, x).  The backward functions return the exact adjoints of the
 forward ones.  No blocking or reordering beyond these definitions.
+
+Storage precision.  forward / backward take an optional rounding function q applied where a
+reduced-precision implementation stores values: the network input, every weight, each
+convolution's activated output, each pooled map, and the gradient entering each convolution's
+backward (after the ReLU mask).  bf16() rounds to bfloat16 (round to nearest, ties to even).
+With q = None everything stays float64.
 """
 from __future__ import annotations
 
 import numpy as np
 
 # -- single operations ------------------------------------------------------------------------
+
+
+def bf16(a):
+    """round to the nearest bfloat16 (8 significant bits; ties to even), returned as float64"""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
 def taps(k):
@@ -133,19 +147,19 @@ def init(cin, cout, chans, seed):
     return p
 
 
-def forward(p, x, levels):
+def forward(p, x, levels, q=None):
     """U-Net forward; returns the output and the cache the backward pass needs"""
-    cache = {}
-    h = x
+    q = q or (lambda a: a)
+    cache = {"q": q}
+    h = q(x)
     skips = []
     for l in range(levels):
         if l > 0:
-            cache[f"pool{l}"] = h.shape
-            h = pool(h)
+            h = q(pool(h))
         for s in "ab":
             n = f"enc{l}{s}"
             cache[n] = h
-            h = relu(conv3d(h, p[n + ".w"], p[n + ".b"]))
+            h = q(relu(conv3d(h, q(p[n + ".w"]), p[n + ".b"])))
             cache[n + ".out"] = h
         skips.append(h)
     for l in range(levels - 2, -1, -1):
@@ -153,22 +167,23 @@ def forward(p, x, levels):
         for s in "ab":
             n = f"dec{l}{s}"
             cache[n] = h
-            h = relu(conv3d(h, p[n + ".w"], p[n + ".b"]))
+            h = q(relu(conv3d(h, q(p[n + ".w"]), p[n + ".b"])))
             cache[n + ".out"] = h
     cache["head"] = h
-    return conv3d(h, p["head.w"], p["head.b"]), cache
+    return conv3d(h, q(p["head.w"]), p["head.b"]), cache
 
 
 def backward(p, cache, dout, levels):
     """gradients {name: array} of the loss with respect to every parameter"""
+    q = cache["q"]
     g = {}
-    dx, g["head.w"], g["head.b"] = conv3d_backward(cache["head"], p["head.w"], dout)
+    dx, g["head.w"], g["head.b"] = conv3d_backward(cache["head"], q(p["head.w"]), q(dout))
     dskip = {}
     for l in range(0, levels - 1):
         for s in "ba":
             n = f"dec{l}{s}"
-            dpre = dx * (cache[n + ".out"] > 0)
-            dx, g[n + ".w"], g[n + ".b"] = conv3d_backward(cache[n], p[n + ".w"], dpre)
+            dpre = q(dx * (cache[n + ".out"] > 0))
+            dx, g[n + ".w"], g[n + ".b"] = conv3d_backward(cache[n], q(p[n + ".w"]), dpre)
         c_up = dx.shape[1] - cache[f"enc{l}b.out"].shape[1]
         dskip[l] = dx[:, c_up:]
         dx = up_backward(dx[:, :c_up])
@@ -177,11 +192,28 @@ def backward(p, cache, dout, levels):
             dx = dx + dskip[l]
         for s in "ba":
             n = f"enc{l}{s}"
-            dpre = dx * (cache[n + ".out"] > 0)
-            dx, g[n + ".w"], g[n + ".b"] = conv3d_backward(cache[n], p[n + ".w"], dpre)
+            dpre = q(dx * (cache[n + ".out"] > 0))
+            dx, g[n + ".w"], g[n + ".b"] = conv3d_backward(cache[n], q(p[n + ".w"]), dpre)
         if l > 0:
             dx = pool_backward(dx)
     return g
+
+
+def flat(p, levels):
+    """parameters as one vector: per layer (in layer_names order) the weights, then the biases"""
+    return np.concatenate([np.concatenate([p[n + ".w"].ravel(), p[n + ".b"].ravel()]) for n in layer_names(levels)])
+
+
+def unflat(v, cin, cout, chans):
+    p, o = {}, 0
+    s = shapes(cin, cout, chans)
+    for n in layer_names(len(chans)):
+        co, ci, k = s[n]
+        p[n + ".w"] = np.asarray(v[o:o + co * ci * k ** 3], dtype=np.float64).reshape(co, ci, k, k, k)
+        o += co * ci * k ** 3
+        p[n + ".b"] = np.asarray(v[o:o + co], dtype=np.float64)
+        o += co
+    return p
 
 
 def adam(p, g, m, v, k, lr, b1=0.9, b2=0.999, eps=1e-8):

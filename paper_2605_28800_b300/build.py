@@ -8,8 +8,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libtdgl.so")
-SOURCES = [os.path.join(HERE, "csrc", "tdgl.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("fft.cuh", "fft_reg.cuh", "kernels.cuh", "kernels_fast.cuh", "kernels_rows.cuh", "tensor.cuh")] + [
+SOURCES = [os.path.join(HERE, "csrc", "tdgl.cu"), os.path.join(HERE, "csrc", "unet.cu")]
+DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("fft.cuh", "fft_reg.cuh", "kernels.cuh", "kernels_fast.cuh", "kernels_rows.cuh", "tensor.cuh", "runtime.cuh", "tc.cuh", "unet_kernels.cuh", "philox.cuh")] + [
     os.path.join(ROOT, "include", "tdgl.h")]
 
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",

@@ -13,6 +13,7 @@
 // lengths in units of the smallest cell edge.  Every kernel takes a table of sim descriptors
 // and a table of work items, so one launch covers a single sim or a batch of uneven sims.
 #pragma once
+#include "philox.cuh"
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -533,20 +534,6 @@ __global__ void k_mask(float *__restrict__ P, const uint8_t *__restrict__ mat, l
         if (!mat[i % ncell]) P[i] = 0.f;
 }
 
-// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) -------------------------------------------
-__device__ __forceinline__ uint32_t philox_first(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                                 uint32_t k0, uint32_t k1) {
-    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
-        const uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
-        const uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
-        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
-        k0 += W0; k1 += W1;
-    }
-    return c0;
-}
 __global__ void k_init_random(float *__restrict__ P, const uint8_t *__restrict__ mat, long ncell,
                               uint32_t k0, uint32_t k1, float amp) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 3 * ncell; i += (long)gridDim.x * blockDim.x) {

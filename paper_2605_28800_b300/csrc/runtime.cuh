@@ -1,0 +1,101 @@
+// Internal runtime shared by the library's translation units: the context object, error
+// reporting and the counted (optionally event-timed) kernel launch.  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/tdgl.h"
+
+struct tdgl_sim;
+struct tdgl_batch;
+struct tdgl_unet;
+
+namespace tdgl_rt {
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+}  // namespace tdgl_rt
+
+struct tdgl_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    long launches = 0;
+    bool profiling = false;
+    std::vector<tdgl_rt::ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[TDGL_K_COUNT] = {0};
+    long prof_n[TDGL_K_COUNT] = {0};
+    std::vector<tdgl_sim *> sims;       // owned: freed by tdgl_ctx_destroy if still alive
+    std::vector<tdgl_batch *> batches;
+    std::vector<tdgl_unet *> nets;
+};
+
+namespace tdgl_rt {
+
+inline int fail(tdgl_ctx *ctx, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    return code;
+}
+
+#define CK(ctx, call)                                                                            \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? TDGL_ENOMEM : TDGL_ECUDA,         \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);   \
+    } while (0)
+
+#define TRY(x)                  \
+    do {                        \
+        int r_ = (x);           \
+        if (r_ != TDGL_OK) return r_; \
+    } while (0)
+
+inline void ctx_set(tdgl_ctx *ctx) { cudaSetDevice(ctx->device); }
+
+inline cudaEvent_t take_event(tdgl_ctx *ctx) {
+    if (!ctx->pool.empty()) {
+        cudaEvent_t e = ctx->pool.back();
+        ctx->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// launch through f() on the context's stream: counted, timed when profiling is on, checked
+template <class F>
+inline int launch(tdgl_ctx *ctx, int kind, F f) {
+    ProfRec r{kind, nullptr, nullptr};
+    if (ctx->profiling) {
+        r.a = take_event(ctx);
+        r.b = take_event(ctx);
+        cudaEventRecord(r.a, ctx->stream);
+    }
+    f();
+    cudaError_t e = cudaGetLastError();
+    if (ctx->profiling) {
+        cudaEventRecord(r.b, ctx->stream);
+        ctx->recs.push_back(r);
+    }
+    ctx->launches++;
+    if (e != cudaSuccess) return fail(ctx, TDGL_ECUDA, "kernel launch (kind %d): %s", kind, cudaGetErrorString(e));
+    return TDGL_OK;
+}
+
+}  // namespace tdgl_rt

@@ -20,8 +20,10 @@
 #include "kernels_fast.cuh"
 #include "kernels_rows.cuh"
 #include "tensor.cuh"
+#include "runtime.cuh"
 
 using namespace tdgl;
+using namespace tdgl_rt;
 
 namespace {
 
@@ -30,27 +32,8 @@ const int kMaxSmem = 200 * 1024;
 
 enum { XS_NONE = 0, XS_PHAT = 1, XS_EHAT = 2 };
 
-struct ProfRec {
-    int kind;
-    cudaEvent_t a, b;
-};
 
 }  // namespace
-
-struct tdgl_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    std::string err;
-    long launches = 0;
-    bool profiling = false;
-    std::vector<ProfRec> recs;
-    std::vector<cudaEvent_t> pool;
-    double prof_ms[TDGL_K_COUNT] = {0};
-    long prof_n[TDGL_K_COUNT] = {0};
-    std::vector<tdgl_sim *> sims;       // owned: freed by tdgl_ctx_destroy if still alive
-    std::vector<tdgl_batch *> batches;
-};
 
 struct tdgl_sim {
     tdgl_ctx *ctx = nullptr;
@@ -119,29 +102,8 @@ static void drop_cache(tdgl_batch *b);
 // ---------------------------------------------------------------------------------------------
 namespace {
 
-int fail(tdgl_ctx *ctx, int code, const char *fmt, ...) {
-    char buf[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
-    va_end(ap);
-    if (ctx) ctx->err = buf;
-    return code;
-}
 
-#define CK(ctx, call)                                                                            \
-    do {                                                                                         \
-        cudaError_t e_ = (call);                                                                 \
-        if (e_ != cudaSuccess)                                                                   \
-            return fail(ctx, e_ == cudaErrorMemoryAllocation ? TDGL_ENOMEM : TDGL_ECUDA,         \
-                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);   \
-    } while (0)
 
-#define TRY(x)                  \
-    do {                        \
-        int r_ = (x);           \
-        if (r_ != TDGL_OK) return r_; \
-    } while (0)
 
 int smooth_at_least(int m, bool even) {
     // smallest 2^a 3^b >= m (even when asked)
@@ -209,37 +171,8 @@ double tetragonal_ps(const tdgl_material &m, double T) {
     return best;
 }
 
-void ctx_set(tdgl_ctx *ctx) { cudaSetDevice(ctx->device); }
 
-cudaEvent_t take_event(tdgl_ctx *ctx) {
-    if (!ctx->pool.empty()) {
-        cudaEvent_t e = ctx->pool.back();
-        ctx->pool.pop_back();
-        return e;
-    }
-    cudaEvent_t e;
-    cudaEventCreate(&e);
-    return e;
-}
 
-template <class F>
-int launch(tdgl_ctx *ctx, int kind, F f) {
-    ProfRec r{kind, nullptr, nullptr};
-    if (ctx->profiling) {
-        r.a = take_event(ctx);
-        r.b = take_event(ctx);
-        cudaEventRecord(r.a, ctx->stream);
-    }
-    f();
-    cudaError_t e = cudaGetLastError();
-    if (ctx->profiling) {
-        cudaEventRecord(r.b, ctx->stream);
-        ctx->recs.push_back(r);
-    }
-    ctx->launches++;
-    if (e != cudaSuccess) return fail(ctx, TDGL_ECUDA, "kernel launch (kind %d): %s", kind, cudaGetErrorString(e));
-    return TDGL_OK;
-}
 
 // Record the launches issued by record() into a CUDA graph and instantiate it.  The launches are
 // not counted at capture time; *kernels receives how many each replay issues.
@@ -822,6 +755,8 @@ void tdgl_ctx_destroy(tdgl_ctx *ctx) {
     for (auto b : bs) tdgl_batch_destroy(b);
     const std::vector<tdgl_sim *> ss = ctx->sims;
     for (auto sm : ss) tdgl_sim_destroy(sm);
+    const std::vector<tdgl_unet *> ns = ctx->nets;
+    for (auto n : ns) tdgl_unet_destroy(n);
     for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);

@@ -1,0 +1,512 @@
+// Kernels of the learned warm start (a 3D U-Net): BF16 tensor-core convolutions with FP32
+// accumulation in tensor memory, and the memory-bound pieces around them.
+//
+// Activations are channels-last ("NDHWC": [voxel][channel], voxel = ((b Z + z) Y + y) X + x) in
+// BF16, gradients flowing back are FP32.  A convolution is an implicit GEMM
+//     Y[v][o] = sum_k A[v][k] W[o][k],   k = (tap, i) -> 8-channel groups g = tap * (Ci/8) + i/8,
+// M = 128 voxels per CTA, N = a tile of output channels, K consumed 16 at a time (two groups).
+// The weight-gradient GEMM swaps the roles: M = output channels, N = (tap, input channel),
+// K = voxels, with both operands transposed to [channel][voxel] first.
+#pragma once
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "philox.cuh"
+#include "tc.cuh"
+
+namespace tdgl {
+namespace unet {
+
+constexpr int kStages = 4;          // cp.async -> MMA pipeline depth
+constexpr long kSpin = 1L << 24;    // mbarrier polls before a wait is declared failed
+
+template <int BN> __host__ __device__ constexpr uint32_t stage_bytes() { return 128u * 32u + (uint32_t)BN * 32u; }
+template <int BN> __host__ __device__ constexpr uint32_t tmem_cols() { return BN < 32 ? 32u : (uint32_t)BN; }
+// dynamic shared memory: the stage ring, barriers and the TMEM slot, padded so that at most
+// 512 / tmem_cols CTAs fit on an SM (their TMEM allocations then always fit together)
+template <int BN> __host__ __device__ constexpr uint32_t gemm_smem() {
+    constexpr uint32_t need = kStages * stage_bytes<BN>() + 128u;
+    constexpr uint32_t per_sm = 232448u;                       // 227 KB + the 1 KB reserve
+    constexpr uint32_t fit = per_sm / (512u / tmem_cols<BN>() + 1u) + 1024u;
+    return (need > fit ? need : fit) + 1024u;                  // + alignment slack
+}
+
+// Pipelined main loop shared by both GEMMs: load(c, a_smem, b_smem) fills stage tiles of K-chunk
+// c with cp.async; one thread issues the MMA of each chunk once every thread's copies landed; a
+// stage is refilled after the MMA that read it has committed.  Returns false (in every thread)
+// if a barrier wait ran out; the caller then still drains and frees.
+template <int BN, class Load>
+__device__ __forceinline__ bool mainloop(Load load, int nch, uint8_t *tiles, uint64_t *bar, uint32_t tmem, int *issued) {
+    constexpr uint32_t ST = stage_bytes<BN>(), AB = 128u * 32u;
+    constexpr uint32_t idesc = tc::idesc_bf16(128, BN);
+    const uint32_t base = tc::saddr(tiles);
+    const int tid = threadIdx.x;
+    bool ok = true;
+    *issued = 0;
+#pragma unroll
+    for (int c = 0; c < kStages - 1; ++c) {
+        if (c < nch) load(c, base + (c % kStages) * ST, base + (c % kStages) * ST + AB);
+        tc::cp_commit();
+    }
+    for (int c = 0; c < nch; ++c) {
+        const int cn = c + kStages - 1;
+        if (cn < nch && ok) {
+            const int s = cn % kStages;
+            if (cn >= kStages) ok = tc::mbar_wait(&bar[s], (unsigned)((cn - kStages) / kStages) & 1u, kSpin);
+            if (ok) load(cn, base + s * ST, base + s * ST + AB);
+        }
+        tc::cp_commit();
+        tc::cp_wait<kStages - 1>();
+        tc::fence_proxy_async();
+        ok = !__syncthreads_or(!ok);
+        if (!ok) break;
+        if (tid == 0) {
+            tc::fence_after();
+            const uint32_t s = (uint32_t)(c % kStages);
+            tc::mma_bf16(tmem, tc::sdesc(base + s * ST), tc::sdesc(base + s * ST + AB), idesc, c > 0 ? 1u : 0u);
+            tc::mma_commit(&bar[s]);
+        }
+        *issued = c + 1;
+    }
+    tc::cp_wait<0>();
+    // the last MMA issued: its barrier phase completes when it (and all before it) finished
+    if (*issued > 0) {
+        const int c = *issued - 1;
+        const bool done = tc::mbar_wait(&bar[c % kStages], (unsigned)(c / kStages) & 1u, kSpin);
+        ok = ok && done;
+    }
+    tc::fence_after();
+    return !__syncthreads_or(!ok);
+}
+
+// CTA prologue: barriers, TMEM allocation by warp 0; returns the TMEM base address
+template <int BN>
+__device__ __forceinline__ uint32_t prologue(uint64_t *bar, uint32_t *tslot) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) tc::mbar_init(&bar[s], 1);
+        tc::mbar_fence_init();
+    }
+    if (threadIdx.x < 32) tc::tmem_alloc(tslot, tmem_cols<BN>());
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    return *tslot;
+}
+
+template <int BN>
+__device__ __forceinline__ void epilogue_free(uint32_t tmem) {
+    tc::fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc::fence_after();
+        tc::tmem_free(tmem, tmem_cols<BN>());
+    }
+}
+
+struct ConvP {
+    const __nv_bfloat16 *x;   // [nvox][Ci]
+    const __nv_bfloat16 *w;   // [Co][G * 8]  (k-group g = tap * Ci/8 + i/8; G even, tail zero)
+    const float *bias;        // [Co] or null
+    void *y;                  // [nvox][Co], BF16 or FP32
+    long nvox;
+    int Z, Y, X, Ci, Co, ntap, G, relu, f32out;
+    int *err;
+};
+
+// Y = act(bias + conv(X, W)) for a 3x3x3 (ntap 27) or 1x1x1 (ntap 1) kernel, zero padding
+template <int BN>
+__global__ void __launch_bounds__(128) k_conv(ConvP p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tiles + kStages * stage_bytes<BN>());
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + kStages);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long v = (long)blockIdx.x * 128 + tid;      // this thread's row: output voxel
+    const int n0 = blockIdx.y * BN;
+    const bool vok = v < p.nvox;
+    int vx = 0, vy = 0, vz = 0;
+    long vb = 0;
+    if (vok) {
+        long q = v;
+        vx = (int)(q % p.X); q /= p.X;
+        vy = (int)(q % p.Y); q /= p.Y;
+        vz = (int)(q % p.Z); vb = q / p.Z;
+    }
+    const int cg = p.Ci >> 3;
+    const uint32_t tmem = prologue<BN>(bar, tslot);
+    auto load = [&](int c, uint32_t a_s, uint32_t b_s) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int g = 2 * c + h;
+            const int tap = g / cg, c8 = g - tap * cg;
+            int dz = 0, dy = 0, dx = 0;
+            if (p.ntap == 27) { dz = tap / 9 - 1; dy = (tap / 3) % 3 - 1; dx = tap % 3 - 1; }
+            const int sz = vz + dz, sy = vy + dy, sx = vx + dx;
+            const bool ok = vok && tap < p.ntap && (unsigned)sz < (unsigned)p.Z && (unsigned)sy < (unsigned)p.Y &&
+                            (unsigned)sx < (unsigned)p.X;
+            const __nv_bfloat16 *src = ok ? p.x + ((((vb * p.Z + sz) * p.Y + sy) * p.X + sx) * p.Ci + c8 * 8) : p.x;
+            tc::cp16(a_s + tc::tile_off(tid, h), src, ok);
+        }
+        for (int i = tid; i < 2 * BN; i += 128) {
+            const int n = i >> 1, h = i & 1, co = n0 + n;
+            const bool ok = co < p.Co;
+            const __nv_bfloat16 *src = ok ? p.w + ((long)co * p.G + 2 * c + h) * 8 : p.w;
+            tc::cp16(b_s + tc::tile_off(n, h), src, ok);
+        }
+    };
+    int issued;
+    const bool ok = mainloop<BN>(load, p.G / 2, tiles, bar, tmem, &issued);
+    if (!ok) {
+        if (tid == 0) atomicOr(p.err, 1);
+    } else {
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float r[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            if (!vok) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int co = n0 + c0 + j;
+                if (co >= p.Co) break;
+                float a = r[j] + (p.bias ? p.bias[co] : 0.f);
+                if (p.relu) a = fmaxf(a, 0.f);
+                if (p.f32out) reinterpret_cast<float *>(p.y)[v * p.Co + co] = a;
+                else reinterpret_cast<__nv_bfloat16 *>(p.y)[v * p.Co + co] = __float2bfloat16_rn(a);
+            }
+        }
+    }
+    epilogue_free<BN>(tmem);
+}
+
+struct WgradP {
+    const __nv_bfloat16 *dyt;   // [Co][nvox]  upstream gradient (after the ReLU mask), transposed
+    const __nv_bfloat16 *xs;    // [3][Ci][nvox]  layer input transposed, shifted by dx = -1, 0, +1
+    float *dw;                  // [Co][ldw], column tap * Ci + i; accumulated atomically
+    long nvox;
+    int Z, Y, X, Ci, Co, ntap, ldw, vchunk;
+    int *err;
+};
+
+// dW[o][tap, i] += sum over this CTA's voxel chunk of dY[v][o] X[v + off(tap)][i]
+template <int BN>
+__global__ void __launch_bounds__(128) k_wgrad(WgradP p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tiles + kStages * stage_bytes<BN>());
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + kStages);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int n0 = blockIdx.x * BN;
+    const long vbase = (long)blockIdx.y * p.vchunk;
+    const long vend = (vbase + p.vchunk < p.nvox) ? vbase + p.vchunk : p.nvox;
+    const int nch = (int)((vend - vbase + 15) / 16);
+    const int N = p.ntap * p.Ci;
+    const long YX = (long)p.Y * p.X;
+    const uint32_t tmem = prologue<BN>(bar, tslot);
+    auto load = [&](int c, uint32_t a_s, uint32_t b_s) {
+        const long k0 = vbase + 16L * c;
+        {   // A: row o = tid, voxels k0 + 8h .. + 7
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const long kv = k0 + 8 * h;
+                const bool ok = tid < p.Co && kv < vend;
+                const __nv_bfloat16 *src = ok ? p.dyt + (long)tid * p.nvox + kv : p.dyt;
+                tc::cp16(a_s + tc::tile_off(tid, h), src, ok);
+            }
+        }
+        for (int i = tid; i < 2 * BN; i += 128) {
+            const int n = i >> 1, h = i & 1, ng = n0 + n;
+            const long kv = k0 + 8 * h;
+            bool ok = ng < N && kv < vend;
+            const __nv_bfloat16 *src = p.xs;
+            if (ok) {
+                const int tap = ng / p.Ci, ci = ng - tap * p.Ci;
+                int dz = 0, dy = 0, dx = 0;
+                if (p.ntap == 27) { dz = tap / 9 - 1; dy = (tap / 3) % 3 - 1; dx = tap % 3 - 1; }
+                const long row = kv / p.X;                        // the 8 voxels share (b, z, y)
+                const int y = (int)(row % p.Y), z = (int)((row / p.Y) % p.Z);
+                ok = (unsigned)(z + dz) < (unsigned)p.Z && (unsigned)(y + dy) < (unsigned)p.Y;
+                if (ok) src = p.xs + ((long)(dx + 1) * p.Ci + ci) * p.nvox + kv + dz * YX + (long)dy * p.X;
+            }
+            tc::cp16(b_s + tc::tile_off(n, h), src, ok);
+        }
+    };
+    int issued;
+    const bool ok = mainloop<BN>(load, nch, tiles, bar, tmem, &issued);
+    if (!ok) {
+        if (tid == 0) atomicOr(p.err, 1);
+    } else {
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float r[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            if (tid >= p.Co) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int ng = n0 + c0 + j;
+                if (ng < N) atomicAdd(&p.dw[(long)tid * p.ldw + ng], r[j]);
+            }
+        }
+    }
+    epilogue_free<BN>(tmem);
+}
+
+// ---- memory-bound helpers ---------------------------------------------------------------------
+
+// [B][C][Z][Y][X] float -> [voxel][Cp] BF16 (channels C..Cp-1 zero)
+__global__ void k_to_ndhwc(const float *__restrict__ in, __nv_bfloat16 *__restrict__ out, long V, int C, int Cp, long vps) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V * Cp; i += (long)gridDim.x * blockDim.x) {
+        const long v = i / Cp;
+        const int c = (int)(i - v * Cp);
+        const long b = v / vps, s = v - b * vps;
+        out[i] = __float2bfloat16_rn(c < C ? in[(b * C + c) * vps + s] : 0.f);
+    }
+}
+// [B][C][Z][Y][X] float -> [voxel][Cp] float (channels C..Cp-1 zero)
+__global__ void k_to_ndhwc_f32(const float *__restrict__ in, float *__restrict__ out, long V, int C, int Cp, long vps) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V * Cp; i += (long)gridDim.x * blockDim.x) {
+        const long v = i / Cp;
+        const int c = (int)(i - v * Cp);
+        const long b = v / vps, s = v - b * vps;
+        out[i] = c < C ? in[(b * C + c) * vps + s] : 0.f;
+    }
+}
+// first C channels of [voxel][Cp] float -> [B][C][Z][Y][X] float
+__global__ void k_from_ndhwc_f32(const float *__restrict__ in, float *__restrict__ out, long V, int C, int Cp, long vps) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V * C; i += (long)gridDim.x * blockDim.x) {
+        const long b = i / (C * vps), r = i - b * C * vps;
+        const int c = (int)(r / vps);
+        const long s = r - (long)c * vps;
+        out[i] = in[(b * vps + s) * Cp + c];
+    }
+}
+
+// 2x2x2 average pooling, BF16 [voxel][C] at (Z, Y, X) -> half resolution
+__global__ void k_pool(const __nv_bfloat16 *__restrict__ in, __nv_bfloat16 *__restrict__ out, long Vh, int C, int Zh,
+                       int Yh, int Xh) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < Vh * C; i += (long)gridDim.x * blockDim.x) {
+        const long vh = i / C;
+        const int c = (int)(i - vh * C);
+        long q = vh;
+        const int x = (int)(q % Xh); q /= Xh;
+        const int y = (int)(q % Yh); q /= Yh;
+        const int z = (int)(q % Zh);
+        const long b = q / Zh;
+        float s = 0.f;
+        for (int d = 0; d < 8; ++d) {
+            const long v = (((b * 2 * Zh + 2 * z + (d >> 2)) * 2 * Yh + 2 * y + ((d >> 1) & 1)) * 2 * Xh + 2 * x + (d & 1));
+            s += __bfloat162float(in[v * C + c]);
+        }
+        out[i] = __float2bfloat16_rn(0.125f * s);
+    }
+}
+// gradient of k_pool: out[v][c] (+)= g[parent(v)][c] / 8   (float)
+__global__ void k_pool_bwd(const float *__restrict__ g, float *__restrict__ out, long V, int C, int Z, int Y, int X,
+                           int accumulate) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V * C; i += (long)gridDim.x * blockDim.x) {
+        const long v = i / C;
+        const int c = (int)(i - v * C);
+        long q = v;
+        const int x = (int)(q % X); q /= X;
+        const int y = (int)(q % Y); q /= Y;
+        const int z = (int)(q % Z);
+        const long b = q / Z;
+        const long vh = ((b * (Z / 2) + z / 2) * (Y / 2) + y / 2) * (X / 2) + x / 2;
+        const float a = 0.125f * g[vh * C + c];
+        out[i] = accumulate ? out[i] + a : a;
+    }
+}
+// nearest upsampling of deep [voxel/8][Cd] concatenated with skip [voxel][Cs] -> [voxel][Cd + Cs]
+__global__ void k_upcat(const __nv_bfloat16 *__restrict__ deep, const __nv_bfloat16 *__restrict__ skip,
+                        __nv_bfloat16 *__restrict__ out, long V, int Cd, int Cs, int Z, int Y, int X) {
+    const int C = Cd + Cs;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V * C; i += (long)gridDim.x * blockDim.x) {
+        const long v = i / C;
+        const int c = (int)(i - v * C);
+        if (c >= Cd) {
+            out[i] = skip[v * Cs + (c - Cd)];
+            continue;
+        }
+        long q = v;
+        const int x = (int)(q % X); q /= X;
+        const int y = (int)(q % Y); q /= Y;
+        const int z = (int)(q % Z);
+        const long b = q / Z;
+        const long vh = ((b * (Z / 2) + z / 2) * (Y / 2) + y / 2) * (X / 2) + x / 2;
+        out[i] = deep[vh * Cd + c];
+    }
+}
+// gradient of k_upcat: deep gradient (sum over the 8 children) and skip gradient (copy)
+__global__ void k_upcat_bwd(const float *__restrict__ g, float *__restrict__ gdeep, float *__restrict__ gskip, long Vh,
+                            int Cd, int Cs, int Zh, int Yh, int Xh) {
+    const int C = Cd + Cs;
+    const long V = Vh * 8;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < Vh * Cd + V * Cs; i += (long)gridDim.x * blockDim.x) {
+        if (i >= Vh * Cd) {
+            const long j = i - Vh * Cd, v = j / Cs;
+            const int c = (int)(j - v * Cs);
+            gskip[j] = g[v * C + Cd + c];
+            continue;
+        }
+        const long vh = i / Cd;
+        const int c = (int)(i - vh * Cd);
+        long q = vh;
+        const int x = (int)(q % Xh); q /= Xh;
+        const int y = (int)(q % Yh); q /= Yh;
+        const int z = (int)(q % Zh);
+        const long b = q / Zh;
+        float s = 0.f;
+        for (int d = 0; d < 8; ++d) {
+            const long v = (((b * 2 * Zh + 2 * z + (d >> 2)) * 2 * Yh + 2 * y + ((d >> 1) & 1)) * 2 * Xh + 2 * x + (d & 1));
+            s += g[v * C + c];
+        }
+        gdeep[i] = s;
+    }
+}
+
+// ReLU backward and the operands of the layer's backward GEMMs:
+//   d[v][c] = g[v][c] * (out[v][c] > 0)  (out null: no ReLU)  -> BF16 [voxel][C] and [C][voxel],
+//   db[c] += sum_v d[v][c].  Block: 32 voxels x C channels through shared memory.
+__global__ void k_relu_bwd(const float *__restrict__ g, const __nv_bfloat16 *__restrict__ out,
+                           __nv_bfloat16 *__restrict__ d, __nv_bfloat16 *__restrict__ dt, float *__restrict__ db, long V,
+                           int C) {
+    __shared__ float tile[32][129];
+    const long v0 = (long)blockIdx.x * 32;
+    for (int i = threadIdx.x; i < 32 * C; i += blockDim.x) {
+        const int r = i / C, c = i - r * C;
+        const long v = v0 + r;
+        float a = 0.f;
+        if (v < V) {
+            a = g[v * C + c];
+            if (out && !(__bfloat162float(out[v * C + c]) > 0.f)) a = 0.f;
+            d[v * C + c] = __float2bfloat16_rn(a);
+        }
+        tile[r][c] = __bfloat162float(__float2bfloat16_rn(a));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 32 * C; i += blockDim.x) {
+        const int c = i / 32, r = i - c * 32;
+        if (v0 + r < V) dt[(long)c * V + v0 + r] = __float2bfloat16_rn(tile[r][c]);
+    }
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float s = 0.f;
+        for (int r = 0; r < 32; ++r) s += tile[r][c];
+        atomicAdd(&db[c], s);
+    }
+}
+
+// layer input transposed and shifted along x: xs[j][c][v] = x[v + (j - 1)][c] when x + j - 1 is
+// inside the row, else 0 (j = 0, 1, 2; only j = 1 for a 1x1x1 kernel)
+__global__ void k_xshift(const __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ xs, long V, int C, int X,
+                         int nshift) {
+    __shared__ __nv_bfloat16 tile[34][193];
+    const long v0 = (long)blockIdx.x * 32;
+    for (int i = threadIdx.x; i < 34 * C; i += blockDim.x) {
+        const int r = i / C, c = i - r * C;
+        const long v = v0 + r - 1;
+        tile[r][c] = (v >= 0 && v < V) ? x[v * C + c] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    const int j0 = nshift == 3 ? 0 : 1;
+    for (int i = threadIdx.x; i < nshift * 32 * C; i += blockDim.x) {
+        const int jj = i / (32 * C), rem = i - jj * 32 * C;
+        const int c = rem / 32, r = rem - c * 32;
+        const long v = v0 + r;
+        if (v >= V) continue;
+        const int j = j0 + jj, xx = (int)(v % X) + j - 1;
+        const __nv_bfloat16 val = ((unsigned)xx < (unsigned)X) ? tile[r + j][c] : __float2bfloat16_rn(0.f);
+        xs[((long)j * C + c) * V + v] = val;
+    }
+}
+
+// squared error of y [n] against t, summed and divided by denom (the number of real elements;
+// padded channels hold 0 in both), and its gradient 2 (y - t) / denom as FP32
+__global__ void k_mse(const float *__restrict__ y, const float *__restrict__ t, float *__restrict__ g, long n,
+                      double denom, double *__restrict__ loss) {
+    __shared__ double red[32];
+    double s = 0.0;
+    const float sc = (float)(2.0 / denom);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float d = y[i] - t[i];
+        s += (double)d * d;
+        g[i] = sc * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
+        atomicAdd(loss, a / denom);
+    }
+}
+
+__global__ void k_add(float *__restrict__ a, const float *__restrict__ b, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) a[i] += b[i];
+}
+
+// Adam on one layer (master weights [Co][Kp] FP32 in the GEMM layout, bias [Co]); refreshes the
+// BF16 forward weights and the BF16 transposed weights of the data-gradient convolution:
+//     wt[i][tap' * Co + o] = w[o][(ntap - 1 - tap') * Ci + i]
+struct AdamP {
+    float *w, *m, *v, *gw;        // [Co][Kp]
+    float *b, *mb, *vb, *gb;      // [Co]
+    __nv_bfloat16 *wf, *wt;       // forward [Co][Kp], transposed [Ci][Kpt] (may be null)
+    int Co, Ci, ntap, Kp, Kpt;
+    float lr, b1, b2, eps, c1, c2;   // c1 = 1 - b1^k, c2 = 1 - b2^k
+};
+__global__ void k_adam(AdamP p) {
+    const long nw = (long)p.Co * p.Kp;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nw + p.Co; i += (long)gridDim.x * blockDim.x) {
+        float *w, *m, *v, g;
+        if (i < nw) { w = p.w + i; m = p.m + i; v = p.v + i; g = p.gw[i]; }
+        else { const long j = i - nw; w = p.b + j; m = p.mb + j; v = p.vb + j; g = p.gb[j]; }
+        const float mm = p.b1 * *m + (1.f - p.b1) * g;
+        const float vv = p.b2 * *v + (1.f - p.b2) * g * g;
+        *m = mm;
+        *v = vv;
+        const float nw_ = *w - p.lr * (mm / p.c1) / (sqrtf(vv / p.c2) + p.eps);
+        *w = nw_;
+        if (i < nw) {
+            p.wf[i] = __float2bfloat16_rn(nw_);
+            const int o = (int)(i / p.Kp), k = (int)(i - (long)o * p.Kp);
+            if (p.wt && k < p.ntap * p.Ci) {
+                const int tap = k / p.Ci, ci = k - tap * p.Ci;
+                p.wt[(long)ci * p.Kpt + (p.ntap - 1 - tap) * p.Co + o] = __float2bfloat16_rn(nw_);
+            }
+        }
+    }
+}
+
+// BF16 copies of master weights (after a host upload): forward and transposed layouts
+__global__ void k_wcopy(const float *__restrict__ w, __nv_bfloat16 *__restrict__ wf, __nv_bfloat16 *__restrict__ wt,
+                        int Co, int Ci, int ntap, int Kp, int Kpt) {
+    const long nw = (long)Co * Kp;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nw; i += (long)gridDim.x * blockDim.x) {
+        const float a = w[i];
+        wf[i] = __float2bfloat16_rn(a);
+        const int o = (int)(i / Kp), k = (int)(i - (long)o * Kp);
+        if (wt && k < ntap * Ci) {
+            const int tap = k / Ci, ci = k - tap * Ci;
+            wt[(long)ci * Kpt + (ntap - 1 - tap) * Co + o] = __float2bfloat16_rn(a);
+        }
+    }
+}
+
+// He-normal initialisation of one layer's master weights [Co][Kp] (zero in the padding columns):
+// standard normals by the Box-Muller transform of two Philox4x32-10 outputs keyed by the seed,
+// counters (layer, element, 0 / 1)
+__global__ void k_init_he(float *__restrict__ w, int Co, int Kp, int K, float sd, uint32_t layer, uint32_t k0,
+                          uint32_t k1) {
+    const long n = (long)Co * Kp;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int k = (int)(i % Kp);
+        if (k >= K) { w[i] = 0.f; continue; }
+        const uint32_t u1 = philox_first(layer, (uint32_t)i, 0u, 0u, k0, k1);
+        const uint32_t u2 = philox_first(layer, (uint32_t)i, 1u, 0u, k0, k1);
+        const double a = ((double)u1 + 0.5) * 2.3283064365386963e-10, b = ((double)u2 + 0.5) * 2.3283064365386963e-10;
+        w[i] = (float)(sd * sqrt(-2.0 * log(a)) * cos(6.283185307179586 * b));
+    }
+}
+
+}  // namespace unet
+}  // namespace tdgl

@@ -18,9 +18,9 @@ LIB_PATH = os.path.join(HERE, "libtdgl.so")
 OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ENOTCONVERGED, ESTATE, ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7
 HOST, DEVICE = 0, 1
 TERM_LANDAU, TERM_GRAD, TERM_ELEC, TERM_EXT, TERM_ALL = 1, 2, 4, 8, 15
-K_STEP, K_YFWD, K_ZCONV, K_YINV, K_XFWD, K_OTHER = range(6)
+K_STEP, K_YFWD, K_ZCONV, K_YINV, K_XFWD, K_OTHER, K_UNET = range(7)
 KERNEL_NAMES = {K_STEP: "k_rows<STEP>", K_YFWD: "k_yfwd", K_ZCONV: "k_zconv", K_YINV: "k_yinv",
-                K_XFWD: "k_rows<XFWD>", K_OTHER: "other"}
+                K_XFWD: "k_rows<XFWD>", K_OTHER: "other", K_UNET: "unet"}
 MAX_MATERIALS, MAX_DIM = 16, 1024
 EULER, HEUN = 0, 1
 
@@ -81,6 +81,16 @@ _SIGS = {
     "tdgl_batch_step": (_I, [_VP, _I, ctypes.POINTER(_D)]),
     "tdgl_batch_relax": (_I, [_VP, ctypes.POINTER(_D), _D, _L, _I, ctypes.POINTER(_L)]),
     "tdgl_elec_field_static": (_I, [_I, _I, _I, _D, _D, _D, _D, _VP, _VP, _VP, _VP]),
+    "tdgl_unet_create": (_I, [_VP, _I, _I, _I, _VP, _I, _I, _I, _I, ctypes.c_uint64, ctypes.POINTER(_VP)]),
+    "tdgl_unet_destroy": (None, [_VP]),
+    "tdgl_unet_param_count": (_L, [_VP]),
+    "tdgl_unet_set_params": (_I, [_VP, _VP]),
+    "tdgl_unet_get_params": (_I, [_VP, _VP]),
+    "tdgl_unet_forward": (_I, [_VP, _VP, _VP, _I, _I]),
+    "tdgl_unet_loss_grad": (_I, [_VP, _VP, _VP, _I, ctypes.POINTER(_D), _VP, _I]),
+    "tdgl_unet_train_step": (_I, [_VP, _VP, _VP, _I, _D, ctypes.POINTER(_D), _I]),
+    "tdgl_conv3d": (_I, [_VP, _VP, _VP, _VP, _VP, _I, _I, _I, _I, _I, _I, _I, _I]),
+    "tdgl_conv3d_backward": (_I, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I, _I, _I, _I, _I, _I, _I]),
     "tdgl_profile": (_I, [_VP, _I]),
     "tdgl_profile_read": (_I, [_VP, _I, ctypes.POINTER(_D), ctypes.POINTER(_L)]),
 }
@@ -346,3 +356,118 @@ def elec_field_static(P, E, cell, eps_b, mat=None, stream=0):
                                     None if not stream else _VP(int(stream)))
     if rc != OK:
         raise TdglError(rc, "tdgl_elec_field_static failed")
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if shape is not None and a.size != int(np.prod(shape)):
+        raise ValueError(f"expected {int(np.prod(shape))} values, got {a.size}")
+    return a
+
+
+class UNet:
+    """The learned warm start (tdgl_unet_*): a 3D U-Net trained and run on the tensor cores.
+
+    Tensors are (batch, channels, nz, ny, nx) float32: numpy arrays (host) or contiguous CUDA
+    torch tensors (device; inputs and outputs must then all be on the device).  Parameters are one
+    flat float32 vector in the layer order of the library (see include/tdgl.h).
+    """
+
+    def __init__(self, ctx: Context, shape, cin, cout, chans=(16, 32, 64, 128), max_batch=4, seed=0):
+        self.ctx, self.lib = ctx, ctx.lib
+        self.nx, self.ny, self.nz = (int(v) for v in shape)
+        self.cin, self.cout, self.levels = int(cin), int(cout), len(chans)
+        ch = (ctypes.c_int * len(chans))(*chans)
+        h = _VP()
+        ctx.check(self.lib.tdgl_unet_create(ctx.h, self.cin, self.cout, self.levels, ch, self.nx, self.ny, self.nz,
+                                            int(max_batch), int(seed), ctypes.byref(h)))
+        self.h = h
+        ctx._adopt(self)
+
+    @property
+    def nvox(self):
+        return self.nx * self.ny * self.nz
+
+    def param_count(self):
+        return int(self.lib.tdgl_unet_param_count(self.h))
+
+    def set_params(self, p):
+        p = _f32(p, (self.param_count(),))
+        self.ctx.check(self.lib.tdgl_unet_set_params(self.h, p.ctypes.data))
+
+    def get_params(self):
+        p = np.empty(self.param_count(), dtype=np.float32)
+        self.ctx.check(self.lib.tdgl_unet_get_params(self.h, p.ctypes.data))
+        return p
+
+    def _io(self, x, c):
+        if isinstance(x, np.ndarray):
+            x = _f32(x)
+            if x.size % (c * self.nvox):
+                raise ValueError("tensor size is not a multiple of channels x cells")
+            return x, x.ctypes.data, HOST, x.size // (c * self.nvox)
+        ptr, where = _ptr(x)
+        return x, ptr, where, x.numel() // (c * self.nvox)
+
+    def forward(self, x):
+        x, px, where, B = self._io(x, self.cin)
+        if where == HOST:
+            y = np.empty((B, self.cout, self.nz, self.ny, self.nx), dtype=np.float32)
+            py = y.ctypes.data
+        else:
+            import torch
+            y = torch.empty((B, self.cout, self.nz, self.ny, self.nx), dtype=torch.float32, device=x.device)
+            py = y.data_ptr()
+        self.ctx.check(self.lib.tdgl_unet_forward(self.h, px, py, B, where))
+        return y
+
+    def loss_grad(self, x, t):
+        x, px, where, B = self._io(x, self.cin)
+        t, pt, _, _ = self._io(t, self.cout)
+        g = np.empty(self.param_count(), dtype=np.float32)
+        loss = _D()
+        self.ctx.check(self.lib.tdgl_unet_loss_grad(self.h, px, pt, B, ctypes.byref(loss), g.ctypes.data, where))
+        return loss.value, g
+
+    def train_step(self, x, t, lr):
+        x, px, where, B = self._io(x, self.cin)
+        t, pt, _, _ = self._io(t, self.cout)
+        loss = _D()
+        self.ctx.check(self.lib.tdgl_unet_train_step(self.h, px, pt, B, float(lr), ctypes.byref(loss), where))
+        return loss.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            if getattr(self.ctx, "h", None):
+                self.lib.tdgl_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def conv3d(ctx: Context, x, w, b, relu=False):
+    """One tensor-core convolution (tdgl_conv3d): x (B, ci, nz, ny, nx), w (co, ci, k, k, k), b (co,)."""
+    x, w, b = _f32(x), _f32(w), _f32(b)
+    B, ci, nz, ny, nx = x.shape
+    co, k = w.shape[0], w.shape[-1]
+    y = np.empty((B, co, nz, ny, nx), dtype=np.float32)
+    ctx.check(ctx.lib.tdgl_conv3d(ctx.h, x.ctypes.data, w.ctypes.data, b.ctypes.data, y.ctypes.data, B, ci, co, k, nx,
+                                  ny, nz, int(relu)))
+    return y
+
+
+def conv3d_backward(ctx: Context, x, w, dy):
+    """Gradients (dx, dw, db) of one convolution for upstream gradient dy (tdgl_conv3d_backward)."""
+    x, w, dy = _f32(x), _f32(w), _f32(dy)
+    B, ci, nz, ny, nx = x.shape
+    co, k = w.shape[0], w.shape[-1]
+    dx = np.empty_like(x)
+    dw = np.empty_like(w)
+    db = np.empty(co, dtype=np.float32)
+    ctx.check(ctx.lib.tdgl_conv3d_backward(ctx.h, x.ctypes.data, w.ctypes.data, dy.ctypes.data, dx.ctypes.data,
+                                           dw.ctypes.data, db.ctypes.data, B, ci, co, k, nx, ny, nz))
+    return dx, dw, db

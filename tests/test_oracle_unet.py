@@ -139,3 +139,23 @@ def test_training_reduces_loss_on_a_fixed_batch():
     t = 0.1 * np.tanh(x[:, :1]).repeat(3, axis=1)
     losses = [U.train_step(p, m, v, k, x, t, levels, lr=3e-3) for k in range(1, 31)]
     assert losses[-1] < 0.5 * losses[0]
+
+
+def test_bf16_rounding_matches_definition():
+    # 1 + 2^-8 is a tie between 1 and 1 + 2^-7: even mantissa wins (1); 1 + 3*2^-9 rounds up
+    assert U.bf16(1.0 + 2.0 ** -8) == 1.0
+    assert U.bf16(1.0 + 3 * 2.0 ** -9) == 1.0 + 2.0 ** -7
+    assert U.bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6          # tie between odd 1+2^-7 and even 1+2^-6
+    assert U.bf16(-3.0) == -3.0 and U.bf16(0.0) == 0.0
+    x = np.random.default_rng(8).normal(size=1000)
+    r = U.bf16(x)
+    assert np.all(np.abs(r - x) <= 2.0 ** -8 * np.abs(x) * (1 + 1e-12))   # half an ulp: 2^-8 of the binade floor
+    assert np.array_equal(U.bf16(r), r)                                  # idempotent
+
+
+def test_flat_roundtrip_and_order():
+    p = U.init(4, 3, (16, 32), seed=9)
+    v = U.flat(p, 2)
+    q = U.unflat(v, 4, 3, (16, 32))
+    assert all(np.array_equal(p[n], q[n]) for n in p)
+    assert v[:16 * 4 * 27].reshape(16, 4, 3, 3, 3)[2, 1, 0, 2, 1] == p["enc0a.w"][2, 1, 0, 2, 1]
