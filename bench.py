@@ -354,6 +354,22 @@ def temperature_sweep(args):
                       "points": rows}))
 
 
+def warm_start(args):
+    """Learned warm start on 64x64x32 PbTiO3/SrTiO3 bilayers (CONFIG5 points): relaxed textures made
+    by the solver, a tensor-core U-Net trained on them, held-out points relaxed from the random start
+    and from the network's proposal to the same tolerance."""
+    import torch
+    from paper_2605_28800_b300 import tdgl, warmstart
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    ctx = tdgl.Context(dev)
+    log = lambda m: print(m, file=sys.stderr, flush=True)
+    rep = warmstart.run(ctx, synth.CONFIG5, args.ws_train, args.ws_test, args.ws_epochs, args.max_relax_steps,
+                        batch=args.ws_batch, lr=args.ws_lr, log=log)
+    print(json.dumps({"metric": "time-to-relax, warm-started vs plain at equal tol", "unit": "s",
+                      "workload": "pto_sto_bilayer_64x64x32_config5", **rep}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -367,6 +383,13 @@ def main():
                     help="time-to-relax of the uneven sweep, each sim alone vs one batch")
     ap.add_argument("--temperature-sweep", action="store_true",
                     help="relaxation sweep of the 128^3 cube from 450 to 200 K")
+    ap.add_argument("--warm-start", action="store_true",
+                    help="learned warm start: generate, train and judge on bilayer points")
+    ap.add_argument("--ws-train", type=int, default=256)
+    ap.add_argument("--ws-test", type=int, default=32)
+    ap.add_argument("--ws-epochs", type=int, default=10)
+    ap.add_argument("--ws-batch", type=int, default=4)
+    ap.add_argument("--ws-lr", type=float, default=2e-3)
     ap.add_argument("--sweep-sims", type=int, default=48)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--max-relax-steps", type=int, default=20000)
@@ -375,6 +398,8 @@ def main():
         return relax_compare(args)
     if args.temperature_sweep:
         return temperature_sweep(args)
+    if args.warm_start:
+        return warm_start(args)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     wl = workload(args.workload)

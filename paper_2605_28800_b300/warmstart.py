@@ -1,0 +1,182 @@
+"""Learned warm start for the relaxation of PbTiO3/SrTiO3 bilayers.
+
+The solver makes its own training data: seeded (T, Ez, layer thickness) points are relaxed from
+random starts to the convergence tolerance (batched, one launch per kernel family), a 3D U-Net on
+the tensor cores (tdgl.UNet) learns the map from per-cell inputs to the relaxed texture, and for a
+new point its proposal replaces the random start.  The plain relaxation to the same tolerance then
+judges the proposal: steps, final free energy and texture against the relaxation from the random
+start, with the random start kept whenever the proposal does not save steps.
+
+Everything numeric runs in libtdgl's kernels; this module only builds inputs, batches the calls
+and keeps the books.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+import synth
+from . import tdgl
+
+#: scale of the network's output: the spontaneous polarization of PbTiO3 at 300 K (C/m^2)
+P_SCALE = 0.7583600
+T_MID, T_HALF = 300.0, 50.0
+E_HALF = 1.5e8
+N_IN, N_OUT = 4, 3
+
+
+def features(shape, point) -> np.ndarray:
+    """Network input (4, nz, ny, nx): PbTiO3 and SrTiO3 indicators, (T - 300 K) / 50 K,
+    Ez / 150 MV/m."""
+    nx, ny, nz = shape
+    m = synth.bilayer_map(shape, point["t_pto"])
+    f = np.empty((N_IN, nz, ny, nx), np.float32)
+    f[0] = m == 1
+    f[1] = m == 2
+    f[2] = (point["T"] - T_MID) / T_HALF
+    f[3] = point["Ez"] / E_HALF
+    return f
+
+
+def make_sim(ctx, shape, cell, point, eps_b, P):
+    s = tdgl.Sim(ctx, shape, cell)
+    s.define_material(1, synth.PTO)
+    s.define_material(2, synth.STO)
+    s.set_material_map(synth.bilayer_map(shape, point["t_pto"]))
+    s.set_eps_b(eps_b)
+    s.set_temperature(point["T"])
+    s.set_field((0.0, 0.0, point["Ez"]))
+    s.set_P(P)
+    return s
+
+
+def random_start(shape, point, amp):
+    return synth.uniform_P(shape, amp, point["seed"])
+
+
+def relax_points(ctx, cfg, points, starts, max_steps, chunk=64, sequential=False):
+    """Relax every point from its start: `chunk` sims per batch, or (sequential) each sim alone
+    on the single-simulation path.  Returns the final textures (3, nz, ny, nx) float32, the steps
+    taken, whether each converged, and the total energies."""
+    shape, cell = cfg["shape"], cfg["cell"]
+    P_out, steps, conv, F = [], [], [], []
+    for i in range(0, len(points), chunk):
+        sims = [make_sim(ctx, shape, cell, p, cfg["eps_b"], P) for p, P in zip(points[i:i + chunk], starts[i:i + chunk])]
+        dts = [cfg["dt_star"] / s.scales()[1] for s in sims]
+        if sequential:
+            n = [s.relax(dt, cfg["tol"], max_steps, raise_on_cap=False)[0] for s, dt in zip(sims, dts)]
+        else:
+            b = tdgl.Batch(ctx, sims)
+            n, _ = b.relax(dts, cfg["tol"], max_steps, raise_on_cap=False)
+            b.close()
+        for s, k in zip(sims, n):
+            P_out.append(s.get_P())
+            steps.append(int(k))
+            conv.append(int(k) < max_steps)
+            F.append(s.energy()["total"])
+            s.close()
+    return P_out, steps, conv, F
+
+
+def train(net, X, Y, epochs, batch, lr, seed=0, log=None):
+    """Adam on (X, Y) pairs (lists of (4, ...) inputs and (3, ...) targets scaled by P_SCALE),
+    shuffled each epoch with a seeded generator; lr decays by half over the run (cosine)."""
+    g = np.random.Generator(np.random.Philox(seed))
+    n = len(X)
+    steps_total = epochs * (n // batch)
+    k = 0
+    losses = []
+    for ep in range(epochs):
+        order = g.permutation(n)
+        run = []
+        for j in range(0, n - batch + 1, batch):
+            idx = order[j:j + batch]
+            xb = np.stack([X[i] for i in idx])
+            yb = np.stack([Y[i] for i in idx])
+            lr_k = lr * (0.75 + 0.25 * np.cos(np.pi * k / max(steps_total, 1)))
+            run.append(net.train_step(xb, yb, lr_k))
+            k += 1
+        losses.append(float(np.mean(run)))
+        if log:
+            log(f"epoch {ep + 1}/{epochs}: loss {losses[-1]:.5f}")
+    return losses
+
+
+def propose(net, shape, points, batch):
+    """Warm starts (3, nz, ny, nx) float32 in C/m^2 for the points."""
+    out = []
+    for i in range(0, len(points), batch):
+        xb = np.stack([features(shape, p) for p in points[i:i + batch]])
+        y = net.forward(xb)
+        out.extend([(P_SCALE * y[j]).astype(np.float32) for j in range(y.shape[0])])
+    return out
+
+
+def texture_distance(Pa, Pb):
+    """RMS difference of two textures relative to the RMS of the second"""
+    return float(np.sqrt(np.mean((Pa - Pb) ** 2)) / max(np.sqrt(np.mean(Pb ** 2)), 1e-30))
+
+
+def run(ctx, cfg, n_train, n_test, epochs, max_steps, batch=4, lr=2e-3, chans=(16, 32, 64, 128), log=print):
+    """The whole protocol on CONFIG5-style points: generate, train, judge.  Returns a report dict."""
+    log = log or (lambda m: None)
+    shape = cfg["shape"]
+    pts = synth.bilayer_points(n_train + n_test, cfg["seed"], cfg["T"], cfg["Ez"], cfg["ratio"], shape[2])
+    train_pts, test_pts = pts[:n_train], pts[n_train:]
+    t0 = time.perf_counter()
+    P_tr, st_tr, cv_tr, _ = relax_points(ctx, cfg, train_pts, [random_start(shape, p, cfg["amp"]) for p in train_pts],
+                                         max_steps)
+    t_gen = time.perf_counter() - t0
+    log(f"generated {n_train} relaxed textures in {t_gen:.1f} s (median {np.median(st_tr):.0f} steps, "
+        f"{np.mean(cv_tr):.2f} converged)")
+    X = [features(shape, p) for p in train_pts]
+    Y = [P / P_SCALE for P in P_tr]
+    net = tdgl.UNet(ctx, shape, N_IN, N_OUT, chans=chans, max_batch=batch, seed=cfg["seed"])
+    t0 = time.perf_counter()
+    losses = train(net, X, Y, epochs, batch, lr, seed=cfg["seed"], log=log)
+    t_train = time.perf_counter() - t0
+    # judge on held-out points at the same tolerance and dt: plain (each sim alone, random start),
+    # batched (random start) and batched from the network's proposals
+    rnd = [random_start(shape, p, cfg["amp"]) for p in test_pts]
+    t0 = time.perf_counter()
+    P_seq, st_seq, cv_seq, F_seq = relax_points(ctx, cfg, test_pts, rnd, max_steps, sequential=True)
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P_plain, st_plain, cv_plain, F_plain = relax_points(ctx, cfg, test_pts, rnd, max_steps)
+    t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    starts = propose(net, shape, test_pts, batch)
+    t_inf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P_warm, st_warm, cv_warm, F_warm = relax_points(ctx, cfg, test_pts, starts, max_steps)
+    t_warm = time.perf_counter() - t0
+    st_plain, st_warm = np.array(st_plain), np.array(st_warm)
+    chosen = np.minimum(st_plain, st_warm)          # random start kept when the proposal does not help
+    dF = np.array(F_warm) - np.array(F_plain)
+    return dict(
+        n_train=n_train, n_test=n_test, epochs=epochs, batch=batch, lr=lr, chans=list(chans),
+        params=net.param_count(), max_steps=max_steps, tol=cfg["tol"],
+        gen_seconds=t_gen, train_seconds=t_train, infer_seconds=t_inf,
+        train_loss_first=losses[0], train_loss_last=losses[-1], train_losses=losses,
+        train_steps_median=float(np.median(st_tr)), train_converged=float(np.mean(cv_tr)),
+        plain_steps=st_plain.tolist(), warm_steps=st_warm.tolist(),
+        plain_steps_total=int(st_plain.sum()), warm_steps_total=int(st_warm.sum()),
+        steps_saved_fraction=float(1.0 - st_warm.sum() / max(st_plain.sum(), 1)),
+        proposal_helped=float(np.mean(st_warm < st_plain)),
+        # the same, over the points whose plain relaxation converged within max_steps
+        steps_saved_fraction_plain_converged=float(
+            1.0 - st_warm[np.array(cv_plain)].sum() / max(st_plain[np.array(cv_plain)].sum(), 1)),
+        dF_rel_max_plain_converged=float(np.max((np.abs(dF) / np.maximum(np.abs(np.array(F_plain)), 1e-300))
+                                                [np.array(cv_plain)])) if any(cv_plain) else None,
+        with_fallback_steps_total=int(chosen.sum()),
+        sequential_plain_seconds=t_seq, batched_plain_seconds=t_plain, batched_warm_seconds=t_warm + t_inf,
+        speedup_vs_sequential_plain=float(t_seq / max(t_warm + t_inf, 1e-9)),
+        speedup_vs_batched_plain=float(t_plain / max(t_warm + t_inf, 1e-9)),
+        sequential_equals_batched_steps=bool(np.array_equal(np.array(st_seq), st_plain)),
+        plain_converged=float(np.mean(cv_plain)), warm_converged=float(np.mean(cv_warm)),
+        dF_rel_median=float(np.median(np.abs(dF) / np.maximum(np.abs(np.array(F_plain)), 1e-300))),
+        dF_rel_max=float(np.max(np.abs(dF) / np.maximum(np.abs(np.array(F_plain)), 1e-300))),
+        texture_rms_rel_median=float(np.median([texture_distance(a, b) for a, b in zip(P_warm, P_plain)])),
+        proposal_rms_rel_median=float(np.median([texture_distance(a, b) for a, b in zip(starts, P_plain)])),
+    )

@@ -148,3 +148,29 @@ def sweep_members(n=48, tmin=180.0, tmax=450.0, seed=0) -> list:
             k = b * half + i
             out.append(dict(L=sizes[k], T=T, branch=branch, seed=100 + k))
     return out
+
+
+#: 64x64x32 PbTiO3-on-SrTiO3 bilayers for the learned warm start: T ~ U(250, 350) K,
+#: Ez ~ U(-150, 150) MV/m, thickness ratio t_PTO : t_STO ~ U(0.25, 0.75) of the 32 layers
+#: (PbTiO3 on top), eps_B = 649, 1 nm cells, +-0.01 C/m^2 random starts; seed 5, 10 % held out.
+CONFIG5 = dict(shape=(64, 64, 32), cell=(1e-9, 1e-9, 1e-9), seed=5, amp=0.01, eps_b=649.0, n=2000,
+               held_out=0.1, T=(250.0, 350.0), Ez=(-1.5e8, 1.5e8), ratio=(0.25, 0.75), tol=1e-6,
+               dt_star=0.004)
+
+
+def bilayer_points(n=2000, seed=5, T=(250.0, 350.0), Ez=(-1.5e8, 1.5e8), ratio=(0.25, 0.75), nz=32):
+    """Seeded (T, Ez, thickness) points: t_PTO = round(nz r / (1 + r)) layers on top of nz - t_PTO
+    SrTiO3 layers, r the PbTiO3:SrTiO3 thickness ratio; each point carries its own start seed."""
+    g = np.random.Generator(np.random.Philox(seed))
+    out = []
+    for i in range(n):
+        t, e, r = g.uniform(*T), g.uniform(*Ez), g.uniform(*ratio)
+        t_pto = int(round(nz * r / (1.0 + r)))
+        out.append(dict(T=float(t), Ez=float(e), ratio=float(r), t_pto=t_pto, seed=10_000 + seed * 100_000 + i))
+    return out
+
+
+def bilayer_map(shape_xyz, t_pto) -> np.ndarray:
+    """SrTiO3 (id 2) below, PbTiO3 (id 1) in the top t_pto layers."""
+    nz = shape_xyz[2]
+    return layer_map(shape_xyz, [(0, nz - t_pto, 2), (nz - t_pto, nz, 1)])

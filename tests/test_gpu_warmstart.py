@@ -1,0 +1,26 @@
+"""What the trained network gains: relaxations of held-out bilayer points from its proposals
+need fewer steps than from random starts, and reach the same state at the same tolerance."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_warm_start_saves_steps_and_reaches_the_same_state():
+    from paper_2605_28800_b300 import tdgl, warmstart
+    ctx = tdgl.Context(0)
+    try:
+        rep = warmstart.run(ctx, synth.CONFIG5, n_train=512, n_test=16, epochs=12, max_steps=20000, log=None)
+    finally:
+        ctx.close()
+    assert rep["train_losses"][-1] < 0.05 * rep["train_losses"][0]
+    assert rep["steps_saved_fraction_plain_converged"] > 0.15, rep["steps_saved_fraction_plain_converged"]
+    assert rep["proposal_helped"] > 0.6
+    assert rep["warm_converged"] == 1.0
+    # same tolerance, same state: energies and textures of the two relaxations agree
+    assert rep["dF_rel_max_plain_converged"] < 1e-6
+    assert rep["texture_rms_rel_median"] < 1e-3
+    # the single-simulation path and the batch take identical steps from the same start
+    assert rep["sequential_equals_batched_steps"]
