@@ -229,8 +229,8 @@ int tdgl_profile(tdgl_ctx *ctx, int enable);
 int tdgl_profile_read(tdgl_ctx *ctx, int kind, double *total_ms, long *launches);
 
 /* ---- learned warm start ----------------------------------------------------------------------
- * The relaxation starts from a proposal instead of a random state (the learned initial guess the
- * paper's outlook, Sec. 5, motivates): a 3D U-Net maps per-cell inputs (material indicators,
+ * The relaxation starts from a proposal instead of a random state (a data-driven model trained on
+ * solver-made textures, the use Sec. 5 names for the solver): a 3D U-Net maps per-cell inputs (material indicators,
  * temperature, applied field) to a polarization texture, and the plain relaxation to the same
  * tolerance then judges it.  The network: `levels` resolution levels with chans[l] channels,
  * two 3x3x3 convolutions + ReLU per level, 2x2x2 average pooling down, nearest-neighbour
@@ -243,10 +243,10 @@ int tdgl_profile_read(tdgl_ctx *ctx, int kind, double *total_ms, long *launches)
  * (offsets -1..1, or a single tap for the head) then the biases b[o].
  *
  * tdgl_unet_create: cin input channels (1..8), cout outputs (1..16), 2 <= levels <= 5, chans[l]
- *   multiples of 16 up to 128, grid nx, ny multiples of 8 * 2^(levels-1) ... precisely: every
- *   level's x extent a multiple of 8 and every extent divisible by 2^(levels-1); max_batch >= 1
- *   samples per call.  Weights He-normal from a counter-based generator (Philox4x32-10) keyed by
- *   seed, biases 0.  Returns TDGL_EINVAL on bad shapes, TDGL_ENOMEM if buffers do not fit.
+ *   multiples of 16 in 16..128; grid: nx a multiple of 8 * 2^(levels-1), ny and nz multiples of
+ *   2^(levels-1); max_batch >= 1 samples per call.  Weights He-normal (std sqrt(2 / fan-in)) from a
+ *   counter-based generator (Philox4x32-10) keyed by seed, biases 0.  Returns TDGL_EINVAL on bad
+ *   shapes, TDGL_ENOMEM if the buffers do not fit.
  * tdgl_unet_param_count: number of floats of the parameter vector.
  * tdgl_unet_set_params / tdgl_unet_get_params: host float32 vector (caller-owned), resets Adam.
  * tdgl_unet_forward: x (B*cin*N floats) -> y (B*cout*N), where = TDGL_HOST or TDGL_DEVICE for both.

@@ -1,8 +1,8 @@
 """ORACLE (test infrastructure).  The learned warm start: a 3D convolutional U-Net, its
 gradients, the mean-squared loss and the Adam update, in plain float64 numpy.
 
-The paper motivates a learned initial guess for the relaxation (Sec. 5, outlook) without fixing
-an architecture; the network here is the one this project builds (a 4-level 3D U-Net, 3x3x3
+Sec. 5 names the solver as a source of datasets for data-driven models without fixing a model;
+the network here is the one this project builds as such a model (a 4-level 3D U-Net, 3x3x3
 convolutions with zero padding, ReLU, 2x2x2 average pooling, nearest-neighbour upsampling with
 skip concatenation, a 1x1x1 output head).  Every operation is written from its definition:
 

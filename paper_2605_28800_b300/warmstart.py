@@ -113,6 +113,29 @@ def propose(net, shape, points, batch):
     return out
 
 
+def conv_flops(shape, cin, cout, chans):
+    """(forward, training) multiply-add flops per sample of the U-Net: 2 V Co Ci taps per
+    convolution for the forward pass; training adds the data gradient (every layer but the first)
+    and the weight gradient, each the same count."""
+    nx, ny, nz = shape
+    fwd = train = 0
+    c_prev = cin
+    layers = []
+    for l, c in enumerate(chans):
+        layers += [(l, c_prev, c, 27, l > 0), (l, c, c, 27, True)]
+        c_prev = c
+    for l in range(len(chans) - 2, -1, -1):
+        layers += [(l, c_prev + chans[l], chans[l], 27, True), (l, chans[l], chans[l], 27, True)]
+        c_prev = chans[l]
+    layers.append((0, chans[0], cout, 1, True))
+    for l, ci, co, taps, dx in layers:
+        v = (nx >> l) * (ny >> l) * (nz >> l)
+        f = 2.0 * v * ci * co * taps
+        fwd += f
+        train += f * (3 if dx else 2)
+    return fwd, train
+
+
 def texture_distance(Pa, Pb):
     """RMS difference of two textures relative to the RMS of the second"""
     return float(np.sqrt(np.mean((Pa - Pb) ** 2)) / max(np.sqrt(np.mean(Pb ** 2)), 1e-30))
@@ -154,7 +177,12 @@ def run(ctx, cfg, n_train, n_test, epochs, max_steps, batch=4, lr=2e-3, chans=(1
     st_plain, st_warm = np.array(st_plain), np.array(st_warm)
     chosen = np.minimum(st_plain, st_warm)          # random start kept when the proposal does not help
     dF = np.array(F_warm) - np.array(F_plain)
+    f_fwd, f_train = conv_flops(shape, N_IN, N_OUT, chans)
+    n_steps = epochs * (n_train // batch)
     return dict(
+        conv_gflop_per_sample_forward=f_fwd / 1e9, conv_gflop_per_sample_training=f_train / 1e9,
+        train_tflops=f_train * batch * n_steps / max(t_train, 1e-9) / 1e12,
+        infer_tflops=f_fwd * n_test / max(t_inf, 1e-9) / 1e12,
         n_train=n_train, n_test=n_test, epochs=epochs, batch=batch, lr=lr, chans=list(chans),
         params=net.param_count(), max_steps=max_steps, tol=cfg["tol"],
         gen_seconds=t_gen, train_seconds=t_train, infer_seconds=t_inf,
