@@ -82,15 +82,15 @@ __device__ __forceinline__ void tfluxes(const TV &V, const SimDev &S, const floa
 // gradient field of the discrete Eq. 4 at centre-plane tile cell (1, py, x) of material ma
 template <class TV>
 __device__ __forceinline__ void tgrad_field(const TV &V, const SimDev &S, const float *coef, int py, int x,
-                                            int ma, const float *pa, float *h) {
+                                            int ma, const float *pa, float *h, bool known_bulk) {
     const float *ca = coef + ma * NCOEF;
     // Bulk cells (the 6 face and, with cross terms, the 12 edge neighbours all of material ma):
     // no ghost rule applies and the coefficients are uniform, so the discrete field below reduces
     // exactly to G (P(+) + P(-) - 2P) / dx^2 per face pair plus (G12 + G44 - G'44) times the
-    // four-corner mixed differences d_e d_f P_f.
-    bool bulk = V.m(1, py, x - 1) == ma && V.m(1, py, x + 1) == ma && V.m(1, py - 1, x) == ma &&
-                V.m(1, py + 1, x) == ma && V.m(0, py, x) == ma && V.m(2, py, x) == ma;
-    if (bulk && S.has_cross)
+    // four-corner mixed differences d_e d_f P_f.  known_bulk: the caller has established it.
+    bool bulk = known_bulk || (V.m(1, py, x - 1) == ma && V.m(1, py, x + 1) == ma && V.m(1, py - 1, x) == ma &&
+                               V.m(1, py + 1, x) == ma && V.m(0, py, x) == ma && V.m(2, py, x) == ma);
+    if (bulk && !known_bulk && S.has_cross)
         bulk = V.m(1, py - 1, x - 1) == ma && V.m(1, py - 1, x + 1) == ma && V.m(1, py + 1, x - 1) == ma &&
                V.m(1, py + 1, x + 1) == ma && V.m(0, py, x - 1) == ma && V.m(0, py, x + 1) == ma &&
                V.m(2, py, x - 1) == ma && V.m(2, py, x + 1) == ma && V.m(0, py - 1, x) == ma &&
@@ -260,7 +260,11 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
         }
         __syncthreads();
     }
-    // ---- stage the P / material tile (cells outside the grid: vacuum, P = 0)
+    // ---- stage the P / material tile (cells outside the grid: vacuum, P = 0); note whether the
+    // whole tile (all planes and halo rows the cells read) is one material inside the grid: then
+    // every cell with 0 < x < nx - 1 is a bulk cell of the discrete Eq. 4
+    bool uniform = MODE != MODE_XFWD;
+    const unsigned m0x4 = 0x01010101u * (unsigned)__ldg(S.mat + ((long)z * ny + y0) * nx);
     {
         const int planes = (MODE == MODE_XFWD) ? 1 : 3;
         const int nrow = planes * TYH;
@@ -273,6 +277,8 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
             const bool in = (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && py <= TY + 1;
             const unsigned v = in ? __ldg(reinterpret_cast<const unsigned *>(S.mat + ((long)gz * ny + gy) * nx) + q) : 0u;
             reinterpret_cast<unsigned *>(Mt + (pz * TYH + py) * nx)[q] = v;
+            // rows past this block's TY + 2 are never read; every other word must be m0 in each byte
+            if (py <= TY + 1 && v != m0x4) uniform = false;
         }
         if ((nx & 3) == 0) {   // rows of nx floats: 16-byte vector copies
             const int nq = nx >> 2;
@@ -297,7 +303,7 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
             }
         }
     }
-    __syncthreads();
+    const bool tile_bulk = __syncthreads_and(uniform && m0x4 != 0u) != 0;
     // ---- cells
     const TileView<nx, TYH> V{Pt, Mt};
     float lmax = 0.f;
@@ -345,7 +351,7 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
                 continue;
             }
             if (S.terms & TERM_LANDAU) landau_field(p, cm, h);
-            if (S.terms & TERM_GRAD) tgrad_field(V, S, s_coef, py, x, m, p, h);
+            if (S.terms & TERM_GRAD) tgrad_field(V, S, s_coef, py, x, m, p, h, tile_bulk && x > 0 && x < nx - 1);
             if (elec) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) h[c] += Eb[(c * TYmax + r) * nx + x];
