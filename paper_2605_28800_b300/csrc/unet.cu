@@ -62,6 +62,21 @@ int conv_bn(int co) {
 int launch_conv(tdgl_ctx *ctx, const __nv_bfloat16 *x, const __nv_bfloat16 *w, const float *b, void *y, long nvox,
                 Dims d, int Ci, int Co, int ntap, int Kp, bool relu, bool f32out, int *err) {
     ConvP p{x, w, b, y, nvox, d.Z, d.Y, d.X, Ci, Co, ntap, Kp / 8, relu ? 1 : 0, f32out ? 1 : 0, err};
+    // the brick kernel: 3x3x3, 16-channel input chunks, 8 x 16 voxel bricks, output tiles up to 64
+    if (ntap == 27 && Ci % 16 == 0 && d.X % 8 == 0 && d.Y % 16 == 0) {
+        const int bn = Co % 64 == 0 ? 64 : (Co % 32 == 0 ? 32 : 16);
+        const bool one = Ci == 16;
+        const dim3 grid((unsigned)(nvox / 128), (unsigned)((Co + bn - 1) / bn));
+        return launch(ctx, TDGL_K_UNET, [&] {
+#define TDGL_BRICK(BN_, S_) k_conv_brick<BN_, S_><<<grid, 128, brick_smem<BN_, S_>(), ctx->stream>>>(p)
+            switch (bn) {
+                case 64: if (one) TDGL_BRICK(64, 1); else TDGL_BRICK(64, 2); break;
+                case 32: if (one) TDGL_BRICK(32, 1); else TDGL_BRICK(32, 2); break;
+                default: if (one) TDGL_BRICK(16, 1); else TDGL_BRICK(16, 2); break;
+            }
+#undef TDGL_BRICK
+        });
+    }
     const int bn = conv_bn(Co);
     const dim3 grid((unsigned)((nvox + 127) / 128), (unsigned)((Co + bn - 1) / bn));
     return launch(ctx, TDGL_K_UNET, [&] {
@@ -74,12 +89,12 @@ int launch_conv(tdgl_ctx *ctx, const __nv_bfloat16 *x, const __nv_bfloat16 *w, c
     });
 }
 
-// dW[o][tap Ci + i] += sum_v dYt[o][v] xs[dx + 1][i][v + dz YX + dy X]
+// dW[o][tap Ci + i] += sum_v xs[dx + 1][i][v + dz YX + dy X] dYt[o][v]
 int launch_wgrad(tdgl_ctx *ctx, const __nv_bfloat16 *dyt, const __nv_bfloat16 *xs, float *dw, long nvox, Dims d,
                  int Ci, int Co, int ntap, int ldw, int *err) {
     const int N = ntap * Ci;
-    const int bn = N >= 128 ? 128 : (N >= 64 ? 64 : (N >= 32 ? 32 : 16));
-    const long ntile = (N + bn - 1) / bn;
+    const int bn = Co <= 16 ? 16 : (Co <= 32 ? 32 : (Co <= 64 ? 64 : 128));
+    const long ntile = (N + 127) / 128;
     long vchunk = (nvox * ntile + 591) / 592;                   // about four CTAs per SM
     vchunk = std::min<long>(std::max<long>((vchunk + 15) / 16 * 16, 256), 16384);
     WgradP p{dyt, xs, dw, nvox, d.Z, d.Y, d.X, Ci, Co, ntap, ldw, (int)vchunk, err};
@@ -94,8 +109,18 @@ int launch_wgrad(tdgl_ctx *ctx, const __nv_bfloat16 *dyt, const __nv_bfloat16 *x
     });
 }
 
+template <int BN, int S>
+int set_brick_attr() {
+    return cudaFuncSetAttribute(k_conv_brick<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)brick_smem<BN, S>()) == cudaSuccess
+               ? 0
+               : -1;
+}
+
 int init_attrs(tdgl_ctx *ctx) {
-    if (set_attr<128>() || set_attr<64>() || set_attr<32>() || set_attr<16>())
+    if (set_attr<128>() || set_attr<64>() || set_attr<32>() || set_attr<16>() || set_brick_attr<64, 1>() ||
+        set_brick_attr<64, 2>() || set_brick_attr<32, 1>() || set_brick_attr<32, 2>() || set_brick_attr<16, 1>() ||
+        set_brick_attr<16, 2>())
         return fail(ctx, TDGL_ECUDA, "cannot raise the shared-memory limit of the tensor-core kernels");
     return TDGL_OK;
 }

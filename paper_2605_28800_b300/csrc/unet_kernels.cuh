@@ -17,10 +17,12 @@
 namespace tdgl {
 namespace unet {
 
-constexpr int kStages = 4;          // cp.async -> MMA pipeline depth
+constexpr int kStages = 3;          // cp.async -> MMA pipeline depth
+constexpr int kSub = 4;             // 16-wide K sub-chunks (one MMA each) per pipeline stage
 constexpr long kSpin = 1L << 24;    // mbarrier polls before a wait is declared failed
 
-template <int BN> __host__ __device__ constexpr uint32_t stage_bytes() { return 128u * 32u + (uint32_t)BN * 32u; }
+// a stage: kSub A sub-tiles (128 rows x 32 bytes each), then kSub B sub-tiles (BN rows x 32 bytes)
+template <int BN> __host__ __device__ constexpr uint32_t stage_bytes() { return kSub * (128u * 32u + (uint32_t)BN * 32u); }
 template <int BN> __host__ __device__ constexpr uint32_t tmem_cols() { return BN < 32 ? 32u : (uint32_t)BN; }
 // dynamic shared memory: the stage ring, barriers and the TMEM slot, padded so that at most
 // 512 / tmem_cols CTAs fit on an SM (their TMEM allocations then always fit together)
@@ -31,29 +33,38 @@ template <int BN> __host__ __device__ constexpr uint32_t gemm_smem() {
     return (need > fit ? need : fit) + 1024u;                  // + alignment slack
 }
 
-// Pipelined main loop shared by both GEMMs: load(c, a_smem, b_smem) fills stage tiles of K-chunk
-// c with cp.async; one thread issues the MMA of each chunk once every thread's copies landed; a
-// stage is refilled after the MMA that read it has committed.  Returns false (in every thread)
-// if a barrier wait ran out; the caller then still drains and frees.
+// Pipelined main loop shared by both GEMMs over nsub 16-wide K sub-chunks: load(j, a_smem, b_smem)
+// fills the tiles of sub-chunk j with cp.async; a stage holds kSub sub-chunks; one thread issues
+// their MMAs once every thread's copies landed; a stage is refilled after the MMAs that read it
+// have committed.  Returns false (in every thread) if a barrier wait ran out; the caller then
+// still drains and frees.
 template <int BN, class Load>
-__device__ __forceinline__ bool mainloop(Load load, int nch, uint8_t *tiles, uint64_t *bar, uint32_t tmem, int *issued) {
-    constexpr uint32_t ST = stage_bytes<BN>(), AB = 128u * 32u;
+__device__ __forceinline__ bool mainloop(Load load, int nsub, uint8_t *tiles, uint64_t *bar, uint32_t tmem, int *issued) {
+    constexpr uint32_t ST = stage_bytes<BN>(), AB = kSub * 128u * 32u, BB = (uint32_t)BN * 32u;
     constexpr uint32_t idesc = tc::idesc_bf16(128, BN);
     const uint32_t base = tc::saddr(tiles);
     const int tid = threadIdx.x;
+    const int nch = (nsub + kSub - 1) / kSub;
+    auto load_stage = [&](int c) {
+        const uint32_t st = base + (uint32_t)(c % kStages) * ST;
+#pragma unroll
+        for (int u = 0; u < kSub; ++u) {
+            const int j = c * kSub + u;
+            if (j < nsub) load(j, st + (uint32_t)u * 4096u, st + AB + (uint32_t)u * BB);
+        }
+    };
     bool ok = true;
     *issued = 0;
 #pragma unroll
     for (int c = 0; c < kStages - 1; ++c) {
-        if (c < nch) load(c, base + (c % kStages) * ST, base + (c % kStages) * ST + AB);
+        if (c < nch) load_stage(c);
         tc::cp_commit();
     }
     for (int c = 0; c < nch; ++c) {
         const int cn = c + kStages - 1;
         if (cn < nch && ok) {
-            const int s = cn % kStages;
-            if (cn >= kStages) ok = tc::mbar_wait(&bar[s], (unsigned)((cn - kStages) / kStages) & 1u, kSpin);
-            if (ok) load(cn, base + s * ST, base + s * ST + AB);
+            if (cn >= kStages) ok = tc::mbar_wait(&bar[cn % kStages], (unsigned)((cn - kStages) / kStages) & 1u, kSpin);
+            if (ok) load_stage(cn);
         }
         tc::cp_commit();
         tc::cp_wait<kStages - 1>();
@@ -62,14 +73,20 @@ __device__ __forceinline__ bool mainloop(Load load, int nch, uint8_t *tiles, uin
         if (!ok) break;
         if (tid == 0) {
             tc::fence_after();
-            const uint32_t s = (uint32_t)(c % kStages);
-            tc::mma_bf16(tmem, tc::sdesc(base + s * ST), tc::sdesc(base + s * ST + AB), idesc, c > 0 ? 1u : 0u);
-            tc::mma_commit(&bar[s]);
+            const uint32_t st = base + (uint32_t)(c % kStages) * ST;
+#pragma unroll
+            for (int u = 0; u < kSub; ++u) {
+                const int j = c * kSub + u;
+                if (j < nsub)
+                    tc::mma_bf16(tmem, tc::sdesc(st + (uint32_t)u * 4096u), tc::sdesc(st + AB + (uint32_t)u * BB), idesc,
+                                 j > 0 ? 1u : 0u);
+            }
+            tc::mma_commit(&bar[c % kStages]);
         }
         *issued = c + 1;
     }
     tc::cp_wait<0>();
-    // the last MMA issued: its barrier phase completes when it (and all before it) finished
+    // the last stage issued: its barrier phase completes when its MMAs (and all before) finished
     if (*issued > 0) {
         const int c = *issued - 1;
         const bool done = tc::mbar_wait(&bar[c % kStages], (unsigned)(c / kStages) & 1u, kSpin);
@@ -155,7 +172,7 @@ __global__ void __launch_bounds__(128) k_conv(ConvP p) {
         }
     };
     int issued;
-    const bool ok = mainloop<BN>(load, p.G / 2, tiles, bar, tmem, &issued);
+    const bool ok = mainloop<BN>(load, p.G / 2, tiles, bar, tmem, &issued);   // sub-chunk j: groups 2j, 2j+1
     if (!ok) {
         if (tid == 0) atomicOr(p.err, 1);
     } else {
@@ -164,6 +181,144 @@ __global__ void __launch_bounds__(128) k_conv(ConvP p) {
             float r[16];
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
             if (!vok) continue;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int co = n0 + c0 + j;
+                if (co >= p.Co) break;
+                float a = r[j] + (p.bias ? p.bias[co] : 0.f);
+                if (p.relu) a = fmaxf(a, 0.f);
+                if (p.f32out) reinterpret_cast<float *>(p.y)[v * p.Co + co] = a;
+                else reinterpret_cast<__nv_bfloat16 *>(p.y)[v * p.Co + co] = __float2bfloat16_rn(a);
+            }
+        }
+    }
+    epilogue_free<BN>(tmem);
+}
+
+// ---- brick convolution: the input brick staged once, the 27 taps as descriptor offsets -----------
+//
+// A CTA owns 128 output voxels: x0..x0+7 (core-matrix rows) by y0..y0+15 (row groups) at one z.
+// Per 16-channel chunk of the input it stages the brick with its one-voxel halo, 10 x 18 x 3 voxels,
+// as two planes (channels 0-7 and 8-15 of the chunk) of 16-byte voxel records, x fastest.  For a tap
+// (dz, dy, dx) the A operand is the same tile read from a shifted start: row group g at
+// ((1 + dz) * 18 + g + 1 + dy) * 10 + 1 + dx records, rows 16 bytes apart, so the descriptor keeps
+// the stride-dimension offset 160 bytes (one brick row) and the leading-dimension offset one plane.
+// The weights of the chunk for all 27 taps are staged next to it; one thread issues 27 MMAs per chunk.
+constexpr int kBX = 10, kBY = 18, kBZ = 3, kBrick = kBX * kBY * kBZ;     // voxel records per plane
+constexpr uint32_t kPlane = kBrick * 16u;                                 // bytes per 8-channel plane
+// S pipeline stages: 1 when the input has a single 16-channel chunk (nothing to overlap; more CTAs
+// fit per SM instead), 2 otherwise
+template <int BN> __host__ __device__ constexpr uint32_t brick_stage_bytes() { return 2u * kPlane + 27u * BN * 32u; }
+template <int BN, int S> __host__ __device__ constexpr uint32_t brick_smem() {
+    return S * brick_stage_bytes<BN>() + 128u + 1024u;
+}
+
+// shared-memory descriptor with explicit leading / stride byte offsets
+__device__ __forceinline__ uint64_t sdesc_lbo_sbo(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+template <int BN, int S>
+__global__ void __launch_bounds__(128) k_conv_brick(ConvP p) {
+    constexpr uint32_t ST = brick_stage_bytes<BN>(), AB = 2u * kPlane;
+    constexpr uint32_t idesc = tc::idesc_bf16(128, BN);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(tiles + S * ST);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + S);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // brick of this CTA
+    const int nbx = p.X / 8, nby = p.Y / 16;
+    long q = blockIdx.x;
+    const int bx = (int)(q % nbx); q /= nbx;
+    const int by = (int)(q % nby); q /= nby;
+    const int z = (int)(q % p.Z);
+    const long b = q / p.Z;
+    const int x0 = bx * 8, y0 = by * 16;
+    const int n0 = blockIdx.y * BN;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) tc::mbar_init(&bar[s], 1);
+        tc::mbar_fence_init();
+    }
+    if (tid < 32) tc::tmem_alloc(tslot, tmem_cols<BN>());
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t base = tc::saddr(tiles);
+    auto load = [&](int c, uint32_t st) {
+        const int c0 = 16 * c;
+        for (int i = tid; i < 2 * kBrick; i += 128) {
+            const int h = i / kBrick, r = i - h * kBrick;
+            const int xx = r % kBX, yy = (r / kBX) % kBY, zz = r / (kBX * kBY);
+            const int gx = x0 + xx - 1, gy = y0 + yy - 1, gz = z + zz - 1;
+            const bool ok = (unsigned)gx < (unsigned)p.X && (unsigned)gy < (unsigned)p.Y && (unsigned)gz < (unsigned)p.Z;
+            const __nv_bfloat16 *src = ok ? p.x + ((((b * p.Z + gz) * p.Y + gy) * p.X + gx) * p.Ci + c0 + 8 * h) : p.x;
+            tc::cp16(st + (uint32_t)h * kPlane + (uint32_t)r * 16u, src, ok);
+        }
+        for (int i = tid; i < 27 * BN * 2; i += 128) {
+            const int t = i / (2 * BN), rem = i - t * 2 * BN, n = rem >> 1, h = rem & 1, co = n0 + n;
+            const bool ok = co < p.Co;
+            const __nv_bfloat16 *src = ok ? p.w + ((long)co * p.G * 8 + (long)t * p.Ci + c0 + 8 * h) : p.w;
+            tc::cp16(st + AB + (uint32_t)t * (BN * 32u) + tc::tile_off(n, h), src, ok);
+        }
+    };
+    const int nch = p.Ci / 16;
+    bool ok = true;
+    int issued = 0;
+#pragma unroll
+    for (int c = 0; c < S - 1; ++c) {
+        if (c < nch) load(c, base + (c % S) * ST);
+        tc::cp_commit();
+    }
+    for (int c = 0; c < nch; ++c) {
+        const int cn = c + S - 1;
+        if (cn < nch && ok) {
+            const int s = cn % S;
+            if (cn >= S) ok = tc::mbar_wait(&bar[s], (unsigned)((cn - S) / S) & 1u, kSpin);
+            if (ok) load(cn, base + s * ST);
+        }
+        tc::cp_commit();
+        tc::cp_wait<S - 1>();
+        tc::fence_proxy_async();
+        ok = !__syncthreads_or(!ok);
+        if (!ok) break;
+        if (tid == 0) {
+            tc::fence_after();
+            const uint32_t st = base + (uint32_t)(c % S) * ST;
+#pragma unroll 1
+            for (int t = 0; t < 27; ++t) {
+                const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+                const uint32_t a = st + (uint32_t)((((1 + dz) * kBY + 1 + dy) * kBX + 1 + dx) * 16);
+                tc::mma_bf16(tmem, sdesc_lbo_sbo(a, kPlane, kBX * 16u), tc::sdesc(st + AB + (uint32_t)t * (BN * 32u)),
+                             idesc, (c > 0 || t > 0) ? 1u : 0u);
+            }
+            tc::mma_commit(&bar[c % S]);
+        }
+        issued = c + 1;
+    }
+    tc::cp_wait<0>();
+    if (issued > 0) {
+        const int c = issued - 1;
+        const bool done = tc::mbar_wait(&bar[c % S], (unsigned)(c / S) & 1u, kSpin);
+        ok = ok && done;
+    }
+    tc::fence_after();
+    ok = !__syncthreads_or(!ok);
+    if (!ok) {
+        if (tid == 0) atomicOr(p.err, 1);
+    } else {
+        // row tid: x = x0 + tid % 8, y = y0 + tid / 8
+        const long v = ((b * p.Z + z) * p.Y + y0 + tid / 8) * p.X + x0 + (tid & 7);
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float r[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int co = n0 + c0 + j;
@@ -187,7 +342,8 @@ struct WgradP {
     int *err;
 };
 
-// dW[o][tap, i] += sum over this CTA's voxel chunk of dY[v][o] X[v + off(tap)][i]
+// dW[o][tap, i] += sum over this CTA's voxel chunk of X[v + off(tap)][i] dY[v][o]:
+// M = 128 (tap, i) rows, N = the output channels (BN >= Co), K = voxels
 template <int BN>
 __global__ void __launch_bounds__(128) k_wgrad(WgradP p) {
     extern __shared__ uint8_t smem_raw[];
@@ -195,39 +351,41 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradP p) {
     uint64_t *bar = reinterpret_cast<uint64_t *>(tiles + kStages * stage_bytes<BN>());
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + kStages);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int n0 = blockIdx.x * BN;
+    const int m0 = blockIdx.x * 128;
     const long vbase = (long)blockIdx.y * p.vchunk;
     const long vend = (vbase + p.vchunk < p.nvox) ? vbase + p.vchunk : p.nvox;
     const int nch = (int)((vend - vbase + 15) / 16);
     const int N = p.ntap * p.Ci;
     const long YX = (long)p.Y * p.X;
+    // this thread's A row: (tap, i) = m0 + tid
+    const int ng = m0 + tid;
+    const bool rok = ng < N;
+    int tap = 0, ci = 0, dz = 0, dy = 0, dx = 0;
+    if (rok) {
+        tap = ng / p.Ci;
+        ci = ng - tap * p.Ci;
+        if (p.ntap == 27) { dz = tap / 9 - 1; dy = (tap / 3) % 3 - 1; dx = tap % 3 - 1; }
+    }
+    const __nv_bfloat16 *xrow = p.xs + ((long)(dx + 1) * p.Ci + ci) * p.nvox + dz * YX + (long)dy * p.X;
     const uint32_t tmem = prologue<BN>(bar, tslot);
     auto load = [&](int c, uint32_t a_s, uint32_t b_s) {
         const long k0 = vbase + 16L * c;
-        {   // A: row o = tid, voxels k0 + 8h .. + 7
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const long kv = k0 + 8 * h;
-                const bool ok = tid < p.Co && kv < vend;
-                const __nv_bfloat16 *src = ok ? p.dyt + (long)tid * p.nvox + kv : p.dyt;
-                tc::cp16(a_s + tc::tile_off(tid, h), src, ok);
-            }
-        }
-        for (int i = tid; i < 2 * BN; i += 128) {
-            const int n = i >> 1, h = i & 1, ng = n0 + n;
+        for (int h = 0; h < 2; ++h) {   // A: row (tap, i), voxels k0 + 8h .. + 7 (one x-row)
             const long kv = k0 + 8 * h;
-            bool ok = ng < N && kv < vend;
-            const __nv_bfloat16 *src = p.xs;
+            bool ok = rok && kv < vend;
             if (ok) {
-                const int tap = ng / p.Ci, ci = ng - tap * p.Ci;
-                int dz = 0, dy = 0, dx = 0;
-                if (p.ntap == 27) { dz = tap / 9 - 1; dy = (tap / 3) % 3 - 1; dx = tap % 3 - 1; }
-                const long row = kv / p.X;                        // the 8 voxels share (b, z, y)
-                const int y = (int)(row % p.Y), z = (int)((row / p.Y) % p.Z);
-                ok = (unsigned)(z + dz) < (unsigned)p.Z && (unsigned)(y + dy) < (unsigned)p.Y;
-                if (ok) src = p.xs + ((long)(dx + 1) * p.Ci + ci) * p.nvox + kv + dz * YX + (long)dy * p.X;
+                const long row = kv / p.X;
+                const int y = (int)(row % p.Y), zz = (int)((row / p.Y) % p.Z);
+                ok = (unsigned)(zz + dz) < (unsigned)p.Z && (unsigned)(y + dy) < (unsigned)p.Y;
             }
-            tc::cp16(b_s + tc::tile_off(n, h), src, ok);
+            tc::cp16(a_s + tc::tile_off(tid, h), ok ? xrow + kv : p.xs, ok);
+        }
+        for (int i = tid; i < 2 * BN; i += 128) {   // B: row o, voxels k0 + 8h .. + 7
+            const int o = i >> 1, h = i & 1;
+            const long kv = k0 + 8 * h;
+            const bool ok = o < p.Co && kv < vend;
+            tc::cp16(b_s + tc::tile_off(o, h), ok ? p.dyt + (long)o * p.nvox + kv : p.dyt, ok);
         }
     };
     int issued;
@@ -239,11 +397,11 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradP p) {
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float r[16];
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-            if (tid >= p.Co) continue;
+            if (!rok) continue;
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const int ng = n0 + c0 + j;
-                if (ng < N) atomicAdd(&p.dw[(long)tid * p.ldw + ng], r[j]);
+                const int o = c0 + j;
+                if (o < p.Co) atomicAdd(&p.dw[(long)o * p.ldw + ng], r[j]);
             }
         }
     }

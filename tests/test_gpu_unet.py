@@ -36,6 +36,13 @@ CONV_CASES = [
     (16, 8, 1, (24, 5, 3), 2),
     (16, 3, 1, (8, 8, 2), 1),
     (64, 64, 3, (16, 16, 8), 1),     # 2048 voxels: 16 tiles of 128
+    # brick path (3x3x3, 16-channel chunks, y a multiple of 16): staged input, taps as offsets
+    (16, 16, 3, (8, 16, 3), 2),
+    (48, 16, 3, (16, 32, 2), 1),
+    (32, 48, 3, (8, 16, 2), 1),      # three output tiles of 16
+    (96, 32, 3, (8, 16, 4), 1),
+    (192, 64, 3, (8, 16, 2), 1),     # twelve input chunks
+    (16, 32, 3, (24, 48, 1), 1),     # one z plane: every tap off the grid in z
 ]
 
 
@@ -86,8 +93,9 @@ def small_net(ctx, seed=3, levels=3, chans=(16, 32, 32), shape=(32, 8, 4), B=2):
     return net, p, x, t, levels
 
 
-def test_unet_forward_matches_oracle(ctx):
-    net, p, x, t, levels = small_net(ctx)
+@pytest.mark.parametrize("shape", [(32, 8, 4), (32, 32, 4)])
+def test_unet_forward_matches_oracle(ctx, shape):
+    net, p, x, t, levels = small_net(ctx, shape=shape)
     y = net.forward(x)
     ref, _ = U.forward(p, x.astype(np.float64), levels, q=U.bf16)
     assert y.shape == ref.shape
@@ -95,8 +103,9 @@ def test_unet_forward_matches_oracle(ctx):
     assert np.sqrt(np.mean((y - ref) ** 2)) / np.sqrt(np.mean(ref ** 2)) < 3e-3
 
 
-def test_unet_gradients_match_oracle(ctx):
-    net, p, x, t, levels = small_net(ctx, seed=5)
+@pytest.mark.parametrize("shape", [(32, 8, 4), (32, 32, 4)])
+def test_unet_gradients_match_oracle(ctx, shape):
+    net, p, x, t, levels = small_net(ctx, seed=5, shape=shape)
     loss, gv = net.loss_grad(x, t)
     y, cache = U.forward(p, x.astype(np.float64), levels, q=U.bf16)
     rl, dy = U.mse(y, t.astype(np.float64))
