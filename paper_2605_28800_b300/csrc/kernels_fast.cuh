@@ -1,5 +1,6 @@
 // Length-specialized y and z passes of the zero-padded convolution (Eqs. 5-6), built on the
-// register FFT of fft_reg.cuh.  Thread (t, l) of a block owns position t of line l (kx0 + l):
+// register FFT of fft_reg.cuh.  Thread (t, l) of a block owns position t of line l (column kx0 + l,
+// or, in an "across" item, row r0 + l of one column):
 // for every register the 16 (or 8) lanes of a half-warp touch consecutive kx of one row, so all
 // global loads and stores are full 64/128-byte segments and every shared-memory exchange
 // (layout [pos][l]) is conflict-free.
@@ -8,6 +9,10 @@
 #include "kernels.cuh"
 
 namespace tdgl {
+
+// work item .w: line count, | kAcross when the lanes run over rows of one column instead of
+// over columns of one row (the Nyquist column x = Mx/2)
+constexpr int kAcross = 1 << 16;
 
 template <int N> __host__ __device__ constexpr int lines_per_block() {
     return (256 / rf::threads_per_line<N>()) < 16 ? (256 / rf::threads_per_line<N>()) : 16;
@@ -32,21 +37,23 @@ __global__ void __launch_bounds__(256) k_ypass(const SimDev *__restrict__ sims, 
     __shared__ float2 tw[N];
     const int4 it = items[blockIdx.x];
     const SimDev &D = sims[it.x];
-    const int cz = it.y, kx0 = it.z, cnt = it.w;
+    const bool across = (it.w & kAcross) != 0;
+    const int cnt = it.w & (kAcross - 1);
     const int l = threadIdx.x % KX, t = threadIdx.x / KX;
+    const int cz = across ? it.y + l : it.y, kx = across ? it.z : it.z + l;   // this lane's line
     const bool ok = l < cnt;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = D.tw[D.py.tw + i];
     const int ny = D.ny, kxp = D.kxp;
     float2 v[E];
     if (!INV) {
-        const float2 *src = D.X + (long)cz * ny * kxp + kx0 + l;
+        const float2 *src = D.X + (long)cz * ny * kxp + kx;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int y = t + T * m;
             v[m] = (ok && y < ny) ? src[(long)y * kxp] : make_float2(0.f, 0.f);
         }
     } else {
-        const float2 *src = D.Y + (long)cz * N * kxp + kx0 + l;
+        const float2 *src = D.Y + (long)cz * N * kxp + kx;
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = ok ? src[(long)(t + T * m) * kxp] : make_float2(0.f, 0.f);
     }
@@ -54,11 +61,11 @@ __global__ void __launch_bounds__(256) k_ypass(const SimDev *__restrict__ sims, 
     rf::fft<rf::Cfg<N>, INV>(v, t, S, [&](int pos) { return pos * KX + l; }, tw);
     if (!ok) return;
     if (!INV) {
-        float2 *dst = D.Y + (long)cz * N * kxp + kx0 + l;
+        float2 *dst = D.Y + (long)cz * N * kxp + kx;
 #pragma unroll
         for (int i = 0; i < E; ++i) dst[(long)rf::final_pos<rf::Cfg<N>>(t, i) * kxp] = v[i];
     } else {
-        float2 *dst = D.X + (long)cz * ny * kxp + kx0 + l;
+        float2 *dst = D.X + (long)cz * ny * kxp + kx;
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int y = rf::final_pos<rf::Cfg<N>>(t, i);
@@ -98,12 +105,14 @@ __global__ void __launch_bounds__(zthreads<N>(), 4) k_zpass(const SimDev *__rest
     float2 *tw = A + 3 * N * KX;                          // [N]
     const int4 it = items[blockIdx.x];
     const SimDev &D = sims[it.x];
-    const int ky = it.y, kx0 = it.z, cnt = it.w;
+    const bool across = (it.w & kAcross) != 0;
+    const int cnt = it.w & (kAcross - 1);
     const int l = threadIdx.x % KX, t = threadIdx.x / KX;
+    const int ky = across ? it.y + l : it.y, kx = across ? it.z : it.z + l;   // this lane's line
     const bool ok = l < cnt;
     const int nz = D.nz, My = D.My, kxp = D.kxp;
     const long zs = (long)My * kxp, cs = (long)nz * zs;
-    const float2 *src = D.Y + (long)ky * kxp + kx0 + l;
+    const float2 *src = D.Y + (long)ky * kxp + kx;
     auto idx = [&](int pos) { return zrow<N, KX>(pos) * KX + l; };
     // inputs of all three components in flight at once: asynchronous 8-byte copies into this
     // thread's own slots, component c in commit group c
@@ -121,6 +130,12 @@ __global__ void __launch_bounds__(zthreads<N>(), 4) k_zpass(const SimDev *__rest
         }
         asm volatile("cp.async.commit_group;\n" ::);
     }
+    // the reduced tensor rows this lane multiplies by (reflection signs for ky > My/2)
+    const int kyr = (ky <= My / 2) ? ky : My - ky;
+    const float sy = (ky <= My / 2) ? 1.f : -1.f;
+    const long ns = (long)D.kzh * D.kyh * kxp;
+    const float2 *Nb = D.Nhat + (long)kyr * kxp + kx;
+    const long rowN = (long)D.kyh * kxp;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = D.tw[D.pz.tw + i];
     // forward transform of component c from this thread's own input slots; Ac is its exchange buffer
     auto forward = [&](int c, float2(&v)[E]) {
@@ -152,12 +167,7 @@ __global__ void __launch_bounds__(zthreads<N>(), 4) k_zpass(const SimDev *__rest
     forward(2, w);
     // E-hat(k) = escale * N-hat(k) P-hat(k); N-hat from the reduced table with reflection signs.
     // x and y results go back to their owner's slots, z stays in w.
-    const int kyr = (ky <= My / 2) ? ky : My - ky;
-    const float sy = (ky <= My / 2) ? 1.f : -1.f;
-    const long ns = (long)D.kzh * D.kyh * kxp;
     const float es = D.escale;
-    const float2 *Nb = D.Nhat + (long)kyr * kxp + kx0 + l;
-    const long rowN = (long)D.kyh * kxp;
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const int kz = rf::final_pos<S>(t, i);
@@ -176,7 +186,7 @@ __global__ void __launch_bounds__(zthreads<N>(), 4) k_zpass(const SimDev *__rest
         A[N * KX + p] = make_float2(es * (nxy * px.x + nyy * py.x + nyz * pz.x), es * (nxy * px.y + nyy * py.y + nyz * pz.y));
         w[i] = make_float2(es * (nxz * px.x + nyz * py.x + nzz * pz.x), es * (nxz * px.y + nyz * py.y + nzz * pz.y));
     }
-    float2 *dst = D.Y + (long)ky * kxp + kx0 + l;
+    float2 *dst = D.Y + (long)ky * kxp + kx;
     auto store = [&](int c, const float2(&v)[E]) {
         if (ok) {
 #pragma unroll

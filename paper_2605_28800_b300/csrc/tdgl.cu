@@ -249,22 +249,37 @@ void build_items(tdgl_sim *s) {
         for (int y0 = 0; y0 < s->ny; y0 += RB) s->it_rows.push_back(make_int4(0, z, y0, std::min(RB, s->ny - y0)));
     s->yN = fast_len(s->My) ? s->My : 0;
     s->zN = fast_len(s->Mz) ? s->Mz : 0;
+    // Kx = Mx/2 + 1 columns: when the first Mx/2 fill whole line groups, the last (Nyquist) column
+    // would be a group of one line; the fast kernels instead take it in "across" items whose lanes
+    // run over rows (cz for y, ky for z) of that column (flag kAcross in .w).
     const int ky = s->yN ? fast_ylines(s->My) : std::max(1, std::min(16, 73728 / (16 * (s->My + 1))));
     s->ky_cnt_max = ky;
+    const bool y_across = s->yN && s->Kx > 1 && (s->Kx - 1) % ky == 0;
+    const int ky_cols = y_across ? s->Kx - 1 : s->Kx;
+    // the across items (uncoalesced, so slower per block) go first: they start in the first wave
+    // instead of trailing behind the last one
+    if (y_across)
+        for (int r0 = 0; r0 < 3 * s->nz; r0 += ky)
+            s->it_y.push_back(make_int4(0, r0, s->Kx - 1, std::min(ky, 3 * s->nz - r0) | kAcross));
     for (int c = 0; c < 3; ++c)
         for (int z = 0; z < s->nz; ++z)
-            for (int k0 = 0; k0 < s->Kx; k0 += ky)
-                s->it_y.push_back(make_int4(0, c * s->nz + z, k0, std::min(ky, s->Kx - k0)));
+            for (int k0 = 0; k0 < ky_cols; k0 += ky)
+                s->it_y.push_back(make_int4(0, c * s->nz + z, k0, std::min(ky, ky_cols - k0)));
     const int kz = s->zN ? fast_zlines(s->Mz) : std::max(1, std::min(16, 102400 / (48 * (s->Mz + 1))));
     s->kz_cnt_max = kz;
+    const bool z_across = s->zN && s->Kx > 1 && (s->Kx - 1) % kz == 0;
+    const int kz_cols = z_across ? s->Kx - 1 : s->Kx;
     // rows ky and My - ky read the same tensor row: issue them back to back so the second read hits L2
     std::vector<int> order;
     for (int k = 0; k <= s->My / 2; ++k) {
         order.push_back(k);
         if (k != 0 && s->My - k != k) order.push_back(s->My - k);
     }
+    if (z_across)
+        for (int r0 = 0; r0 < s->My; r0 += kz)
+            s->it_z.push_back(make_int4(0, r0, s->Kx - 1, std::min(kz, s->My - r0) | kAcross));
     for (int k : order)
-        for (int k0 = 0; k0 < s->Kx; k0 += kz) s->it_z.push_back(make_int4(0, k, k0, std::min(kz, s->Kx - k0)));
+        for (int k0 = 0; k0 < kz_cols; k0 += kz) s->it_z.push_back(make_int4(0, k, k0, std::min(kz, kz_cols - k0)));
 }
 
 size_t xrows_smem_for(int hx) {
