@@ -3,7 +3,8 @@
 Eq. 2: F = F_Land + F_Grad + F_Elec + F_Ext; Eq. 7: F_Ext = -int E_ext . P, so the external
 field enters the effective field as +E_ext.  A time-dependent excitation (Sec. 3; the AC loops of
 Sec. 4.4) is E_ext(t) = E_ext + E_ac sin(2 pi f t + phase), taken at the time of each step.  Eq. 1 with L = 1 (Sec. 2), integrated with the
-forward Euler rule (the simplest of the explicit schemes named in Sec. 3):
+forward Euler rule (the simplest of the explicit schemes named in Sec. 3; Heun, RK45 and AB3M2
+below are the three the paper lists):
     P <- P + dt * L * (h_Land + h_Grad + E_el + E_ext)      on material cells;
 vacuum cells keep P = 0 (Sec. 2: P = 0 outside the sample).
 """
@@ -130,8 +131,51 @@ class System:
         h1 = self.fields(Pt, t + dt)["total"]
         return np.where(self.m, P + 0.5 * dt * self.L * (h0 + h1), 0.0)
 
+    # Runge-Kutta-Fehlberg 4(5) (Fehlberg 1969): nodes, stage matrix, fourth- and fifth-order weights
+    RKF_C = (0.0, 1 / 4, 3 / 8, 12 / 13, 1.0, 1 / 2)
+    RKF_A = ((), (1 / 4,), (3 / 32, 9 / 32), (1932 / 2197, -7200 / 2197, 7296 / 2197),
+             (439 / 216, -8.0, 3680 / 513, -845 / 4104), (-8 / 27, 2.0, -3544 / 2565, 1859 / 4104, -11 / 40))
+    RKF_B4 = (25 / 216, 0.0, 1408 / 2565, 2197 / 4104, -1 / 5, 0.0)
+    RKF_B5 = (16 / 135, 0.0, 6656 / 12825, 28561 / 56430, -9 / 50, 2 / 55)
+
+    def rkf45_step(self, P, dt, t=0.0):
+        """One Runge-Kutta-Fehlberg step (the RK45 of Sec. 3): returns (P4, P5), the fourth-order
+        solution that advances and the fifth-order one whose difference estimates the local error."""
+        P = np.asarray(P, dtype=np.float64)
+        k = []
+        for i in range(6):
+            Pi = P + dt * self.L * sum(a * kj for a, kj in zip(self.RKF_A[i], k)) if i else P
+            k.append(self.fields(np.where(self.m, Pi, 0.0), t + self.RKF_C[i] * dt)["total"])
+        P4 = P + dt * self.L * sum(b * kj for b, kj in zip(self.RKF_B4, k))
+        P5 = P + dt * self.L * sum(b * kj for b, kj in zip(self.RKF_B5, k))
+        return np.where(self.m, P4, 0.0), np.where(self.m, P5, 0.0)
+
+    def ab3m2_run(self, P, dt, n, t0=0.0):
+        """n steps of the Adams pair (the AB3M2 of Sec. 3) in predict-evaluate-correct-evaluate
+        form: predictor Adams-Bashforth with the newest q = min(step + 1, 3) derivatives,
+        corrector Adams-Moulton with q - 1 past derivatives (the trapezoid rule on the first step,
+        so that step is Heun's method), then the derivative at the new state."""
+        P = np.asarray(P, dtype=np.float64)
+        f = lambda Q, t: self.fields(np.where(self.m, Q, 0.0), t)["total"]
+        hist = [f(P, t0)]                                   # newest first
+        AB = {1: (1.0,), 2: (3 / 2, -1 / 2), 3: (23 / 12, -16 / 12, 5 / 12)}
+        AM = {1: (1 / 2, 1 / 2), 2: (5 / 12, 8 / 12, -1 / 12), 3: (5 / 12, 8 / 12, -1 / 12)}
+        for i in range(n):
+            t = t0 + i * dt
+            q = len(hist)
+            Pp = P + dt * self.L * sum(c * h for c, h in zip(AB[q], hist))
+            fs = f(Pp, t + dt)
+            P = np.where(self.m, P + dt * self.L * sum(c * h for c, h in zip(AM[q], [fs] + hist)), 0.0)
+            hist = [f(P, t + dt)] + hist[:2]
+        return P
+
     def run(self, P, dt, n, t0=0.0, method="euler"):
-        f = self.heun_step if method == "heun" else self.step
+        if method == "ab3m2":
+            return self.ab3m2_run(P, dt, n, t0)
+        if method == "rk45":
+            f = lambda Q, dt_, t: self.rkf45_step(Q, dt_, t)[0]
+        else:
+            f = self.heun_step if method == "heun" else self.step
         for i in range(n):
             P = f(P, dt, t0 + i * dt)
         return P
