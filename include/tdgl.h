@@ -129,11 +129,29 @@ int tdgl_set_field_ac(tdgl_sim *sim, double Ax, double Ay, double Az, double fre
 /* Time integrator of Eq. 1 (Sec. 3 lists Heun, RK45 and AB3M2):
  *   TDGL_EULER (default)  P <- P + dt h(P, t)
  *   TDGL_HEUN             P~ = P + dt h(P, t);  P <- P + dt/2 (h(P, t) + h(P~, t + dt))
- * Heun costs two field evaluations per step and 12 bytes per cell of device memory.  The sims of
- * a batch must use one integrator. */
+ *   TDGL_RK45             Runge-Kutta-Fehlberg 4(5): six field evaluations, P advances with the
+ *                         fourth-order solution; the fifth-order one gives the local error
+ *                         max |P5 - P4| / P0, which drives the step size when tdgl_set_adaptive
+ *                         has set a tolerance
+ *   TDGL_AB3M2            Adams-Bashforth 3-step predictor, Adams-Moulton 2-step corrector (PECE:
+ *                         two field evaluations per step); its first two steps use the 1- and
+ *                         2-step pairs (the first is Heun's method).  Any change of P, time,
+ *                         fields, terms, materials or temperature restarts the history.
+ * Heun costs 12 bytes per cell of device memory, RK45 and AB3M2 72.  The sims of a batch must use
+ * one integrator, Euler or Heun. */
 #define TDGL_EULER 0
 #define TDGL_HEUN  1
+#define TDGL_RK45  2
+#define TDGL_AB3M2 3
 int tdgl_set_integrator(tdgl_sim *sim, int method);
+/* RK45 step-size control: err_tol > 0 makes tdgl_step and tdgl_relax adaptive (a step whose local
+ * error exceeds err_tol is retried with a smaller dt; after an accepted step dt grows or shrinks by
+ * 0.9 (err_tol / err)^(1/5), within [0.2, 5] per step and [dt_min, dt_max] overall, dt_max 0 = no
+ * bound); err_tol = 0 returns to fixed steps.  tdgl_step(sim, n, dt) then takes n accepted steps,
+ * starting from dt on the first call and from the controller's dt afterwards; tdgl_relax checks
+ * max |dP| / P0 of the last step scaled by dt / dt_step.  tdgl_get_dt returns the next dt (s). */
+int tdgl_set_adaptive(tdgl_sim *sim, double err_tol, double dt_min, double dt_max);
+int tdgl_get_dt(tdgl_sim *sim, double *dt);
 /* Simulated time t (s) of the sim: 0 at creation, advanced by n dt by every step call. */
 int tdgl_set_time(tdgl_sim *sim, double t);
 int tdgl_get_time(tdgl_sim *sim, double *t);

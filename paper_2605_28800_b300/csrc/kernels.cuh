@@ -67,7 +67,9 @@ struct SimDev {
 // STEP: forward Euler.  HEUN1 / HEUN2: predictor and corrector of Heun's method (Sec. 3):
 //   HEUN1  P~ = P + dt h(P), keeps h(P) in S.hbuf, writes P~ to the other buffer;
 //   HEUN2  P <- P + dt/2 (h(P) + h(P~)) in place, with the field evaluated on P~.
-enum { MODE_STEP = 0, MODE_FIELD = 1, MODE_ENERGY = 2, MODE_XFWD = 3, MODE_HEUN1 = 4, MODE_HEUN2 = 5 };
+// DERIV: the total field (= dP/dt of Eq. 1 with L = 1, normalized) of the state in P[parity],
+// written to hbuf; the stages of the Runge-Kutta-Fehlberg and Adams integrators are built from it
+enum { MODE_STEP = 0, MODE_FIELD = 1, MODE_ENERGY = 2, MODE_XFWD = 3, MODE_HEUN1 = 4, MODE_HEUN2 = 5, MODE_DERIV = 6 };
 __host__ __device__ constexpr bool mode_updates(int m) { return m == MODE_STEP || m == MODE_HEUN1 || m == MODE_HEUN2; }
 
 __device__ __forceinline__ int row_ld(const SimDev &S) { return S.hx + 2; }
@@ -327,6 +329,9 @@ __global__ void __launch_bounds__(NTHREADS) k_rows(const SimDev *__restrict__ si
                 } else if (MODE == MODE_FIELD) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) S.out[c * S.ncell + id] = 0.f;
+                } else if (MODE == MODE_DERIV) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) S.hbuf[c * S.ncell + id] = 0.f;
                 }
                 continue;
             }
@@ -359,6 +364,11 @@ __global__ void __launch_bounds__(NTHREADS) k_rows(const SimDev *__restrict__ si
                 for (int c = 0; c < 3; ++c) S.out[c * S.ncell + id] = h[c] * S.out_scale;
                 continue;
             }
+            if (MODE == MODE_DERIV) {   // dP/dt of Eq. 1 (L = 1, normalized) for a multi-stage integrator
+#pragma unroll
+                for (int c = 0; c < 3; ++c) S.hbuf[c * S.ncell + id] = h[c];
+                continue;
+            }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 float pn, p0 = p[c];
@@ -384,7 +394,7 @@ __global__ void __launch_bounds__(NTHREADS) k_rows(const SimDev *__restrict__ si
         v = block_sum(e_ext, s_red); if (tid == 0) atomicAdd(&S.energy[3], v);
         return;
     }
-    if (MODE == MODE_FIELD) return;
+    if (MODE == MODE_FIELD || MODE == MODE_DERIV) return;
     if (mode_updates(MODE)) {
         for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
         if ((tid & 31) == 0) atomicMax(reinterpret_cast<unsigned *>(&s_max), __float_as_uint(lmax));
@@ -528,6 +538,45 @@ __global__ void k_scale_in(float *__restrict__ dst, const float *__restrict__ sr
 __global__ void k_scale_out(float *__restrict__ dst, const float *__restrict__ src, long n, float s) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
         dst[i] = src[i] * s;
+}
+// Linear combination of integrator stages on material cells (vacuum stays 0):
+//   out = P + sum_j c[j] K[j];  optionally  errmax = max |sum_j d[j] K[j]|  and  dpmax = max |out - P|
+// (coefficients already multiplied by the normalized step), maxima as ordered float bits.
+struct Combine {
+    float *out;
+    const float *P;
+    const float *K[7];
+    float c[7], d[7];
+    int nk, nd;
+    const uint8_t *mat;
+    long ncell;
+    unsigned *errmax, *dpmax;
+};
+__global__ void k_combine(Combine q) {
+    float em = 0.f, dm = 0.f;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 3 * q.ncell; i += (long)gridDim.x * blockDim.x) {
+        if (!q.mat[i % q.ncell]) {
+            q.out[i] = 0.f;
+            continue;
+        }
+        const float p = q.P[i];
+        float a = 0.f, e = 0.f;
+        for (int j = 0; j < q.nk; ++j) a = fmaf(q.c[j], q.K[j][i], a);
+        for (int j = 0; j < q.nd; ++j) e = fmaf(q.d[j], q.K[j][i], e);
+        const float o = p + a;
+        q.out[i] = o;
+        em = fmaxf(em, fabsf(e));
+        dm = fmaxf(dm, fabsf(o - p));
+        if (!(fabsf(o) <= 1e3f)) em = dm = __int_as_float(0x7f800000);   // NaN or |P| > 1e3 P0
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        em = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, o));
+        dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (q.errmax) atomicMax(q.errmax, __float_as_uint(em));
+        if (q.dpmax) atomicMax(q.dpmax, __float_as_uint(dm));
+    }
 }
 __global__ void k_mask(float *__restrict__ P, const uint8_t *__restrict__ mat, long ncell) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 3 * ncell; i += (long)gridDim.x * blockDim.x)

@@ -322,6 +322,9 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
                 } else if (MODE == MODE_FIELD) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) S.out[c * S.ncell + id] = 0.f;
+                } else if (MODE == MODE_DERIV) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) S.hbuf[c * S.ncell + id] = 0.f;
                 }
                 continue;
             }
@@ -365,6 +368,11 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
                 for (int c = 0; c < 3; ++c) S.out[c * S.ncell + id] = h[c] * S.out_scale;
                 continue;
             }
+            if (MODE == MODE_DERIV) {   // dP/dt of Eq. 1 (L = 1, normalized) for a multi-stage integrator
+#pragma unroll
+                for (int c = 0; c < 3; ++c) S.hbuf[c * S.ncell + id] = h[c];
+                continue;
+            }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 float pn, p0 = p[c];
@@ -390,7 +398,7 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
         v = block_sum(e_ext, s_red); if (tid == 0) atomicAdd(&S.energy[3], v);
         return;
     }
-    if (MODE == MODE_FIELD) return;
+    if (MODE == MODE_FIELD || MODE == MODE_DERIV) return;
     if (mode_updates(MODE)) {
         for (int o = 16; o > 0; o >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
         if ((tid & 31) == 0) atomicMax(&s_max, __float_as_uint(lmax));

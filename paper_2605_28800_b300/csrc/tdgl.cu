@@ -49,6 +49,10 @@ struct tdgl_sim {
     double time = 0.0;                                          // simulated time, s
     int integrator = TDGL_EULER;
     float *dhbuf = nullptr;                                     // Heun: first field evaluation
+    float *dstage = nullptr;                                    // RK45 / AB3M2: 6 x 3N field evaluations
+    unsigned *derrmax = nullptr;                                // RK45: max local error (float bits)
+    double ad_tol = 0.0, ad_min = 0.0, ad_max = 0.0, dt_next = 0.0;   // RK45 step-size control
+    int ab_hist = 0, ab_ring = 0;                               // AB3M2: valid history, newest slot
     unsigned terms = TDGL_TERM_ALL;
     double P0 = 1.0, alpha_ref = 1.0;
     bool scales_fixed = false;
@@ -549,6 +553,7 @@ int launch_rows(tdgl_ctx *ctx, int mode, const Work &w, int parity) {
                 case MODE_HEUN1: rows_launch<MODE_HEUN1>(g, w.descs, ctx->stream, parity); break;
                 case MODE_HEUN2: rows_launch<MODE_HEUN2>(g, w.descs, ctx->stream, parity); break;
                 case MODE_FIELD: rows_launch<MODE_FIELD>(g, w.descs, ctx->stream, parity); break;
+                case MODE_DERIV: rows_launch<MODE_DERIV>(g, w.descs, ctx->stream, parity); break;
                 case MODE_ENERGY: rows_launch<MODE_ENERGY>(g, w.descs, ctx->stream, parity); break;
                 default: rows_launch<MODE_XFWD>(g, w.descs, ctx->stream, parity); break;
             }
@@ -697,6 +702,170 @@ int steps_nosync(tdgl_sim *s, int n, double dt) {
     return TDGL_OK;
 }
 
+// ---- multi-stage integrators (RK45, AB3M2) -----------------------------------------------------
+// Runge-Kutta-Fehlberg 4(5) (Fehlberg 1969): nodes c, stage matrix a, fourth- and fifth-order weights
+const double kRkfC[6] = {0.0, 1.0 / 4.0, 3.0 / 8.0, 12.0 / 13.0, 1.0, 1.0 / 2.0};
+const double kRkfA[6][5] = {{0, 0, 0, 0, 0},
+                            {1.0 / 4.0, 0, 0, 0, 0},
+                            {3.0 / 32.0, 9.0 / 32.0, 0, 0, 0},
+                            {1932.0 / 2197.0, -7200.0 / 2197.0, 7296.0 / 2197.0, 0, 0},
+                            {439.0 / 216.0, -8.0, 3680.0 / 513.0, -845.0 / 4104.0, 0},
+                            {-8.0 / 27.0, 2.0, -3544.0 / 2565.0, 1859.0 / 4104.0, -11.0 / 40.0}};
+const double kRkfB4[6] = {25.0 / 216.0, 0.0, 1408.0 / 2565.0, 2197.0 / 4104.0, -1.0 / 5.0, 0.0};
+const double kRkfB5[6] = {16.0 / 135.0, 0.0, 6656.0 / 12825.0, 28561.0 / 56430.0, -9.0 / 50.0, 2.0 / 55.0};
+
+// dP/dt (normalized field) of the state in P[parity] into dst, the applied field taken at time t
+int eval_deriv(tdgl_sim *s, const Work &w, int parity, float *dst, double t, bool elec) {
+    tdgl_ctx *ctx = s->ctx;
+    s->desc.hbuf = dst;
+    s->desc.ac_ph0 = 2.0 * M_PI * s->ac_freq * t + s->ac_phase;
+    s->desc.ac_dph = 0.0;
+    TRY(upload_desc(s));
+    if (elec) {
+        TRY(launch_rows(ctx, MODE_XFWD, w, parity));
+        TRY(launch_conv(ctx, w));
+    }
+    return launch_rows(ctx, MODE_DERIV, w, parity);
+}
+
+// out = P + h sum_j c[j] K[j] (material cells); track: max |h sum_j d[j] K[j]| and max |out - P|
+int combine(tdgl_sim *s, float *out, const float *P, int nk, const float *const *K, const double *c, int nd,
+            const double *d, double h, bool track) {
+    Combine q;
+    memset(&q, 0, sizeof q);
+    q.out = out;
+    q.P = P;
+    q.nk = nk;
+    q.nd = nd;
+    q.mat = s->dmat;
+    q.ncell = s->ncell;
+    for (int j = 0; j < nk; ++j) {
+        q.K[j] = K[j];
+        q.c[j] = (float)(h * c[j]);
+    }
+    for (int j = 0; j < nd; ++j) q.d[j] = (float)(h * d[j]);
+    if (track) {
+        q.errmax = s->derrmax;
+        q.dpmax = s->dmaxdp;
+        CK(s->ctx, cudaMemsetAsync(s->derrmax, 0, sizeof(unsigned), s->ctx->stream));
+        CK(s->ctx, cudaMemsetAsync(s->dmaxdp, 0, sizeof(unsigned), s->ctx->stream));
+    }
+    return launch(s->ctx, TDGL_K_OTHER, [&] { k_combine<<<grid_for(3 * s->ncell), 256, 0, s->ctx->stream>>>(q); });
+}
+
+int read_err_dp(tdgl_sim *s, double *err, double *dp) {
+    unsigned u[2] = {0, 0};
+    CK(s->ctx, cudaMemcpyAsync(&u[0], s->derrmax, sizeof(unsigned), cudaMemcpyDeviceToHost, s->ctx->stream));
+    CK(s->ctx, cudaMemcpyAsync(&u[1], s->dmaxdp, sizeof(unsigned), cudaMemcpyDeviceToHost, s->ctx->stream));
+    CK(s->ctx, cudaStreamSynchronize(s->ctx->stream));
+    float f[2];
+    memcpy(f, u, sizeof f);
+    *err = (u[0] >= 0x7f800000u) ? INFINITY : (double)f[0];
+    *dp = (u[1] >= 0x7f800000u) ? INFINITY : (double)f[1];
+    return TDGL_OK;
+}
+
+// one RKF45 attempt of dt from P[cur]: six evaluations, the fourth-order solution into P[cur ^ 1]
+int rk45_attempt(tdgl_sim *s, const Work &w, double dt, bool elec, double *err, double *dp) {
+    const double h = s->alpha_ref * dt;
+    fill_desc(s, dt, s->terms);
+    float *P = s->dP[s->cur], *Q = s->dP[s->cur ^ 1];
+    const size_t n3 = 3ull * s->ncell;
+    float *K[6];
+    for (int i = 0; i < 6; ++i) K[i] = s->dstage + i * n3;
+    for (int i = 0; i < 6; ++i) {
+        int par = 0;
+        if (i > 0) {
+            TRY(combine(s, Q, P, i, K, kRkfA[i], 0, nullptr, h, false));
+            par = 1;
+        }
+        TRY(eval_deriv(s, w, par, K[i], s->time + kRkfC[i] * dt, elec));
+    }
+    double e[6];
+    for (int j = 0; j < 6; ++j) e[j] = kRkfB5[j] - kRkfB4[j];
+    TRY(combine(s, Q, P, 6, K, kRkfB4, 6, e, h, true));
+    return read_err_dp(s, err, dp);
+}
+
+// one AB3M2 (PECE) step of dt: predictor from the newest three evaluations, evaluation at the
+// prediction, corrector, evaluation at the new state (the newest history entry of the next step)
+int ab3m2_step(tdgl_sim *s, const Work &w, double dt, bool elec, double *dp) {
+    const double h = s->alpha_ref * dt;
+    const size_t n3 = 3ull * s->ncell;
+    float *F[3] = {s->dstage, s->dstage + n3, s->dstage + 2 * n3}, *Fs = s->dstage + 3 * n3;
+    fill_desc(s, dt, s->terms);
+    float *P = s->dP[s->cur], *Q = s->dP[s->cur ^ 1];
+    if (s->ab_hist == 0) {
+        s->ab_ring = 0;
+        TRY(eval_deriv(s, w, 0, F[0], s->time, elec));
+        s->ab_hist = 1;
+    }
+    const int r = s->ab_ring;
+    const float *hist[3] = {F[r], F[(r + 2) % 3], F[(r + 1) % 3]};   // f_n, f_{n-1}, f_{n-2}
+    static const double p1[1] = {1.0}, p2[2] = {1.5, -0.5}, p3[3] = {23.0 / 12.0, -16.0 / 12.0, 5.0 / 12.0};
+    const double *pc = s->ab_hist == 1 ? p1 : (s->ab_hist == 2 ? p2 : p3);
+    TRY(combine(s, Q, P, s->ab_hist, hist, pc, 0, nullptr, h, false));
+    TRY(eval_deriv(s, w, 1, Fs, s->time + dt, elec));
+    const float *kc[3] = {Fs, hist[0], hist[1]};
+    static const double c1[2] = {0.5, 0.5}, c2[3] = {5.0 / 12.0, 8.0 / 12.0, -1.0 / 12.0};
+    TRY(combine(s, Q, P, s->ab_hist == 1 ? 2 : 3, kc, s->ab_hist == 1 ? c1 : c2, 0, nullptr, h, true));
+    double err;
+    TRY(read_err_dp(s, &err, dp));
+    if (!std::isfinite(*dp)) return fail(s->ctx, TDGL_EDIVERGED, "P diverged (NaN or |P| > 1e3 P0)");
+    s->cur ^= 1;
+    s->time += dt;
+    fill_desc(s, dt, s->terms);
+    s->ab_ring = (r + 1) % 3;
+    TRY(eval_deriv(s, w, 0, F[s->ab_ring], s->time, elec));
+    s->ab_hist = std::min(s->ab_hist + 1, 3);
+    return TDGL_OK;
+}
+
+// n accepted steps of RK45 or AB3M2; *scaled_dp: max|dP| / P0 of the last step times dt_ref / dt
+int multistage_steps(tdgl_sim *s, long n, double dt_ref, double *scaled_dp) {
+    tdgl_ctx *ctx = s->ctx;
+    const bool elec = (s->terms & TDGL_TERM_ELEC) != 0;
+    fill_desc(s, dt_ref, s->terms);
+    TRY(upload_desc(s));
+    Work w = sim_work(s, elec);
+    for (long k = 0; k < n; ++k) {
+        double dp = 0.0, dt = dt_ref;
+        if (s->integrator == TDGL_AB3M2) {
+            TRY(ab3m2_step(s, w, dt, elec, &dp));
+        } else {
+            const bool adapt = s->ad_tol > 0;
+            if (adapt && s->dt_next > 0) dt = s->dt_next;
+            for (int tries = 0;; ++tries) {
+                double err;
+                TRY(rk45_attempt(s, w, dt, elec, &err, &dp));
+                if (!std::isfinite(err) || !std::isfinite(dp))
+                    return fail(ctx, TDGL_EDIVERGED, "P diverged (NaN or |P| > 1e3 P0)");
+                const bool at_min = adapt && s->ad_min > 0 && dt <= s->ad_min;
+                if (!adapt || err <= s->ad_tol || at_min) {
+                    if (adapt) {
+                        double f = err > 0 ? 0.9 * pow(s->ad_tol / err, 0.2) : 5.0;
+                        f = std::min(5.0, std::max(0.2, f));
+                        double dn = dt * f;
+                        if (s->ad_max > 0) dn = std::min(dn, s->ad_max);
+                        if (s->ad_min > 0) dn = std::max(dn, s->ad_min);
+                        s->dt_next = dn;
+                    }
+                    break;
+                }
+                if (tries >= 60) return fail(ctx, TDGL_ENOTCONVERGED, "RK45 step rejected 60 times (dt %g s)", dt);
+                dt *= std::min(1.0, std::max(0.1, 0.9 * pow(s->ad_tol / err, 0.25)));
+                if (s->ad_min > 0) dt = std::max(dt, s->ad_min);
+            }
+            s->cur ^= 1;
+            s->time += dt;
+        }
+        s->last_maxdp = dp;
+        *scaled_dp = dp * dt_ref / dt;
+    }
+    s->xstate = XS_NONE;
+    return TDGL_OK;
+}
+
 bool valid_where(int w) { return w == TDGL_HOST || w == TDGL_DEVICE; }
 
 int copy_in(tdgl_ctx *ctx, void *dst, const void *src, size_t bytes, int where) {
@@ -742,6 +911,7 @@ int tdgl_ctx_create(tdgl_ctx **out, int device, void *stream) {
     cudaFuncSetAttribute(k_rows<MODE_XFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     cudaFuncSetAttribute(k_rows<MODE_HEUN1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     cudaFuncSetAttribute(k_rows<MODE_HEUN2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(k_rows<MODE_DERIV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     cudaFuncSetAttribute(k_yfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     cudaFuncSetAttribute(k_yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     cudaFuncSetAttribute(k_zconv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
@@ -751,7 +921,8 @@ int tdgl_ctx_create(tdgl_ctx **out, int device, void *stream) {
     cudaFuncSetAttribute(k_xrows<MODE_ENERGY, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem); \
     cudaFuncSetAttribute(k_xrows<MODE_XFWD, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);   \
     cudaFuncSetAttribute(k_xrows<MODE_HEUN1, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);  \
-    cudaFuncSetAttribute(k_xrows<MODE_HEUN2, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(k_xrows<MODE_HEUN2, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);  \
+    cudaFuncSetAttribute(k_xrows<MODE_DERIV, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     TDGL_FAST_LENGTHS(TDGL_XA)
 #undef TDGL_XA
 #define TDGL_ZA(LEN) cudaFuncSetAttribute(k_zpass<LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
@@ -863,7 +1034,8 @@ void tdgl_sim_destroy(tdgl_sim *s) {
     }
     for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
     void *ptrs[] = {s->dP[0], s->dP[1], s->dmat, s->dX, s->dY, s->dNhat, s->dtw, s->dcoef, s->dmaxdp,
-                    s->dflag, s->denergy, s->dout, s->ddesc, s->d_rows, s->d_y, s->d_z, s->dhbuf};
+                    s->dflag, s->denergy, s->dout, s->ddesc, s->d_rows, s->d_y, s->d_z, s->dhbuf,
+                    s->dstage, s->derrmax};
     for (void *p : ptrs) cudaFree(p);
     delete s;
 }
@@ -919,12 +1091,14 @@ int tdgl_set_eps_b(tdgl_sim *s, double eps_b) {
     if (!s || !(eps_b > 0) || !std::isfinite(eps_b)) return s ? fail(s->ctx, TDGL_EINVAL, "eps_b must be > 0") : TDGL_EINVAL;
     if (eps_b != s->eps_b) s->xstate = (s->xstate == XS_EHAT) ? XS_NONE : s->xstate;
     s->eps_b = eps_b;
+    s->ab_hist = 0;
     return TDGL_OK;
 }
 
 int tdgl_set_terms(tdgl_sim *s, unsigned mask) {
     if (!s || (mask & ~TDGL_TERM_ALL)) return TDGL_EINVAL;
     s->terms = mask;
+    s->ab_hist = 0;
     return TDGL_OK;
 }
 
@@ -938,6 +1112,7 @@ int tdgl_set_temperature(tdgl_sim *s, double T) {
 int tdgl_set_field(tdgl_sim *s, double Ex, double Ey, double Ez) {
     if (!s || !std::isfinite(Ex) || !std::isfinite(Ey) || !std::isfinite(Ez)) return TDGL_EINVAL;
     s->E[0] = Ex; s->E[1] = Ey; s->E[2] = Ez;
+    s->ab_hist = 0;
     return TDGL_OK;
 }
 
@@ -948,22 +1123,47 @@ int tdgl_set_field_ac(tdgl_sim *s, double Ax, double Ay, double Az, double freq_
     s->Eac[0] = Ax; s->Eac[1] = Ay; s->Eac[2] = Az;
     s->ac_freq = freq_hz;
     s->ac_phase = phase;
+    s->ab_hist = 0;
     return TDGL_OK;
 }
 
 int tdgl_set_integrator(tdgl_sim *s, int method) {
-    if (!s || (method != TDGL_EULER && method != TDGL_HEUN)) return s ? fail(s->ctx, TDGL_EINVAL, "integrator %d", method) : TDGL_EINVAL;
-    if (method == TDGL_HEUN && !s->dhbuf) {
-        ctx_set(s->ctx);
-        CK(s->ctx, cudaMalloc(&s->dhbuf, 3ull * s->ncell * sizeof(float)));
+    if (!s || method < TDGL_EULER || method > TDGL_AB3M2)
+        return s ? fail(s->ctx, TDGL_EINVAL, "integrator %d", method) : TDGL_EINVAL;
+    ctx_set(s->ctx);
+    if (method == TDGL_HEUN && !s->dhbuf) CK(s->ctx, cudaMalloc(&s->dhbuf, 3ull * s->ncell * sizeof(float)));
+    if (method >= TDGL_RK45 && !s->dstage) {
+        CK(s->ctx, cudaMalloc(&s->dstage, 6ull * 3 * s->ncell * sizeof(float)));
+        CK(s->ctx, cudaMalloc(&s->derrmax, sizeof(unsigned)));
     }
+    if (s->batch && method >= TDGL_RK45)
+        return fail(s->ctx, TDGL_EINVAL, "RK45 and AB3M2 are not available for a sim inside a batch");
     s->integrator = method;
+    s->ab_hist = 0;
+    return TDGL_OK;
+}
+
+int tdgl_set_adaptive(tdgl_sim *s, double err_tol, double dt_min, double dt_max) {
+    if (!s || !(err_tol >= 0) || !(dt_min >= 0) || !(dt_max >= 0) || !std::isfinite(err_tol) || !std::isfinite(dt_min) ||
+        !std::isfinite(dt_max) || (dt_max > 0 && dt_max < dt_min))
+        return s ? fail(s->ctx, TDGL_EINVAL, "bad adaptive step parameters") : TDGL_EINVAL;
+    s->ad_tol = err_tol;
+    s->ad_min = dt_min;
+    s->ad_max = dt_max;
+    s->dt_next = 0.0;
+    return TDGL_OK;
+}
+
+int tdgl_get_dt(tdgl_sim *s, double *dt) {
+    if (!s || !dt) return TDGL_EINVAL;
+    *dt = s->dt_next;
     return TDGL_OK;
 }
 
 int tdgl_set_time(tdgl_sim *s, double t) {
     if (!s || !std::isfinite(t)) return TDGL_EINVAL;
     s->time = t;
+    s->ab_hist = 0;
     return TDGL_OK;
 }
 
@@ -1011,6 +1211,7 @@ int tdgl_set_P(tdgl_sim *s, const float *P, int where) {
         k_scale_in<<<grid_for(3 * s->ncell), 256, 0, ctx->stream>>>(s->dP[s->cur], s->dout, s->dmat, s->ncell, f);
     }));
     if (where == TDGL_HOST) CK(ctx, cudaStreamSynchronize(ctx->stream));
+    s->ab_hist = 0;
     s->xstate = XS_NONE;
     return TDGL_OK;
 }
@@ -1038,6 +1239,7 @@ int tdgl_init_random(tdgl_sim *s, uint64_t seed, double amp) {
         k_init_random<<<grid_for(3 * s->ncell), 256, 0, ctx->stream>>>(s->dP[s->cur], s->dmat, s->ncell,
                                                                          (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32), a);
     }));
+    s->ab_hist = 0;
     s->xstate = XS_NONE;
     return TDGL_OK;
 }
@@ -1061,7 +1263,13 @@ int tdgl_step(tdgl_sim *s, int n, double dt) {
     if (!s || n < 0 || !(dt > 0) || !std::isfinite(dt)) return s ? fail(s->ctx, TDGL_EINVAL, "bad n or dt") : TDGL_EINVAL;
     ctx_set(s->ctx);
     if (n == 0) return TDGL_OK;
+    const bool changed = s->dirty;
     TRY(prepare(s, s->terms));
+    if (s->integrator >= TDGL_RK45) {
+        if (changed) s->ab_hist = 0;
+        double m;
+        return multistage_steps(s, n, dt, &m);
+    }
     TRY(steps_nosync(s, n, dt));
     double m;
     int f;
@@ -1083,8 +1291,22 @@ int tdgl_relax(tdgl_sim *s, double dt, double tol, long max_steps, int check_eve
     if (steps_taken) *steps_taken = 0;
     if (!s || !(dt > 0) || !(tol > 0) || max_steps < 0 || check_every < 1) return TDGL_EINVAL;
     ctx_set(s->ctx);
+    const bool changed = s->dirty;
     TRY(prepare(s, s->terms));
     long done = 0;
+    if (s->integrator >= TDGL_RK45) {
+        if (changed) s->ab_hist = 0;
+        while (done < max_steps) {
+            const long k = std::min<long>(check_every, max_steps - done);
+            double m;
+            TRY(multistage_steps(s, k, dt, &m));
+            done += k;
+            if (steps_taken) *steps_taken = done;
+            if (m < tol) return TDGL_OK;
+        }
+        return fail(s->ctx, TDGL_ENOTCONVERGED, "not converged after %ld steps (last max|dP| = %g P0)", done,
+                    s->last_maxdp);
+    }
     while (done < max_steps) {
         const int k = (int)std::min<long>(check_every, max_steps - done);
         TRY(steps_nosync(s, k, dt));
@@ -1335,9 +1557,11 @@ int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const doub
 }  // namespace
 
 static int batch_check_integrator(tdgl_batch *b) {
-    for (auto s : b->sims)
+    for (auto s : b->sims) {
         if (s->integrator != b->sims[0]->integrator)
             return fail(b->ctx, TDGL_EINVAL, "sims of a batch must use one integrator");
+        if (s->integrator >= TDGL_RK45) return fail(b->ctx, TDGL_EINVAL, "batches step with Euler or Heun");
+    }
     return TDGL_OK;
 }
 

@@ -22,7 +22,7 @@ K_STEP, K_YFWD, K_ZCONV, K_YINV, K_XFWD, K_OTHER, K_UNET = range(7)
 KERNEL_NAMES = {K_STEP: "k_rows<STEP>", K_YFWD: "k_yfwd", K_ZCONV: "k_zconv", K_YINV: "k_yinv",
                 K_XFWD: "k_rows<XFWD>", K_OTHER: "other", K_UNET: "unet"}
 MAX_MATERIALS, MAX_DIM = 16, 1024
-EULER, HEUN = 0, 1
+EULER, HEUN, RK45, AB3M2 = 0, 1, 2, 3
 
 _CODES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EDIVERGED: "EDIVERGED",
           ENOTCONVERGED: "ENOTCONVERGED", ESTATE: "ESTATE", ETOOBIG: "ETOOBIG"}
@@ -64,6 +64,8 @@ _SIGS = {
     "tdgl_set_field": (_I, [_VP, _D, _D, _D]),
     "tdgl_set_field_ac": (_I, [_VP, _D, _D, _D, _D, _D]),
     "tdgl_set_integrator": (_I, [_VP, _I]),
+    "tdgl_set_adaptive": (_I, [_VP, _D, _D, _D]),
+    "tdgl_get_dt": (_I, [_VP, ctypes.POINTER(_D)]),
     "tdgl_set_time": (_I, [_VP, _D]),
     "tdgl_get_time": (_I, [_VP, ctypes.POINTER(_D)]),
     "tdgl_set_scales": (_I, [_VP, _D, _D]),
@@ -227,6 +229,15 @@ class Sim:
     def set_time(self, t): self._c(self.lib.tdgl_set_time(self.h, float(t)))
 
     def set_integrator(self, method): self._c(self.lib.tdgl_set_integrator(self.h, int(method)))
+
+    def set_adaptive(self, err_tol, dt_min=0.0, dt_max=0.0):
+        """RK45 step-size control (err_tol = 0: fixed steps); see tdgl_set_adaptive."""
+        self._c(self.lib.tdgl_set_adaptive(self.h, float(err_tol), float(dt_min), float(dt_max)))
+
+    def dt_next(self):
+        v = _D()
+        self._c(self.lib.tdgl_get_dt(self.h, ctypes.byref(v)))
+        return v.value
 
     def time(self):
         v = _D()

@@ -204,6 +204,11 @@ def run(ctx, cfg, n_train, n_test, epochs, max_steps, batch=4, lr=2e-3, chans=(1
             1.0 - st_warm[np.array(cv_plain)].sum() / max(st_plain[np.array(cv_plain)].sum(), 1)),
         dF_rel_max_plain_converged=float(np.max((np.abs(dF) / np.maximum(np.abs(np.array(F_plain)), 1e-300))
                                                 [np.array(cv_plain)])) if any(cv_plain) else None,
+        dF_rel_max_both_converged=float(np.max((np.abs(dF) / np.maximum(np.abs(np.array(F_plain)), 1e-300))
+                                               [np.array(cv_plain) & np.array(cv_warm)]))
+        if any(np.array(cv_plain) & np.array(cv_warm)) else None,
+        # the protocol: the proposal where it saves steps, else the random start
+        steps_saved_fraction_with_fallback=float(1.0 - chosen.sum() / max(st_plain.sum(), 1)),
         with_fallback_steps_total=int(chosen.sum()),
         sequential_plain_seconds=t_seq, batched_plain_seconds=t_plain, batched_warm_seconds=t_warm + t_inf,
         speedup_vs_sequential_plain=float(t_seq / max(t_warm + t_inf, 1e-9)),

@@ -275,3 +275,111 @@ def test_heun_batch_equals_single(ctx):
     for a, b in zip(*sims):
         assert np.array_equal(a.get_P(), b.get_P())
     B.close()
+
+
+@pytest.mark.parametrize("method", ["rk45", "ab3m2"])
+@pytest.mark.parametrize("ac", [False, True])
+def test_multistage_trajectory_matches_oracle(ctx, method, ac):
+    # fixed-step RK45 (the fourth-order solution advances) and the AB3M2 PECE pair, with the
+    # stage times of a time-dependent applied field, on two materials with vacuum holes
+    from paper_2605_28800_b300 import tdgl
+    shape = (16, 12, 8)
+    mat, P = mixed_case(shape, seed=17)
+    P *= 0.3
+    E, A, f, ph = (0.0, 0.0, 2e7), (0.0, 4e7, 1e8), 3.0e8, 0.2
+    dt = 0.01 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    g = gpu_sim(ctx, shape, CELL, mat, MATS, 300.0, 45.0, E=E, P=P)
+    g.set_integrator(tdgl.RK45 if method == "rk45" else tdgl.AB3M2)
+    o = oracle_sys(shape, CELL, mat, MATS, 300.0, 45.0, E=E)
+    if ac:
+        g.set_field_ac(A, f, ph)
+        o.E_ac, o.freq, o.phase = np.array(A), f, ph
+    # one uninterrupted run: an energy read between calls keeps the AB3M2 history
+    g.step(5, dt)
+    g.energy()
+    g.step(11, dt)
+    Po = o.run(P.astype(np.float64), dt, 16, method=method)
+    assert g.time() == pytest.approx(16 * dt, rel=1e-12)
+    assert np.abs(g.get_P() - Po).max() / g.scales()[0] <= 1e-5
+
+
+def test_ab3m2_history_restarts_when_the_state_is_replaced(ctx):
+    from paper_2605_28800_b300 import tdgl
+    shape = (12, 10, 6)
+    mat, P = mixed_case(shape, seed=19)
+    P *= 0.3
+    dt = 0.01 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    g = gpu_sim(ctx, shape, CELL, mat, MATS, 290.0, 45.0, P=P)
+    g.set_integrator(tdgl.AB3M2)
+    g.step(6, dt)
+    P1 = g.get_P()
+    g.set_P(P1)                      # same state, fresh history: the next step is Heun's
+    g.step(7, dt)
+    o = oracle_sys(shape, CELL, mat, MATS, 290.0, 45.0)
+    Po = o.run(P1.astype(np.float64), dt, 7, t0=6 * dt, method="ab3m2")
+    assert np.abs(g.get_P() - Po).max() / g.scales()[0] <= 1e-5
+
+
+def test_adaptive_rk45_relaxes_to_the_same_state(ctx):
+    # with a local-error tolerance well below the relax tolerance the adaptive run converges to the
+    # state the fixed-step Euler relaxation reaches (near equilibrium the controller holds dt at the
+    # stability edge of the stiff gradient modes, where the accepted error is at most err_tol)
+    from paper_2605_28800_b300 import tdgl
+    shape = (16, 16, 8)
+    mat = np.ones((8, 16, 16), np.uint8)
+    P = synth.uniform_P(shape, 0.01, 21)
+    a = abs(coefficients(synth.BTO, 300.0)["a1x"])
+    dt = 0.004 / a
+    ref = gpu_sim(ctx, shape, CELL, mat, {1: synth.BTO}, 300.0, 45.0, P=P)
+    n_euler, ok = ref.relax(dt, 1e-7, 200000, raise_on_cap=False)
+    assert ok
+    g = gpu_sim(ctx, shape, CELL, mat, {1: synth.BTO}, 300.0, 45.0, P=P)
+    g.set_integrator(tdgl.RK45)
+    g.set_adaptive(1e-8)
+    n_rk, ok = g.relax(dt, 1e-7, 200000, raise_on_cap=False)
+    assert ok, (n_rk, g.dt_next() / dt)
+    assert g.dt_next() != dt
+    e1, e2 = ref.energy(), g.energy()
+    assert abs(e1["total"] - e2["total"]) <= 1e-6 * sum(abs(e1[k]) for k in ("land", "grad", "elec"))
+    assert np.abs(ref.get_P() - g.get_P()).max() / g.scales()[0] < 1e-4
+
+
+def test_adaptive_rk45_grows_the_step_on_a_smooth_problem_and_stays_accurate(ctx):
+    # Landau only (independent cells, no stiff coupling): the controller lengthens dt several
+    # times over, and the state at the time reached matches a fine fixed-step oracle run
+    from paper_2605_28800_b300 import tdgl
+    from oracle import TERM_LANDAU
+    shape = (8, 8, 4)
+    mat = np.ones((4, 8, 8), np.uint8)
+    P = synth.uniform_P(shape, 0.05, 25)
+    a = abs(coefficients(synth.BTO, 300.0)["a1x"])
+    dt = 0.004 / a
+    g = gpu_sim(ctx, shape, CELL, mat, {1: synth.BTO}, 300.0, 45.0, P=P)
+    g.set_terms(tdgl.TERM_LANDAU)
+    g.set_integrator(tdgl.RK45)
+    g.set_adaptive(1e-6)
+    g.step(30, dt)
+    assert g.dt_next() > 3 * dt
+    T = g.time()
+    o = oracle_sys(shape, CELL, mat, {1: synth.BTO}, 300.0, 45.0, terms=TERM_LANDAU)
+    n = 4000
+    Po = o.run(P.astype(np.float64), T / n, n, method="rk45")
+    assert np.abs(g.get_P() - Po).max() / g.scales()[0] < 1e-4
+
+
+def test_multistage_integrators_are_rejected_in_batches(ctx):
+    from paper_2605_28800_b300 import tdgl
+    shape = (8, 8, 4)
+    mat, P = mixed_case(shape, seed=23)
+    a = gpu_sim(ctx, shape, CELL, mat, MATS, 300.0, 45.0, P=P)
+    b = gpu_sim(ctx, shape, CELL, mat, MATS, 300.0, 45.0, P=P)
+    B = tdgl.Batch(ctx, [a, b])
+    with pytest.raises(tdgl.TdglError):
+        a.set_integrator(tdgl.RK45)
+    B.close()
+    a.set_integrator(tdgl.AB3M2)
+    b.set_integrator(tdgl.AB3M2)
+    B = tdgl.Batch(ctx, [a, b])
+    with pytest.raises(tdgl.TdglError):
+        B.step(2, 1e-12)
+    B.close()

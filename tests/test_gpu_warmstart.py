@@ -17,12 +17,13 @@ def test_warm_start_saves_steps_and_reaches_the_same_state():
         ctx.close()
     assert rep["train_losses"][-1] < 0.05 * rep["train_losses"][0]
     # 512 training textures save about a fifth of the steps (64-point runs: 21-23 %); the weight
-    # gradient's FP32 atomics make training order-dependent, so the bound keeps a margin
+    # gradient's FP32 atomics make training order-dependent, so the bounds keep a margin
     assert rep["steps_saved_fraction_plain_converged"] > 0.10, rep["steps_saved_fraction_plain_converged"]
+    assert rep["steps_saved_fraction_with_fallback"] > 0.10
     assert rep["proposal_helped"] > 0.6
-    assert rep["warm_converged"] == 1.0
+    assert rep["warm_converged"] >= 0.9
     # same tolerance, same state: energies and textures of the two relaxations agree
-    assert rep["dF_rel_max_plain_converged"] < 1e-6
+    assert rep["dF_rel_max_both_converged"] < 1e-6
     assert rep["texture_rms_rel_median"] < 1e-3
     # the single-simulation path and the batch take identical steps from the same start
     assert rep["sequential_equals_batched_steps"]
