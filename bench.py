@@ -248,8 +248,11 @@ def gpu_arm(args, rank, world):
         s.step(1, dt)       # returns after reading the step's max|dP| and divergence flag
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
+    zvar = {n: ctx.zpass_variant(n) for n in (256, 512)}
     return dict(ms=ms, launches=launches, prof=prof, clocks=clk.summary(), ncell=ncell, wl=wl,
-                e2e=aggregate_rate(ncell * e2e_steps, world, e2e_s), e2e_h2d=Ph.numel() * 4)
+                e2e=aggregate_rate(ncell * e2e_steps, world, e2e_s), e2e_h2d=Ph.numel() * 4,
+                zpass_tuning={str(n): {"variant": v, "us": [round(u, 2) for u in us]}
+                              for n, (v, us) in zvar.items() if v >= 0})
 
 
 # ---- CPU oracle ----------------------------------------------------------------------------------
@@ -457,8 +460,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
             "hbm_frac_of_fused_floor": value / world * B_ALG_FUSED / (hbm * 1e9),
-            "fft_pad": list(M), "roofline": roof, "kernels": kernels, "clocks": r["clocks"],
-            "gpu_launches": r["launches"],
+            "fft_pad": list(M), "zpass_tuning": r["zpass_tuning"], "roofline": roof, "kernels": kernels,
+            "clocks": r["clocks"], "gpu_launches": r["launches"],
             "e2e": {"value": r["e2e"], "unit": UNIT, "h2d_bytes_per_step": r["e2e_h2d"], "d2h_bytes_per_step": 8}}
     if world == 1 and not args.no_cpu_baseline:
         import multiprocessing

@@ -18,16 +18,23 @@ template <int N> __host__ __device__ constexpr int lines_per_block() {
     return (256 / rf::threads_per_line<N>()) < 16 ? (256 / rf::threads_per_line<N>()) : 16;
 }
 
-// Shapes of the z pass.  For 256 and 512 points, 8 elements per thread (radices 8 8 4 and
-// 8 8 8): half the registers of the 16-element shapes, so a block of 256 threads keeps the
-// shared memory of a 128-thread block of those and an SM holds twice the warps.
-template <int N> struct ZCfg : rf::Cfg<N> {};
-template <> struct ZCfg<256> : rf::Shape<256, 8, 8, 8, 4> {};
-template <> struct ZCfg<512> : rf::Shape<512, 8, 8, 8, 8> {};
-template <int N> __host__ __device__ constexpr int zthreads() { return ZCfg<N>::E == 8 ? 256 : 128; }
-template <int N> __host__ __device__ constexpr int zlines_per_block() {
-    return (zthreads<N>() / ZCfg<N>::T) < 16 ? (zthreads<N>() / ZCfg<N>::T) : 16;
+// Shapes of the z pass, V = radix-schedule variant (picked per length by the host's autotuner):
+//   V = 0: the default shapes (16 elements per thread; radices 16 16 for 256, 16 16 2 for 512),
+//          128-thread blocks;
+//   V = 1: for 256 and 512 points 8 elements per thread (radices 8 8 4, 8 8 8): half the
+//          registers, 256-thread blocks with the same lines and shared memory, so an SM holds
+//          twice the warps, at the price of one more exchange.
+// Both variants give every length the same lines per block, hence the same work items.
+template <int N, int V> struct ZCfg : rf::Cfg<N> {};
+template <> struct ZCfg<256, 1> : rf::Shape<256, 8, 8, 8, 4> {};
+template <> struct ZCfg<512, 1> : rf::Shape<512, 8, 8, 8, 8> {};
+template <int N, int V> __host__ __device__ constexpr int zthreads() { return ZCfg<N, V>::E == 8 ? 256 : 128; }
+template <int N, int V> __host__ __device__ constexpr int zlines_per_block() {
+    return (zthreads<N, V>() / ZCfg<N, V>::T) < 16 ? (zthreads<N, V>() / ZCfg<N, V>::T) : 16;
 }
+static_assert(zlines_per_block<256, 0>() == zlines_per_block<256, 1>() &&
+                  zlines_per_block<512, 0>() == zlines_per_block<512, 1>(),
+              "z-pass variants must share the work items");
 
 // y transform of the x-spectrum: forward (ny -> My, zero padded) or inverse (My -> first ny)
 template <int N, bool INV>
@@ -75,8 +82,8 @@ __global__ void __launch_bounds__(256) k_ypass(const SimDev *__restrict__ sims, 
 }
 
 // dynamic shared memory of k_zpass: three component spectra [3][N][KX] and the twiddles
-template <int N> __host__ __device__ constexpr size_t zpass_smem() {
-    return (3 * N * zlines_per_block<N>() + N) * sizeof(float2);
+template <int N, int V> __host__ __device__ constexpr size_t zpass_smem() {
+    return (3 * N * zlines_per_block<N, V>() + N) * sizeof(float2);
 }
 
 // Row of position pos in a [N][KX] exchange buffer.  With KX < 16 lines a half-warp covers
@@ -84,8 +91,8 @@ template <int N> __host__ __device__ constexpr size_t zpass_smem() {
 // same bank.  Rows inside each aligned group of G are permuted by (pos / R0) mod G, which
 // spreads those writes over G different bank groups and keeps consecutive positions (every
 // other access) in distinct bank groups too.
-template <int N, int KX> __device__ __forceinline__ int zrow(int pos) {
-    constexpr int G = KX >= 16 ? 1 : 16 / KX, R0 = ZCfg<N>::R0;
+template <int N, int V, int KX> __device__ __forceinline__ int zrow(int pos) {
+    constexpr int G = KX >= 16 ? 1 : 16 / KX, R0 = ZCfg<N, V>::R0;
     static_assert(G == 1 || (R0 % G == 0 && (G & (G - 1)) == 0), "swizzle group must divide the first radix");
     if constexpr (G == 1) return pos;
     else return pos ^ ((pos / R0) & (G - 1));
@@ -96,10 +103,10 @@ template <int N, int KX> __device__ __forceinline__ int zrow(int pos) {
 // each, so the x transform starts while y and z are still in flight.  The forward spectra of x
 // and y are parked in shared memory (each thread's own slots); z stays in registers through the
 // multiply and its inverse runs first, straight from registers.
-template <int N>
-__global__ void __launch_bounds__(zthreads<N>(), 4) k_zpass(const SimDev *__restrict__ sims, const int4 *__restrict__ items) {
-    using S = ZCfg<N>;
-    constexpr int E = S::E, T = S::T, KX = zlines_per_block<N>();
+template <int N, int V>
+__global__ void __launch_bounds__(zthreads<N, V>(), 4) k_zpass(const SimDev *__restrict__ sims, const int4 *__restrict__ items) {
+    using S = ZCfg<N, V>;
+    constexpr int E = S::E, T = S::T, KX = zlines_per_block<N, V>();
     extern __shared__ float4 smem4[];
     float2 *A = reinterpret_cast<float2 *>(smem4);      // [3][N][KX]
     float2 *tw = A + 3 * N * KX;                          // [N]
@@ -113,7 +120,7 @@ __global__ void __launch_bounds__(zthreads<N>(), 4) k_zpass(const SimDev *__rest
     const int nz = D.nz, My = D.My, kxp = D.kxp;
     const long zs = (long)My * kxp, cs = (long)nz * zs;
     const float2 *src = D.Y + (long)ky * kxp + kx;
-    auto idx = [&](int pos) { return zrow<N, KX>(pos) * KX + l; };
+    auto idx = [&](int pos) { return zrow<N, V, KX>(pos) * KX + l; };
     // inputs of all three components in flight at once: asynchronous 8-byte copies into this
     // thread's own slots, component c in commit group c
 #pragma unroll

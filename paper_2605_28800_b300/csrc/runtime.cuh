@@ -37,6 +37,10 @@ struct tdgl_ctx {
     std::vector<tdgl_sim *> sims;       // owned: freed by tdgl_ctx_destroy if still alive
     std::vector<tdgl_batch *> batches;
     std::vector<tdgl_unet *> nets;
+    // z-pass radix-schedule autotuning for 256- and 512-point lines: chosen variant (-1 = not
+    // yet tuned) and the measured microseconds per launch of variants 0 and 1
+    int zvar[2] = {-1, -1};
+    double zus[2][2] = {{0, 0}, {0, 0}};
 };
 
 namespace tdgl_rt {

@@ -233,7 +233,7 @@ int fast_ylines(int n) {    // lines per block of the y pass
 }
 int fast_zlines(int n) {    // lines per block of the z pass
     switch (n) {
-#define TDGL_C(LEN) case LEN: return zlines_per_block<LEN>();
+#define TDGL_C(LEN) case LEN: return zlines_per_block<LEN, 0>();
         TDGL_FAST_LENGTHS(TDGL_C)
 #undef TDGL_C
     }
@@ -491,6 +491,8 @@ void fill_desc(tdgl_sim *s, double dt, unsigned terms) {
     D.out_scale = (float)(s->alpha_ref * s->P0);
 }
 
+int autotune_z(tdgl_sim *s);
+
 int prepare(tdgl_sim *s, unsigned need_terms) {
     tdgl_ctx *ctx = s->ctx;
     if (s->dirty) {   // validation and coefficient upload only after a change
@@ -508,6 +510,7 @@ int prepare(tdgl_sim *s, unsigned need_terms) {
     if (need_terms & TDGL_TERM_ELEC) {
         TRY(alloc_spectra(s));
         if (!s->tensor_ready) TRY(build_tensor(s));
+        TRY(autotune_z(s));
     }
     return TDGL_OK;
 }
@@ -577,14 +580,32 @@ void ypass(const Group &g, const SimDev *d, cudaStream_t st) {
     }
 }
 
-void zpass(const Group &g, const SimDev *d, cudaStream_t st) {
+int zvar_index(int N) { return N == 256 ? 0 : (N == 512 ? 1 : -1); }
+
+template <int N, int V>
+void zpass_v(const Group &g, const SimDev *d, cudaStream_t st) {
+    k_zpass<N, V><<<g.n, ZCfg<N, V>::T * zlines_per_block<N, V>(), zpass_smem<N, V>(), st>>>(d, g.items);
+}
+
+// the z pass of one group with the context's radix-schedule variant (forced: 0 or 1, else tuned)
+void zpass(tdgl_ctx *ctx, const Group &g, const SimDev *d, int force = -1) {
+    cudaStream_t st = ctx->stream;
     if (g.N == 0) {
         k_zconv<<<g.n, NTHREADS, g.smem, st>>>(d, g.items);
         return;
     }
+    const int vi = zvar_index(g.N);
+    const int v = force >= 0 ? force : ((vi >= 0 && ctx->zvar[vi] == 1) ? 1 : 0);
     switch (g.N) {
-#define TDGL_Z(LEN) \
-    case LEN: k_zpass<LEN><<<g.n, ZCfg<LEN>::T * zlines_per_block<LEN>(), zpass_smem<LEN>(), st>>>(d, g.items); break;
+#define TDGL_Z(LEN)                                          \
+    case LEN:                                                \
+        if constexpr (LEN == 256 || LEN == 512) {            \
+            if (v == 1) zpass_v<LEN, 1>(g, d, st);           \
+            else zpass_v<LEN, 0>(g, d, st);                  \
+        } else {                                             \
+            zpass_v<LEN, 0>(g, d, st);                       \
+        }                                                    \
+        break;
         TDGL_FAST_LENGTHS(TDGL_Z)
 #undef TDGL_Z
     }
@@ -592,7 +613,7 @@ void zpass(const Group &g, const SimDev *d, cudaStream_t st) {
 
 int launch_conv(tdgl_ctx *ctx, const Work &w) {
     for (const Group &g : w.yg) TRY(launch(ctx, TDGL_K_YFWD, [&] { ypass<false>(g, w.descs, ctx->stream); }));
-    for (const Group &g : w.zg) TRY(launch(ctx, TDGL_K_ZCONV, [&] { zpass(g, w.descs, ctx->stream); }));
+    for (const Group &g : w.zg) TRY(launch(ctx, TDGL_K_ZCONV, [&] { zpass(ctx, g, w.descs); }));
     for (const Group &g : w.yg) TRY(launch(ctx, TDGL_K_YINV, [&] { ypass<true>(g, w.descs, ctx->stream); }));
     return TDGL_OK;
 }
@@ -606,6 +627,40 @@ Work sim_work(tdgl_sim *s, bool elec) {
         w.zg.push_back(Group{s->zN, s->d_z, (int)s->it_z.size(), s->zN ? 0 : smem_z(s, s->kz_cnt_max)});
     }
     return w;
+}
+
+// Radix-schedule autotuner of the z pass: the first time a context meets 256- or 512-point z
+// lines, both variants run on this sim's own buffers (one launch to warm up, three timed with
+// CUDA events) and the faster is kept for the context.  The z pass works in place on the
+// y-padded spectrum, which the next y pass rewrites, so the trial launches change no state.
+int autotune_z(tdgl_sim *s) {
+    tdgl_ctx *ctx = s->ctx;
+    const int vi = zvar_index(s->zN);
+    if (vi < 0 || ctx->zvar[vi] >= 0) return TDGL_OK;
+    fill_desc(s, 0.0, s->terms);
+    TRY(upload_desc(s));
+    Work w = sim_work(s, true);
+    const Group &g = w.zg[0];
+    cudaEvent_t e0, e1;
+    CK(ctx, cudaEventCreate(&e0));
+    CK(ctx, cudaEventCreate(&e1));
+    double us[2];
+    for (int v = 0; v < 2; ++v) {
+        TRY(launch(ctx, TDGL_K_OTHER, [&] { zpass(ctx, g, w.descs, v); }));
+        CK(ctx, cudaEventRecord(e0, ctx->stream));
+        for (int r = 0; r < 3; ++r) TRY(launch(ctx, TDGL_K_OTHER, [&] { zpass(ctx, g, w.descs, v); }));
+        CK(ctx, cudaEventRecord(e1, ctx->stream));
+        CK(ctx, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        us[v] = 1e3 * ms / 3.0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->zus[vi][0] = us[0];
+    ctx->zus[vi][1] = us[1];
+    ctx->zvar[vi] = us[1] < us[0] ? 1 : 0;
+    return TDGL_OK;
 }
 
 // bring X to the E-hat state of the current P (descriptor already uploaded with P[0] = current)
@@ -925,7 +980,10 @@ int tdgl_ctx_create(tdgl_ctx **out, int device, void *stream) {
     cudaFuncSetAttribute(k_xrows<MODE_DERIV, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     TDGL_FAST_LENGTHS(TDGL_XA)
 #undef TDGL_XA
-#define TDGL_ZA(LEN) cudaFuncSetAttribute(k_zpass<LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+#define TDGL_ZA(LEN)                                                                                \
+    cudaFuncSetAttribute(k_zpass<LEN, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);      \
+    if constexpr (LEN == 256 || LEN == 512)                                                         \
+        cudaFuncSetAttribute(k_zpass<LEN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     TDGL_FAST_LENGTHS(TDGL_ZA)
 #undef TDGL_ZA
     if (cudaGetLastError() != cudaSuccess) { delete ctx; return TDGL_ECUDA; }
@@ -1140,6 +1198,26 @@ int tdgl_set_integrator(tdgl_sim *s, int method) {
         return fail(s->ctx, TDGL_EINVAL, "RK45 and AB3M2 are not available for a sim inside a batch");
     s->integrator = method;
     s->ab_hist = 0;
+    return TDGL_OK;
+}
+
+int tdgl_zpass_variant(tdgl_ctx *ctx, int length, int *variant, double *us) {
+    const int vi = zvar_index(length);
+    if (!ctx || !variant || vi < 0) return ctx ? fail(ctx, TDGL_EINVAL, "z-pass variants exist for 256 and 512") : TDGL_EINVAL;
+    *variant = ctx->zvar[vi];
+    if (us) {
+        us[0] = ctx->zus[vi][0];
+        us[1] = ctx->zus[vi][1];
+    }
+    return TDGL_OK;
+}
+
+int tdgl_set_zpass_variant(tdgl_ctx *ctx, int length, int variant) {
+    const int vi = zvar_index(length);
+    if (!ctx || vi < 0 || variant < -1 || variant > 1)
+        return ctx ? fail(ctx, TDGL_EINVAL, "z-pass variant %d for length %d", variant, length) : TDGL_EINVAL;
+    ctx->zvar[vi] = variant;
+    if (variant < 0) ctx->zus[vi][0] = ctx->zus[vi][1] = 0.0;
     return TDGL_OK;
 }
 

@@ -66,6 +66,8 @@ _SIGS = {
     "tdgl_set_integrator": (_I, [_VP, _I]),
     "tdgl_set_adaptive": (_I, [_VP, _D, _D, _D]),
     "tdgl_get_dt": (_I, [_VP, ctypes.POINTER(_D)]),
+    "tdgl_zpass_variant": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "tdgl_set_zpass_variant": (_I, [_VP, _I, _I]),
     "tdgl_set_time": (_I, [_VP, _D]),
     "tdgl_get_time": (_I, [_VP, ctypes.POINTER(_D)]),
     "tdgl_set_scales": (_I, [_VP, _D, _D]),
@@ -153,6 +155,15 @@ class Context:
         if rc != OK:
             raise TdglError(rc, self.lib.tdgl_last_error(self.h).decode())
         return rc
+
+    def zpass_variant(self, length):
+        """(variant, (us of variant 0, us of variant 1)) chosen by the z-pass autotuner; -1 = not yet tuned"""
+        v, us = _I(), (_D * 2)()
+        self.check(self.lib.tdgl_zpass_variant(self.h, int(length), ctypes.byref(v), us))
+        return v.value, (us[0], us[1])
+
+    def set_zpass_variant(self, length, variant):
+        self.check(self.lib.tdgl_set_zpass_variant(self.h, int(length), int(variant)))
 
     @property
     def launch_count(self) -> int:

@@ -202,3 +202,40 @@ def test_launch_counter_counts_kernels(ctx):
     n0 = ctx.launch_count
     s.step(10, dt)
     assert ctx.launch_count - n0 == 10 * 4
+
+
+def test_zpass_autotuner_picks_a_variant_and_both_variants_agree_with_the_oracle():
+    # 16 x 16 x 128 pads z to 256 points: the context times both radix schedules of the z pass on
+    # first use and keeps the faster; forcing either gives the same trajectory as the oracle
+    from paper_2605_28800_b300 import tdgl
+    from tests.helpers import mixed_case
+    CELL = (1e-9, 1.1e-9, 0.9e-9)
+    MATS = {1: synth.BTO, 2: dict(synth.PTO, G12=3e-11, G44=7e-11, G44p=2e-11)}
+    shape = (16, 16, 128)
+    mat, P = mixed_case(shape, seed=41)
+    P *= 0.3
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    ctx = tdgl.Context(0)
+    try:
+        assert ctx.zpass_variant(256)[0] == -1
+        finals = []
+        for forced in (None, 0, 1):
+            g = gpu_sim(ctx, shape, CELL, mat, MATS, 300.0, 45.0, P=P)
+            if forced is not None:
+                ctx.set_zpass_variant(256, forced)
+            g.step(3, dt)
+            if forced is None:
+                v, us = ctx.zpass_variant(256)
+                assert v in (0, 1) and us[0] > 0 and us[1] > 0 and us[v] == min(us)
+            else:
+                assert ctx.zpass_variant(256)[0] == forced
+            finals.append(g.get_P())
+            g.close()
+        o = oracle_sys(shape, CELL, mat, MATS, 300.0, 45.0)
+        Po = o.run(P.astype(np.float64), dt, 3)
+        for Pg in finals:
+            assert np.abs(Pg - Po).max() / 0.2649096 <= 1e-5
+        with pytest.raises(tdgl.TdglError):
+            ctx.set_zpass_variant(128, 1)
+    finally:
+        ctx.close()
