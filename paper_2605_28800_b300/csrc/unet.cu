@@ -3,6 +3,8 @@
 // A 3D U-Net whose convolutions run on the tensor cores (unet_kernels.cuh).  The host side owns
 // the layer table, the device buffers of one batch of activations and gradients, the FP32 master
 // weights with their Adam moments, and issues every launch on the context's stream.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -38,6 +40,7 @@ struct Layer {
     bool relu, need_dx;
     size_t ow, ob;                  // offsets of w [Co][Kp] and b [Co] in the parameter arrays
     __nv_bfloat16 *wf = nullptr, *wt = nullptr;
+    __nv_bfloat16 *wfb = nullptr, *wtb = nullptr;   // brick-kernel weights [27][Co][Ci], [27][Ci][Co]
     // activation buffers (set per network): input, output (BF16 or, for the head, FP32)
     __nv_bfloat16 *in = nullptr;
     void *out = nullptr;
@@ -58,17 +61,65 @@ int conv_bn(int co) {
     return 16;
 }
 
-// Y[v][o] = act(b + conv(X, W)) over nvox voxels of dims d
-int launch_conv(tdgl_ctx *ctx, const __nv_bfloat16 *x, const __nv_bfloat16 *w, const float *b, void *y, long nvox,
-                Dims d, int Ci, int Co, int ntap, int Kp, bool relu, bool f32out, int *err) {
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+// activations [B][Z][Y][X][C] BF16 as (C, X, Y, Z, B), box (8, 10, 18, 3, 1): one 8-channel plane of
+// a brick with its halo; out-of-range voxels read as zero
+bool act_map(CUtensorMap *m, const void *x, int C, Dims d, long B) {
+    auto enc = tmap_encode();
+    if (!enc) return false;
+    const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)d.X, (cuuint64_t)d.Y, (cuuint64_t)d.Z, (cuuint64_t)B};
+    const cuuint64_t e = 2;
+    const cuuint64_t strides[4] = {C * e, (cuuint64_t)d.X * C * e, (cuuint64_t)d.Y * d.X * C * e,
+                                   (cuuint64_t)d.Z * d.Y * d.X * C * e};
+    const cuuint32_t box[5] = {8, (cuuint32_t)kBX, (cuuint32_t)kBY, (cuuint32_t)kBZ, 1};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(x), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// brick weights [27][Co][Ci] BF16 as (Ci, Co, 27), box (8, bn, 27): one half of a chunk, all taps
+bool wgt_map(CUtensorMap *m, const void *w, int Ci, int Co, int bn) {
+    auto enc = tmap_encode();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)Ci, (cuuint64_t)Co, 27};
+    const cuuint64_t strides[2] = {(cuuint64_t)Ci * 2, (cuuint64_t)Co * Ci * 2};
+    const cuuint32_t box[3] = {8, (cuuint32_t)bn, 27};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(w), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Y[v][o] = act(b + conv(X, W)) over nvox voxels of dims d.  w: gather-kernel weights [Co][Kp];
+// wb: the same weights as [27][Co][Ci] for the brick kernel (null: gather kernel only)
+int launch_conv(tdgl_ctx *ctx, const __nv_bfloat16 *x, const __nv_bfloat16 *w, const __nv_bfloat16 *wb, const float *b,
+                void *y, long nvox, Dims d, int Ci, int Co, int ntap, int Kp, bool relu, bool f32out, int *err) {
     ConvP p{x, w, b, y, nvox, d.Z, d.Y, d.X, Ci, Co, ntap, Kp / 8, relu ? 1 : 0, f32out ? 1 : 0, err};
     // the brick kernel: 3x3x3, 16-channel input chunks, 8 x 16 voxel bricks, output tiles up to 64
-    if (ntap == 27 && Ci % 16 == 0 && d.X % 8 == 0 && d.Y % 16 == 0) {
+    if (wb && ntap == 27 && Ci % 16 == 0 && d.X % 8 == 0 && d.Y % 16 == 0) {
         const int bn = Co % 64 == 0 ? 64 : (Co % 32 == 0 ? 32 : 16);
+        BrickP bp;
+        memset(&bp, 0, sizeof bp);
+        bp.c = p;
+        if (!act_map(&bp.tx, x, Ci, d, nvox / d.vps()) || !wgt_map(&bp.tw, wb, Ci, Co, bn))
+            return fail(ctx, TDGL_ECUDA, "cannot encode the tensor maps of a convolution");
         const bool one = Ci == 16;
         const dim3 grid((unsigned)(nvox / 128), (unsigned)((Co + bn - 1) / bn));
         return launch(ctx, TDGL_K_UNET, [&] {
-#define TDGL_BRICK(BN_, S_) k_conv_brick<BN_, S_><<<grid, 128, brick_smem<BN_, S_>(), ctx->stream>>>(p)
+#define TDGL_BRICK(BN_, S_) k_conv_brick<BN_, S_><<<grid, 128, brick_smem<BN_, S_>(), ctx->stream>>>(bp)
             switch (bn) {
                 case 64: if (one) TDGL_BRICK(64, 1); else TDGL_BRICK(64, 2); break;
                 case 32: if (one) TDGL_BRICK(32, 1); else TDGL_BRICK(32, 2); break;
@@ -208,6 +259,10 @@ int build(tdgl_unet *n) {
     for (auto &l : n->L) {
         TRY(dalloc(n, &l.wf, (size_t)l.Co * l.Kp));
         TRY(dalloc(n, &l.wt, (size_t)l.Ci * l.Kpt));
+        if (l.ntap == 27) {
+            TRY(dalloc(n, &l.wfb, (size_t)27 * l.Co * l.Ci));
+            TRY(dalloc(n, &l.wtb, (size_t)27 * l.Ci * l.Co));
+        }
         const size_t V = (size_t)nvox(n, l.lev, n->maxb);
         max_dpre = std::max(max_dpre, V * l.Co);
         max_xs = std::max(max_xs, 3 * V * l.Ci);
@@ -270,8 +325,8 @@ int build(tdgl_unet *n) {
 int refresh_bf16(tdgl_unet *n) {
     for (auto &l : n->L)
         TRY(launch(n->ctx, TDGL_K_UNET, [&] {
-            k_wcopy<<<grid_n((long)l.Co * l.Kp), 256, 0, n->ctx->stream>>>(n->P + l.ow, l.wf, l.wt, l.Co, l.Ci, l.ntap,
-                                                                            l.Kp, l.Kpt);
+            k_wcopy<<<grid_n((long)l.Co * l.Kp), 256, 0, n->ctx->stream>>>(n->P + l.ow, l.wf, l.wt, l.wfb, l.wtb, l.Co,
+                                                                            l.Ci, l.ntap, l.Kp, l.Kpt);
         }));
     return TDGL_OK;
 }
@@ -297,7 +352,7 @@ int forward(tdgl_unet *n, const float *x, int B) {
         }
         for (int s = 0; s < 2; ++s, ++li) {
             Layer &ly = n->L[li];
-            TRY(launch_conv(ctx, ly.in, ly.wf, n->P + ly.ob, ly.out, V, n->dims[l], ly.Ci, ly.Co, ly.ntap, ly.Kp, true,
+            TRY(launch_conv(ctx, ly.in, ly.wf, ly.wfb, n->P + ly.ob, ly.out, V, n->dims[l], ly.Ci, ly.Co, ly.ntap, ly.Kp, true,
                             false, n->derr));
         }
     }
@@ -313,12 +368,12 @@ int forward(tdgl_unet *n, const float *x, int B) {
         }));
         for (int s = 0; s < 2; ++s, ++li) {
             Layer &ly = n->L[li];
-            TRY(launch_conv(ctx, ly.in, ly.wf, n->P + ly.ob, ly.out, V, d, ly.Ci, ly.Co, ly.ntap, ly.Kp, true, false,
+            TRY(launch_conv(ctx, ly.in, ly.wf, ly.wfb, n->P + ly.ob, ly.out, V, d, ly.Ci, ly.Co, ly.ntap, ly.Kp, true, false,
                             n->derr));
         }
     }
     Layer &hd = n->L[li];
-    return launch_conv(ctx, hd.in, hd.wf, n->P + hd.ob, hd.out, V0, n->dims[0], hd.Ci, hd.Co, 1, hd.Kp, false, true,
+    return launch_conv(ctx, hd.in, hd.wf, nullptr, n->P + hd.ob, hd.out, V0, n->dims[0], hd.Ci, hd.Co, 1, hd.Kp, false, true,
                        n->derr);
 }
 
@@ -337,7 +392,8 @@ int conv_backward(tdgl_unet *n, Layer &ly, int B) {
     }));
     TRY(launch_wgrad(ctx, n->dpret, n->xs, gw, V, d, ly.Ci, ly.Co, ly.ntap, ly.Kp, n->derr));
     if (ly.need_dx)
-        TRY(launch_conv(ctx, n->dpre, ly.wt, nullptr, ly.g_in, V, d, ly.Co, ly.Ci, ly.ntap, ly.Kpt, false, true, n->derr));
+        TRY(launch_conv(ctx, n->dpre, ly.wt, ly.wtb, nullptr, ly.g_in, V, d, ly.Co, ly.Ci, ly.ntap, ly.Kpt, false, true,
+                        n->derr));
     return TDGL_OK;
 }
 
@@ -606,7 +662,7 @@ int tdgl_unet_train_step(tdgl_unet *n, const float *x, const float *t, int batch
     const double b1 = 0.9, b2 = 0.999;
     for (auto &l : n->L) {
         AdamP p{n->P + l.ow, n->M + l.ow, n->V + l.ow, n->G + l.ow, n->P + l.ob, n->M + l.ob, n->V + l.ob, n->G + l.ob,
-                l.wf, l.wt, l.Co, l.Ci, l.ntap, l.Kp, l.Kpt, (float)lr, (float)b1, (float)b2, 1e-8f,
+                l.wf, l.wt, l.wfb, l.wtb, l.Co, l.Ci, l.ntap, l.Kp, l.Kpt, (float)lr, (float)b1, (float)b2, 1e-8f,
                 (float)(1.0 - pow(b1, (double)n->step)), (float)(1.0 - pow(b2, (double)n->step))};
         TRY(launch(ctx, TDGL_K_UNET, [&] { k_adam<<<grid_n((long)l.Co * l.Kp + l.Co), 256, 0, ctx->stream>>>(p); }));
     }
@@ -643,7 +699,7 @@ int conv_check(tdgl_ctx *ctx, int batch, int ci, int co, int k, int nx, int ny, 
 
 // weights [co][ci][t] (host) -> device GEMM layouts: FP32 master [co][Kp], BF16 forward and transposed
 int upload_w(tdgl_ctx *ctx, Scratch &S, const float *w, int ci, int co, int ntap, float **wm, __nv_bfloat16 **wf,
-             __nv_bfloat16 **wt, int *Kp, int *Kpt) {
+             __nv_bfloat16 **wt, __nv_bfloat16 **wfb, __nv_bfloat16 **wtb, int *Kp, int *Kpt) {
     *Kp = pad16(ntap * ci);
     *Kpt = pad16(ntap * co);
     std::vector<float> g((size_t)co * *Kp, 0.f);
@@ -653,9 +709,14 @@ int upload_w(tdgl_ctx *ctx, Scratch &S, const float *w, int ci, int co, int ntap
     TRY(S.get(ctx, wm, g.size()));
     TRY(S.get(ctx, wf, g.size()));
     TRY(S.get(ctx, wt, (size_t)ci * *Kpt));
+    *wfb = *wtb = nullptr;
+    if (ntap == 27) {
+        TRY(S.get(ctx, wfb, (size_t)27 * co * ci));
+        TRY(S.get(ctx, wtb, (size_t)27 * ci * co));
+    }
     CK(ctx, cudaMemcpyAsync(*wm, g.data(), g.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     return launch(ctx, TDGL_K_UNET, [&] {
-        k_wcopy<<<grid_n((long)co * *Kp), 256, 0, ctx->stream>>>(*wm, *wf, *wt, co, ci, ntap, *Kp, *Kpt);
+        k_wcopy<<<grid_n((long)co * *Kp), 256, 0, ctx->stream>>>(*wm, *wf, *wt, *wfb, *wtb, co, ci, ntap, *Kp, *Kpt);
     });
 }
 }  // namespace
@@ -673,7 +734,7 @@ int tdgl_conv3d(tdgl_ctx *ctx, const float *x, const float *w, const float *b, f
     const Dims d{nz, ny, nx};
     const long V = (long)batch * d.vps();
     float *dx, *db = nullptr, *dy, *dy2, *wm;
-    __nv_bfloat16 *xb, *wf, *wt;
+    __nv_bfloat16 *xb, *wf, *wt, *wfb, *wtb;
     int Kp, Kpt, *derr;
     TRY(S.get(ctx, &dx, (size_t)V * ci));
     TRY(S.get(ctx, &xb, (size_t)V * ci));
@@ -682,12 +743,12 @@ int tdgl_conv3d(tdgl_ctx *ctx, const float *x, const float *w, const float *b, f
     TRY(S.get(ctx, &derr, 1));
     CK(ctx, cudaMemcpyAsync(dx, x, (size_t)V * ci * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     TRY(launch(ctx, TDGL_K_UNET, [&] { k_to_ndhwc<<<grid_n(V * ci), 256, 0, ctx->stream>>>(dx, xb, V, ci, ci, d.vps()); }));
-    TRY(upload_w(ctx, S, w, ci, co, ntap, &wm, &wf, &wt, &Kp, &Kpt));
+    TRY(upload_w(ctx, S, w, ci, co, ntap, &wm, &wf, &wt, &wfb, &wtb, &Kp, &Kpt));
     if (b) {
         TRY(S.get(ctx, &db, (size_t)co));
         CK(ctx, cudaMemcpyAsync(db, b, co * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     }
-    TRY(launch_conv(ctx, xb, wf, db, dy, V, d, ci, co, ntap, Kp, relu != 0, true, derr));
+    TRY(launch_conv(ctx, xb, wf, wfb, db, dy, V, d, ci, co, ntap, Kp, relu != 0, true, derr));
     TRY(launch(ctx, TDGL_K_UNET, [&] { k_from_ndhwc_f32<<<grid_n(V * co), 256, 0, ctx->stream>>>(dy, dy2, V, co, co, d.vps()); }));
     CK(ctx, cudaMemcpyAsync(y, dy2, (size_t)V * co * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
     return check_err(ctx, derr);
@@ -705,7 +766,7 @@ int tdgl_conv3d_backward(tdgl_ctx *ctx, const float *x, const float *w, const fl
     const Dims d{nz, ny, nx};
     const long V = (long)batch * d.vps();
     float *xf, *gy, *gyn, *gx, *gxo, *wm, *gw, *gb;
-    __nv_bfloat16 *xb, *wf, *wt, *dpre, *dpret, *xs;
+    __nv_bfloat16 *xb, *wf, *wt, *wfb, *wtb, *dpre, *dpret, *xs;
     int Kp, Kpt, *derr;
     TRY(S.get(ctx, &xf, (size_t)V * ci));
     TRY(S.get(ctx, &xb, (size_t)V * ci));
@@ -717,7 +778,7 @@ int tdgl_conv3d_backward(tdgl_ctx *ctx, const float *x, const float *w, const fl
     TRY(S.get(ctx, &dpret, (size_t)V * co));
     TRY(S.get(ctx, &xs, (size_t)3 * V * ci));
     TRY(S.get(ctx, &derr, 1));
-    TRY(upload_w(ctx, S, w, ci, co, ntap, &wm, &wf, &wt, &Kp, &Kpt));
+    TRY(upload_w(ctx, S, w, ci, co, ntap, &wm, &wf, &wt, &wfb, &wtb, &Kp, &Kpt));
     TRY(S.get(ctx, &gw, (size_t)co * Kp));
     TRY(S.get(ctx, &gb, (size_t)co));
     CK(ctx, cudaMemcpyAsync(xf, x, (size_t)V * ci * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
@@ -731,7 +792,7 @@ int tdgl_conv3d_backward(tdgl_ctx *ctx, const float *x, const float *w, const fl
         k_xshift<<<(unsigned)((V + 31) / 32), 256, 0, ctx->stream>>>(xb, xs, V, ci, d.X, ntap == 27 ? 3 : 1);
     }));
     TRY(launch_wgrad(ctx, dpret, xs, gw, V, d, ci, co, ntap, Kp, derr));
-    TRY(launch_conv(ctx, dpre, wt, nullptr, gx, V, d, co, ci, ntap, Kpt, false, true, derr));
+    TRY(launch_conv(ctx, dpre, wt, wtb, nullptr, gx, V, d, co, ci, ntap, Kpt, false, true, derr));
     TRY(launch(ctx, TDGL_K_UNET, [&] { k_from_ndhwc_f32<<<grid_n(V * ci), 256, 0, ctx->stream>>>(gx, gxo, V, ci, ci, d.vps()); }));
     std::vector<float> g((size_t)co * Kp);
     CK(ctx, cudaMemcpyAsync(dxh, gxo, (size_t)V * ci * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));

@@ -11,6 +11,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <cuda.h>
+
 #include "philox.cuh"
 #include "tc.cuh"
 
@@ -198,19 +200,22 @@ __global__ void __launch_bounds__(128) k_conv(ConvP p) {
 // ---- brick convolution: the input brick staged once, the 27 taps as descriptor offsets -----------
 //
 // A CTA owns 128 output voxels: x0..x0+7 (core-matrix rows) by y0..y0+15 (row groups) at one z.
-// Per 16-channel chunk of the input it stages the brick with its one-voxel halo, 10 x 18 x 3 voxels,
-// as two planes (channels 0-7 and 8-15 of the chunk) of 16-byte voxel records, x fastest.  For a tap
-// (dz, dy, dx) the A operand is the same tile read from a shifted start: row group g at
-// ((1 + dz) * 18 + g + 1 + dy) * 10 + 1 + dx records, rows 16 bytes apart, so the descriptor keeps
-// the stride-dimension offset 160 bytes (one brick row) and the leading-dimension offset one plane.
-// The weights of the chunk for all 27 taps are staged next to it; one thread issues 27 MMAs per chunk.
+// Per 16-channel chunk of the input, two TMA loads bring the brick with its one-voxel halo,
+// 10 x 18 x 3 voxels, as two planes (channels 0-7 and 8-15 of the chunk) of 16-byte voxel records,
+// x fastest (out-of-grid voxels read as zero), and two more bring the chunk's weights for all 27
+// taps as [half][tap][output channel] records.  For a tap (dz, dy, dx) the A operand is the brick
+// read from a shifted start: row group g at ((1 + dz) * 18 + g + 1 + dy) * 10 + 1 + dx records, rows
+// 16 bytes apart, so its descriptor keeps the stride-dimension offset 160 bytes (one brick row) and
+// the leading-dimension offset one plane; the B operand of the tap is its slice of the weights.
+// One elected thread drives the pipeline: TMA into a stage, wait for its bytes, 27 MMAs, commit to
+// the stage's "empty" barrier, refill the stage once those MMAs are done.
 constexpr int kBX = 10, kBY = 18, kBZ = 3, kBrick = kBX * kBY * kBZ;     // voxel records per plane
-constexpr uint32_t kPlane = kBrick * 16u;                                 // bytes per 8-channel plane
-// S pipeline stages: 1 when the input has a single 16-channel chunk (nothing to overlap; more CTAs
-// fit per SM instead), 2 otherwise
-template <int BN> __host__ __device__ constexpr uint32_t brick_stage_bytes() { return 2u * kPlane + 27u * BN * 32u; }
+constexpr uint32_t kPlane = 8704u;                                        // 540 records, padded to 128 B
+template <int BN> __host__ __device__ constexpr uint32_t brick_wplane() { return 27u * BN * 16u; }
+template <int BN> __host__ __device__ constexpr uint32_t brick_stage_bytes() { return 2u * kPlane + 2u * brick_wplane<BN>(); }
+// S pipeline stages: 1 when the input has a single 16-channel chunk, 2 otherwise
 template <int BN, int S> __host__ __device__ constexpr uint32_t brick_smem() {
-    return S * brick_stage_bytes<BN>() + 128u + 1024u;
+    return S * brick_stage_bytes<BN>() + 256u + 1024u;
 }
 
 // shared-memory descriptor with explicit leading / stride byte offsets
@@ -223,26 +228,38 @@ __device__ __forceinline__ uint64_t sdesc_lbo_sbo(uint32_t addr, uint32_t lbo, u
     return d;
 }
 
+struct BrickP {
+    ConvP c;
+    CUtensorMap tx;   // activations [B][Z][Y][X][Ci] BF16 as (Ci, X, Y, Z, B), box (8, 10, 18, 3, 1)
+    CUtensorMap tw;   // weights [27][Co][Ci] BF16 as (Ci, Co, 27), box (8, BN, 27)
+};
+
 template <int BN, int S>
-__global__ void __launch_bounds__(128) k_conv_brick(ConvP p) {
-    constexpr uint32_t ST = brick_stage_bytes<BN>(), AB = 2u * kPlane;
+__global__ void __launch_bounds__(128) k_conv_brick(const __grid_constant__ BrickP bp) {
+    const ConvP &p = bp.c;
+    constexpr uint32_t ST = brick_stage_bytes<BN>(), AB = 2u * kPlane, WP = brick_wplane<BN>();
     constexpr uint32_t idesc = tc::idesc_bf16(128, BN);
+    constexpr uint32_t kBytes = 2u * (uint32_t)kBrick * 16u + 2u * 27u * BN * 16u;   // per stage
     extern __shared__ uint8_t smem_raw[];
     uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *bar = reinterpret_cast<uint64_t *>(tiles + S * ST);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + S);
+    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + S * ST);
+    uint64_t *empty = full + S;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(empty + S);
+    int *s_state = reinterpret_cast<int *>(tslot + 2);     // [0] MMA stages issued, [1] ok
     const int tid = threadIdx.x, warp = tid >> 5;
-    // brick of this CTA
     const int nbx = p.X / 8, nby = p.Y / 16;
     long q = blockIdx.x;
     const int bx = (int)(q % nbx); q /= nbx;
     const int by = (int)(q % nby); q /= nby;
     const int z = (int)(q % p.Z);
-    const long b = q / p.Z;
+    const int b = (int)(q / p.Z);
     const int x0 = bx * 8, y0 = by * 16;
     const int n0 = blockIdx.y * BN;
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) tc::mbar_init(&bar[s], 1);
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
         tc::mbar_fence_init();
     }
     if (tid < 32) tc::tmem_alloc(tslot, tmem_cols<BN>());
@@ -251,62 +268,50 @@ __global__ void __launch_bounds__(128) k_conv_brick(ConvP p) {
     tc::fence_after();
     const uint32_t tmem = *tslot;
     const uint32_t base = tc::saddr(tiles);
-    auto load = [&](int c, uint32_t st) {
-        const int c0 = 16 * c;
-        for (int i = tid; i < 2 * kBrick; i += 128) {
-            const int h = i / kBrick, r = i - h * kBrick;
-            const int xx = r % kBX, yy = (r / kBX) % kBY, zz = r / (kBX * kBY);
-            const int gx = x0 + xx - 1, gy = y0 + yy - 1, gz = z + zz - 1;
-            const bool ok = (unsigned)gx < (unsigned)p.X && (unsigned)gy < (unsigned)p.Y && (unsigned)gz < (unsigned)p.Z;
-            const __nv_bfloat16 *src = ok ? p.x + ((((b * p.Z + gz) * p.Y + gy) * p.X + gx) * p.Ci + c0 + 8 * h) : p.x;
-            tc::cp16(st + (uint32_t)h * kPlane + (uint32_t)r * 16u, src, ok);
-        }
-        for (int i = tid; i < 27 * BN * 2; i += 128) {
-            const int t = i / (2 * BN), rem = i - t * 2 * BN, n = rem >> 1, h = rem & 1, co = n0 + n;
-            const bool ok = co < p.Co;
-            const __nv_bfloat16 *src = ok ? p.w + ((long)co * p.G * 8 + (long)t * p.Ci + c0 + 8 * h) : p.w;
-            tc::cp16(st + AB + (uint32_t)t * (BN * 32u) + tc::tile_off(n, h), src, ok);
-        }
-    };
     const int nch = p.Ci / 16;
-    bool ok = true;
-    int issued = 0;
-#pragma unroll
-    for (int c = 0; c < S - 1; ++c) {
-        if (c < nch) load(c, base + (c % S) * ST);
-        tc::cp_commit();
-    }
-    for (int c = 0; c < nch; ++c) {
-        const int cn = c + S - 1;
-        if (cn < nch && ok) {
-            const int s = cn % S;
-            if (cn >= S) ok = tc::mbar_wait(&bar[s], (unsigned)((cn - S) / S) & 1u, kSpin);
-            if (ok) load(cn, base + s * ST);
-        }
-        tc::cp_commit();
-        tc::cp_wait<S - 1>();
-        tc::fence_proxy_async();
-        ok = !__syncthreads_or(!ok);
-        if (!ok) break;
-        if (tid == 0) {
+    if (tid == 0) {
+        auto load = [&](int c) {
+            const int s = c % S;
+            const uint32_t st = base + (uint32_t)s * ST;
+            tc::mbar_expect_tx(&full[s], kBytes);
+            for (int h = 0; h < 2; ++h) {
+                tc::tma_load_5d(st + (uint32_t)h * kPlane, &bp.tx, &full[s], 16 * c + 8 * h, x0 - 1, y0 - 1, z - 1, b);
+                tc::tma_load_3d(st + AB + (uint32_t)h * WP, &bp.tw, &full[s], 16 * c + 8 * h, n0, 0);
+            }
+        };
+        bool ok = true;
+        int loaded = 0, issued = 0;
+        for (; loaded < S && loaded < nch; ++loaded) load(loaded);
+        for (int c = 0; c < nch && ok; ++c) {
+            const int s = c % S;
+            ok = tc::mbar_wait(&full[s], (unsigned)(c / S) & 1u, kSpin);
+            if (!ok) break;
             tc::fence_after();
-            const uint32_t st = base + (uint32_t)(c % S) * ST;
+            const uint32_t st = base + (uint32_t)s * ST;
 #pragma unroll 1
             for (int t = 0; t < 27; ++t) {
                 const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
                 const uint32_t a = st + (uint32_t)((((1 + dz) * kBY + 1 + dy) * kBX + 1 + dx) * 16);
-                tc::mma_bf16(tmem, sdesc_lbo_sbo(a, kPlane, kBX * 16u), tc::sdesc(st + AB + (uint32_t)t * (BN * 32u)),
+                tc::mma_bf16(tmem, sdesc_lbo_sbo(a, kPlane, kBX * 16u), sdesc_lbo_sbo(st + AB + (uint32_t)t * (BN * 16u), WP, 128u),
                              idesc, (c > 0 || t > 0) ? 1u : 0u);
             }
-            tc::mma_commit(&bar[c % S]);
+            tc::mma_commit(&empty[s]);
+            issued = c + 1;
+            if (loaded < nch) {   // refill this stage once its MMAs are done
+                ok = tc::mbar_wait(&empty[s], (unsigned)(c / S) & 1u, kSpin);
+                if (ok) load(loaded++);
+            }
         }
-        issued = c + 1;
+        // every TMA load issued must have landed before the CTA may exit
+        for (int c = issued; c < loaded; ++c) tc::mbar_wait(&full[c % S], (unsigned)(c / S) & 1u, kSpin);
+        s_state[0] = issued;
+        s_state[1] = ok && issued == nch;
     }
-    tc::cp_wait<0>();
-    if (issued > 0) {
-        const int c = issued - 1;
-        const bool done = tc::mbar_wait(&bar[c % S], (unsigned)(c / S) & 1u, kSpin);
-        ok = ok && done;
+    __syncthreads();
+    bool ok = s_state[1] != 0;
+    if (s_state[0] > 0) {
+        const int c = s_state[0] - 1;
+        ok = tc::mbar_wait(&empty[c % S], (unsigned)(c / S) & 1u, kSpin) && ok;
     }
     tc::fence_after();
     ok = !__syncthreads_or(!ok);
@@ -314,7 +319,7 @@ __global__ void __launch_bounds__(128) k_conv_brick(ConvP p) {
         if (tid == 0) atomicOr(p.err, 1);
     } else {
         // row tid: x = x0 + tid % 8, y = y0 + tid / 8
-        const long v = ((b * p.Z + z) * p.Y + y0 + tid / 8) * p.X + x0 + (tid & 7);
+        const long v = (((long)b * p.Z + z) * p.Y + y0 + tid / 8) * p.X + x0 + (tid & 7);
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float r[16];
@@ -609,6 +614,7 @@ struct AdamP {
     float *w, *m, *v, *gw;        // [Co][Kp]
     float *b, *mb, *vb, *gb;      // [Co]
     __nv_bfloat16 *wf, *wt;       // forward [Co][Kp], transposed [Ci][Kpt] (may be null)
+    __nv_bfloat16 *wfb, *wtb;     // brick-kernel copies [27][Co][Ci] and [27][Ci][Co] (3x3x3 only)
     int Co, Ci, ntap, Kp, Kpt;
     float lr, b1, b2, eps, c1, c2;   // c1 = 1 - b1^k, c2 = 1 - b2^k
 };
@@ -627,9 +633,12 @@ __global__ void k_adam(AdamP p) {
         if (i < nw) {
             p.wf[i] = __float2bfloat16_rn(nw_);
             const int o = (int)(i / p.Kp), k = (int)(i - (long)o * p.Kp);
-            if (p.wt && k < p.ntap * p.Ci) {
+            if (k < p.ntap * p.Ci) {
                 const int tap = k / p.Ci, ci = k - tap * p.Ci;
-                p.wt[(long)ci * p.Kpt + (p.ntap - 1 - tap) * p.Co + o] = __float2bfloat16_rn(nw_);
+                const __nv_bfloat16 h = __float2bfloat16_rn(nw_);
+                if (p.wt) p.wt[(long)ci * p.Kpt + (p.ntap - 1 - tap) * p.Co + o] = h;
+                if (p.wfb) p.wfb[((long)tap * p.Co + o) * p.Ci + ci] = h;
+                if (p.wtb) p.wtb[((long)(p.ntap - 1 - tap) * p.Ci + ci) * p.Co + o] = h;
             }
         }
     }
@@ -637,15 +646,19 @@ __global__ void k_adam(AdamP p) {
 
 // BF16 copies of master weights (after a host upload): forward and transposed layouts
 __global__ void k_wcopy(const float *__restrict__ w, __nv_bfloat16 *__restrict__ wf, __nv_bfloat16 *__restrict__ wt,
-                        int Co, int Ci, int ntap, int Kp, int Kpt) {
+                        __nv_bfloat16 *__restrict__ wfb, __nv_bfloat16 *__restrict__ wtb, int Co, int Ci, int ntap,
+                        int Kp, int Kpt) {
     const long nw = (long)Co * Kp;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nw; i += (long)gridDim.x * blockDim.x) {
         const float a = w[i];
-        wf[i] = __float2bfloat16_rn(a);
+        const __nv_bfloat16 h = __float2bfloat16_rn(a);
+        wf[i] = h;
         const int o = (int)(i / Kp), k = (int)(i - (long)o * Kp);
-        if (wt && k < ntap * Ci) {
+        if (k < ntap * Ci) {
             const int tap = k / Ci, ci = k - tap * Ci;
-            wt[(long)ci * Kpt + (ntap - 1 - tap) * Co + o] = __float2bfloat16_rn(a);
+            if (wt) wt[(long)ci * Kpt + (ntap - 1 - tap) * Co + o] = h;
+            if (wfb) wfb[((long)tap * Co + o) * Ci + ci] = h;
+            if (wtb) wtb[((long)(ntap - 1 - tap) * Ci + ci) * Co + o] = h;
         }
     }
 }
