@@ -1,8 +1,9 @@
 // Row kernel with a shared-memory tile and register x-transforms (x complex length HX).
 //
-// A block owns TY consecutive x-rows (y0 .. y0+TY-1) of one plane z.  It stages P and the
-// material ids of planes z-1, z, z+1, rows y0-1 .. y0+TY, all x, in shared memory: that covers
-// every neighbour the discrete Eq. 4 needs (faces, and the edge cells of the cross terms), with
+// A block owns TY consecutive x-rows (y0 .. y0+TY-1) of one plane z.  It stages the material ids of
+// planes z-1, z, z+1 and P of plane z, rows y0-1 .. y0+TY, all x, in shared memory; P of planes z-1
+// and z+1 comes from global memory through the L1 cache.  That covers every neighbour the discrete
+// Eq. 4 needs (faces, and the edge cells of the cross terms), with
 // cells outside the grid stored as vacuum.  Per mode:
 //   STEP    x-inverse of the field spectrum (C2R) -> E_el rows; Landau (Eq. 3), gradient (Eq. 4),
 //           E_ext (Eq. 7); forward Euler update (Eq. 1); x-forward (R2C) of the new rows.
@@ -25,9 +26,9 @@ template <int HX> __host__ __device__ constexpr int xrows_threads() {
     return ((3 * xrows_tile<HX>() * rf::threads_per_line<HX>()) + 31) / 32 * 32;
 }
 template <int HX> __host__ __device__ constexpr int xrows_ldp() { return HX + HX / 16 + 1; }
-// floats of the region shared by the P tile and the x-transform exchange (multiple of 4)
+// floats of the region shared by the centre-plane P tile and the x-transform exchange (multiple of 4)
 template <int HX> __host__ __device__ constexpr int xrows_region() {
-    constexpr int tile = 9 * (xrows_tile<HX>() + 2) * HX;
+    constexpr int tile = 3 * (xrows_tile<HX>() + 2) * HX;
     constexpr int exch = 2 * (xrows_threads<HX>() / rf::threads_per_line<HX>()) * xrows_ldp<HX>();
     return ((tile > exch ? tile : exch) + 3) & ~3;
 }
@@ -37,15 +38,23 @@ template <int HX> __host__ __device__ constexpr size_t xrows_smem() {
              3ull * (xrows_tile<HX>() + 2) * HX) + 15) & ~(size_t)15;
 }
 
+// Neighbourhood of a block's cells: materials of planes z-1, z, z+1 (rows y0-1 .. y0+TY, all x,
+// out-of-grid cells vacuum) and P of the centre plane in shared memory; P of planes z-1 and z+1
+// is read through the L1 cache from global memory.  Every caller reads P only at material cells
+// (checked on the material tile first), which are inside the grid.
 template <int NX, int TYH>
 struct TileView {
-    const float *P;       // [3 comps][3 planes][TYH rows][NX]
+    const float *P;       // centre plane [3 comps][TYH rows][NX], shared memory
+    const float *G;       // the sim's P (global), component stride ncell
+    long ncell;
+    long row0[2];         // index of (plane z-1 / z+1, row y0-1, x 0) in one component of G
     const uint8_t *M;     // [3 planes][TYH][NX]
     __device__ __forceinline__ int m(int pz, int py, int x) const {
         return (unsigned)x < (unsigned)NX ? (int)M[(pz * TYH + py) * NX + x] : 0;
     }
     __device__ __forceinline__ float p(int c, int pz, int py, int x) const {
-        return P[((c * 3 + pz) * TYH + py) * NX + x];
+        if (pz == 1) return P[(c * TYH + py) * NX + x];
+        return __ldg(G + c * ncell + row0[pz >> 1] + py * NX + x);
     }
 };
 
@@ -280,32 +289,31 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
             // rows past this block's TY + 2 are never read; every other word must be m0 in each byte
             if (py <= TY + 1 && v != m0x4) uniform = false;
         }
+        // P: the centre plane only (planes z +- 1 are read from global memory by the cells)
         if ((nx & 3) == 0) {   // rows of nx floats: 16-byte vector copies
             const int nq = nx >> 2;
-            for (int w = tid; w < 3 * nrow * nq; w += nthr) {
+            for (int w = tid; w < 3 * TYH * nq; w += nthr) {
                 const int q = w % nq, rr = w / nq;
-                const int py = rr % TYH, pc = rr / TYH;
-                const int c = pc / planes, pz = (MODE == MODE_XFWD) ? 1 : pc % planes;
-                const int gy = y0 - 1 + py, gz = z - 1 + pz;
-                const bool in = (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && py <= TY + 1;
+                const int py = rr % TYH, c = rr / TYH;
+                const int gy = y0 - 1 + py;
+                const bool in = (unsigned)gy < (unsigned)ny && py <= TY + 1;
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (in) v = __ldg(reinterpret_cast<const float4 *>(Pc + c * S.ncell + ((long)gz * ny + gy) * nx) + q);
-                reinterpret_cast<float4 *>(Pt + ((c * 3 + pz) * TYH + py) * nx)[q] = v;
+                if (in) v = __ldg(reinterpret_cast<const float4 *>(Pc + c * S.ncell + ((long)z * ny + gy) * nx) + q);
+                reinterpret_cast<float4 *>(Pt + (c * TYH + py) * nx)[q] = v;
             }
         } else {
-            for (int w = tid; w < 3 * nrow * nx; w += nthr) {
+            for (int w = tid; w < 3 * TYH * nx; w += nthr) {
                 const int x = w % nx, rr = w / nx;
-                const int py = rr % TYH, pc = rr / TYH;
-                const int c = pc / planes, pz = (MODE == MODE_XFWD) ? 1 : pc % planes;
-                const int gy = y0 - 1 + py, gz = z - 1 + pz;
-                const bool in = (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && py <= TY + 1;
-                Pt[((c * 3 + pz) * TYH + py) * nx + x] = in ? __ldg(&Pc[c * S.ncell + ((long)gz * ny + gy) * nx + x]) : 0.f;
+                const int py = rr % TYH, c = rr / TYH;
+                const int gy = y0 - 1 + py;
+                const bool in = (unsigned)gy < (unsigned)ny && py <= TY + 1;
+                Pt[(c * TYH + py) * nx + x] = in ? __ldg(&Pc[c * S.ncell + ((long)z * ny + gy) * nx + x]) : 0.f;
             }
         }
     }
     const bool tile_bulk = __syncthreads_and(uniform && m0x4 != 0u) != 0;
     // ---- cells
-    const TileView<nx, TYH> V{Pt, Mt};
+    const TileView<nx, TYH> V{Pt, Pc, S.ncell, {((long)(z - 1) * ny + y0 - 1) * nx, ((long)(z + 1) * ny + y0 - 1) * nx}, Mt};
     float lmax = 0.f;
     bool bad = false;
     double e_land = 0.0, e_grad = 0.0, e_elec = 0.0, e_ext = 0.0;
@@ -411,7 +419,7 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
     // ---- x-forward of the new (STEP) or current (XFWD) rows: z_j = (x_2j, x_2j+1), zero padded
     {
         float2 v[E];
-        const float *src = (MODE == MODE_XFWD) ? Pt + ((lc * 3 + 1) * TYH + lr + 1) * nx : Eb + (lc * TYmax + lr) * nx;
+        const float *src = (MODE == MODE_XFWD) ? Pt + (lc * TYH + lr + 1) * nx : Eb + (lc * TYmax + lr) * nx;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int j = t + T * m;
