@@ -14,6 +14,7 @@
 // and a table of work items, so one launch covers a single sim or a batch of uneven sims.
 #pragma once
 #include "philox.cuh"
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,11 +53,15 @@ struct SimDev {
     unsigned terms;
     int has_cross;
     unsigned *maxdp;          // float bits of max |dP*| of the step
-    int *flag;                // bit 0: divergence
+    int *flag;                // bit 0: divergence; bit 1: a bounded pipeline wait timed out
     double *energy;           // [4] land grad elec ext, normalized (times alpha_ref P0^2 V -> J)
     float *out;               // field readback [3][ncell]
     float *hbuf;              // Heun: field of the predictor's starting point [3][ncell]
     float out_scale;          // alpha_ref P0
+    int has_ymap;             // ymap below is valid (the z pass then loads its lines with TMA)
+    // Y viewed as float32 (2 kxp, My, nz, 3), box (2 x lines per block, 1, nz, 1): the z lines of
+    // one ky and one group of kx, one component per copy
+    alignas(64) CUtensorMap ymap;
 };
 
 // work item: x = sim index, y/z/w kernel specific

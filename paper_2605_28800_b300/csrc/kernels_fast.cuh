@@ -7,6 +7,7 @@
 #pragma once
 #include "fft_reg.cuh"
 #include "kernels.cuh"
+#include "tc.cuh"
 
 namespace tdgl {
 
@@ -81,9 +82,10 @@ __global__ void __launch_bounds__(256) k_ypass(const SimDev *__restrict__ sims, 
     }
 }
 
-// dynamic shared memory of k_zpass: three component spectra [3][N][KX] and the twiddles
+// dynamic shared memory of k_zpass: three component spectra [3][N][KX] and the twiddles, plus
+// slack to start the spectra on a 128-byte boundary (the alignment of a TMA destination)
 template <int N, int V> __host__ __device__ constexpr size_t zpass_smem() {
-    return (3 * N * zlines_per_block<N, V>() + N) * sizeof(float2);
+    return (3 * N * zlines_per_block<N, V>() + N) * sizeof(float2) + 128;
 }
 
 // Row of position pos in a [N][KX] exchange buffer.  With KX < 16 lines a half-warp covers
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(zthreads<N, V>(), 4) k_zpass(const SimDev *__r
     using S = ZCfg<N, V>;
     constexpr int E = S::E, T = S::T, KX = zlines_per_block<N, V>();
     extern __shared__ float4 smem4[];
-    float2 *A = reinterpret_cast<float2 *>(smem4);      // [3][N][KX]
+    float2 *A = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem4) + 127) & ~uintptr_t(127));   // [3][N][KX]
     float2 *tw = A + 3 * N * KX;                          // [N]
     const int4 it = items[blockIdx.x];
     const SimDev &D = sims[it.x];
@@ -120,23 +122,53 @@ __global__ void __launch_bounds__(zthreads<N, V>(), 4) k_zpass(const SimDev *__r
     const int nz = D.nz, My = D.My, kxp = D.kxp;
     const long zs = (long)My * kxp, cs = (long)nz * zs;
     const float2 *src = D.Y + (long)ky * kxp + kx;
-    auto idx = [&](int pos) { return zrow<N, V, KX>(pos) * KX + l; };
-    // inputs of all three components in flight at once: asynchronous 8-byte copies into this
-    // thread's own slots, component c in commit group c
+    auto idx = [&](int pos) { return zrow<N, V, KX>(pos) * KX + l; };   // exchange layout
+    auto at = [&](int z) { return z * KX + l; };                          // input layout [z][line]
+    // inputs of all three components in flight at once, component c on its own barrier / group:
+    // regular items with one TMA copy per component (the z lines of KX columns), the Nyquist items
+    // (lanes over ky) with 8-byte copies into each thread's own slots
+    __shared__ uint64_t zbar[3];
+    // (the TMA destinations A + c N KX must be 128-byte aligned; checked, else the per-lane copies)
+    const bool tma = D.has_ymap && !across && (tc::saddr(A) & 127u) == 0u;
+    if (tma) {
+        if (threadIdx.x == 0) {
+            for (int c = 0; c < 3; ++c) tc::mbar_init(&zbar[c], 1);
+            tc::mbar_fence_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int c = 0; c < 3; ++c) {
+                tc::mbar_expect_tx(&zbar[c], (uint32_t)(nz * KX * sizeof(float2)));
+                tc::tma_load_4d(tc::saddr(A + c * N * KX), &D.ymap, &zbar[c], 2 * it.z, ky, 0, c);
+            }
+    } else {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        if (ok) {
+        for (int c = 0; c < 3; ++c) {
+            if (ok) {
 #pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int z = t + T * m;
-                if (z < nz) {
-                    const unsigned dst = (unsigned)__cvta_generic_to_shared(A + c * N * KX + idx(z));
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src + c * cs + z * zs));
+                for (int m = 0; m < E; ++m) {
+                    const int z = t + T * m;
+                    if (z < nz) {
+                        const unsigned dst = (unsigned)__cvta_generic_to_shared(A + c * N * KX + at(z));
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src + c * cs + z * zs));
+                    }
                 }
             }
+            asm volatile("cp.async.commit_group;\n" ::);
         }
-        asm volatile("cp.async.commit_group;\n" ::);
     }
+    // component c's inputs have landed (for this thread's slots, or for the whole TMA box)
+    auto arrived = [&](int c) {
+        if (tma) {
+            if (!tc::mbar_wait(&zbar[c], 0u, 1L << 24) && threadIdx.x == 0) atomicOr(D.flag, 2);
+        } else if (c == 0) {
+            asm volatile("cp.async.wait_group 2;\n" ::);
+        } else if (c == 1) {
+            asm volatile("cp.async.wait_group 1;\n" ::);
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::);
+        }
+    };
     // the reduced tensor rows this lane multiplies by (reflection signs for ky > My/2)
     const int kyr = (ky <= My / 2) ? ky : My - ky;
     const float sy = (ky <= My / 2) ? 1.f : -1.f;
@@ -150,26 +182,26 @@ __global__ void __launch_bounds__(zthreads<N, V>(), 4) k_zpass(const SimDev *__r
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int z = t + T * m;
-            v[m] = (ok && z < nz) ? Ac[idx(z)] : make_float2(0.f, 0.f);
+            v[m] = (ok && z < nz) ? Ac[at(z)] : make_float2(0.f, 0.f);
         }
-        __syncthreads();   // own slots (and the twiddles) read before the exchanges overwrite them
+        __syncthreads();   // inputs (and the twiddles) read before the exchanges overwrite them
         rf::fft<S, false>(v, t, Ac, idx, tw);
     };
     {
-        asm volatile("cp.async.wait_group 2;\n" ::);
+        arrived(0);
         float2 v[E];
         forward(0, v);
 #pragma unroll
         for (int i = 0; i < E; ++i) A[idx(rf::final_pos<S>(t, i))] = v[i];
     }
     {
-        asm volatile("cp.async.wait_group 1;\n" ::);
+        arrived(1);
         float2 v[E];
         forward(1, v);
 #pragma unroll
         for (int i = 0; i < E; ++i) A[N * KX + idx(rf::final_pos<S>(t, i))] = v[i];
     }
-    asm volatile("cp.async.wait_group 0;\n" ::);
+    arrived(2);
     float2 w[E];
     forward(2, w);
     // E-hat(k) = escale * N-hat(k) P-hat(k); N-hat from the reduced table with reflection signs.

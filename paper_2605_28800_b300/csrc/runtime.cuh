@@ -1,6 +1,8 @@
 // Internal runtime shared by the library's translation units: the context object, error
 // reporting and the counted (optionally event-timed) kernel launch.  Not part of the C ABI.
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -100,6 +102,19 @@ inline int launch(tdgl_ctx *ctx, int kind, F f) {
     ctx->launches++;
     if (e != cudaSuccess) return fail(ctx, TDGL_ECUDA, "kernel launch (kind %d): %s", kind, cudaGetErrorString(e));
     return TDGL_OK;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (null if unavailable)
+inline PFN_cuTensorMapEncodeTiled_v12000 tmap_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
 }
 
 }  // namespace tdgl_rt

@@ -50,6 +50,8 @@ struct tdgl_sim {
     int integrator = TDGL_EULER;
     float *dhbuf = nullptr;                                     // Heun: first field evaluation
     float *dstage = nullptr;                                    // RK45 / AB3M2: 6 x 3N field evaluations
+    CUtensorMap ymap;                                           // TMA view of dY for the z pass
+    bool has_ymap = false;
     unsigned *derrmax = nullptr;                                // RK45: max local error (float bits)
     double ad_tol = 0.0, ad_min = 0.0, ad_max = 0.0, dt_next = 0.0;   // RK45 step-size control
     int ab_hist = 0, ab_ring = 0;                               // AB3M2: valid history, newest slot
@@ -457,6 +459,20 @@ int alloc_spectra(tdgl_sim *s) {
     CK(ctx, cudaMalloc(&s->dY, 3ull * s->nz * s->My * s->kxp * sizeof(float2)));
     CK(ctx, cudaMalloc(&s->dNhat, 3ull * s->kzh * s->kyh * s->kxp * sizeof(float2)));
     s->spectra_alloc = true;
+    // the z pass's TMA view of Y: float32 (2 kxp, My, nz, 3), box (2 KX, 1, nz, 1) where KX is the
+    // pass's lines per block (the same for both radix-schedule variants)
+    s->has_ymap = false;
+    if (s->zN && s->nz <= 256) {
+        auto enc = tmap_encode();
+        const int KX = fast_zlines(s->Mz);
+        const cuuint64_t dims[4] = {2ull * s->kxp, (cuuint64_t)s->My, (cuuint64_t)s->nz, 3};
+        const cuuint64_t strides[3] = {8ull * s->kxp, 8ull * s->kxp * s->My, 8ull * s->kxp * s->My * s->nz};
+        const cuuint32_t box[4] = {(cuuint32_t)(2 * KX), 1, (cuuint32_t)s->nz, 1};
+        const cuuint32_t es[4] = {1, 1, 1, 1};
+        s->has_ymap = enc && enc(&s->ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, s->dY, dims, strides, box, es,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
     return TDGL_OK;
 }
 
@@ -489,6 +505,8 @@ void fill_desc(tdgl_sim *s, double dt, unsigned terms) {
     D.maxdp = s->dmaxdp; D.flag = s->dflag; D.energy = s->denergy;
     D.out = s->dout;
     D.out_scale = (float)(s->alpha_ref * s->P0);
+    D.has_ymap = s->has_ymap ? 1 : 0;
+    if (s->has_ymap) D.ymap = s->ymap;
 }
 
 int autotune_z(tdgl_sim *s);
@@ -1354,6 +1372,7 @@ int tdgl_step(tdgl_sim *s, int n, double dt) {
     TRY(read_status(s, &m, &f));
     if (f) {
         CK(s->ctx, cudaMemsetAsync(s->dflag, 0, sizeof(int), s->ctx->stream));
+        if (f & 2) return fail(s->ctx, TDGL_ECUDA, "a bounded wait for a tensor copy timed out");
         return fail(s->ctx, TDGL_EDIVERGED, "P diverged (NaN or |P| > 1e3 P0)");
     }
     return TDGL_OK;
@@ -1395,6 +1414,7 @@ int tdgl_relax(tdgl_sim *s, double dt, double tol, long max_steps, int check_eve
         if (steps_taken) *steps_taken = done;
         if (f) {
             CK(s->ctx, cudaMemsetAsync(s->dflag, 0, sizeof(int), s->ctx->stream));
+            if (f & 2) return fail(s->ctx, TDGL_ECUDA, "a bounded wait for a tensor copy timed out");
             return fail(s->ctx, TDGL_EDIVERGED, "P diverged after %ld steps", done);
         }
         if (m < tol) return TDGL_OK;

@@ -61,19 +61,6 @@ int conv_bn(int co) {
     return 16;
 }
 
-// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
-PFN_cuTensorMapEncodeTiled_v12000 tmap_encode() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-    }
-    return fn;
-}
-
 // activations [B][Z][Y][X][C] BF16 as (C, X, Y, Z, B), box (8, 10, 18, 3, 1): one 8-channel plane of
 // a brick with its halo; out-of-range voxels read as zero
 bool act_map(CUtensorMap *m, const void *x, int C, Dims d, long B) {
