@@ -96,7 +96,7 @@ def kernel_bytes(shape):
 def kernel_sources_sha():
     h = hashlib.sha256()
     # device code of the step kernels (host runtime changes do not invalidate the counters)
-    for f in ("fft.cuh", "fft_reg.cuh", "kernels.cuh", "kernels_fast.cuh", "kernels_rows.cuh"):
+    for f in ("fft.cuh", "fft_reg.cuh", "kernels.cuh", "kernels_fast.cuh", "kernels_rows.cuh", "philox.cuh", "tc.cuh"):
         with open(os.path.join(ROOT, "paper_2605_28800_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -62,6 +62,10 @@ struct SimDev {
     // Y viewed as float32 (2 kxp, My, nz, 3), box (2 x lines per block, 1, nz, 1): the z lines of
     // one ky and one group of kx, one component per copy
     alignas(64) CUtensorMap ymap;
+    int has_nmap;             // nmap below is valid (staged z-pass variant)
+    // Nhat viewed as float32 (2 kxp, kyh, kzh, 3), box (2 x lines per block, 1, kzh, 1): the rows
+    // of one reduced ky for one group of kx, one component pair per copy
+    alignas(64) CUtensorMap nmap;
 };
 
 // work item: x = sim index, y/z/w kernel specific

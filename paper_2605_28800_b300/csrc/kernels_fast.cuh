@@ -25,10 +25,17 @@ template <int N> __host__ __device__ constexpr int lines_per_block() {
 //   V = 1: for 256 and 512 points 8 elements per thread (radices 8 8 4, 8 8 8): half the
 //          registers, 256-thread blocks with the same lines and shared memory, so an SM holds
 //          twice the warps, at the price of one more exchange.
-// Both variants give every length the same lines per block, hence the same work items.
+//   V = 2: for 256 points the shape of V = 1, plus the block's rows of the tensor table staged
+//          in shared memory by one TMA copy per component pair at the start, so that their
+//          latency overlaps the forward transforms instead of stalling the multiply (three
+//          blocks per SM instead of four).
+// All variants give every length the same lines per block, hence the same work items.
 template <int N, int V> struct ZCfg : rf::Cfg<N> {};
 template <> struct ZCfg<256, 1> : rf::Shape<256, 8, 8, 8, 4> {};
 template <> struct ZCfg<512, 1> : rf::Shape<512, 8, 8, 8, 8> {};
+template <> struct ZCfg<256, 2> : ZCfg<256, 1> {};
+// variant V stages the tensor rows in shared memory
+template <int V> __host__ __device__ constexpr bool zstaged() { return V == 2; }
 template <int N, int V> __host__ __device__ constexpr int zthreads() { return ZCfg<N, V>::E == 8 ? 256 : 128; }
 template <int N, int V> __host__ __device__ constexpr int zlines_per_block() {
     return (zthreads<N, V>() / ZCfg<N, V>::T) < 16 ? (zthreads<N, V>() / ZCfg<N, V>::T) : 16;
@@ -82,10 +89,17 @@ __global__ void __launch_bounds__(256) k_ypass(const SimDev *__restrict__ sims, 
     }
 }
 
-// dynamic shared memory of k_zpass: three component spectra [3][N][KX] and the twiddles, plus
-// slack to start the spectra on a 128-byte boundary (the alignment of a TMA destination)
+// rows per component pair of the staged tensor tile (N/2 + 1 values of kz for each of the KX
+// columns), rounded up so that every pair starts on a 128-byte boundary
+template <int N, int KX> __host__ __device__ constexpr int ztile_rows() {
+    return ((N / 2 + 1) * KX * (int)sizeof(float2) + 127) / 128 * 128 / (KX * (int)sizeof(float2));
+}
+// dynamic shared memory of k_zpass: three component spectra [3][N][KX], the twiddles and (staged
+// variants) the tensor tile [3][rows][KX], plus slack to start the spectra on a 128-byte boundary
+// (the alignment of a TMA destination)
 template <int N, int V> __host__ __device__ constexpr size_t zpass_smem() {
-    return (3 * N * zlines_per_block<N, V>() + N) * sizeof(float2) + 128;
+    constexpr int KX = zlines_per_block<N, V>();
+    return (3 * N * KX + N + (zstaged<V>() ? 3 * ztile_rows<N, KX>() * KX : 0)) * sizeof(float2) + 128;
 }
 
 // Row of position pos in a [N][KX] exchange buffer.  With KX < 16 lines a half-warp covers
@@ -106,12 +120,15 @@ template <int N, int V, int KX> __device__ __forceinline__ int zrow(int pos) {
 // and y are parked in shared memory (each thread's own slots); z stays in registers through the
 // multiply and its inverse runs first, straight from registers.
 template <int N, int V>
-__global__ void __launch_bounds__(zthreads<N, V>(), 4) k_zpass(const SimDev *__restrict__ sims, const int4 *__restrict__ items) {
+__global__ void __launch_bounds__(zthreads<N, V>(), zstaged<V>() ? 3 : 4)
+    k_zpass(const SimDev *__restrict__ sims, const int4 *__restrict__ items) {
     using S = ZCfg<N, V>;
-    constexpr int E = S::E, T = S::T, KX = zlines_per_block<N, V>();
+    constexpr int E = S::E, T = S::T, KX = zlines_per_block<N, V>(), NR = ztile_rows<N, KX>();
     extern __shared__ float4 smem4[];
     float2 *A = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem4) + 127) & ~uintptr_t(127));   // [3][N][KX]
     float2 *tw = A + 3 * N * KX;                          // [N]
+    float2 *Nt = tw + N;                                  // [3][NR][KX] staged tensor rows (V = 2)
+    static_assert(!zstaged<V>() || ((3 * N * KX + N) * sizeof(float2)) % 128 == 0, "staged tile must start on 128 bytes");
     const int4 it = items[blockIdx.x];
     const SimDev &D = sims[it.x];
     const bool across = (it.w & kAcross) != 0;
@@ -123,24 +140,35 @@ __global__ void __launch_bounds__(zthreads<N, V>(), 4) k_zpass(const SimDev *__r
     const long zs = (long)My * kxp, cs = (long)nz * zs;
     const float2 *src = D.Y + (long)ky * kxp + kx;
     auto idx = [&](int pos) { return zrow<N, V, KX>(pos) * KX + l; };   // exchange layout
+    // the reduced tensor rows this lane multiplies by (reflection signs for ky > My/2)
+    const int kyr = (ky <= My / 2) ? ky : My - ky;
+    const float sy = (ky <= My / 2) ? 1.f : -1.f;
     auto at = [&](int z) { return z * KX + l; };                          // input layout [z][line]
     // inputs of all three components in flight at once, component c on its own barrier / group:
     // regular items with one TMA copy per component (the z lines of KX columns), the Nyquist items
     // (lanes over ky) with 8-byte copies into each thread's own slots
-    __shared__ uint64_t zbar[3];
+    // (staged variant) the block's tensor rows follow on barrier 3: (kz = 0 .. N/2, kyr, its KX
+    // columns) of each component pair
+    __shared__ uint64_t zbar[4];
     // (the TMA destinations A + c N KX must be 128-byte aligned; checked, else the per-lane copies)
     const bool tma = D.has_ymap && !across && (tc::saddr(A) & 127u) == 0u;
+    const bool staged = zstaged<V>() && tma && D.has_nmap;
     if (tma) {
         if (threadIdx.x == 0) {
-            for (int c = 0; c < 3; ++c) tc::mbar_init(&zbar[c], 1);
+            for (int c = 0; c < 4; ++c) tc::mbar_init(&zbar[c], 1);
             tc::mbar_fence_init();
         }
         __syncthreads();
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             for (int c = 0; c < 3; ++c) {
                 tc::mbar_expect_tx(&zbar[c], (uint32_t)(nz * KX * sizeof(float2)));
                 tc::tma_load_4d(tc::saddr(A + c * N * KX), &D.ymap, &zbar[c], 2 * it.z, ky, 0, c);
             }
+            if (staged) {
+                tc::mbar_expect_tx(&zbar[3], (uint32_t)(3 * (N / 2 + 1) * KX * sizeof(float2)));
+                for (int p = 0; p < 3; ++p) tc::tma_load_4d(tc::saddr(Nt + p * NR * KX), &D.nmap, &zbar[3], 2 * it.z, kyr, 0, p);
+            }
+        }
     } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -169,9 +197,6 @@ __global__ void __launch_bounds__(zthreads<N, V>(), 4) k_zpass(const SimDev *__r
             asm volatile("cp.async.wait_group 0;\n" ::);
         }
     };
-    // the reduced tensor rows this lane multiplies by (reflection signs for ky > My/2)
-    const int kyr = (ky <= My / 2) ? ky : My - ky;
-    const float sy = (ky <= My / 2) ? 1.f : -1.f;
     const long ns = (long)D.kzh * D.kyh * kxp;
     const float2 *Nb = D.Nhat + (long)kyr * kxp + kx;
     const long rowN = (long)D.kyh * kxp;
@@ -204,6 +229,7 @@ __global__ void __launch_bounds__(zthreads<N, V>(), 4) k_zpass(const SimDev *__r
     arrived(2);
     float2 w[E];
     forward(2, w);
+    if (staged && !tc::mbar_wait(&zbar[3], 0u, 1L << 24) && threadIdx.x == 0) atomicOr(D.flag, 2);
     // E-hat(k) = escale * N-hat(k) P-hat(k); N-hat from the reduced table with reflection signs.
     // x and y results go back to their owner's slots, z stays in w.
     const float es = D.escale;
@@ -214,7 +240,12 @@ __global__ void __launch_bounds__(zthreads<N, V>(), 4) k_zpass(const SimDev *__r
         const float sz = (kz <= N / 2) ? 1.f : -1.f;
         const float2 *Np = Nb + kzr * rowN;
         float nxx = 0.f, nyy = 0.f, nzz = 0.f, nxy = 0.f, nxz = 0.f, nyz = 0.f;
-        if (ok) {
+        if (staged) {
+            const float2 *Nl = Nt + kzr * KX + l;
+            const float2 n0 = Nl[0], n1 = Nl[NR * KX], n2 = Nl[2 * NR * KX];
+            nxx = n0.x; nyy = n0.y; nzz = n1.x;
+            nxy = sy * n1.y; nxz = sz * n2.x; nyz = sy * sz * n2.y;
+        } else if (ok) {
             const float2 n0 = __ldg(Np), n1 = __ldg(Np + ns), n2 = __ldg(Np + 2 * ns);
             nxx = n0.x; nyy = n0.y; nzz = n1.x;
             nxy = sy * n1.y; nxz = sz * n2.x; nyz = sy * sz * n2.y;

@@ -42,7 +42,7 @@ struct tdgl_ctx {
     // z-pass radix-schedule autotuning for 256- and 512-point lines: chosen variant (-1 = not
     // yet tuned) and the measured microseconds per launch of variants 0 and 1
     int zvar[2] = {-1, -1};
-    double zus[2][2] = {{0, 0}, {0, 0}};
+    double zus[2][TDGL_ZPASS_VARIANTS] = {};
 };
 
 namespace tdgl_rt {

@@ -29,6 +29,7 @@ namespace {
 
 const double kEps0 = 8.8541878128e-12;   // F/m
 const int kMaxSmem = 200 * 1024;
+constexpr int kZVariants = TDGL_ZPASS_VARIANTS;
 
 enum { XS_NONE = 0, XS_PHAT = 1, XS_EHAT = 2 };
 
@@ -52,6 +53,8 @@ struct tdgl_sim {
     float *dstage = nullptr;                                    // RK45 / AB3M2: 6 x 3N field evaluations
     CUtensorMap ymap;                                           // TMA view of dY for the z pass
     bool has_ymap = false;
+    CUtensorMap nmap;                                           // TMA view of dNhat (staged z pass)
+    bool has_nmap = false;
     unsigned *derrmax = nullptr;                                // RK45: max local error (float bits)
     double ad_tol = 0.0, ad_min = 0.0, ad_max = 0.0, dt_next = 0.0;   // RK45 step-size control
     int ab_hist = 0, ab_ring = 0;                               // AB3M2: valid history, newest slot
@@ -461,7 +464,7 @@ int alloc_spectra(tdgl_sim *s) {
     s->spectra_alloc = true;
     // the z pass's TMA view of Y: float32 (2 kxp, My, nz, 3), box (2 KX, 1, nz, 1) where KX is the
     // pass's lines per block (the same for both radix-schedule variants)
-    s->has_ymap = false;
+    s->has_ymap = s->has_nmap = false;
     if (s->zN && s->nz <= 256) {
         auto enc = tmap_encode();
         const int KX = fast_zlines(s->Mz);
@@ -472,6 +475,15 @@ int alloc_spectra(tdgl_sim *s) {
         s->has_ymap = enc && enc(&s->ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, s->dY, dims, strides, box, es,
                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        // the staged variant's view of the tensor table: float32 (2 kxp, kyh, kzh, 3), box
+        // (2 KX, 1, kzh, 1), all kz rows of one reduced ky and KX columns per copy
+        const cuuint64_t ndims[4] = {2ull * s->kxp, (cuuint64_t)s->kyh, (cuuint64_t)s->kzh, 3};
+        const cuuint64_t nstrides[3] = {8ull * s->kxp, 8ull * s->kxp * s->kyh, 8ull * s->kxp * s->kyh * s->kzh};
+        const cuuint32_t nbox[4] = {(cuuint32_t)(2 * KX), 1, (cuuint32_t)s->kzh, 1};
+        s->has_nmap = s->has_ymap && s->kzh <= 256 &&
+                      enc(&s->nmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, s->dNhat, ndims, nstrides, nbox, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     }
     return TDGL_OK;
 }
@@ -507,6 +519,8 @@ void fill_desc(tdgl_sim *s, double dt, unsigned terms) {
     D.out_scale = (float)(s->alpha_ref * s->P0);
     D.has_ymap = s->has_ymap ? 1 : 0;
     if (s->has_ymap) D.ymap = s->ymap;
+    D.has_nmap = s->has_nmap ? 1 : 0;
+    if (s->has_nmap) D.nmap = s->nmap;
 }
 
 int autotune_z(tdgl_sim *s);
@@ -599,13 +613,36 @@ void ypass(const Group &g, const SimDev *d, cudaStream_t st) {
 }
 
 int zvar_index(int N) { return N == 256 ? 0 : (N == 512 ? 1 : -1); }
+// radix-schedule variants of the z pass per length: 256 has three (V = 2 stages the tensor rows),
+// 512 two (its staged tile would not fit beside the spectra)
+int zvar_count(int N) { return N == 256 ? 3 : (N == 512 ? 2 : 0); }
 
 template <int N, int V>
 void zpass_v(const Group &g, const SimDev *d, cudaStream_t st) {
     k_zpass<N, V><<<g.n, ZCfg<N, V>::T * zlines_per_block<N, V>(), zpass_smem<N, V>(), st>>>(d, g.items);
 }
 
-// the z pass of one group with the context's radix-schedule variant (forced: 0 or 1, else tuned)
+// variant v of the z pass for LEN-point lines (a template, so the lengths without variants
+// instantiate only variant 0)
+template <int LEN> void zpass_len(int v, const Group &g, const SimDev *d, cudaStream_t st) {
+    if constexpr (LEN == 256) {
+        if (v == 2) zpass_v<LEN, 2>(g, d, st);
+        else if (v == 1) zpass_v<LEN, 1>(g, d, st);
+        else zpass_v<LEN, 0>(g, d, st);
+    } else if constexpr (LEN == 512) {
+        if (v == 1) zpass_v<LEN, 1>(g, d, st);
+        else zpass_v<LEN, 0>(g, d, st);
+    } else {
+        zpass_v<LEN, 0>(g, d, st);
+    }
+}
+template <int LEN> void zpass_attrs(int smem) {
+    cudaFuncSetAttribute(k_zpass<LEN, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if constexpr (LEN == 256 || LEN == 512) cudaFuncSetAttribute(k_zpass<LEN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if constexpr (LEN == 256) cudaFuncSetAttribute(k_zpass<LEN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+// the z pass of one group with the context's radix-schedule variant (forced >= 0, else tuned)
 void zpass(tdgl_ctx *ctx, const Group &g, const SimDev *d, int force = -1) {
     cudaStream_t st = ctx->stream;
     if (g.N == 0) {
@@ -613,16 +650,11 @@ void zpass(tdgl_ctx *ctx, const Group &g, const SimDev *d, int force = -1) {
         return;
     }
     const int vi = zvar_index(g.N);
-    const int v = force >= 0 ? force : ((vi >= 0 && ctx->zvar[vi] == 1) ? 1 : 0);
+    const int v = force >= 0 ? force : ((vi >= 0 && ctx->zvar[vi] > 0) ? ctx->zvar[vi] : 0);
     switch (g.N) {
-#define TDGL_Z(LEN)                                          \
-    case LEN:                                                \
-        if constexpr (LEN == 256 || LEN == 512) {            \
-            if (v == 1) zpass_v<LEN, 1>(g, d, st);           \
-            else zpass_v<LEN, 0>(g, d, st);                  \
-        } else {                                             \
-            zpass_v<LEN, 0>(g, d, st);                       \
-        }                                                    \
+#define TDGL_Z(LEN)                   \
+    case LEN:                         \
+        zpass_len<LEN>(v, g, d, st);  \
         break;
         TDGL_FAST_LENGTHS(TDGL_Z)
 #undef TDGL_Z
@@ -648,8 +680,8 @@ Work sim_work(tdgl_sim *s, bool elec) {
 }
 
 // Radix-schedule autotuner of the z pass: the first time a context meets 256- or 512-point z
-// lines, both variants run on this sim's own buffers (one launch to warm up, three timed with
-// CUDA events) and the faster is kept for the context.  The z pass works in place on the
+// lines, every variant of that length runs on this sim's own buffers (one launch to warm up,
+// three timed with CUDA events) and the fastest is kept for the context.  The z pass works in place on the
 // y-padded spectrum, which the next y pass rewrites, so the trial launches change no state.
 int autotune_z(tdgl_sim *s) {
     tdgl_ctx *ctx = s->ctx;
@@ -662,8 +694,9 @@ int autotune_z(tdgl_sim *s) {
     cudaEvent_t e0, e1;
     CK(ctx, cudaEventCreate(&e0));
     CK(ctx, cudaEventCreate(&e1));
-    double us[2];
-    for (int v = 0; v < 2; ++v) {
+    double us[kZVariants] = {0.0};
+    const int nv = zvar_count(s->zN);
+    for (int v = 0; v < nv; ++v) {
         TRY(launch(ctx, TDGL_K_OTHER, [&] { zpass(ctx, g, w.descs, v); }));
         CK(ctx, cudaEventRecord(e0, ctx->stream));
         for (int r = 0; r < 3; ++r) TRY(launch(ctx, TDGL_K_OTHER, [&] { zpass(ctx, g, w.descs, v); }));
@@ -675,9 +708,12 @@ int autotune_z(tdgl_sim *s) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->zus[vi][0] = us[0];
-    ctx->zus[vi][1] = us[1];
-    ctx->zvar[vi] = us[1] < us[0] ? 1 : 0;
+    int best = 0;
+    for (int v = 0; v < kZVariants; ++v) {
+        ctx->zus[vi][v] = us[v];
+        if (v < nv && us[v] < us[best]) best = v;
+    }
+    ctx->zvar[vi] = best;
     return TDGL_OK;
 }
 
@@ -998,10 +1034,7 @@ int tdgl_ctx_create(tdgl_ctx **out, int device, void *stream) {
     cudaFuncSetAttribute(k_xrows<MODE_DERIV, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     TDGL_FAST_LENGTHS(TDGL_XA)
 #undef TDGL_XA
-#define TDGL_ZA(LEN)                                                                                \
-    cudaFuncSetAttribute(k_zpass<LEN, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);      \
-    if constexpr (LEN == 256 || LEN == 512)                                                         \
-        cudaFuncSetAttribute(k_zpass<LEN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+#define TDGL_ZA(LEN) zpass_attrs<LEN>(kMaxSmem);
     TDGL_FAST_LENGTHS(TDGL_ZA)
 #undef TDGL_ZA
     if (cudaGetLastError() != cudaSuccess) { delete ctx; return TDGL_ECUDA; }
@@ -1223,19 +1256,18 @@ int tdgl_zpass_variant(tdgl_ctx *ctx, int length, int *variant, double *us) {
     const int vi = zvar_index(length);
     if (!ctx || !variant || vi < 0) return ctx ? fail(ctx, TDGL_EINVAL, "z-pass variants exist for 256 and 512") : TDGL_EINVAL;
     *variant = ctx->zvar[vi];
-    if (us) {
-        us[0] = ctx->zus[vi][0];
-        us[1] = ctx->zus[vi][1];
-    }
+    if (us)
+        for (int v = 0; v < kZVariants; ++v) us[v] = ctx->zus[vi][v];
     return TDGL_OK;
 }
 
 int tdgl_set_zpass_variant(tdgl_ctx *ctx, int length, int variant) {
     const int vi = zvar_index(length);
-    if (!ctx || vi < 0 || variant < -1 || variant > 1)
+    if (!ctx || vi < 0 || variant < -1 || variant >= zvar_count(length))
         return ctx ? fail(ctx, TDGL_EINVAL, "z-pass variant %d for length %d", variant, length) : TDGL_EINVAL;
     ctx->zvar[vi] = variant;
-    if (variant < 0) ctx->zus[vi][0] = ctx->zus[vi][1] = 0.0;
+    if (variant < 0)
+        for (int v = 0; v < kZVariants; ++v) ctx->zus[vi][v] = 0.0;
     return TDGL_OK;
 }
 

@@ -23,6 +23,7 @@ KERNEL_NAMES = {K_STEP: "k_rows<STEP>", K_YFWD: "k_yfwd", K_ZCONV: "k_zconv", K_
                 K_XFWD: "k_rows<XFWD>", K_OTHER: "other", K_UNET: "unet"}
 MAX_MATERIALS, MAX_DIM = 16, 1024
 EULER, HEUN, RK45, AB3M2 = 0, 1, 2, 3
+ZPASS_VARIANTS = 3
 
 _CODES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EDIVERGED: "EDIVERGED",
           ENOTCONVERGED: "ENOTCONVERGED", ESTATE: "ESTATE", ETOOBIG: "ETOOBIG"}
@@ -157,10 +158,11 @@ class Context:
         return rc
 
     def zpass_variant(self, length):
-        """(variant, (us of variant 0, us of variant 1)) chosen by the z-pass autotuner; -1 = not yet tuned"""
-        v, us = _I(), (_D * 2)()
+        """(variant, microseconds per launch of each variant, 0 where the length has none) chosen by
+        the z-pass autotuner; -1 = not yet tuned"""
+        v, us = _I(), (_D * ZPASS_VARIANTS)()
         self.check(self.lib.tdgl_zpass_variant(self.h, int(length), ctypes.byref(v), us))
-        return v.value, (us[0], us[1])
+        return v.value, tuple(us)
 
     def set_zpass_variant(self, length, variant):
         self.check(self.lib.tdgl_set_zpass_variant(self.h, int(length), int(variant)))

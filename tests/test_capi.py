@@ -48,3 +48,15 @@ def test_library_reports_errors_without_device(lib):
     h = ctypes.c_void_p()
     rc = lib.tdgl_ctx_create(ctypes.byref(h), 0, None)
     assert rc != 0
+
+
+def test_binding_constants_match_the_header():
+    # every #define of the header that the binding mirrors has the same value there
+    from paper_2605_28800_b300 import tdgl
+    defs = dict(re.findall(r"#define\s+TDGL_([A-Z0-9_]+)\s+\(?(-?\d+)", open(HEADER).read()))
+    pairs = {"ZPASS_VARIANTS": tdgl.ZPASS_VARIANTS, "EULER": tdgl.EULER, "HEUN": tdgl.HEUN, "RK45": tdgl.RK45,
+             "AB3M2": tdgl.AB3M2, "K_STEP": tdgl.K_STEP, "K_ZCONV": tdgl.K_ZCONV, "K_UNET": tdgl.K_UNET,
+             "EINVAL": tdgl.EINVAL, "ECUDA": tdgl.ECUDA, "EDIVERGED": tdgl.EDIVERGED}
+    for name, value in pairs.items():
+        assert name in defs, name
+        assert int(defs[name]) == value, name

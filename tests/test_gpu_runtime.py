@@ -204,9 +204,9 @@ def test_launch_counter_counts_kernels(ctx):
     assert ctx.launch_count - n0 == 10 * 4
 
 
-def test_zpass_autotuner_picks_a_variant_and_both_variants_agree_with_the_oracle():
-    # 16 x 16 x 128 pads z to 256 points: the context times both radix schedules of the z pass on
-    # first use and keeps the faster; forcing either gives the same trajectory as the oracle
+def test_zpass_autotuner_picks_a_variant_and_every_variant_agrees_with_the_oracle():
+    # 16 x 16 x 128 pads z to 256 points: the context times the three variants of the z pass on
+    # first use and keeps the fastest; forcing any of them gives the same trajectory as the oracle
     from paper_2605_28800_b300 import tdgl
     from tests.helpers import mixed_case
     CELL = (1e-9, 1.1e-9, 0.9e-9)
@@ -219,14 +219,15 @@ def test_zpass_autotuner_picks_a_variant_and_both_variants_agree_with_the_oracle
     try:
         assert ctx.zpass_variant(256)[0] == -1
         finals = []
-        for forced in (None, 0, 1):
+        for forced in (None, 0, 1, 2):
             g = gpu_sim(ctx, shape, CELL, mat, MATS, 300.0, 45.0, P=P)
             if forced is not None:
                 ctx.set_zpass_variant(256, forced)
             g.step(3, dt)
             if forced is None:
                 v, us = ctx.zpass_variant(256)
-                assert v in (0, 1) and us[0] > 0 and us[1] > 0 and us[v] == min(us)
+                assert len(us) == tdgl.ZPASS_VARIANTS == 3
+                assert v in (0, 1, 2) and min(us) > 0 and us[v] == min(us)
             else:
                 assert ctx.zpass_variant(256)[0] == forced
             finals.append(g.get_P())
@@ -237,5 +238,8 @@ def test_zpass_autotuner_picks_a_variant_and_both_variants_agree_with_the_oracle
             assert np.abs(Pg - Po).max() / 0.2649096 <= 1e-5
         with pytest.raises(tdgl.TdglError):
             ctx.set_zpass_variant(128, 1)
+        with pytest.raises(tdgl.TdglError):
+            ctx.set_zpass_variant(512, 2)          # the staged variant exists for 256 only
+        ctx.set_zpass_variant(512, 1)
     finally:
         ctx.close()
