@@ -128,23 +128,49 @@ int launch_conv(tdgl_ctx *ctx, const __nv_bfloat16 *x, const __nv_bfloat16 *w, c
 }
 
 // dW[o][tap Ci + i] += sum_v xs[dx + 1][i][v + dz YX + dy X] dYt[o][v]
-int launch_wgrad(tdgl_ctx *ctx, const __nv_bfloat16 *dyt, const __nv_bfloat16 *xs, float *dw, long nvox, Dims d,
-                 int Ci, int Co, int ntap, int ldw, int *err) {
+// voxels per CTA of the weight gradient (about four CTAs per SM over the (tap, i) tiles) and the
+// number of voxel chunks, each leaving one partial gradient
+long wgrad_vchunk(long nvox, int N) {
+    const long ntile = (N + 127) / 128;
+    const long v = (nvox * ntile + 591) / 592;
+    return std::min<long>(std::max<long>((v + 15) / 16 * 16, 256), 16384);
+}
+long wgrad_chunks(long nvox, int N) { return (nvox + wgrad_vchunk(nvox, N) - 1) / wgrad_vchunk(nvox, N); }
+// floats of the partial-gradient workspace of one convolution (weights, then biases)
+size_t wgrad_part_floats(long nvox, int Ci, int Co, int ntap, int ldw) {
+    return (size_t)wgrad_chunks(nvox, ntap * Ci) * Co * ldw;
+}
+size_t bias_part_floats(long nvox, int Co) { return (size_t)((nvox + 31) / 32) * Co; }
+
+// dw += the weight gradient: per-chunk partials into part, then summed in chunk order
+int launch_wgrad(tdgl_ctx *ctx, const __nv_bfloat16 *dyt, const __nv_bfloat16 *xs, float *dw, float *part, long nvox,
+                 Dims d, int Ci, int Co, int ntap, int ldw, int *err) {
     const int N = ntap * Ci;
     const int bn = Co <= 16 ? 16 : (Co <= 32 ? 32 : (Co <= 64 ? 64 : 128));
     const long ntile = (N + 127) / 128;
-    long vchunk = (nvox * ntile + 591) / 592;                   // about four CTAs per SM
-    vchunk = std::min<long>(std::max<long>((vchunk + 15) / 16 * 16, 256), 16384);
-    WgradP p{dyt, xs, dw, nvox, d.Z, d.Y, d.X, Ci, Co, ntap, ldw, (int)vchunk, err};
-    const dim3 grid((unsigned)ntile, (unsigned)((nvox + vchunk - 1) / vchunk));
-    return launch(ctx, TDGL_K_UNET, [&] {
+    const long vchunk = wgrad_vchunk(nvox, N), nchunk = wgrad_chunks(nvox, N);
+    WgradP p{dyt, xs, part, nvox, d.Z, d.Y, d.X, Ci, Co, ntap, ldw, (int)vchunk, err};
+    const dim3 grid((unsigned)ntile, (unsigned)nchunk);
+    TRY(launch(ctx, TDGL_K_UNET, [&] {
         switch (bn) {
             case 128: k_wgrad<128><<<grid, 128, gemm_smem<128>(), ctx->stream>>>(p); break;
             case 64: k_wgrad<64><<<grid, 128, gemm_smem<64>(), ctx->stream>>>(p); break;
             case 32: k_wgrad<32><<<grid, 128, gemm_smem<32>(), ctx->stream>>>(p); break;
             default: k_wgrad<16><<<grid, 128, gemm_smem<16>(), ctx->stream>>>(p); break;
         }
+    }));
+    return launch(ctx, TDGL_K_UNET, [&] {
+        k_wsum<<<grid_n((long)Co * N), 256, 0, ctx->stream>>>(dw, part, (int)nchunk, Co, N, ldw);
     });
+}
+
+// ReLU mask of the upstream gradient (BF16 copies in both layouts) and db += its sum over voxels:
+// per-block partials into part, summed in block order
+int launch_relu_bwd(tdgl_ctx *ctx, const float *g, const __nv_bfloat16 *out, __nv_bfloat16 *d, __nv_bfloat16 *dt,
+                    float *db, float *part, long V, int C) {
+    const long nb = (V + 31) / 32;
+    TRY(launch(ctx, TDGL_K_UNET, [&] { k_relu_bwd<<<(unsigned)nb, 256, 0, ctx->stream>>>(g, out, d, dt, part, V, C); }));
+    return launch(ctx, TDGL_K_UNET, [&] { k_colsum<<<(unsigned)C, 256, 0, ctx->stream>>>(db, part, nb, C); });
 }
 
 template <int BN, int S>
@@ -190,7 +216,8 @@ struct tdgl_unet {
     __nv_bfloat16 *xin = nullptr;       // [V0][8]
     float *tgt = nullptr, *yout = nullptr;   // [V0][coutp]
     __nv_bfloat16 *dpre = nullptr, *dpret = nullptr, *xs = nullptr;   // backward scratch
-    double *dloss = nullptr;
+    float *wpart = nullptr, *bpart = nullptr;                          // partial gradients
+    double *dloss = nullptr, *lpart = nullptr;   // loss and its per-block partials
     int *derr = nullptr;
     float *hx = nullptr, *hy = nullptr;  // device staging of host tensors
 };
@@ -242,7 +269,7 @@ int build(tdgl_unet *n) {
     TRY(dalloc(n, &n->G, n->nparam));
     TRY(dalloc(n, &n->M, n->nparam));
     TRY(dalloc(n, &n->V, n->nparam));
-    size_t max_dpre = 0, max_xs = 0;
+    size_t max_dpre = 0, max_xs = 0, max_wpart = 0, max_bpart = 0;
     for (auto &l : n->L) {
         TRY(dalloc(n, &l.wf, (size_t)l.Co * l.Kp));
         TRY(dalloc(n, &l.wt, (size_t)l.Ci * l.Kpt));
@@ -253,7 +280,11 @@ int build(tdgl_unet *n) {
         const size_t V = (size_t)nvox(n, l.lev, n->maxb);
         max_dpre = std::max(max_dpre, V * l.Co);
         max_xs = std::max(max_xs, 3 * V * l.Ci);
+        max_wpart = std::max(max_wpart, wgrad_part_floats((long)V, l.Ci, l.Co, l.ntap, l.Kp));
+        max_bpart = std::max(max_bpart, bias_part_floats((long)V, l.Co));
     }
+    TRY(dalloc(n, &n->wpart, max_wpart));
+    TRY(dalloc(n, &n->bpart, max_bpart));
     // activations: every layer's output, the pooled / concatenated inputs, the input
     const int B = n->maxb;
     TRY(dalloc(n, &n->xin, (size_t)nvox(n, 0, B) * 8));
@@ -303,6 +334,7 @@ int build(tdgl_unet *n) {
     TRY(dalloc(n, &n->dpret, max_dpre));
     TRY(dalloc(n, &n->xs, max_xs));
     TRY(dalloc(n, &n->dloss, 1));
+    TRY(dalloc(n, &n->lpart, (size_t)grid_n(1L << 40)));
     TRY(dalloc(n, &n->derr, 1));
     TRY(dalloc(n, &n->hx, (size_t)nvox(n, 0, B) * std::max(n->cin, n->cout)));
     TRY(dalloc(n, &n->hy, (size_t)nvox(n, 0, B) * std::max(n->cin, n->cout)));
@@ -371,13 +403,11 @@ int conv_backward(tdgl_unet *n, Layer &ly, int B) {
     const Dims &d = n->dims[ly.lev];
     float *gw = n->G + ly.ow, *gb = n->G + ly.ob;
     const __nv_bfloat16 *out = ly.relu ? reinterpret_cast<const __nv_bfloat16 *>(ly.out) : nullptr;
-    TRY(launch(ctx, TDGL_K_UNET, [&] {
-        k_relu_bwd<<<(unsigned)((V + 31) / 32), 256, 0, ctx->stream>>>(ly.g_out, out, n->dpre, n->dpret, gb, V, ly.Co);
-    }));
+    TRY(launch_relu_bwd(ctx, ly.g_out, out, n->dpre, n->dpret, gb, n->bpart, V, ly.Co));
     TRY(launch(ctx, TDGL_K_UNET, [&] {
         k_xshift<<<(unsigned)((V + 31) / 32), 256, 0, ctx->stream>>>(ly.in, n->xs, V, ly.Ci, d.X, ly.ntap == 27 ? 3 : 1);
     }));
-    TRY(launch_wgrad(ctx, n->dpret, n->xs, gw, V, d, ly.Ci, ly.Co, ly.ntap, ly.Kp, n->derr));
+    TRY(launch_wgrad(ctx, n->dpret, n->xs, gw, n->wpart, V, d, ly.Ci, ly.Co, ly.ntap, ly.Kp, n->derr));
     if (ly.need_dx)
         TRY(launch_conv(ctx, n->dpre, ly.wt, ly.wtb, nullptr, ly.g_in, V, d, ly.Co, ly.Ci, ly.ntap, ly.Kpt, false, true,
                         n->derr));
@@ -448,11 +478,11 @@ int loss(tdgl_unet *n, const float *t, int B) {
         k_to_ndhwc_f32<<<grid_n(V0 * n->coutp), 256, 0, ctx->stream>>>(t, n->tgt, V0, n->cout, n->coutp,
                                                                           n->dims[0].vps());
     }));
-    CK(ctx, cudaMemsetAsync(n->dloss, 0, sizeof(double), ctx->stream));
-    return launch(ctx, TDGL_K_UNET, [&] {
-        k_mse<<<grid_n(V0 * n->coutp), 256, 0, ctx->stream>>>(n->yout, n->tgt, hd.g_out, V0 * n->coutp,
-                                                                (double)V0 * n->cout, n->dloss);
-    });
+    const int nb = grid_n(V0 * n->coutp);
+    TRY(launch(ctx, TDGL_K_UNET, [&] {
+        k_mse<<<nb, 256, 0, ctx->stream>>>(n->yout, n->tgt, hd.g_out, V0 * n->coutp, (double)V0 * n->cout, n->lpart);
+    }));
+    return launch(ctx, TDGL_K_UNET, [&] { k_dsum<<<1, 256, 0, ctx->stream>>>(n->dloss, n->lpart, nb); });
 }
 
 int check_batch(tdgl_unet *n, int B) {
@@ -752,7 +782,7 @@ int tdgl_conv3d_backward(tdgl_ctx *ctx, const float *x, const float *w, const fl
     const int ntap = k * k * k;
     const Dims d{nz, ny, nx};
     const long V = (long)batch * d.vps();
-    float *xf, *gy, *gyn, *gx, *gxo, *wm, *gw, *gb;
+    float *xf, *gy, *gyn, *gx, *gxo, *wm, *gw, *gb, *wpart, *bpart;
     __nv_bfloat16 *xb, *wf, *wt, *wfb, *wtb, *dpre, *dpret, *xs;
     int Kp, Kpt, *derr;
     TRY(S.get(ctx, &xf, (size_t)V * ci));
@@ -768,17 +798,17 @@ int tdgl_conv3d_backward(tdgl_ctx *ctx, const float *x, const float *w, const fl
     TRY(upload_w(ctx, S, w, ci, co, ntap, &wm, &wf, &wt, &wfb, &wtb, &Kp, &Kpt));
     TRY(S.get(ctx, &gw, (size_t)co * Kp));
     TRY(S.get(ctx, &gb, (size_t)co));
+    TRY(S.get(ctx, &wpart, wgrad_part_floats(V, ci, co, ntap, Kp)));
+    TRY(S.get(ctx, &bpart, bias_part_floats(V, co)));
     CK(ctx, cudaMemcpyAsync(xf, x, (size_t)V * ci * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, cudaMemcpyAsync(gy, dyh, (size_t)V * co * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     TRY(launch(ctx, TDGL_K_UNET, [&] { k_to_ndhwc<<<grid_n(V * ci), 256, 0, ctx->stream>>>(xf, xb, V, ci, ci, d.vps()); }));
     TRY(launch(ctx, TDGL_K_UNET, [&] { k_to_ndhwc_f32<<<grid_n(V * co), 256, 0, ctx->stream>>>(gy, gyn, V, co, co, d.vps()); }));
-    TRY(launch(ctx, TDGL_K_UNET, [&] {
-        k_relu_bwd<<<(unsigned)((V + 31) / 32), 256, 0, ctx->stream>>>(gyn, nullptr, dpre, dpret, gb, V, co);
-    }));
+    TRY(launch_relu_bwd(ctx, gyn, nullptr, dpre, dpret, gb, bpart, V, co));
     TRY(launch(ctx, TDGL_K_UNET, [&] {
         k_xshift<<<(unsigned)((V + 31) / 32), 256, 0, ctx->stream>>>(xb, xs, V, ci, d.X, ntap == 27 ? 3 : 1);
     }));
-    TRY(launch_wgrad(ctx, dpret, xs, gw, V, d, ci, co, ntap, Kp, derr));
+    TRY(launch_wgrad(ctx, dpret, xs, gw, wpart, V, d, ci, co, ntap, Kp, derr));
     TRY(launch_conv(ctx, dpre, wt, wtb, nullptr, gx, V, d, co, ci, ntap, Kpt, false, true, derr));
     TRY(launch(ctx, TDGL_K_UNET, [&] { k_from_ndhwc_f32<<<grid_n(V * ci), 256, 0, ctx->stream>>>(gx, gxo, V, ci, ci, d.vps()); }));
     std::vector<float> g((size_t)co * Kp);

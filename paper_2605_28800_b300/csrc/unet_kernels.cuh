@@ -341,14 +341,15 @@ __global__ void __launch_bounds__(128) k_conv_brick(const __grid_constant__ Bric
 struct WgradP {
     const __nv_bfloat16 *dyt;   // [Co][nvox]  upstream gradient (after the ReLU mask), transposed
     const __nv_bfloat16 *xs;    // [3][Ci][nvox]  layer input transposed, shifted by dx = -1, 0, +1
-    float *dw;                  // [Co][ldw], column tap * Ci + i; accumulated atomically
+    float *part;                // [voxel chunk][Co][ldw], column tap * Ci + i: one partial sum per chunk
     long nvox;
     int Z, Y, X, Ci, Co, ntap, ldw, vchunk;
     int *err;
 };
 
-// dW[o][tap, i] += sum over this CTA's voxel chunk of X[v + off(tap)][i] dY[v][o]:
-// M = 128 (tap, i) rows, N = the output channels (BN >= Co), K = voxels
+// partial dW[o][tap, i] = sum over this CTA's voxel chunk of X[v + off(tap)][i] dY[v][o]:
+// M = 128 (tap, i) rows, N = the output channels (BN >= Co), K = voxels.  k_wsum adds the chunks'
+// partials in chunk order, so the gradient does not depend on the order the CTAs finish in.
 template <int BN>
 __global__ void __launch_bounds__(128) k_wgrad(WgradP p) {
     extern __shared__ uint8_t smem_raw[];
@@ -406,11 +407,39 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradP p) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int o = c0 + j;
-                if (o < p.Co) atomicAdd(&p.dw[(long)o * p.ldw + ng], r[j]);
+                if (o < p.Co) p.part[((long)blockIdx.y * p.Co + o) * p.ldw + ng] = r[j];
             }
         }
     }
     epilogue_free<BN>(tmem);
+}
+
+// dw[o][col] += sum over chunks s = 0, 1, ... of part[s][o][col], for the N real columns
+__global__ void k_wsum(float *__restrict__ dw, const float *__restrict__ part, int nchunk, int Co, int N, int ldw) {
+    const long n = (long)Co * N;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int o = (int)(i / N), col = (int)(i - (long)o * N);
+        const long e = (long)o * ldw + col;
+        float s = 0.f;
+        for (int c = 0; c < nchunk; ++c) s += part[(long)c * Co * ldw + e];
+        dw[e] += s;
+    }
+}
+
+// db[c] += sum over blocks b = 0, 1, ... of part[b][c]: one block per channel, a fixed strided
+// sum per thread and a fixed tree over the threads (independent of scheduling)
+__global__ void __launch_bounds__(256) k_colsum(float *__restrict__ db, const float *__restrict__ part, long nb, int C) {
+    __shared__ float red[256];
+    const int c = blockIdx.x;
+    float s = 0.f;
+    for (long b = threadIdx.x; b < nb; b += 256) s += part[b * C + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[c] += red[0];
 }
 
 // ---- memory-bound helpers ---------------------------------------------------------------------
@@ -528,9 +557,10 @@ __global__ void k_upcat_bwd(const float *__restrict__ g, float *__restrict__ gde
 
 // ReLU backward and the operands of the layer's backward GEMMs:
 //   d[v][c] = g[v][c] * (out[v][c] > 0)  (out null: no ReLU)  -> BF16 [voxel][C] and [C][voxel],
-//   db[c] += sum_v d[v][c].  Block: 32 voxels x C channels through shared memory.
+//   dbp[block][c] = sum over the block's 32 voxels of d[v][c] (k_colsum adds the blocks in order).
+//   Block: 32 voxels x C channels through shared memory.
 __global__ void k_relu_bwd(const float *__restrict__ g, const __nv_bfloat16 *__restrict__ out,
-                           __nv_bfloat16 *__restrict__ d, __nv_bfloat16 *__restrict__ dt, float *__restrict__ db, long V,
+                           __nv_bfloat16 *__restrict__ d, __nv_bfloat16 *__restrict__ dt, float *__restrict__ dbp, long V,
                            int C) {
     __shared__ float tile[32][129];
     const long v0 = (long)blockIdx.x * 32;
@@ -553,7 +583,7 @@ __global__ void k_relu_bwd(const float *__restrict__ g, const __nv_bfloat16 *__r
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
         float s = 0.f;
         for (int r = 0; r < 32; ++r) s += tile[r][c];
-        atomicAdd(&db[c], s);
+        dbp[(long)blockIdx.x * C + c] = s;
     }
 }
 
@@ -581,10 +611,11 @@ __global__ void k_xshift(const __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__r
     }
 }
 
-// squared error of y [n] against t, summed and divided by denom (the number of real elements;
-// padded channels hold 0 in both), and its gradient 2 (y - t) / denom as FP32
+// squared error of y [n] against t divided by denom (the number of real elements; padded channels
+// hold 0 in both), one partial sum per block (k_dsum adds them in order), and its gradient
+// 2 (y - t) / denom as FP32
 __global__ void k_mse(const float *__restrict__ y, const float *__restrict__ t, float *__restrict__ g, long n,
-                      double denom, double *__restrict__ loss) {
+                      double denom, double *__restrict__ part) {
     __shared__ double red[32];
     double s = 0.0;
     const float sc = (float)(2.0 / denom);
@@ -599,8 +630,22 @@ __global__ void k_mse(const float *__restrict__ y, const float *__restrict__ t, 
     if (threadIdx.x == 0) {
         double a = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[w];
-        atomicAdd(loss, a / denom);
+        part[blockIdx.x] = a / denom;
     }
+}
+
+// loss = sum over blocks b = 0, 1, ... of part[b] (one block of 256 threads, fixed order)
+__global__ void __launch_bounds__(256) k_dsum(double *__restrict__ loss, const double *__restrict__ part, int nb) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 256) s += part[b];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = red[0];
 }
 
 __global__ void k_add(float *__restrict__ a, const float *__restrict__ b, long n) {

@@ -169,6 +169,20 @@ def test_unet_training_reduces_loss(ctx):
     assert losses[-1] < 0.5 * losses[0]
 
 
+def test_unet_training_is_reproducible(ctx):
+    # the gradient reductions add partial sums in a fixed order (no FP32 atomics): the same seed,
+    # data and steps give bit-identical losses, gradients and parameters
+    runs = []
+    for _ in range(2):
+        net, p, x, t, levels = small_net(ctx, seed=17, shape=(32, 32, 4))
+        losses = [net.train_step(x, t, 2e-3) for _ in range(3)]
+        loss, g = net.loss_grad(x, t)
+        runs.append((losses + [loss], g, net.get_params()))
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1])
+    assert np.array_equal(runs[0][2], runs[1][2])
+
+
 def test_unet_device_tensors_match_host(ctx):
     import torch
     net, p, x, t, levels = small_net(ctx, seed=13)
