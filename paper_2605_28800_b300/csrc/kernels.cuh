@@ -68,6 +68,16 @@ struct SimDev {
     alignas(64) CUtensorMap nmap;
 };
 
+// Programmatic dependent launch.  A kernel of the step chain (row, y and z passes) reads only
+// constant data (descriptor, twiddles, coefficients, tensor spectrum) before this call; the call
+// waits until the grids it depends on have completed with their writes visible (a no-op after an
+// ordinary launch), then lets the next grid of the stream be scheduled, so that its constant
+// prologue overlaps this grid's last wave.
+__device__ __forceinline__ void pdl_wait_then_release() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // work item: x = sim index, y/z/w kernel specific
 //   rows kernels: y = z, z = y0, w = row count
 //   y kernels:    y = c*nz + z, z = kx0, w = kx count
