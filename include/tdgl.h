@@ -199,7 +199,10 @@ int tdgl_last_max_dP(tdgl_sim *sim, double *out);
 /* Relaxation (Sec. 4: equilibrium as the steady state of Eq. 1): step with dt until the
  * max |dP| of a step, checked every `check_every` steps (>= 1), is below tol * P0, or until
  * max_steps.  *steps_taken (may be NULL) receives the steps done.  Returns TDGL_OK on
- * convergence, TDGL_ENOTCONVERGED at the cap, TDGL_EDIVERGED on divergence. */
+ * convergence, TDGL_ENOTCONVERGED at the cap, TDGL_EDIVERGED on divergence.  For forward Euler
+ * with an even check_every, and for Heun, without a time-dependent applied field, the check runs
+ * on the device inside one CUDA graph (the host waits once per call); the steps taken and the
+ * result are the same as with a host check every check_every steps. */
 int tdgl_relax(tdgl_sim *sim, double dt, double tol, long max_steps, int check_every,
                long *steps_taken);
 /* Energy terms of Eq. 2 for the current P (joules, float64 accumulation). */

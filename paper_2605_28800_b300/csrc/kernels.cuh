@@ -78,6 +78,14 @@ __device__ __forceinline__ void pdl_wait_then_release() {
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
+// State of the device-side relaxation loop (the relaxation to equilibrium of Sec. 2): steps done,
+// the step cap, the tolerance on max |dP*| of a step and the steps per loop body.
+struct RelaxState {
+    long done, max_steps;
+    double tol;
+    int k;
+};
+
 // work item: x = sim index, y/z/w kernel specific
 //   rows kernels: y = z, z = y0, w = row count
 //   y kernels:    y = c*nz + z, z = kx0, w = kx count

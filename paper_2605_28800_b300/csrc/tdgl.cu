@@ -89,6 +89,8 @@ struct tdgl_sim {
     bool dirty = true;      // map, materials, T or scales changed since the last prepare()
     struct GraphRec { int n; bool elec; int p0; int integ; cudaGraphExec_t exec; long kernels; };
     std::vector<GraphRec> graphs;   // captured steady step sequences
+    std::vector<GraphRec> relax_graphs;   // device-side relaxation loops (n = steps per chunk)
+    RelaxState *drelax = nullptr;         // their loop state
     double last_maxdp = 0.0;
     tdgl_batch *batch = nullptr;
 };
@@ -761,6 +763,26 @@ int read_status(tdgl_sim *s, double *maxdp, int *flag) {
     return TDGL_OK;
 }
 
+// Launches of steps i0..n-1, starting from P-hat in X.  Euler: convolution, row kernel (launch
+// index i, parity i & 1).  Heun: predictor on P (index 2i), convolution of the predictor,
+// corrector (index 2i + 2); P stays in the same buffer.  maxdp is reset before the last step.
+int record_steps(tdgl_sim *s, const Work &w, int i0, int n, bool elec, bool heun) {
+    tdgl_ctx *ctx = s->ctx;
+    for (int i = i0; i < n; ++i) {
+        if (elec) TRY(launch_conv(ctx, w));
+        if (heun) {
+            TRY(launch_rows(ctx, MODE_HEUN1, w, 2 * i));
+            if (elec) TRY(launch_conv(ctx, w));
+            if (i == n - 1) CK(ctx, cudaMemsetAsync(s->dmaxdp, 0, sizeof(unsigned), ctx->stream));
+            TRY(launch_rows(ctx, MODE_HEUN2, w, 2 * i + 2));
+        } else {
+            if (i == n - 1) CK(ctx, cudaMemsetAsync(s->dmaxdp, 0, sizeof(unsigned), ctx->stream));
+            TRY(launch_rows(ctx, MODE_STEP, w, i));
+        }
+    }
+    return TDGL_OK;
+}
+
 // n steps of one sim without a status read; maxdp reset before the last step
 int steps_nosync(tdgl_sim *s, int n, double dt) {
     tdgl_ctx *ctx = s->ctx;
@@ -785,24 +807,7 @@ int steps_nosync(tdgl_sim *s, int n, double dt) {
         }
         i0 = 1;
     }
-    // steps i0..n-1 start from P-hat in X.  Euler: convolution, row kernel (launch index i,
-    // parity i & 1).  Heun: predictor on P (index 2i), convolution of the predictor, corrector
-    // (index 2i + 2); P stays in the same buffer.
-    auto record = [&]() -> int {
-        for (int i = i0; i < n; ++i) {
-            if (elec) TRY(launch_conv(ctx, w));
-            if (heun) {
-                TRY(launch_rows(ctx, MODE_HEUN1, w, 2 * i));
-                if (elec) TRY(launch_conv(ctx, w));
-                if (i == n - 1) CK(ctx, cudaMemsetAsync(s->dmaxdp, 0, sizeof(unsigned), ctx->stream));
-                TRY(launch_rows(ctx, MODE_HEUN2, w, 2 * i + 2));
-            } else {
-                if (i == n - 1) CK(ctx, cudaMemsetAsync(s->dmaxdp, 0, sizeof(unsigned), ctx->stream));
-                TRY(launch_rows(ctx, MODE_STEP, w, i));
-            }
-        }
-        return TDGL_OK;
-    };
+    auto record = [&]() -> int { return record_steps(s, w, i0, n, elec, heun); };
     const int m = n - i0;
     // repeated sequences replay a captured graph (the descriptor, read by the kernels from device
     // memory, carries dt and the current P buffer); not while profiling
@@ -1159,9 +1164,10 @@ void tdgl_sim_destroy(tdgl_sim *s) {
         drop_cache(s->batch);              // indices in the cached work lists changed
     }
     for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto &g : s->relax_graphs) cudaGraphExecDestroy(g.exec);
     void *ptrs[] = {s->dP[0], s->dP[1], s->dmat, s->dX, s->dY, s->dNhat, s->dtw, s->dcoef, s->dmaxdp,
                     s->dflag, s->denergy, s->dout, s->ddesc, s->d_rows, s->d_y, s->d_z, s->dhbuf,
-                    s->dstage, s->derrmax};
+                    s->dstage, s->derrmax, s->drelax};
     for (void *p : ptrs) cudaFree(p);
     delete s;
 }
@@ -1433,6 +1439,94 @@ int tdgl_last_max_dP(tdgl_sim *s, double *out) {
     return TDGL_OK;
 }
 
+// Relaxation with its convergence loop on the device: one CUDA graph whose conditional WHILE
+// node repeats a body of k steps (the launches of steps_nosync) followed by k_relax_check, which
+// counts the steps and clears the loop condition once max|dP*| of the body's last step is below
+// tol, a kernel raised the divergence or timeout flag, or another body would pass max_steps.  The
+// host waits once per call instead of once per k steps; the steps taken and the final state are
+// those of the host-checked loop.  Usable for Euler with even k (P returns to the same buffer
+// after each body, so one descriptor serves every iteration) and for Heun, without a
+// time-dependent applied field (the body replays the same launch indices).
+// End of one loop body: count its k steps and keep looping while no kernel raised a flag, the
+// last step's max |dP*| (float bits in maxdp) is not below tol and another body fits under the cap.
+__global__ void k_relax_check(cudaGraphConditionalHandle h, RelaxState *st, const unsigned *maxdp, const int *flag) {
+    const long done = st->done + st->k;
+    st->done = done;
+    const unsigned u = *maxdp;
+    const bool conv = u < 0x7f800000u && (double)__uint_as_float(u) < st->tol;
+    const bool more = *flag == 0 && !conv && done + st->k <= st->max_steps;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+bool relax_on_device_ok(const tdgl_sim *s, int k) {
+    const bool ac = s->ac_freq != 0.0 && (s->Eac[0] != 0.0 || s->Eac[1] != 0.0 || s->Eac[2] != 0.0);
+    const bool parity_ok = s->integrator == TDGL_HEUN || (s->integrator == TDGL_EULER && (k & 1) == 0);
+    return parity_ok && !ac && !s->ctx->profiling && s->ctx->stream != nullptr;
+}
+
+int relax_on_device(tdgl_sim *s, double dt, double tol, long max_steps, int k, long *done, double *maxdp, int *flag) {
+    tdgl_ctx *ctx = s->ctx;
+    const bool elec = (s->terms & TDGL_TERM_ELEC) != 0;
+    const bool heun = s->integrator == TDGL_HEUN;
+    fill_desc(s, dt, s->terms);
+    TRY(upload_desc(s));
+    Work w = sim_work(s, elec);
+    if (elec && s->xstate != XS_PHAT) {   // the body starts from P-hat of the current P
+        TRY(launch_rows(ctx, MODE_XFWD, w, 0));
+        s->xstate = XS_PHAT;
+    }
+    if (!s->drelax) CK(ctx, cudaMalloc(&s->drelax, sizeof(RelaxState)));
+    tdgl_sim::GraphRec *G = nullptr;
+    for (auto &g : s->relax_graphs)
+        if (g.n == k && g.elec == elec && g.integ == s->integrator) G = &g;
+    if (!G) {
+        cudaGraph_t g = nullptr;
+        CK(ctx, cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle h;
+        cudaGraphNodeParams np = {};
+        cudaGraphNode_t node;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) {
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+        }
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            CK(ctx, e);
+        }
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        const long l0 = ctx->launches;
+        CK(ctx, cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        int rc = record_steps(s, w, 0, k, elec, heun);
+        if (rc == TDGL_OK)
+            rc = launch(ctx, TDGL_K_OTHER, [&] { k_relax_check<<<1, 1, 0, ctx->stream>>>(h, s->drelax, s->dmaxdp, s->dflag); });
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(ctx->stream, &captured);
+        const long kernels = ctx->launches - l0;
+        ctx->launches = l0;
+        cudaGraphExec_t exec = nullptr;
+        if (rc == TDGL_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (rc != TDGL_OK) return rc;
+        CK(ctx, e);
+        s->relax_graphs.push_back(tdgl_sim::GraphRec{k, elec, 0, s->integrator, exec, kernels});
+        G = &s->relax_graphs.back();
+    }
+    RelaxState st{0, max_steps, tol, k};
+    CK(ctx, cudaMemcpyAsync(s->drelax, &st, sizeof st, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaGraphLaunch(G->exec, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(&st, s->drelax, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+    TRY(read_status(s, maxdp, flag));     // synchronizes
+    *done = st.done;
+    ctx->launches += (st.done / k) * G->kernels;
+    for (long c = 0; c < st.done / k; ++c) s->time += k * dt;   // as the host loop adds it
+    s->xstate = elec ? XS_PHAT : XS_NONE;
+    return TDGL_OK;
+}
+
 int tdgl_relax(tdgl_sim *s, double dt, double tol, long max_steps, int check_every, long *steps_taken) {
     if (steps_taken) *steps_taken = 0;
     if (!s || !(dt > 0) || !(tol > 0) || max_steps < 0 || check_every < 1) return TDGL_EINVAL;
@@ -1453,6 +1547,19 @@ int tdgl_relax(tdgl_sim *s, double dt, double tol, long max_steps, int check_eve
         return fail(s->ctx, TDGL_ENOTCONVERGED, "not converged after %ld steps (last max|dP| = %g P0)", done,
                     s->last_maxdp);
     }
+    auto flagged = [&](int f) {
+        CK(s->ctx, cudaMemsetAsync(s->dflag, 0, sizeof(int), s->ctx->stream));
+        if (f & 2) return fail(s->ctx, TDGL_ECUDA, "a bounded wait for a tensor copy timed out");
+        return fail(s->ctx, TDGL_EDIVERGED, "P diverged after %ld steps", done);
+    };
+    if (max_steps >= check_every && relax_on_device_ok(s, check_every)) {
+        double m;
+        int f;
+        TRY(relax_on_device(s, dt, tol, max_steps, check_every, &done, &m, &f));
+        if (steps_taken) *steps_taken = done;
+        if (f) return flagged(f);
+        if (m < tol) return TDGL_OK;
+    }
     while (done < max_steps) {
         const int k = (int)std::min<long>(check_every, max_steps - done);
         TRY(steps_nosync(s, k, dt));
@@ -1461,11 +1568,7 @@ int tdgl_relax(tdgl_sim *s, double dt, double tol, long max_steps, int check_eve
         int f;
         TRY(read_status(s, &m, &f));
         if (steps_taken) *steps_taken = done;
-        if (f) {
-            CK(s->ctx, cudaMemsetAsync(s->dflag, 0, sizeof(int), s->ctx->stream));
-            if (f & 2) return fail(s->ctx, TDGL_ECUDA, "a bounded wait for a tensor copy timed out");
-            return fail(s->ctx, TDGL_EDIVERGED, "P diverged after %ld steps", done);
-        }
+        if (f) return flagged(f);
         if (m < tol) return TDGL_OK;
     }
     return fail(s->ctx, TDGL_ENOTCONVERGED, "not converged after %ld steps (last max|dP| = %g P0)", done, s->last_maxdp);

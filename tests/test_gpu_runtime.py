@@ -182,6 +182,45 @@ def test_divergence_is_reported(ctx):
     assert e.value.code == tdgl.EDIVERGED
 
 
+@pytest.mark.parametrize("integ", ["euler", "heun"])
+@pytest.mark.parametrize("shape", [(16, 16, 16), (9, 7, 5)])
+def test_device_relax_loop_matches_the_host_checked_loop(ctx, integ, shape):
+    # tdgl_relax runs its convergence loop inside one CUDA graph (conditional while node) when
+    # it can; with profiling on it checks on the host after every k steps.  Both take the same
+    # steps to the same bits: to convergence, and to a step cap that is not a multiple of k
+    from paper_2605_28800_b300 import tdgl
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    for tol, cap in ((1e-6, 400000), (1e-12, 100)):
+        runs = []
+        for host in (False, True):
+            s, _ = _bto(ctx, shape, seed=23)
+            if integ == "heun":
+                s.set_integrator(tdgl.HEUN)
+            ctx.profile(host)
+            try:
+                n, ok = s.relax(dt, tol, cap, check_every=16, raise_on_cap=False)
+            finally:
+                ctx.profile(False)
+            runs.append((n, ok, s.get_P(), s.time()))
+            s.close()
+        (n0, ok0, P0, t0), (n1, ok1, P1, t1) = runs
+        assert (n0, ok0) == (n1, ok1)
+        assert ok0 == (cap > 1000)
+        if cap == 100:
+            assert n0 == 100
+        assert np.array_equal(P0, P1)
+        assert t0 == t1
+
+
+def test_device_relax_loop_reports_divergence(ctx):
+    from paper_2605_28800_b300 import tdgl
+    s, _ = _bto(ctx, (6, 6, 6))
+    with pytest.raises(tdgl.TdglError) as e:
+        s.relax(1e-6, 1e-6, 1000, check_every=16)    # far beyond the explicit stability bound
+    assert e.value.code == tdgl.EDIVERGED
+    assert "after 16 steps" in str(e.value)
+
+
 def test_device_buffers_round_trip(ctx):
     import torch
     shape = (10, 6, 4)
