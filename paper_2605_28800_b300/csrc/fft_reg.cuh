@@ -121,6 +121,18 @@ __device__ __forceinline__ void fft(float2 (&v)[S::E], int t, float2 *X, Idx idx
 template <class S>
 __device__ __forceinline__ int final_pos(int t, int i) { return out_pos<S, S::NP - 1>(t, i); }
 
+// Zero padding to at least twice the data length (N >= 2n): the input registers m >= E/2 hold
+// positions t + T m >= N/2 >= n, which are zero, and the output registers i whose last-pass index
+// q = i mod R (R the last radix) is >= R/2 hold positions (b - j) R + j + q N/R >= N/2, which are
+// not kept.  These compile-time forms of facts the run-time bounds already imply let the compiler
+// drop the arithmetic on known zeros and on discarded outputs.
+template <class S> __host__ __device__ constexpr bool padded_in(int m) {
+    return S::N % 2 != 0 || S::E % 2 != 0 || m < S::E / 2;
+}
+template <class S> __host__ __device__ constexpr bool kept_out(int i) {
+    return radix<S>(S::NP - 1) % 2 != 0 || (i % radix<S>(S::NP - 1)) < radix<S>(S::NP - 1) / 2;
+}
+
 // register index holding X[t + T m] after a forward transform (inverse of final_pos within a thread)
 template <class S>
 __host__ __device__ constexpr int final_reg(int m) {

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_ypass(const SimDev *__restrict__ sims, 
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int y = t + T * m;
-            v[m] = (ok && y < ny) ? src[(long)y * kxp] : make_float2(0.f, 0.f);
+            v[m] = (rf::padded_in<rf::Cfg<N>>(m) && ok && y < ny) ? src[(long)y * kxp] : make_float2(0.f, 0.f);
         }
     } else {
         const float2 *src = D.Y + (long)cz * N * kxp + kx;
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) k_ypass(const SimDev *__restrict__ sims, 
 #pragma unroll
         for (int i = 0; i < E; ++i) {
             const int y = rf::final_pos<rf::Cfg<N>>(t, i);
-            if (y < ny) dst[(long)y * kxp] = v[i];
+            if (rf::kept_out<rf::Cfg<N>>(i) && y < ny) dst[(long)y * kxp] = v[i];
         }
     }
 }
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(zthreads<N, V>(), zstaged<V>() ? 3 : 4)
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int z = t + T * m;
-            v[m] = (ok && z < nz) ? Ac[at(z)] : make_float2(0.f, 0.f);
+            v[m] = (rf::padded_in<S>(m) && ok && z < nz) ? Ac[at(z)] : make_float2(0.f, 0.f);
         }
         __syncthreads();   // inputs (and the twiddles) read before the exchanges overwrite them
         rf::fft<S, false>(v, t, Ac, idx, tw);
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(zthreads<N, V>(), zstaged<V>() ? 3 : 4)
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 const int z = rf::final_pos<S>(t, i);
-                if (z < nz) dst[c * cs + z * zs] = v[i];
+                if (rf::kept_out<S>(i) && z < nz) dst[c * cs + z * zs] = v[i];
             }
         }
     };

@@ -264,8 +264,8 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
                 const int j = rf::final_pos<rf::Cfg<HX>>(t, i);
                 const int x0 = 2 * j;
                 float *er = Eb + (lc * TYmax + lr) * nx;
-                if (x0 < nx) er[x0] = v[i].x;
-                if (x0 + 1 < nx) er[x0 + 1] = v[i].y;
+                if (rf::kept_out<rf::Cfg<HX>>(i) && x0 < nx) er[x0] = v[i].x;
+                if (rf::kept_out<rf::Cfg<HX>>(i) && x0 + 1 < nx) er[x0 + 1] = v[i].y;
             }
         }
         __syncthreads();
@@ -425,7 +425,8 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
         for (int m = 0; m < E; ++m) {
             const int j = t + T * m;
             const int x0 = 2 * j;
-            v[m] = make_float2((lok && x0 < nx) ? src[x0] : 0.f, (lok && x0 + 1 < nx) ? src[x0 + 1] : 0.f);
+            const bool in = rf::padded_in<rf::Cfg<HX>>(m) && lok;   // x0 = 2j, j >= HX/2: padding
+            v[m] = make_float2((in && x0 < nx) ? src[x0] : 0.f, (in && x0 + 1 < nx) ? src[x0 + 1] : 0.f);
         }
         __syncthreads();   // the exchange below reuses the tile's memory
         rf::fft<rf::Cfg<HX>, false>(v, t, X2, xidx, s_tw);
