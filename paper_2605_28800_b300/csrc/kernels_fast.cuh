@@ -260,8 +260,25 @@ __global__ void __launch_bounds__(zthreads<N, V>(), zstaged<V>() ? 3 : 4)
         w[i] = make_float2(es * (nxz * px.x + nyz * py.x + nzz * pz.x), es * (nxz * px.y + nyz * py.y + nzz * pz.y));
     }
     float2 *dst = D.Y + (long)ky * kxp + kx;
+    // component c's first nz outputs back into Y.  Regular items: into its exchange buffer (free
+    // once its inverse has returned) in the layout of the input box, then one TMA store of the box
+    // (in a partial item the columns past the count fall into Y's padding, which nothing reads);
+    // Nyquist items: 8-byte stores from each lane.
     auto store = [&](int c, const float2(&v)[E]) {
-        if (ok) {
+        if (tma) {
+            float2 *Ac = A + c * N * KX;
+#pragma unroll
+            for (int i = 0; i < E; ++i) {
+                const int z = rf::final_pos<S>(t, i);
+                if (rf::kept_out<S>(i) && z < nz) Ac[at(z)] = v[i];
+            }
+            tc::fence_proxy_async();   // the box's generic-proxy writes before the copy reads it
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                tc::tma_store_4d(&D.ymap, tc::saddr(Ac), 2 * it.z, ky, 0, c);
+                tc::bulk_commit();
+            }
+        } else if (ok) {
 #pragma unroll
             for (int i = 0; i < E; ++i) {
                 const int z = rf::final_pos<S>(t, i);
@@ -288,6 +305,7 @@ __global__ void __launch_bounds__(zthreads<N, V>(), zstaged<V>() ? 3 : 4)
         rf::fft<S, true>(v, t, Ac, idx, tw);
         store(c, v);
     }
+    if (tma && threadIdx.x == 0) tc::bulk_wait_read_all();   // the boxes read before shared memory goes
 }
 
 }  // namespace tdgl
