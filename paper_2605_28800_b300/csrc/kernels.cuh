@@ -68,16 +68,6 @@ struct SimDev {
     alignas(64) CUtensorMap nmap;
 };
 
-// Programmatic dependent launch.  A kernel of the step chain (row, y and z passes) reads only
-// constant data (descriptor, twiddles, coefficients, tensor spectrum) before this call; the call
-// waits until the grids it depends on have completed with their writes visible (a no-op after an
-// ordinary launch), then lets the next grid of the stream be scheduled, so that its constant
-// prologue overlaps this grid's last wave.
-__device__ __forceinline__ void pdl_wait_then_release() {
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-}
-
 // State of the device-side relaxation loop (the relaxation to equilibrium of Sec. 2): steps done,
 // the step cap, the tolerance on max |dP*| of a step and the steps per loop body.
 struct RelaxState {

@@ -58,7 +58,6 @@ __global__ void __launch_bounds__(256) k_ypass(const SimDev *__restrict__ sims, 
     const int cz = across ? it.y + l : it.y, kx = across ? it.z : it.z + l;   // this lane's line
     const bool ok = l < cnt;
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = D.tw[D.py.tw + i];
-    pdl_wait_then_release();   // X / Y come from the previous kernel
     const int ny = D.ny, kxp = D.kxp;
     float2 v[E];
     if (!INV) {
@@ -160,18 +159,16 @@ __global__ void __launch_bounds__(zthreads<N, V>(), zstaged<V>() ? 3 : 4)
             tc::mbar_fence_init();
         }
         __syncthreads();
-        if (threadIdx.x == 0 && staged) {   // the tensor rows are constant: before the dependency wait
-            tc::mbar_expect_tx(&zbar[3], (uint32_t)(3 * (N / 2 + 1) * KX * sizeof(float2)));
-            for (int p = 0; p < 3; ++p) tc::tma_load_4d(tc::saddr(Nt + p * NR * KX), &D.nmap, &zbar[3], 2 * it.z, kyr, 0, p);
-        }
-    }
-    pdl_wait_then_release();   // Y comes from the y pass
-    if (tma) {
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             for (int c = 0; c < 3; ++c) {
                 tc::mbar_expect_tx(&zbar[c], (uint32_t)(nz * KX * sizeof(float2)));
                 tc::tma_load_4d(tc::saddr(A + c * N * KX), &D.ymap, &zbar[c], 2 * it.z, ky, 0, c);
             }
+            if (staged) {
+                tc::mbar_expect_tx(&zbar[3], (uint32_t)(3 * (N / 2 + 1) * KX * sizeof(float2)));
+                for (int p = 0; p < 3; ++p) tc::tma_load_4d(tc::saddr(Nt + p * NR * KX), &D.nmap, &zbar[3], 2 * it.z, kyr, 0, p);
+            }
+        }
     } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {

@@ -237,7 +237,6 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
     for (int i = tid; i < HX; i += nthr) s_tw[i] = S.tw[S.px.tw + i];
     for (int i = tid; i <= HX; i += nthr) s_twr[i] = S.tw[S.twr + i];
     if (tid == 0) s_max = 0u;
-    pdl_wait_then_release();   // X and P come from the previous kernels
     // ---- x-inverse of the field spectrum: line l = c*TY + r held by T threads
     const int line = tid / T, t = tid % T;
     const int nlines = 3 * TYmax;

@@ -567,23 +567,6 @@ struct Work {
     std::vector<Group> rg, yg, zg;   // row, y and z work by transform length
 };
 
-// launch of a step-chain kernel that calls pdl_wait_then_release before reading what the
-// kernels before it wrote: it may be scheduled while the previous kernel's last wave runs
-template <class... P, class... A>
-void launch_pdl(void (*kernel)(P...), unsigned grid, unsigned block, size_t smem, cudaStream_t st, A... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, args...);   // a failure is left for cudaGetLastError
-}
-
 template <int MODE>
 void rows_launch(const Group &g, const SimDev *d, cudaStream_t st, int parity) {
     if (g.N == 0) {
@@ -591,7 +574,7 @@ void rows_launch(const Group &g, const SimDev *d, cudaStream_t st, int parity) {
         return;
     }
     switch (g.N) {
-#define TDGL_R(LEN) case LEN: launch_pdl(k_xrows<MODE, LEN>, g.n, xrows_threads<LEN>(), g.smem, st, d, g.items, parity); break;
+#define TDGL_R(LEN) case LEN: k_xrows<MODE, LEN><<<g.n, xrows_threads<LEN>(), g.smem, st>>>(d, g.items, parity); break;
         TDGL_FAST_LENGTHS(TDGL_R)
 #undef TDGL_R
     }
@@ -625,7 +608,7 @@ void ypass(const Group &g, const SimDev *d, cudaStream_t st) {
     }
     switch (g.N) {
 #define TDGL_Y(LEN) \
-    case LEN: launch_pdl(k_ypass<LEN, INV>, g.n, rf::threads_per_line<LEN>() * lines_per_block<LEN>(), 0, st, d, g.items); break;
+    case LEN: k_ypass<LEN, INV><<<g.n, rf::threads_per_line<LEN>() * lines_per_block<LEN>(), 0, st>>>(d, g.items); break;
         TDGL_FAST_LENGTHS(TDGL_Y)
 #undef TDGL_Y
     }
@@ -638,7 +621,7 @@ int zvar_count(int N) { return N == 256 ? 3 : (N == 512 ? 2 : 0); }
 
 template <int N, int V>
 void zpass_v(const Group &g, const SimDev *d, cudaStream_t st) {
-    launch_pdl(k_zpass<N, V>, g.n, ZCfg<N, V>::T * zlines_per_block<N, V>(), zpass_smem<N, V>(), st, d, g.items);
+    k_zpass<N, V><<<g.n, ZCfg<N, V>::T * zlines_per_block<N, V>(), zpass_smem<N, V>(), st>>>(d, g.items);
 }
 
 // variant v of the z pass for LEN-point lines (a template, so the lengths without variants
