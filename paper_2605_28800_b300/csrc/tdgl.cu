@@ -1535,15 +1535,21 @@ int tdgl_relax(tdgl_sim *s, double dt, double tol, long max_steps, int check_eve
         if (f & 2) return fail(s->ctx, TDGL_ECUDA, "a bounded wait for a tensor copy timed out");
         return fail(s->ctx, TDGL_EDIVERGED, "P diverged after %ld steps", done);
     };
-    if (max_steps >= check_every && relax_on_device_ok(s, check_every)) {
-        double m;
-        int f;
-        TRY(relax_on_device(s, dt, tol, max_steps, check_every, &done, &m, &f));
-        if (steps_taken) *steps_taken = done;
-        if (f) return flagged(f);
-        if (m < tol) return TDGL_OK;
-    }
+    const bool elec = (s->terms & TDGL_TERM_ELEC) != 0;
     while (done < max_steps) {
+        // whole chunks on the device, unless the field spectrum of the current P is already in X
+        // (left by an energy or field call): the host-checked chunk's first step uses it
+        if (max_steps - done >= check_every && relax_on_device_ok(s, check_every) && !(elec && s->xstate == XS_EHAT)) {
+            long d = 0;
+            double m;
+            int f;
+            TRY(relax_on_device(s, dt, tol, max_steps - done, check_every, &d, &m, &f));
+            done += d;
+            if (steps_taken) *steps_taken = done;
+            if (f) return flagged(f);
+            if (m < tol) return TDGL_OK;
+            continue;   // fewer than check_every steps remain
+        }
         const int k = (int)std::min<long>(check_every, max_steps - done);
         TRY(steps_nosync(s, k, dt));
         done += k;
