@@ -77,7 +77,9 @@ def padded(n, even):
 
 
 def kernel_bytes(shape):
-    """Algorithmic bytes per launch of each kernel of one step ('Roofline')."""
+    """Algorithmic bytes per launch of each kernel of one step: what each kernel of this four-kernel
+    decomposition must read and write at minimum (P and materials, the x- and y-padded spectra, the
+    reduced tensor table), without re-reads."""
     nx, ny, nz = shape
     Mx, My, Mz = padded(2 * nx - 1, True), padded(2 * ny - 1, False), padded(2 * nz - 1, False)
     Kx = Mx // 2 + 1
@@ -210,6 +212,10 @@ def gpu_arm(args, rank, world):
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
     ctx = tdgl.Context(dev, stream=stream.cuda_stream)
+    if args.zpass_variant >= 0:   # profiling runs: a profiler distorts the autotuner's trial timings
+        for n in (256, 512):
+            if args.zpass_variant < (3 if n == 256 else 2):
+                ctx.set_zpass_variant(n, args.zpass_variant)
     wl = workload(args.workload)
     s, dt = make_sim(ctx, wl)
     ncell = int(np.prod(wl["shape"]))
@@ -401,6 +407,8 @@ def main():
     ap.add_argument("--ws-lr", type=float, default=2e-3)
     ap.add_argument("--sweep-sims", type=int, default=48)
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--zpass-variant", type=int, default=-1,
+                    help="force the z-pass variant for 256/512-point lines instead of autotuning (for profiler runs)")
     ap.add_argument("--max-relax-steps", type=int, default=20000)
     args = ap.parse_args()
     if args.relax_compare:
