@@ -22,8 +22,12 @@ namespace tdgl {
 template <int HX> __host__ __device__ constexpr int xrows_tile() {
     return (192 / (3 * rf::threads_per_line<HX>())) < 16 ? (192 / (3 * rf::threads_per_line<HX>())) : 16;
 }
+// (at least 192: for short rows the threads past the transform lines still share the staging and
+// the cells)
 template <int HX> __host__ __device__ constexpr int xrows_threads() {
-    return ((3 * xrows_tile<HX>() * rf::threads_per_line<HX>()) + 31) / 32 * 32;
+    return ((3 * xrows_tile<HX>() * rf::threads_per_line<HX>()) + 31) / 32 * 32 > 192
+               ? ((3 * xrows_tile<HX>() * rf::threads_per_line<HX>()) + 31) / 32 * 32
+               : 192;
 }
 template <int HX> __host__ __device__ constexpr int xrows_ldp() { return HX + HX / 16 + 1; }
 // floats of the region shared by the centre-plane P tile and the x-transform exchange (multiple of 4)

@@ -27,6 +27,7 @@ struct ProfRec {
 
 struct tdgl_ctx {
     int device = 0;
+    int nsm = 148;                      // streaming multiprocessors of the device
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     std::string err;

@@ -79,6 +79,7 @@ struct tdgl_sim {
     int twr = 0;
     // work items
     std::vector<int4> it_rows, it_y, it_z;
+    std::vector<int4> it_rows_full;   // row items of full tiles (batches)
     int rows_cnt_max = 1, ky_cnt_max = 1, kz_cnt_max = 1;
     int xN = 0, yN = 0, zN = 0;   // specialized x / y / z transform length (0 = generic kernels)
     int4 *d_rows = nullptr, *d_y = nullptr, *d_z = nullptr;
@@ -249,6 +250,7 @@ int fast_zlines(int n) {    // lines per block of the z pass
 
 void build_items(tdgl_sim *s) {
     s->it_rows.clear();
+    s->it_rows_full.clear();
     s->it_y.clear();
     s->it_z.clear();
     // the tiled row kernel needs the row length to equal the x half-length (2 nx smooth)
@@ -256,8 +258,15 @@ void build_items(tdgl_sim *s) {
     const int RB = s->xN ? fast_rowtile(s->hx)
                          : std::max(1, std::min(s->ny, std::max(1, 512 / s->nx)));
     s->rows_cnt_max = RB;
-    for (int z = 0; z < s->nz; ++z)
-        for (int y0 = 0; y0 < s->ny; y0 += RB) s->it_rows.push_back(make_int4(0, z, y0, std::min(RB, s->ny - y0)));
+    // A sim run alone whose full tiles would give fewer blocks than SMs takes fewer rows per block,
+    // about one block per SM (such a small grid is bound by each block's latency, not by the
+    // tile's halo overhead); in a batch the members' full tiles already fill the GPU.
+    const long rows = (long)s->ny * s->nz;
+    const int RB1 = s->xN ? (int)std::min<long>(RB, std::max<long>(1, (rows + s->ctx->nsm - 1) / s->ctx->nsm)) : RB;
+    for (int z = 0; z < s->nz; ++z) {
+        for (int y0 = 0; y0 < s->ny; y0 += RB1) s->it_rows.push_back(make_int4(0, z, y0, std::min(RB1, s->ny - y0)));
+        for (int y0 = 0; y0 < s->ny; y0 += RB) s->it_rows_full.push_back(make_int4(0, z, y0, std::min(RB, s->ny - y0)));
+    }
     s->yN = fast_len(s->My) ? s->My : 0;
     s->zN = fast_len(s->Mz) ? s->Mz : 0;
     // Kx = Mx/2 + 1 columns: when the first Mx/2 fill whole line groups, the last (Nyquist) column
@@ -1013,6 +1022,10 @@ int tdgl_ctx_create(tdgl_ctx **out, int device, void *stream) {
     tdgl_ctx *ctx = new tdgl_ctx();
     ctx->device = device;
     if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return TDGL_ECUDA; }
+    if (cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || ctx->nsm < 1) {
+        delete ctx;
+        return TDGL_ECUDA;
+    }
     if (stream) {
         ctx->stream = (cudaStream_t)stream;
     } else {
@@ -1668,7 +1681,7 @@ int build_batch_work(tdgl_batch *b, const std::vector<int> &active, Work &w) {
         tdgl_sim *s = b->sims[idx];
         const bool elec = (s->terms & TDGL_TERM_ELEC) != 0;
         const size_t gr = group_of(rgr, rsm, s->xN);
-        for (auto it : s->it_rows) rgr[gr].second.push_back(make_int4(idx, it.y, it.z, it.w));
+        for (auto it : s->it_rows_full) rgr[gr].second.push_back(make_int4(idx, it.y, it.z, it.w));
         rsm[gr] = std::max(rsm[gr], smem_rows(s, s->rows_cnt_max));
         if (elec) {
             const size_t gy = group_of(ygr, ysm, s->yN), gz = group_of(zgr, zsm, s->zN);
@@ -1732,9 +1745,9 @@ int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const doub
             tdgl_sim *s = b->sims[idx];
             if ((s->terms & TDGL_TERM_ELEC) && s->xstate != XS_PHAT) {
                 const size_t g = group_of(pgr, psm, s->xN);
-                for (auto it : s->it_rows) pgr[g].second.push_back(make_int4(idx, it.y, it.z, it.w));
+                for (auto it : s->it_rows_full) pgr[g].second.push_back(make_int4(idx, it.y, it.z, it.w));
                 psm[g] = std::max(psm[g], smem_rows(s, s->rows_cnt_max));
-                npro += s->it_rows.size();
+                npro += s->it_rows_full.size();
             }
         }
         if (npro) {
