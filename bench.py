@@ -213,8 +213,8 @@ def gpu_arm(args, rank, world):
     stream = torch.cuda.Stream()
     ctx = tdgl.Context(dev, stream=stream.cuda_stream)
     if args.zpass_variant >= 0:   # profiling runs: a profiler distorts the autotuner's trial timings
-        for n in (256, 512):
-            if args.zpass_variant < (3 if n == 256 else 2):
+        for n in (128, 256, 512):
+            if args.zpass_variant < (2 if n == 512 else 3):
                 ctx.set_zpass_variant(n, args.zpass_variant)
     wl = workload(args.workload)
     s, dt = make_sim(ctx, wl)
@@ -260,7 +260,7 @@ def gpu_arm(args, rank, world):
         s.step(1, dt)       # returns after reading the step's max|dP| and divergence flag
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
-    zvar = {n: ctx.zpass_variant(n) for n in (256, 512)}
+    zvar = {n: ctx.zpass_variant(n) for n in (128, 256, 512)}
     return dict(ms=ms, launches=launches, prof=prof, clocks=clk.summary(), ncell=ncell, wl=wl, warm=warm,
                 e2e=aggregate_rate(ncell * e2e_steps, world, e2e_s), e2e_h2d=Ph.numel() * 4,
                 zpass_tuning={str(n): {"variant": v, "us": [round(u, 2) for u in us]}

@@ -20,17 +20,19 @@ template <int N> __host__ __device__ constexpr int lines_per_block() {
 }
 
 // Shapes of the z pass, V = radix-schedule variant (picked per length by the host's autotuner):
-//   V = 0: the default shapes (16 elements per thread; radices 16 16 for 256, 16 16 2 for 512),
-//          128-thread blocks;
-//   V = 1: for 256 and 512 points 8 elements per thread (radices 8 8 4, 8 8 8): half the
-//          registers, 256-thread blocks with the same lines and shared memory, so an SM holds
+//   V = 0: the default shapes (16 elements per thread; radices 16 8 for 128, 16 16 for 256,
+//          16 16 2 for 512), 128-thread blocks;
+//   V = 1: for 128, 256 and 512 points 8 elements per thread (radices 8 8 2, 8 8 4, 8 8 8): half
+//          the registers, 256-thread blocks with the same lines and shared memory, so an SM holds
 //          twice the warps, at the price of one more exchange.
-//   V = 2: for 256 points the shape of V = 1, plus the block's rows of the tensor table staged
+//   V = 2: for 128 and 256 points the shape of V = 1, plus the block's rows of the tensor table staged
 //          in shared memory by one TMA copy per component pair at the start, so that their
 //          latency overlaps the forward transforms instead of stalling the multiply (three
 //          blocks per SM instead of four).
 // All variants give every length the same lines per block, hence the same work items.
 template <int N, int V> struct ZCfg : rf::Cfg<N> {};
+template <> struct ZCfg<128, 1> : rf::Shape<128, 8, 8, 8, 2> {};
+template <> struct ZCfg<128, 2> : ZCfg<128, 1> {};
 template <> struct ZCfg<256, 1> : rf::Shape<256, 8, 8, 8, 4> {};
 template <> struct ZCfg<512, 1> : rf::Shape<512, 8, 8, 8, 8> {};
 template <> struct ZCfg<256, 2> : ZCfg<256, 1> {};
@@ -40,7 +42,8 @@ template <int N, int V> __host__ __device__ constexpr int zthreads() { return ZC
 template <int N, int V> __host__ __device__ constexpr int zlines_per_block() {
     return (zthreads<N, V>() / ZCfg<N, V>::T) < 16 ? (zthreads<N, V>() / ZCfg<N, V>::T) : 16;
 }
-static_assert(zlines_per_block<256, 0>() == zlines_per_block<256, 1>() &&
+static_assert(zlines_per_block<128, 0>() == zlines_per_block<128, 1>() &&
+                  zlines_per_block<256, 0>() == zlines_per_block<256, 1>() &&
                   zlines_per_block<512, 0>() == zlines_per_block<512, 1>(),
               "z-pass variants must share the work items");
 

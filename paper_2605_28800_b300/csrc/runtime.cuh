@@ -40,10 +40,10 @@ struct tdgl_ctx {
     std::vector<tdgl_sim *> sims;       // owned: freed by tdgl_ctx_destroy if still alive
     std::vector<tdgl_batch *> batches;
     std::vector<tdgl_unet *> nets;
-    // z-pass radix-schedule autotuning for 256- and 512-point lines: chosen variant (-1 = not
+    // z-pass radix-schedule autotuning for 256-, 512- and 128-point lines (in that index order): chosen variant (-1 = not
     // yet tuned) and the measured microseconds per launch of variants 0 and 1
-    int zvar[2] = {-1, -1};
-    double zus[2][TDGL_ZPASS_VARIANTS] = {};
+    int zvar[3] = {-1, -1, -1};
+    double zus[3][TDGL_ZPASS_VARIANTS] = {};
 };
 
 namespace tdgl_rt {

@@ -623,10 +623,10 @@ void ypass(const Group &g, const SimDev *d, cudaStream_t st) {
     }
 }
 
-int zvar_index(int N) { return N == 256 ? 0 : (N == 512 ? 1 : -1); }
+int zvar_index(int N) { return N == 256 ? 0 : (N == 512 ? 1 : (N == 128 ? 2 : -1)); }
 // radix-schedule variants of the z pass per length: 256 has three (V = 2 stages the tensor rows),
 // 512 two (its staged tile would not fit beside the spectra)
-int zvar_count(int N) { return N == 256 ? 3 : (N == 512 ? 2 : 0); }
+int zvar_count(int N) { return (N == 128 || N == 256) ? 3 : (N == 512 ? 2 : 0); }
 
 template <int N, int V>
 void zpass_v(const Group &g, const SimDev *d, cudaStream_t st) {
@@ -636,7 +636,7 @@ void zpass_v(const Group &g, const SimDev *d, cudaStream_t st) {
 // variant v of the z pass for LEN-point lines (a template, so the lengths without variants
 // instantiate only variant 0)
 template <int LEN> void zpass_len(int v, const Group &g, const SimDev *d, cudaStream_t st) {
-    if constexpr (LEN == 256) {
+    if constexpr (LEN == 128 || LEN == 256) {
         if (v == 2) zpass_v<LEN, 2>(g, d, st);
         else if (v == 1) zpass_v<LEN, 1>(g, d, st);
         else zpass_v<LEN, 0>(g, d, st);
@@ -649,8 +649,9 @@ template <int LEN> void zpass_len(int v, const Group &g, const SimDev *d, cudaSt
 }
 template <int LEN> void zpass_attrs(int smem) {
     cudaFuncSetAttribute(k_zpass<LEN, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if constexpr (LEN == 256 || LEN == 512) cudaFuncSetAttribute(k_zpass<LEN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if constexpr (LEN == 256) cudaFuncSetAttribute(k_zpass<LEN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if constexpr (LEN == 128 || LEN == 256 || LEN == 512)
+        cudaFuncSetAttribute(k_zpass<LEN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if constexpr (LEN == 128 || LEN == 256) cudaFuncSetAttribute(k_zpass<LEN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 // the z pass of one group with the context's radix-schedule variant (forced >= 0, else tuned)
@@ -1273,7 +1274,7 @@ int tdgl_set_integrator(tdgl_sim *s, int method) {
 
 int tdgl_zpass_variant(tdgl_ctx *ctx, int length, int *variant, double *us) {
     const int vi = zvar_index(length);
-    if (!ctx || !variant || vi < 0) return ctx ? fail(ctx, TDGL_EINVAL, "z-pass variants exist for 256 and 512") : TDGL_EINVAL;
+    if (!ctx || !variant || vi < 0) return ctx ? fail(ctx, TDGL_EINVAL, "z-pass variants exist for 128, 256 and 512") : TDGL_EINVAL;
     *variant = ctx->zvar[vi];
     if (us)
         for (int v = 0; v < kZVariants; ++v) us[v] = ctx->zus[vi][v];

@@ -243,32 +243,34 @@ def test_launch_counter_counts_kernels(ctx):
     assert ctx.launch_count - n0 == 10 * 4
 
 
-def test_zpass_autotuner_picks_a_variant_and_every_variant_agrees_with_the_oracle():
-    # 16 x 16 x 128 pads z to 256 points: the context times the three variants of the z pass on
-    # first use and keeps the fastest; forcing any of them gives the same trajectory as the oracle
+@pytest.mark.parametrize("nz,length", [(128, 256), (64, 128)])
+def test_zpass_autotuner_picks_a_variant_and_every_variant_agrees_with_the_oracle(nz, length):
+    # 16 x 16 x 128 pads z to 256 points, 16 x 16 x 64 to 128: the context times the three
+    # variants of the z pass on first use and keeps the fastest; forcing any of them gives the
+    # same trajectory as the oracle
     from paper_2605_28800_b300 import tdgl
     from tests.helpers import mixed_case
     CELL = (1e-9, 1.1e-9, 0.9e-9)
     MATS = {1: synth.BTO, 2: dict(synth.PTO, G12=3e-11, G44=7e-11, G44p=2e-11)}
-    shape = (16, 16, 128)
+    shape = (16, 16, nz)
     mat, P = mixed_case(shape, seed=41)
     P *= 0.3
     dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
     ctx = tdgl.Context(0)
     try:
-        assert ctx.zpass_variant(256)[0] == -1
+        assert ctx.zpass_variant(length)[0] == -1
         finals = []
         for forced in (None, 0, 1, 2):
             g = gpu_sim(ctx, shape, CELL, mat, MATS, 300.0, 45.0, P=P)
             if forced is not None:
-                ctx.set_zpass_variant(256, forced)
+                ctx.set_zpass_variant(length, forced)
             g.step(3, dt)
             if forced is None:
-                v, us = ctx.zpass_variant(256)
+                v, us = ctx.zpass_variant(length)
                 assert len(us) == tdgl.ZPASS_VARIANTS == 3
                 assert v in (0, 1, 2) and min(us) > 0 and us[v] == min(us)
             else:
-                assert ctx.zpass_variant(256)[0] == forced
+                assert ctx.zpass_variant(length)[0] == forced
             finals.append(g.get_P())
             g.close()
         o = oracle_sys(shape, CELL, mat, MATS, 300.0, 45.0)
@@ -276,9 +278,9 @@ def test_zpass_autotuner_picks_a_variant_and_every_variant_agrees_with_the_oracl
         for Pg in finals:
             assert np.abs(Pg - Po).max() / 0.2649096 <= 1e-5
         with pytest.raises(tdgl.TdglError):
-            ctx.set_zpass_variant(128, 1)
+            ctx.set_zpass_variant(64, 1)           # 64-point lines have one shape
         with pytest.raises(tdgl.TdglError):
-            ctx.set_zpass_variant(512, 2)          # the staged variant exists for 256 only
+            ctx.set_zpass_variant(512, 2)          # the staged variant exists for 128 and 256 only
         ctx.set_zpass_variant(512, 1)
     finally:
         ctx.close()
