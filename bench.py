@@ -76,6 +76,19 @@ def padded(n, even):
     return best
 
 
+def kernel_flops(shape):
+    """Nominal FP32 flops per launch of the transform kernels: 5 N log2 N per complex transform of N
+    points (the usual count; the zero padding the kernels skip is not subtracted) and, in the z
+    pass, 36 per wavevector for the 3x3 real-by-complex multiply and the scale."""
+    import math
+    nx, ny, nz = shape
+    Mx, My, Mz = padded(2 * nx - 1, True), padded(2 * ny - 1, False), padded(2 * nz - 1, False)
+    Kx = Mx // 2 + 1
+    fft = lambda n: 5.0 * n * math.log2(n)
+    y = 3 * nz * Kx * fft(My)
+    return {"k_yfwd": y, "k_yinv": y, "k_zconv": Kx * My * (6 * fft(Mz) + 36.0 * Mz)}
+
+
 def kernel_bytes(shape):
     """Algorithmic bytes per launch of each kernel of one step: what each kernel of this four-kernel
     decomposition must read and write at minimum (P and materials, the x- and y-padded spectra, the
@@ -261,7 +274,8 @@ def gpu_arm(args, rank, world):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, "cuda")
     zvar = {n: ctx.zpass_variant(n) for n in (128, 256, 512)}
-    return dict(ms=ms, launches=launches, prof=prof, clocks=clk.summary(), ncell=ncell, wl=wl, warm=warm,
+    fma_peak = ctx.fp32_fma_peak()      # after the timed region
+    return dict(ms=ms, launches=launches, prof=prof, clocks=clk.summary(), ncell=ncell, wl=wl, warm=warm, fma=fma_peak,
                 e2e=aggregate_rate(ncell * e2e_steps, world, e2e_s), e2e_h2d=Ph.numel() * 4,
                 zpass_tuning={str(n): {"variant": v, "us": [round(u, 2) for u in us]}
                               for n, (v, us) in zvar.items() if v >= 0})
@@ -578,7 +592,7 @@ def main():
     prof = {k: v for k, v in r["prof"].items() if k in kb and v[1] > 0}
     dom = max(prof, key=lambda k: prof[k][0]) if prof else None
     total_prof = sum(v[0] for v in r["prof"].values()) or 1.0
-    roof = None
+    roof = alu_roof = None
     if dom:
         avg_ms = prof[dom][0] / prof[dom][1]
         ach = kb[dom] / (avg_ms * 1e-3) / 1e9
@@ -586,6 +600,14 @@ def main():
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "peak_kind": peak_kind, "traffic": tr, "alg_bytes_per_launch": kb[dom],
                 "avg_launch_ms": avg_ms}
+        kf = kernel_flops(wl["shape"])
+        if dom in kf:
+            af = kf[dom] / (avg_ms * 1e-3) / 1e12
+            nominal = 148 * 128 * 2 * r["clocks"].get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+            alu_roof = {"bound": "alu", "kernel": dom, "achieved": af, "peak": r["fma"], "unit": "TFLOP/s",
+                        "frac": af / r["fma"], "peak_kind": "measured FP32 FMA throughput (tdgl_fp32_fma_peak)",
+                        "nominal_peak": nominal, "flops_per_launch": kf[dom],
+                        "flop_count": "5 N log2 N per complex transform, 36 per wavevector for the 3x3 multiply"}
     kernels = {k: {"ms_total": v[0], "launches": v[1], "share": v[0] / total_prof,
                    "GBps": (kb[k] / (v[0] / v[1] * 1e-3) / 1e9) if (k in kb and v[1]) else None}
                for k, v in r["prof"].items() if v[1]}
@@ -593,7 +615,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
             "hbm_frac_of_fused_floor": value / world * B_ALG_FUSED / (hbm * 1e9),
-            "fft_pad": list(M), "zpass_tuning": r["zpass_tuning"], "roofline": roof, "kernels": kernels,
+            "fft_pad": list(M), "zpass_tuning": r["zpass_tuning"], "roofline": roof, "alu_roofline": alu_roof,
+            "kernels": kernels,
             "clocks": r["clocks"], "gpu_launches": r["launches"], "warmup_steps_run": r["warm"],
             "timing": "timed steps replay the library's step graphs (profiling off); per-kernel times "
                       "come from a separate pass with CUDA events around each launch",

@@ -264,6 +264,14 @@ int tdgl_elec_field_static(int nx, int ny, int nz, double dx, double dy, double 
 int tdgl_profile(tdgl_ctx *ctx, int enable);
 int tdgl_profile_read(tdgl_ctx *ctx, int kind, double *total_ms, long *launches);
 
+/* Measurement helper (it computes nothing of the paper's method): the device's FP32 fused
+ * multiply-add throughput, the denominator of the FP32-ALU roofline of the transform kernels.  One
+ * launch of 8 independent FMA chains per thread on every SM (a warm-up launch, then three timed with
+ * CUDA events on the context's stream); *tflops receives 2 flops per FMA over the mean launch time,
+ * in TFLOP/s.  Uses a 4-byte device buffer that it allocates and frees.  Returns TDGL_ECUDA on a
+ * CUDA error. */
+int tdgl_fp32_fma_peak(tdgl_ctx *ctx, double *tflops);
+
 /* ---- learned warm start ----------------------------------------------------------------------
  * The relaxation starts from a proposal instead of a random state (a data-driven model trained on
  * solver-made textures, the use Sec. 5 names for the solver): a 3D U-Net maps per-cell inputs (material indicators,

@@ -1080,6 +1080,51 @@ void tdgl_ctx_destroy(tdgl_ctx *ctx) {
 const char *tdgl_last_error(const tdgl_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 long tdgl_launch_count(const tdgl_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+// FP32 FMA throughput probe: 8 independent dependency chains per thread, so every SM sub-partition
+// has independent FMAs to issue each cycle; the result is stored only if it equals a value it never
+// takes, which keeps the chains from being removed
+__global__ void __launch_bounds__(256) k_fma_peak(float *sink, int iters, float b, float c) {
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (float)(threadIdx.x + k) * 1e-3f;
+#pragma unroll 8
+    for (int i = 0; i < iters; ++i) {   // unrolled: loop control is a few instructions per 64 FMAs
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], b, c);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == -1.2345f) sink[0] = s;
+}
+
+int tdgl_fp32_fma_peak(tdgl_ctx *ctx, double *tflops) {
+    if (!ctx || !tflops) return TDGL_EINVAL;
+    ctx_set(ctx);
+    float *sink = nullptr;
+    CK(ctx, cudaMalloc(&sink, sizeof(float)));
+    const int blocks = ctx->nsm * 8, threads = 256, iters = 1 << 14;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // b slightly below 1 and c small keep the chains finite
+    k_fma_peak<<<blocks, threads, 0, ctx->stream>>>(sink, iters, 0.999999f, 1e-7f);
+    cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < 3; ++r) k_fma_peak<<<blocks, threads, 0, ctx->stream>>>(sink, iters, 0.999999f, 1e-7f);
+    cudaEventRecord(e1, ctx->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    CK(ctx, e);
+    CK(ctx, cudaGetLastError());
+    const double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+    *tflops = flops / (ms / 3.0 * 1e-3) / 1e12;
+    return TDGL_OK;
+}
+
 int tdgl_sim_create(tdgl_ctx *ctx, int nx, int ny, int nz, double dx, double dy, double dz, tdgl_sim **out) {
     if (!ctx || !out) return TDGL_EINVAL;
     *out = nullptr;

@@ -68,6 +68,7 @@ _SIGS = {
     "tdgl_set_adaptive": (_I, [_VP, _D, _D, _D]),
     "tdgl_get_dt": (_I, [_VP, ctypes.POINTER(_D)]),
     "tdgl_zpass_variant": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "tdgl_fp32_fma_peak": (_I, [_VP, ctypes.POINTER(_D)]),
     "tdgl_set_zpass_variant": (_I, [_VP, _I, _I]),
     "tdgl_set_time": (_I, [_VP, _D]),
     "tdgl_get_time": (_I, [_VP, ctypes.POINTER(_D)]),
@@ -163,6 +164,12 @@ class Context:
         v, us = _I(), (_D * ZPASS_VARIANTS)()
         self.check(self.lib.tdgl_zpass_variant(self.h, int(length), ctypes.byref(v), us))
         return v.value, tuple(us)
+
+    def fp32_fma_peak(self) -> float:
+        """measured FP32 fused multiply-add throughput of the device, TFLOP/s"""
+        v = _D()
+        self.check(self.lib.tdgl_fp32_fma_peak(self.h, ctypes.byref(v)))
+        return v.value
 
     def set_zpass_variant(self, length, variant):
         self.check(self.lib.tdgl_set_zpass_variant(self.h, int(length), int(variant)))

@@ -284,3 +284,12 @@ def test_zpass_autotuner_picks_a_variant_and_every_variant_agrees_with_the_oracl
         ctx.set_zpass_variant(512, 1)
     finally:
         ctx.close()
+
+
+def test_fp32_fma_peak_is_plausible(ctx):
+    # the probe reports between a tenth and 1.1 times the nominal FP32 rate of the device
+    import torch
+    p = torch.cuda.get_device_properties(0)
+    nominal = p.multi_processor_count * 128 * 2 * 2.2e9 / 1e12       # 128 FP32 lanes per SM, <= 2.2 GHz
+    v = ctx.fp32_fma_peak()
+    assert 0.1 * nominal < v < 1.1 * nominal, (v, nominal)
