@@ -400,6 +400,41 @@ def warm_start(args):
                       "workload": "pto_sto_bilayer_64x64x32_config5", **rep}))
 
 
+def hysteresis(args):
+    """The DC field loop of the bilayer workload (256x256x64 PbTiO3 on SrTiO3, 81 out-of-plane field
+    points from +200 to -200 MV/m and back): at each point the state relaxes from the previous one
+    to the tolerance or at most --loop-steps steps.  Reports the loop time (relaxations only, and
+    with the per-point readback of P), the steps and the mean P_z of the PbTiO3 layers per point."""
+    import torch
+    from paper_2605_28800_b300 import tdgl
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    ctx = tdgl.Context(dev)
+    wl = workload("pto_sto_bilayer_256x256x64")
+    s, dt = make_sim(ctx, wl)
+    s.energy()                      # one-off tensor build, outside the timed loop
+    pto = wl["mat"] == 1
+    ncell = int(np.prod(wl["shape"]))
+    points, t_relax = [], 0.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for E in synth.CONFIG4["fields"]:
+        s.set_field((0.0, 0.0, E))
+        ta = time.perf_counter()
+        n, ok = s.relax(dt, args.tol, args.loop_steps, CHECK_EVERY, raise_on_cap=False)
+        t_relax += time.perf_counter() - ta
+        P = s.get_P()
+        points.append({"Ez_MV_per_m": E / 1e6, "steps": n, "converged": ok, "mean_Pz_PTO": float(P[2][pto].mean())})
+    wall = time.perf_counter() - t0
+    steps = sum(p["steps"] for p in points)
+    line = {"metric": "DC hysteresis loop time", "unit": "s", "workload": "pto_sto_bilayer_256x256x64",
+            "points": len(points), "tol": args.tol, "max_steps_per_point": args.loop_steps,
+            "relax_seconds": t_relax, "loop_seconds": wall, "total_steps": steps,
+            "cell_updates_per_s": steps * ncell / t_relax, "converged_points": sum(p["converged"] for p in points),
+            "per_point": points}
+    print(json.dumps(line))
+
+
 def padded_from_impulses(K, M):
     """The 3x3 kernel on the zero-padded grid M = (Mx, My, Mz) from its impulse responses K
     [3][3][nz][ny][nx] over offsets r >= 0.  N_ij is odd in coordinate a when exactly one of i, j
@@ -540,11 +575,16 @@ def main():
     ap.add_argument("--zpass-variant", type=int, default=-1,
                     help="force the z-pass variant for 256/512-point lines instead of autotuning (for profiler runs)")
     ap.add_argument("--max-relax-steps", type=int, default=20000)
+    ap.add_argument("--hysteresis", action="store_true",
+                    help="DC field loop of the 256x256x64 bilayer (81 points, relaxed from point to point)")
+    ap.add_argument("--loop-steps", type=int, default=400, help="step cap per field point of --hysteresis")
     ap.add_argument("--cufft-compare", action="store_true",
                     help="electrostatic field of the bench cube: this library vs a cuFFT (torch.fft) convolution")
     args = ap.parse_args()
     if args.cufft_compare:
         return cufft_compare(args)
+    if args.hysteresis:
+        return hysteresis(args)
     if args.relax_compare:
         return relax_compare(args)
     if args.temperature_sweep:
