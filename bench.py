@@ -435,6 +435,44 @@ def hysteresis(args):
     print(json.dumps(line))
 
 
+def ensemble(args):
+    """Landau-only ensemble (Sec. 4.2, Fig. 2(c)): at each temperature 1500 independent BaTiO3 cells
+    start from random orientations (|P| uniform in 0.5..1.5e-3 C/m^2, seeded) and relax under the
+    Landau term alone to max|dP|/P0 < 1e-7 per step; reports the phase counts (C: |P| < 0.01 C/m^2;
+    T, O, R: one, two or three components above 1 % of the largest) and the time per temperature."""
+    import torch
+    from paper_2605_28800_b300 import tdgl
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    ctx = tdgl.Context(dev)
+    n, shape = 1500, (50, 30, 1)
+    rows = []
+    for T in range(10, 451, 10):
+        rng = np.random.default_rng(T + 7)
+        d = rng.normal(size=(3, n))
+        d /= np.linalg.norm(d, axis=0)
+        P = (d * rng.uniform(0.5e-3, 1.5e-3, n)).astype(np.float32).reshape(3, 1, 30, 50)
+        s = tdgl.Sim(ctx, shape, (1e-9,) * 3)
+        s.define_material(1, synth.BTO)
+        s.set_material_map(np.ones((1, 30, 50), np.uint8))
+        s.set_temperature(float(T))
+        s.set_terms(tdgl.TERM_LANDAU)
+        s.set_P(P)
+        dt = 0.01 / s.scales()[1]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        steps, ok = s.relax(dt, 1e-7, 400000, 64, raise_on_cap=False)
+        el = time.perf_counter() - t0
+        a = np.sort(np.abs(s.get_P().reshape(3, -1)), axis=0)[::-1]
+        phase = np.where(a[0] < 0.01, "C", np.where(a[1] < 1e-2 * a[0], "T", np.where(a[2] < 1e-2 * a[0], "O", "R")))
+        rows.append({"T_K": T, "steps": int(steps), "converged": bool(ok), "seconds": el,
+                     **{"n_" + ph: int((phase == ph).sum()) for ph in "CTOR"}})
+        s.close()
+    line = {"metric": "Landau-only ensemble: phase counts per temperature", "workload": "bto_single_cells_1500",
+            "starts_per_T": n, "tol": 1e-7, "total_seconds": sum(r["seconds"] for r in rows), "per_T": rows}
+    print(json.dumps(line))
+
+
 def padded_from_impulses(K, M):
     """The 3x3 kernel on the zero-padded grid M = (Mx, My, Mz) from its impulse responses K
     [3][3][nz][ny][nx] over offsets r >= 0.  N_ij is odd in coordinate a when exactly one of i, j
@@ -575,6 +613,8 @@ def main():
     ap.add_argument("--zpass-variant", type=int, default=-1,
                     help="force the z-pass variant for 256/512-point lines instead of autotuning (for profiler runs)")
     ap.add_argument("--max-relax-steps", type=int, default=20000)
+    ap.add_argument("--ensemble", action="store_true",
+                    help="Landau-only ensemble: 1500 random single-cell starts per temperature, phase counts")
     ap.add_argument("--hysteresis", action="store_true",
                     help="DC field loop of the 256x256x64 bilayer (81 points, relaxed from point to point)")
     ap.add_argument("--loop-steps", type=int, default=400, help="step cap per field point of --hysteresis")
@@ -585,6 +625,8 @@ def main():
         return cufft_compare(args)
     if args.hysteresis:
         return hysteresis(args)
+    if args.ensemble:
+        return ensemble(args)
     if args.relax_compare:
         return relax_compare(args)
     if args.temperature_sweep:
