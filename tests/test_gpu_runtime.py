@@ -212,6 +212,32 @@ def test_device_relax_loop_matches_the_host_checked_loop(ctx, integ, shape):
         assert t0 == t1
 
 
+def test_relax_after_an_energy_call_matches_the_host_checked_loop(ctx):
+    # an energy call leaves the field spectrum of the current P; relax then runs its first chunk
+    # host-checked (using that spectrum) and the rest in the device loop: same steps, same bits as
+    # checking on the host throughout, across several relax / energy rounds
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    runs = []
+    for host in (False, True):
+        s, _ = _bto(ctx, (16, 16, 16), seed=29)
+        ctx.profile(host)
+        try:
+            out = []
+            for _ in range(3):
+                e = s.energy()
+                n, ok = s.relax(dt, 1e-12, 48, check_every=16, raise_on_cap=False)
+                out.append((n, ok, e["total"]))
+            out.append(s.get_P())
+        finally:
+            ctx.profile(False)
+        runs.append(out)
+        s.close()
+    for a, b in zip(runs[0][:-1], runs[1][:-1]):
+        assert a[:2] == b[:2]
+        assert a[2] == pytest.approx(b[2], rel=1e-12)     # float64 block sums added in any order
+    assert np.array_equal(runs[0][-1], runs[1][-1])
+
+
 def test_device_relax_loop_reports_divergence(ctx):
     from paper_2605_28800_b300 import tdgl
     s, _ = _bto(ctx, (6, 6, 6))
