@@ -473,6 +473,38 @@ def ensemble(args):
     print(json.dumps(line))
 
 
+def size_sweep(args):
+    """Step time of single sims of several sizes run alone (BaTiO3 at 250 K, all four terms): each
+    relaxes with tolerance 1e-30 (so every step runs) in the device relaxation loop, after 32
+    warm-up steps; microseconds per step = wall time of the relax call / steps."""
+    import torch
+    from paper_2605_28800_b300 import tdgl
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    ctx = tdgl.Context(dev)
+    rows = []
+    for shape in [(32, 32, 8), (32, 32, 32), (64, 64, 64), (96, 96, 96), (128, 128, 128)]:
+        nx, ny, nz = shape
+        s = tdgl.Sim(ctx, shape, (1e-9,) * 3)
+        s.define_material(1, synth.BTO)
+        s.set_material_map(np.ones((nz, ny, nx), np.uint8))
+        s.set_temperature(250.0)
+        s.set_eps_b(45.0)
+        s.set_P(synth.uniform_P(shape, 0.01, 3))
+        s.energy()
+        dt = 0.004 / s.scales()[1]
+        s.relax(dt, 1e-30, 32, CHECK_EVERY, raise_on_cap=False)
+        n = 3000 if nx < 128 else 800
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k, _ = s.relax(dt, 1e-30, n, CHECK_EVERY, raise_on_cap=False)
+        el = time.perf_counter() - t0
+        rows.append({"grid": list(shape), "steps": int(k), "us_per_step": 1e6 * el / k,
+                     "cell_updates_per_s": nx * ny * nz * k / el})
+        s.close()
+    print(json.dumps({"metric": "step time of single sims run alone", "unit": "us per step", "per_grid": rows}))
+
+
 def padded_from_impulses(K, M):
     """The 3x3 kernel on the zero-padded grid M = (Mx, My, Mz) from its impulse responses K
     [3][3][nz][ny][nx] over offsets r >= 0.  N_ij is odd in coordinate a when exactly one of i, j
@@ -613,6 +645,8 @@ def main():
     ap.add_argument("--zpass-variant", type=int, default=-1,
                     help="force the z-pass variant for 256/512-point lines instead of autotuning (for profiler runs)")
     ap.add_argument("--max-relax-steps", type=int, default=20000)
+    ap.add_argument("--size-sweep", action="store_true",
+                    help="step time of single sims from 32x32x8 to 128^3 run alone (device relaxation loop)")
     ap.add_argument("--ensemble", action="store_true",
                     help="Landau-only ensemble: 1500 random single-cell starts per temperature, phase counts")
     ap.add_argument("--hysteresis", action="store_true",
@@ -627,6 +661,8 @@ def main():
         return hysteresis(args)
     if args.ensemble:
         return ensemble(args)
+    if args.size_sweep:
+        return size_sweep(args)
     if args.relax_compare:
         return relax_compare(args)
     if args.temperature_sweep:
