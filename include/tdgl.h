@@ -225,9 +225,11 @@ int  tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_step
 
 /* ---- field without allocation ------------------------------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that cannot call cudaMalloc:
- * code running while a stream is captured into a CUDA graph (an allocation there is not
- * capturable, and elsewhere it synchronizes the device), plug-ins whose host owns all device
- * memory through its own pool, and real-time loops that must not wait on the allocator.
+ * plug-ins whose host application owns all device memory through its own pool allocator, and
+ * real-time loops that must not wait on the driver's allocator (cudaMalloc can synchronize the
+ * device).  The arithmetic is that of tdgl_get_field with TDGL_TERM_ELEC alone, run through the
+ * library's generic (any-length) kernels; the FP64 tensor spectrum is rebuilt on every call, so a
+ * call costs more GPU time than a tdgl_get_field on a prepared sim.
  *
  * tdgl_elec_field_static computes the open-boundary electrostatic field E_el of P (the same
  * quantity as tdgl_get_field with TDGL_TERM_ELEC) on an nx*ny*nz grid of dx*dy*dz cells:

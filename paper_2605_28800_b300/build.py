@@ -33,12 +33,33 @@ def up_to_date() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc()] + NVCC_FLAGS + ["-o", tmp] + SOURCES
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    tag = f".tmp{os.getpid()}"
+    objs = [os.path.join(HERE, os.path.basename(s) + tag + ".o") for s in SOURCES]
+    compile_flags = [f for f in NVCC_FLAGS if f != "-shared"]
+    procs = []
+    try:
+        # one nvcc per translation unit, in parallel, then one link
+        for s, o in zip(SOURCES, objs):
+            cmd = [nvcc()] + compile_flags + ["-c", "-o", o, s]
+            if verbose:
+                print(" ".join(cmd), file=sys.stderr)
+            procs.append(subprocess.Popen(cmd))
+        for p in procs:
+            if p.wait() != 0:
+                raise subprocess.CalledProcessError(p.returncode, p.args)
+        tmp = LIB + tag
+        cmd = [nvcc(), "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp] + objs
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        subprocess.check_call(cmd)
+        os.replace(tmp, LIB)
+    finally:
+        for p in procs:
+            if p.poll() is None:
+                p.kill()
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

@@ -12,7 +12,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <tuple>
+#include <utility>
 #include <vector>
 
 #include "../../include/tdgl.h"
@@ -1961,13 +1964,14 @@ int tdgl_profile_read(tdgl_ctx *ctx, int kind, double *total_ms, long *launches)
 // =============================================================================================
 // Electrostatic field without any allocation (tdgl_elec_field_static).
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being captured into a
-// CUDA graph (cudaMalloc is not a capturable operation and, outside capture, synchronizes the
-// device), plug-ins whose host application owns every device byte through its own pool, and
-// real-time loops that may not block on the driver's allocator.  For them this entry point
-// computes the open-boundary field of a given P with every intermediate buffer (descriptor,
-// work lists, twiddles, FP64 tensor temporaries, tensor spectrum, x- and y-spectra) carved out
-// of one file-scope device array of fixed size.  It runs the same kernels as tdgl_get_field.
+// Some callers cannot call cudaMalloc: plug-ins whose host application owns every device byte
+// through its own pool allocator, and real-time loops that may not block on the driver's
+// allocator (cudaMalloc can synchronize the device).  For them this entry point computes the
+// open-boundary field of a given P with every intermediate buffer (descriptor, work lists,
+// twiddles, FP64 tensor temporaries, tensor spectrum, x- and y-spectra) carved out of one
+// file-scope device array of fixed size.  The arithmetic is that of tdgl_get_field with the
+// electrostatic term alone, but through the generic (any-length) row, y and z kernels, and the
+// FP64 tensor spectrum is rebuilt on every call, since nothing survives between calls.
 // =============================================================================================
 namespace {
 
@@ -1975,6 +1979,20 @@ static __device__ __align__(256) unsigned char g_static_scratch[TDGL_STATIC_SCRA
 
 const int kMaxDevices = 64;
 void *g_static_ptr[kMaxDevices] = {nullptr};   // device address of g_static_scratch, per device
+std::mutex g_static_setup;                      // guards the once-per-device set-up below
+
+// Launch k<<<g, b, sm, st>>>(a...) and return the launch's own status (unlike cudaGetLastError,
+// this neither reports nor clears an error that the caller left pending).
+template <class... KA, class... A>
+cudaError_t launch_status(void (*k)(KA...), dim3 g, dim3 b, size_t sm, cudaStream_t st, A &&...a) {
+    std::tuple<KA...> t(std::forward<A>(a)...);
+    void *args[sizeof...(KA) > 0 ? sizeof...(KA) : 1];
+    std::apply([&](auto &...x) {
+        int i = 0;
+        ((args[i++] = static_cast<void *>(&x)), ...);
+    }, t);
+    return cudaLaunchKernel(reinterpret_cast<const void *>(k), g, b, args, sm, st);
+}
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -2061,6 +2079,16 @@ __global__ void k_static_items(int4 *rows, int4 *ys, int4 *zs, StaticPlan q) {
     }
 }
 
+// the kernel descriptor's bytes, passed by value (kernel arguments are copied at launch) and stored
+// on the device by one warp
+struct DescBytes {
+    unsigned long long w[(sizeof(SimDev) + 7) / 8];
+};
+__global__ void k_static_desc(unsigned long long *dst, DescBytes D) {
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < (int)(sizeof(D.w) / 8); i += blockDim.x) dst[i] = D.w[i];
+}
+
 // FFT twiddles W_n^t (float32 from float64 sincospi) and the tensor transform's cos/sin tables
 __global__ void k_static_tables(float2 *tw, double *trig, StaticPlan q) {
     const int ntw = q.hx + q.My + q.Mz + q.hx + 1;
@@ -2101,18 +2129,22 @@ extern "C" int tdgl_elec_field_static(int nx, int ny, int nz, double dx, double 
     if (q.total > (size_t)TDGL_STATIC_SCRATCH_BYTES) return TDGL_ETOOBIG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TDGL_ECUDA;
-    if (!g_static_ptr[dev]) {
+    {
         // once per device, with that device current: device address of the scratch array and
-        // the dynamic shared-memory limits of the kernels used below
-        void *ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) return TDGL_ECUDA;
-        cudaFuncSetAttribute(k_rows<MODE_XFWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-        cudaFuncSetAttribute(k_rows<MODE_FIELD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-        cudaFuncSetAttribute(k_yfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-        cudaFuncSetAttribute(k_yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-        cudaFuncSetAttribute(k_zconv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-        if (cudaGetLastError() != cudaSuccess) return TDGL_ECUDA;
-        g_static_ptr[dev] = ptr;
+        // the dynamic shared-memory limits of the kernels used below (serialized across threads)
+        std::lock_guard<std::mutex> lock(g_static_setup);
+        if (!g_static_ptr[dev]) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) return TDGL_ECUDA;
+            const void *ks[5] = {reinterpret_cast<const void *>(k_rows<MODE_XFWD>),
+                                 reinterpret_cast<const void *>(k_rows<MODE_FIELD>),
+                                 reinterpret_cast<const void *>(k_yfwd), reinterpret_cast<const void *>(k_yinv),
+                                 reinterpret_cast<const void *>(k_zconv)};
+            for (const void *k : ks)
+                if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) != cudaSuccess)
+                    return TDGL_ECUDA;
+            g_static_ptr[dev] = ptr;
+        }
     }
     unsigned char *base = static_cast<unsigned char *>(g_static_ptr[dev]);
     cudaStream_t st = (cudaStream_t)stream;
@@ -2160,29 +2192,41 @@ extern "C" int tdgl_elec_field_static(int nx, int ny, int nz, double dx, double 
         rule.m[k] = ms[k];
         gauss_legendre01(ms[k], rule.tau[k], rule.wt[k]);
     }
-    if (cudaMemcpyAsync(base + q.o_desc, &D, sizeof D, cudaMemcpyHostToDevice, st) != cudaSuccess) return TDGL_ECUDA;
     if (cudaMemsetAsync(base + q.o_coef, 0, sizeof(float) * MAXMAT * NCOEF, st) != cudaSuccess) return TDGL_ECUDA;
     if (!mat && cudaMemsetAsync(base + q.o_mat, 1, (size_t)q.ncell, st) != cudaSuccess) return TDGL_ECUDA;
     const int ntab = q.hx + q.My + q.Mz + q.hx + 1 + q.Mx + q.My + q.Mz;
-    k_static_items<<<grid_for(q.n_rows + q.n_y + q.n_z), 256, 0, st>>>(rows, ys, zs, q);
-    k_static_tables<<<grid_for(ntab), 256, 0, st>>>(reinterpret_cast<float2 *>(base + q.o_tw), trig, q);
-    // tensor spectrum (FP64), lengths in units of the smallest cell edge
-    k_tensor_real<<<grid_for(q.ncell), 256, 0, st>>>(dN, nx, ny, nz, dx / ell, dy / ell, dz / ell, 5.0, 16.0, 40.0, rule);
-    k_tensor_dft<<<grid_for(6 * q.n1), 256, 0, st>>>(dN, dT1, 0, nx, q.Kx, q.Mx, 1, nz * ny, trig, trig + q.Mx);
-    k_tensor_dft<<<grid_for(6 * q.n2), 256, 0, st>>>(dT1, dT2, 1, ny, q.kyh, q.My, q.Kx, nz, trig + 2 * q.Mx,
-                                                      trig + 2 * q.Mx + q.My);
-    k_tensor_dft<<<grid_for(6 * q.n3), 256, 0, st>>>(dT2, dT1, 2, nz, q.kzh, q.Mz, q.kyh * q.Kx, 1,
-                                                      trig + 2 * (q.Mx + q.My), trig + 2 * (q.Mx + q.My) + q.Mz);
-    k_tensor_store<<<grid_for(3L * q.kzh * q.kyh * q.kxp), 256, 0, st>>>(dT1, reinterpret_cast<float2 *>(base + q.o_Nhat),
-                                                                         (long)q.kzh * q.kyh, q.Kx, q.kxp);
-    // x forward, y/z convolution, x inverse into E (the kernels of tdgl_get_field)
+    SimDev *desc_dst = reinterpret_cast<SimDev *>(base + q.o_desc);
+    DescBytes Db;
+    memset(&Db, 0, sizeof Db);
+    memcpy(&Db, &D, sizeof D);
+    float2 *tw_dst = reinterpret_cast<float2 *>(base + q.o_tw);
+    float2 *nhat_dst = reinterpret_cast<float2 *>(base + q.o_Nhat);
+    const dim3 b256(256);
+    // x forward, y/z convolution, x inverse into E (the generic kernels)
     const size_t sm_rows = 2ull * 3 * q.RB * (q.hx + 2) * sizeof(float2);
     const size_t sm_y = 2ull * q.KY * (q.My + 1) * sizeof(float2);
     const size_t sm_z = 2ull * 3 * q.KZ * (q.Mz + 1) * sizeof(float2);
-    k_rows<MODE_XFWD><<<q.n_rows, NTHREADS, sm_rows, st>>>(ddesc, rows, 0);
-    k_yfwd<<<q.n_y, NTHREADS, sm_y, st>>>(ddesc, ys);
-    k_zconv<<<q.n_z, NTHREADS, sm_z, st>>>(ddesc, zs);
-    k_yinv<<<q.n_y, NTHREADS, sm_y, st>>>(ddesc, ys);
-    k_rows<MODE_FIELD><<<q.n_rows, NTHREADS, sm_rows, st>>>(ddesc, rows, 0);
-    return cudaGetLastError() == cudaSuccess ? TDGL_OK : TDGL_ECUDA;
+    const cudaError_t es[] = {
+        launch_status(k_static_desc, dim3(1), dim3(32), 0, st, reinterpret_cast<unsigned long long *>(desc_dst), Db),
+        launch_status(k_static_items, dim3(grid_for(q.n_rows + q.n_y + q.n_z)), b256, 0, st, rows, ys, zs, q),
+        launch_status(k_static_tables, dim3(grid_for(ntab)), b256, 0, st, tw_dst, trig, q),
+        // tensor spectrum (FP64), lengths in units of the smallest cell edge
+        launch_status(k_tensor_real, dim3(grid_for(q.ncell)), b256, 0, st, dN, nx, ny, nz, dx / ell, dy / ell,
+                      dz / ell, 5.0, 16.0, 40.0, rule),
+        launch_status(k_tensor_dft, dim3(grid_for(6 * q.n1)), b256, 0, st, dN, dT1, 0, nx, q.Kx, q.Mx, 1, nz * ny,
+                      trig, trig + q.Mx),
+        launch_status(k_tensor_dft, dim3(grid_for(6 * q.n2)), b256, 0, st, dT1, dT2, 1, ny, q.kyh, q.My, q.Kx, nz,
+                      trig + 2 * q.Mx, trig + 2 * q.Mx + q.My),
+        launch_status(k_tensor_dft, dim3(grid_for(6 * q.n3)), b256, 0, st, dT2, dT1, 2, nz, q.kzh, q.Mz,
+                      q.kyh * q.Kx, 1, trig + 2 * (q.Mx + q.My), trig + 2 * (q.Mx + q.My) + q.Mz),
+        launch_status(k_tensor_store, dim3(grid_for(3L * q.kzh * q.kyh * q.kxp)), b256, 0, st, dT1, nhat_dst,
+                      (long)q.kzh * q.kyh, q.Kx, q.kxp),
+        launch_status(k_rows<MODE_XFWD>, dim3(q.n_rows), dim3(NTHREADS), sm_rows, st, ddesc, rows, 0),
+        launch_status(k_yfwd, dim3(q.n_y), dim3(NTHREADS), sm_y, st, ddesc, ys),
+        launch_status(k_zconv, dim3(q.n_z), dim3(NTHREADS), sm_z, st, ddesc, zs),
+        launch_status(k_yinv, dim3(q.n_y), dim3(NTHREADS), sm_y, st, ddesc, ys),
+        launch_status(k_rows<MODE_FIELD>, dim3(q.n_rows), dim3(NTHREADS), sm_rows, st, ddesc, rows, 0)};
+    for (cudaError_t e : es)
+        if (e != cudaSuccess) return TDGL_ECUDA;
+    return TDGL_OK;
 }

@@ -8,7 +8,7 @@ judges the proposal: steps, final free energy and texture against the relaxation
 start, with the random start kept whenever the proposal does not save steps.
 
 Everything numeric runs in libtdgl's kernels; this module only builds inputs, batches the calls
-and keeps the books.
+and keeps the books.  The caller supplies the (T, Ez, thickness) points and the random starts.
 """
 from __future__ import annotations
 
@@ -16,8 +16,8 @@ import time
 
 import numpy as np
 
-import synth
 from . import tdgl
+from .materials import PTO, STO
 
 #: scale of the network's output: the spontaneous polarization of PbTiO3 at 300 K (C/m^2)
 P_SCALE = 0.7583600
@@ -26,11 +26,19 @@ E_HALF = 1.5e8
 N_IN, N_OUT = 4, 3
 
 
+def bilayer_map(shape, t_pto) -> np.ndarray:
+    """uint8 material map (nz, ny, nx): SrTiO3 (id 2) below, PbTiO3 (id 1) in the top t_pto layers."""
+    nx, ny, nz = shape
+    m = np.full((nz, ny, nx), 2, np.uint8)
+    m[nz - t_pto:] = 1
+    return m
+
+
 def features(shape, point) -> np.ndarray:
     """Network input (4, nz, ny, nx): PbTiO3 and SrTiO3 indicators, (T - 300 K) / 50 K,
     Ez / 150 MV/m."""
     nx, ny, nz = shape
-    m = synth.bilayer_map(shape, point["t_pto"])
+    m = bilayer_map(shape, point["t_pto"])
     f = np.empty((N_IN, nz, ny, nx), np.float32)
     f[0] = m == 1
     f[1] = m == 2
@@ -41,18 +49,14 @@ def features(shape, point) -> np.ndarray:
 
 def make_sim(ctx, shape, cell, point, eps_b, P):
     s = tdgl.Sim(ctx, shape, cell)
-    s.define_material(1, synth.PTO)
-    s.define_material(2, synth.STO)
-    s.set_material_map(synth.bilayer_map(shape, point["t_pto"]))
+    s.define_material(1, PTO)
+    s.define_material(2, STO)
+    s.set_material_map(bilayer_map(shape, point["t_pto"]))
     s.set_eps_b(eps_b)
     s.set_temperature(point["T"])
     s.set_field((0.0, 0.0, point["Ez"]))
     s.set_P(P)
     return s
-
-
-def random_start(shape, point, amp):
-    return synth.uniform_P(shape, amp, point["seed"])
 
 
 def relax_points(ctx, cfg, points, starts, max_steps, chunk=64, sequential=False):
@@ -148,14 +152,19 @@ def texture_distance(Pa, Pb):
     return float(np.sqrt(np.mean((Pa - Pb) ** 2)) / max(np.sqrt(np.mean(Pb ** 2)), 1e-30))
 
 
-def run(ctx, cfg, n_train, n_test, epochs, max_steps, batch=4, lr=2e-3, chans=(16, 32, 64, 128), log=print):
-    """The whole protocol on CONFIG5-style points: generate, train, judge.  Returns a report dict."""
+def run(ctx, cfg, points, random_start, n_train, n_test, epochs, max_steps, batch=4, lr=2e-3,
+        chans=(16, 32, 64, 128), log=print):
+    """The whole protocol: generate, train, judge.  cfg: shape, cell, eps_b, dt_star, tol, seed;
+    points: at least n_train + n_test dicts with T, Ez, t_pto (PbTiO3 layers on top); random_start
+    (shape, point) -> the float32 (3, nz, ny, nx) random start of a point.  The first n_train points
+    train, the next n_test are held out.  Returns a report dict."""
     log = log or (lambda m: None)
     shape = cfg["shape"]
-    pts = synth.bilayer_points(n_train + n_test, cfg["seed"], cfg["T"], cfg["Ez"], cfg["ratio"], shape[2])
-    train_pts, test_pts = pts[:n_train], pts[n_train:]
+    if len(points) < n_train + n_test:
+        raise ValueError("fewer points than n_train + n_test")
+    train_pts, test_pts = points[:n_train], points[n_train:n_train + n_test]
     t0 = time.perf_counter()
-    P_tr, st_tr, cv_tr, _ = relax_points(ctx, cfg, train_pts, [random_start(shape, p, cfg["amp"]) for p in train_pts],
+    P_tr, st_tr, cv_tr, _ = relax_points(ctx, cfg, train_pts, [random_start(shape, p) for p in train_pts],
                                          max_steps)
     t_gen = time.perf_counter() - t0
     log(f"generated {n_train} relaxed textures in {t_gen:.1f} s (median {np.median(st_tr):.0f} steps, "
@@ -168,7 +177,7 @@ def run(ctx, cfg, n_train, n_test, epochs, max_steps, batch=4, lr=2e-3, chans=(1
     t_train = time.perf_counter() - t0
     # judge on held-out points at the same tolerance and dt: plain (each sim alone, random start),
     # batched (random start) and batched from the network's proposals
-    rnd = [random_start(shape, p, cfg["amp"]) for p in test_pts]
+    rnd = [random_start(shape, p) for p in test_pts]
     t0 = time.perf_counter()
     P_seq, st_seq, cv_seq, F_seq = relax_points(ctx, cfg, test_pts, rnd, max_steps, sequential=True)
     t_seq = time.perf_counter() - t0

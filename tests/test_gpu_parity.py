@@ -16,7 +16,10 @@ pytestmark = pytest.mark.gpu
 
 CELL = (1e-9, 1.1e-9, 0.9e-9)
 MATS = {1: synth.BTO, 2: dict(synth.PTO, G12=3e-11, G44=7e-11, G44p=2e-11, r_s=1.3)}
-SHAPES = [(1, 1, 1), (1, 1, 6), (5, 1, 1), (3, 5, 7), (8, 8, 4), (17, 9, 5), (32, 32, 8), (24, 12, 20)]
+SHAPES = [(1, 1, 1), (1, 1, 6), (5, 1, 1), (3, 5, 7), (8, 8, 4), (17, 9, 5), (32, 32, 8), (24, 12, 20),
+          # the transform lengths of the uneven sweep's 48^3 and 96^3 members, one axis at a time:
+          # x half-lengths 96 / 48 and y lengths 96 / 192, z lengths 96 / 192 (radix-3 register FFTs)
+          (96, 48, 8), (48, 96, 8), (8, 8, 48), (8, 8, 96)]
 
 
 @pytest.fixture(scope="module")
@@ -148,11 +151,13 @@ def _sample_cells(shape, n, seed):
     return corners + rand
 
 
-@pytest.mark.parametrize("workload", ["bto_cube_128", "pto_sto_bilayer_256x256x64"])
+@pytest.mark.parametrize("workload", ["bto_cube_128", "pto_sto_bilayer_256x256x64", "bto_cube_48", "bto_cube_64",
+                                      "bto_cube_96"])
 def test_full_size_field_and_step_at_sampled_cells(ctx, workload):
-    if workload == "bto_cube_128":
+    if workload.startswith("bto_cube"):
         c = synth.CONFIG2
-        shape = c["shape"]
+        L = int(workload.rsplit("_", 1)[1])
+        shape = (L, L, L)
         nx, ny, nz = shape
         mat = np.ones((nz, ny, nx), np.uint8)
         mats = {1: c["material"]}

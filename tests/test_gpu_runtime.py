@@ -52,6 +52,38 @@ def test_batch_equals_single_runs_bitwise(ctx, nsteps):
     B.close()
 
 
+def test_batch_members_match_oracle(ctx):
+    # every member of a ragged batch (radix-2 and radix-3 transform lengths, the 48^3 member of the
+    # uneven sweep among them) against the FP64 oracle run of the same sim: 8 batched steps, an
+    # energy call on each member (it leaves the field spectrum for the next step), 8 more steps
+    from paper_2605_28800_b300 import tdgl
+    members = [((16, 16, 16), 300.0, 1.0), ((12, 20, 8), 250.0, 0.8), ((48, 48, 48), 300.0, 1.0),
+               ((96, 24, 8), 200.0, 0.5), ((9, 7, 5), 350.0, 1.2)]
+    a1 = abs(coefficients(synth.BTO, 300.0)["a1x"])
+    sims, starts, dts = [], [], []
+    for i, (sh, T, f) in enumerate(members):
+        nx, ny, nz = sh
+        P = synth.uniform_P(sh, 0.15, 40 + i)
+        sims.append(gpu_sim(ctx, sh, (1e-9,) * 3, np.ones((nz, ny, nx), np.uint8), {1: synth.BTO}, T, 45.0, P=P))
+        starts.append(P)
+        dts.append(0.004 / a1 * f)
+    B = tdgl.Batch(ctx, sims)
+    B.step(8, dts)
+    for s in sims:
+        s.energy()
+    B.step(8, dts)
+    for (sh, T, _), s, P, dt in zip(members, sims, starts, dts):
+        nx, ny, nz = sh
+        o = oracle_sys(sh, (1e-9,) * 3, np.ones((nz, ny, nx), np.uint8), {1: synth.BTO}, T, 45.0)
+        want = o.run(P.astype(np.float64), dt, 16)
+        got = s.get_P()
+        moved = np.abs(want - P).max()
+        err = np.abs(got - want).max()
+        assert err / s.scales()[0] <= 1e-5, (sh, err)
+        assert err <= 1e-3 * moved, (sh, err, moved)
+    B.close()
+
+
 def test_batch_relax_converged_sims_leave_the_work_list(ctx):
     from paper_2605_28800_b300 import tdgl
     sims = []

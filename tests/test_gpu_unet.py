@@ -162,6 +162,30 @@ def test_unet_train_step_matches_oracle_adam(ctx):
     assert np.allclose(np.abs(step[big]), lr, rtol=1e-3)
 
 
+def test_unet_adam_three_steps_match_oracle_adam(ctx):
+    # Adam beyond the first step (bias corrections 1 - b^k at k = 2, 3): each GPU train step is
+    # compared with the oracle's Adam applied to the GPU's own previous parameters and gradient
+    # (the gradient is read with loss_grad first; training is bit-reproducible, so train_step
+    # recomputes the same one), with the oracle's moments accumulated in float64
+    net, p, x, t, levels = small_net(ctx, seed=23)
+    lr = 2e-3
+    prev = net.get_params().astype(np.float64)
+    om = {"w": np.zeros_like(prev)}
+    ov = {"w": np.zeros_like(prev)}
+    for k in (1, 2, 3):
+        _, g = net.loss_grad(x, t)
+        g = g.astype(np.float64)
+        net.train_step(x, t, lr)
+        got = net.get_params().astype(np.float64)
+        want = {"w": prev.copy()}
+        U.adam(want, {"w": g}, om, ov, k, lr)
+        # float32 moments and update: a relative 1e-6 of a step (|step| is of order lr) plus the
+        # rounding of the parameter itself
+        assert np.max(np.abs(got - want["w"])) <= 1e-4 * lr + 1e-6 * np.max(np.abs(prev)), k
+        assert np.max(np.abs(got - prev)) > 0.5 * lr, k
+        prev = got
+
+
 def test_unet_training_reduces_loss(ctx):
     net, p, x, t, levels = small_net(ctx, seed=9)
     t = (0.2 * np.tanh(x[:, :3])).astype(np.float32)

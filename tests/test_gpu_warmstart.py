@@ -12,7 +12,10 @@ def test_warm_start_saves_steps_and_reaches_the_same_state():
     from paper_2605_28800_b300 import tdgl, warmstart
     ctx = tdgl.Context(0)
     try:
-        rep = warmstart.run(ctx, synth.CONFIG5, n_train=512, n_test=32, epochs=12, max_steps=20000, log=None)
+        cfg = synth.CONFIG5
+        pts = synth.bilayer_points(512 + 32, cfg["seed"], cfg["T"], cfg["Ez"], cfg["ratio"], cfg["shape"][2])
+        rep = warmstart.run(ctx, cfg, pts, lambda shape, p: synth.uniform_P(shape, cfg["amp"], p["seed"]),
+                            n_train=512, n_test=32, epochs=12, max_steps=20000, log=None)
     finally:
         ctx.close()
     assert rep["train_losses"][-1] < 0.05 * rep["train_losses"][0]

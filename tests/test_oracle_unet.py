@@ -129,6 +129,49 @@ def test_adam_first_step_closed_form():
     assert np.allclose(p["w"], -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
 
 
+def test_adam_constant_gradient_moves_lr_every_step():
+    # Bias correction makes both moment estimates exact for a stationary gradient (Kingma & Ba,
+    # Sec. 3): with g fixed, m_k = (1 - b1^k) g and v_k = (1 - b2^k) g^2, so m_hat = g, v_hat = g^2
+    # and every step k moves each parameter by lr * g / (|g| + eps).  A wrong exponent in either
+    # correction (k - 1, k + 1, or b^k in place of 1 - b^k) breaks this from step 2 on.
+    g = np.array([0.5, -2.0, 1e-3, 3e-6])
+    p = {"w": np.zeros(4)}
+    m = {"w": np.zeros(4)}
+    v = {"w": np.zeros(4)}
+    lr = 0.01
+    for k in range(1, 8):
+        before = p["w"].copy()
+        U.adam(p, {"w": g}, m, v, k, lr=lr)
+        assert np.allclose(p["w"] - before, -lr * g / (np.abs(g) + 1e-8), rtol=1e-10, atol=0), k
+
+
+def test_adam_is_invariant_to_gradient_scale_without_eps():
+    # with eps = 0 the update m_hat / sqrt(v_hat) is homogeneous of degree 0 in g: scaling every
+    # gradient of a changing sequence by c > 0 leaves the trajectory unchanged
+    rng = np.random.default_rng(3)
+    seq = [rng.normal(size=5) for _ in range(4)]
+    traj = []
+    for c in (1.0, 37.0):
+        p, m, v = {"w": np.ones(5)}, {"w": np.zeros(5)}, {"w": np.zeros(5)}
+        for k, g in enumerate(seq, 1):
+            U.adam(p, {"w": c * g}, m, v, k, lr=0.05, eps=0.0)
+        traj.append(p["w"])
+    assert np.allclose(traj[0], traj[1], rtol=1e-12, atol=1e-14)
+
+
+def test_adam_second_step_sign_reversal_bound():
+    # two steps with g1 = +g then g2 = -g: m_2 = (1 - b1) g (b1 - 1), so m_hat_2 = -(1 - b1) g / (1 + b1)
+    # (since 1 - b1^2 = (1 - b1)(1 + b1)), and v_hat_2 = g^2 (stationary magnitude): the second step
+    # moves by +lr (1 - b1)/(1 + b1) * sign(g), a value fixed by the moment algebra, not by the code
+    g = np.array([0.7, -1.3])
+    b1 = 0.9
+    p, m, v = {"w": np.zeros(2)}, {"w": np.zeros(2)}, {"w": np.zeros(2)}
+    U.adam(p, {"w": g}, m, v, 1, lr=0.1, eps=0.0)
+    before = p["w"].copy()
+    U.adam(p, {"w": -g}, m, v, 2, lr=0.1, eps=0.0)
+    assert np.allclose(p["w"] - before, 0.1 * (1 - b1) / (1 + b1) * np.sign(g), rtol=1e-12, atol=0)
+
+
 def test_training_reduces_loss_on_a_fixed_batch():
     levels, chans = 2, (4, 8)
     p = U.init(2, 3, chans, seed=6)

@@ -1,7 +1,9 @@
-"""The allocation-free field entry point (tdgl_elec_field_static) against tdgl_get_field.
+"""The allocation-free field entry point (tdgl_elec_field_static) against tdgl_get_field and
+against the FP64 oracle's electrostatic field.
 
-tdgl_elec_field_static serves callers that cannot call cudaMalloc (stream capture, host-owned
-device memory pools, real-time loops): its scratch is one static device array.  This file is
+tdgl_elec_field_static serves callers that cannot call cudaMalloc (hosts that own all device
+memory through their own pool allocator, real-time loops that must not wait on the driver's
+allocator): its scratch is one static device array.  This file is
 named to be collected last, so that a run stopping at the first failure has run everything else
 first; it passes alone in a fresh process and after the other tests.
 """
@@ -9,7 +11,7 @@ import numpy as np
 import pytest
 
 import synth
-from tests.helpers import gpu_sim, mixed_case
+from tests.helpers import gpu_sim, mixed_case, oracle_sys
 
 pytestmark = pytest.mark.gpu
 
@@ -39,6 +41,9 @@ def test_static_field_matches_get_field_on_two_calls(ctx, shape, cell, with_map)
     eps_b = 45.0
     ref_sim = gpu_sim(ctx, shape, cell, mat, {1: synth.BTO, 2: synth.PTO}, 300.0, eps_b, P=P)
     ref = ref_sim.get_field(tdgl.TERM_ELEC)
+    want = oracle_sys(shape, cell, mat, {1: synth.BTO, 2: synth.PTO}, 300.0, eps_b).electrostatic_field(
+        P.astype(np.float64))
+    want[:, mat == 0] = 0.0
     Pt = torch.from_numpy(P).cuda()
     mt = torch.from_numpy(mat).cuda() if with_map else None
     for call in range(2):
@@ -50,6 +55,8 @@ def test_static_field_matches_get_field_on_two_calls(ctx, shape, cell, with_map)
         assert np.all(np.isfinite(got)), call
         err = np.abs(got - ref).max() / np.abs(ref).max()
         assert err <= TOL, (call, err)
+        err_o = np.abs(got - want).max() / np.abs(want).max()
+        assert err_o <= TOL, (call, err_o)
 
 
 def test_static_field_rejects_oversized_and_bad_arguments():
