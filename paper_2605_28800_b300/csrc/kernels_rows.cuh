@@ -13,6 +13,8 @@
 // Line (c, r) of the x-transforms is held by T = HX/E threads, thread t holding elements
 // t + T m; the exchange buffer is [line][pos] padded by one slot in 16.
 #pragma once
+#include <type_traits>
+
 #include "fft_reg.cuh"
 #include "kernels.cuh"
 
@@ -125,11 +127,12 @@ __device__ __forceinline__ void tgrad_field(const TV &V, const SimDev &S, const 
                 return V.p(f, 1, py + 1, x + 1) - V.p(f, 1, py - 1, x + 1) - V.p(f, 1, py + 1, x - 1) +
                        V.p(f, 1, py - 1, x - 1);
             };
+            // (P(z+1) - P(z-1)) at x+1 minus the same at x-1, and the y analogue
             auto cxz = [&](int f) {
-                return V.p(f, 2, py, x + 1) - V.p(f, 0, py, x + 1) - V.p(f, 2, py, x - 1) + V.p(f, 0, py, x - 1);
+                return (V.p(f, 2, py, x + 1) - V.p(f, 0, py, x + 1)) - (V.p(f, 2, py, x - 1) - V.p(f, 0, py, x - 1));
             };
             auto cyz = [&](int f) {
-                return V.p(f, 2, py + 1, x) - V.p(f, 0, py + 1, x) - V.p(f, 2, py - 1, x) + V.p(f, 0, py - 1, x);
+                return (V.p(f, 2, py + 1, x) - V.p(f, 0, py + 1, x)) - (V.p(f, 2, py - 1, x) - V.p(f, 0, py - 1, x));
             };
             h[0] = fmaf(wxy, cxy(1), fmaf(wxz, cxz(2), h[0]));
             h[1] = fmaf(wxy, cxy(0), fmaf(wyz, cyz(2), h[1]));
@@ -207,7 +210,7 @@ __device__ __forceinline__ float tgrad_energy(const TV &V, const SimDev &S, cons
 }
 
 template <int MODE, int HX>
-__global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, const int4 *__restrict__ items,
+__global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sims, const int4 *__restrict__ items,
                                                int istep) {
     constexpr int E = rf::Cfg<HX>::E, T = HX / E, LDP = xrows_ldp<HX>();
     constexpr int nx = HX, TYmax = xrows_tile<HX>(), TYH = TYmax + 2, nthr = xrows_threads<HX>();
@@ -217,6 +220,9 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
     __shared__ float2 s_twr[HX + 1];     // W_Mx^k for the real pre/post-processing
     __shared__ double s_red[8];
     __shared__ unsigned s_max;
+    __shared__ unsigned s_bad;           // bit py: tile row py is not all material m0 (or outside)
+    __shared__ unsigned s_bad2;          // bit py: tile row py has a cell inside the grid that is not m0
+    __shared__ unsigned char s_rowidx[2][16];   // the block's bulk rows, then its other rows, in order
     const int4 it = items[blockIdx.x];
     const SimDev &S = sims[it.x];
     const int z = it.y, y0 = it.z, TY = it.w;     // TY rows of this block (<= tile)
@@ -237,25 +243,50 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
     const bool elec = (S.terms & TERM_ELEC) != 0;
     float eext[3];
     ext_field(S, istep, eext);
+    // material tile of planes z-1, z, z+1 (XFWD: z only), rows y0-1 .. y0+TY: 4-byte asynchronous
+    // copies issued now, zero (vacuum) outside the grid, waited for before the cells
+    const unsigned m0x4 = 0x01010101u * (unsigned)__ldg(S.mat + ((long)z * ny + y0) * nx);
+    const int mrow = ((MODE == MODE_XFWD) ? 1 : 3) * TYH;
+    static_assert(nx % 4 == 0, "row length must be a multiple of 4");
+    for (int w = tid; w < mrow * (nx / 4); w += nthr) {
+        const int q = w % (nx / 4), rr = w / (nx / 4);
+        const int py = rr % TYH;
+        const int pz = (MODE == MODE_XFWD) ? 1 : rr / TYH;
+        const int gy = y0 - 1 + py, gz = z - 1 + pz;
+        const bool in = (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && py <= TY + 1;
+        const uint8_t *g = in ? S.mat + ((long)gz * ny + gy) * nx + 4 * q : S.mat;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(Mt + (pz * TYH + py) * nx + 4 * q);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(g), "r"(in ? 4 : 0));
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
     for (int i = tid; i < MAXMAT * NCOEF; i += nthr) s_coef[i] = S.coef[i];
     for (int i = tid; i < HX; i += nthr) s_tw[i] = S.tw[S.px.tw + i];
     for (int i = tid; i <= HX; i += nthr) s_twr[i] = S.tw[S.twr + i];
-    if (tid == 0) s_max = 0u;
+    if (tid == 0) { s_max = 0u; s_bad = 0u; s_bad2 = 0u; }
     // ---- x-inverse of the field spectrum: line l = c*TY + r held by T threads
     const int line = tid / T, t = tid % T;
     const int nlines = 3 * TYmax;
     const int lc = line / TYmax, lr = line % TYmax;
     const bool lok = line < nlines && lr < TY;
     auto xidx = [&](int pos) { return line * LDP + pos + (pos >> 4); };
-    __syncthreads();   // twiddle and coefficient tables
+    // the field spectrum's rows are loaded before the table barrier, so that both latencies overlap
+    float2 xa[(MODE != MODE_XFWD) ? E : 1], xb[(MODE != MODE_XFWD) ? E : 1];
     if (MODE != MODE_XFWD && elec) {
-        float2 v[E];
         const float2 *row = S.X + (((long)lc * nz + z) * ny + y0 + lr) * S.kxp;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int k = t + T * m;
-            float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-            if (lok) { a = row[k]; b = cconj(row[HX - k]); }
+            xa[m] = lok ? row[k] : make_float2(0.f, 0.f);
+            xb[m] = lok ? cconj(row[HX - k]) : make_float2(0.f, 0.f);
+        }
+    }
+    __syncthreads();   // twiddle and coefficient tables
+    if (MODE != MODE_XFWD && elec) {
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int k = t + T * m;
+            const float2 a = xa[m], b = xb[m];
             const float2 w = cconj(s_twr[k]);               // W^{-k}
             const float2 d = cmul(csub(a, b), w);
             v[m] = make_float2(a.x + b.x - d.y, a.y + b.y + d.x);
@@ -273,25 +304,24 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
         }
         __syncthreads();
     }
-    // ---- stage the P / material tile (cells outside the grid: vacuum, P = 0); note whether the
-    // whole tile (all planes and halo rows the cells read) is one material inside the grid: then
-    // every cell with 0 < x < nx - 1 is a bulk cell of the discrete Eq. 4
-    bool uniform = MODE != MODE_XFWD;
-    const unsigned m0x4 = 0x01010101u * (unsigned)__ldg(S.mat + ((long)z * ny + y0) * nx);
+    // ---- stage the P / material tile (cells outside the grid: vacuum, P = 0); note which tile rows
+    // are, in all three planes, inside the grid and of one material m0: a cell with 0 < x < nx - 1
+    // whose own row and the rows on either side are all such rows is a bulk cell of the discrete
+    // Eq. 4 (all 18 neighbours inside the grid and of its own material)
     {
-        const int planes = (MODE == MODE_XFWD) ? 1 : 3;
-        const int nrow = planes * TYH;
-        static_assert(nx % 4 == 0, "row length must be a multiple of 4");
-        for (int w = tid; w < nrow * (nx / 4); w += nthr) {
+        // the material tile has arrived (its copies were issued at the start); rows past this
+        // block's TY + 2 are never read; every other word must be m0 in each byte
+        asm volatile("cp.async.wait_group 0;\n" ::);
+        for (int w = tid; w < mrow * (nx / 4); w += nthr) {
             const int q = w % (nx / 4), rr = w / (nx / 4);
             const int py = rr % TYH;
             const int pz = (MODE == MODE_XFWD) ? 1 : rr / TYH;
-            const int gy = y0 - 1 + py, gz = z - 1 + pz;
-            const bool in = (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && py <= TY + 1;
-            const unsigned v = in ? __ldg(reinterpret_cast<const unsigned *>(S.mat + ((long)gz * ny + gy) * nx) + q) : 0u;
-            reinterpret_cast<unsigned *>(Mt + (pz * TYH + py) * nx)[q] = v;
-            // rows past this block's TY + 2 are never read; every other word must be m0 in each byte
-            if (py <= TY + 1 && v != m0x4) uniform = false;
+            const unsigned v = reinterpret_cast<const unsigned *>(Mt + (pz * TYH + py) * nx)[q];
+            if (MODE != MODE_XFWD && py <= TY + 1 && v != m0x4) {
+                const int gy = y0 - 1 + py, gz = z - 1 + pz;
+                atomicOr(&s_bad, 1u << py);
+                if ((unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz) atomicOr(&s_bad2, 1u << py);
+            }
         }
         // P: the centre plane only (planes z +- 1 are read from global memory by the cells)
         if ((nx & 3) == 0) {   // rows of nx floats: 16-byte vector copies
@@ -315,90 +345,274 @@ __global__ void __launch_bounds__(192) k_xrows(const SimDev *__restrict__ sims, 
             }
         }
     }
-    const bool tile_bulk = __syncthreads_and(uniform && m0x4 != 0u) != 0;
+    __syncthreads();
+    // bit r: row r of the block is a bulk row (rows r - 1, r, r + 1 = tile rows r .. r + 2 all good)
+    const unsigned badrows = s_bad, badrows2 = s_bad2;
+    const unsigned bulk_rows = (m0x4 != 0u && MODE != MODE_XFWD)
+                                   ? ~(badrows | (badrows >> 1) | (badrows >> 2)) & ((1u << TY) - 1u) : 0u;
+    // rows whose cells see only material m0 or the outside of the grid (a superset of the bulk rows)
+    const unsigned box_rows = (m0x4 != 0u && MODE != MODE_XFWD)
+                                  ? ~(badrows2 | (badrows2 >> 1) | (badrows2 >> 2)) & ((1u << TY) - 1u) : 0u;
+    const int m0 = (int)(m0x4 & 0xffu);
+    const unsigned other_rows = ~bulk_rows & ((1u << TY) - 1u);
+    if (tid < TY) {
+        const unsigned below = (1u << tid) - 1u;
+        if ((bulk_rows >> tid) & 1u) s_rowidx[0][__popc(bulk_rows & below)] = (unsigned char)tid;
+        else s_rowidx[1][__popc(other_rows & below)] = (unsigned char)tid;
+    }
+    __syncthreads();
     // ---- cells
     const TileView<nx, TYH> V{Pt, Pc, S.ncell, {((long)(z - 1) * ny + y0 - 1) * nx, ((long)(z + 1) * ny + y0 - 1) * nx}, Mt};
+    // The sim's scalars and material m0's coefficients in registers: the cell loops store to global
+    // memory, after which every field of the descriptor (itself in global memory) would be reloaded.
+    const long ncell = S.ncell;
+    const unsigned terms = S.terms;
+    const bool cross = S.has_cross != 0;
+    const float dtc = S.dt, pmax = S.pmax, oscale = S.out_scale;
+    float *const hbuf = S.hbuf;
+    float *const outp = S.out;
+    float land0[8], gd[3], go[3], wxy = 0.f, wxz = 0.f, wyz = 0.f;
+    const float inv2d[3] = {S.inv_2d[0], S.inv_2d[1], S.inv_2d[2]};
+    const float c10 = s_coef[m0 * NCOEF + 10], c11 = s_coef[m0 * NCOEF + 11];
+    {
+        const float *c0 = s_coef + m0 * NCOEF;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) land0[i] = c0[i];
+        const float i2[3] = {S.inv_d2[0], S.inv_d2[1], S.inv_d2[2]};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) { gd[d] = c0[8] * i2[d]; go[d] = c0[9] * i2[d]; }
+        if (cross) {
+            const float C = c0[10] + c0[11];
+            wxy = C * S.inv_2d[0] * S.inv_2d[1];
+            wxz = C * S.inv_2d[0] * S.inv_2d[2];
+            wyz = C * S.inv_2d[1] * S.inv_2d[2];
+        }
+    }
+    const float *const zlo = Pc + V.row0[0];   // plane z - 1, tile row 0, x 0 (component 0)
+    const float *const zhi = Pc + V.row0[1];   // plane z + 1
     float lmax = 0.f;
     bool bad = false;
     double e_land = 0.0, e_grad = 0.0, e_elec = 0.0, e_ext = 0.0;
-    if (MODE != MODE_XFWD) {
-        for (int w = tid; w < TY * nx; w += nthr) {
-            const int r = w / nx, x = w - r * nx;
-            const int py = r + 1;
-            const long id = ((long)z * ny + y0 + r) * nx + x;
-            const int m = V.m(1, py, x);
-            if (m == 0) {
-                if (mode_updates(MODE)) {
+    // Gradient field of a bulk cell of material m0 (all 18 neighbours inside the grid and of m0):
+    // the discrete Eq. 4 reduces to G (P(+) + P(-) - 2P) / dx^2 per face pair plus
+    // (G12 + G44 - G'44) times the four-corner mixed differences d_e d_f P_f (tgrad_field's bulk form).
+    auto bulk_grad = [&](const int py, const int x, const float *p, float *h) {
+        constexpr int TS = TYH * nx;                  // component stride of the shared tile
+        const float *c = Pt + py * nx + x;            // centre plane, component 0
+        const float *lo = zlo + py * nx + x, *hi = zhi + py * nx + x;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) { Pn[c * S.ncell + id] = 0.f; Eb[(c * TYmax + r) * nx + x] = 0.f; }
-                } else if (MODE == MODE_FIELD) {
+        for (int i = 0; i < 3; ++i) {
+            const float lx = c[i * TS - 1] + c[i * TS + 1] - 2.f * p[i];
+            const float ly = c[i * TS - nx] + c[i * TS + nx] - 2.f * p[i];
+            const float lz = __ldg(lo + i * ncell) + __ldg(hi + i * ncell) - 2.f * p[i];
+            h[i] = fmaf(i == 0 ? gd[0] : go[0], lx, fmaf(i == 1 ? gd[1] : go[1], ly, fmaf(i == 2 ? gd[2] : go[2], lz, h[i])));
+        }
+        if (cross) {
+            // (x+,y+) - (x+,y-) - (x-,y+) + (x-,y-) and the xz / yz analogues
+            auto cxy = [&](int f) {
+                const float *q = c + f * TS;
+                return q[nx + 1] - q[-nx + 1] - q[nx - 1] + q[-nx - 1];
+            };
+            auto cxz = [&](int f) {
+                const float *a = hi + f * ncell, *b = lo + f * ncell;
+                return (__ldg(a + 1) - __ldg(b + 1)) - (__ldg(a - 1) - __ldg(b - 1));
+            };
+            auto cyz = [&](int f) {
+                const float *a = hi + f * ncell, *b = lo + f * ncell;
+                return (__ldg(a + nx) - __ldg(b + nx)) - (__ldg(a - nx) - __ldg(b - nx));
+            };
+            h[0] = fmaf(wxy, cxy(1), fmaf(wxz, cxz(2), h[0]));
+            h[1] = fmaf(wxy, cxy(0), fmaf(wyz, cyz(2), h[1]));
+            h[2] = fmaf(wxz, cxz(0), fmaf(wyz, cyz(1), h[2]));
+        }
+    };
+    // Gradient field of a cell whose neighbours inside the grid are all of material m0 while some
+    // lie outside it (grid faces, edges and corners of a one-material region): the ghost rules of
+    // the discrete Eq. 4 (no face term to the outside; mirror ghosts in the central differences; odd
+    // ghosts for the cross fluxes) with in-grid flags taken from the coordinates instead of the
+    // material tile, and m0's coefficients in registers.  The operations and their order are those
+    // of tgrad_field's general form, so both give the same result bit for bit.
+    auto box_grad = [&](const int py, const int x, const float *pa, float *h) {
+        const int gy = y0 - 1 + py;
+        const bool fin[3][2] = {{x > 0, x < nx - 1}, {gy > 0, gy < ny - 1}, {z > 0, z < nz - 1}};
+        // P_f at offset (dz, dy, dx) from the cell; an offset outside the grid reads the cell itself
+        auto P = [&](int f, int dz, int dy, int dx) -> float {
+            if (dx < 0 && !fin[0][0]) dx = 0;
+            if (dx > 0 && !fin[0][1]) dx = 0;
+            if (dy < 0 && !fin[1][0]) dy = 0;
+            if (dy > 0 && !fin[1][1]) dy = 0;
+            if (dz < 0 && !fin[2][0]) dz = 0;
+            if (dz > 0 && !fin[2][1]) dz = 0;
+            return V.p(f, 1 + dz, py + dy, x + dx);
+        };
+        auto in = [&](int dz, int dy, int dx) {
+            return (dx >= 0 || fin[0][0]) && (dx <= 0 || fin[0][1]) && (dy >= 0 || fin[1][0]) &&
+                   (dy <= 0 || fin[1][1]) && (dz >= 0 || fin[2][0]) && (dz <= 0 || fin[2][1]);
+        };
+        auto off = [](int d, int s, int &dz, int &dy, int &dx) {
+            if (d == 0) dx += s; else if (d == 1) dy += s; else dz += s;
+        };
+        // D_a P_f at offset q (mirror ghosts)
+        auto tc = [&](int qz, int qy, int qx, int a, int f) {
+            const float q0 = P(f, qz, qy, qx);
+            int az = qz, ay = qy, ax = qx, bz = qz, by = qy, bx = qx;
+            off(a, 1, az, ay, ax);
+            off(a, -1, bz, by, bx);
+            const float qp = in(az, ay, ax) ? P(f, az, ay, ax) : q0;
+            const float qm = in(bz, by, bx) ? P(f, bz, by, bx) : q0;
+            return (qp - qm) * inv2d[a];
+        };
+        auto fl = [&](int qz, int qy, int qx, int d, float &Sd, float *T) {
+            float s = 0.f;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) S.out[c * S.ncell + id] = 0.f;
-                } else if (MODE == MODE_DERIV) {
+            for (int j = 0; j < 3; ++j)
+                if (j != d) s += tc(qz, qy, qx, j, j);
+            Sd = c10 * s;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) S.hbuf[c * S.ncell + id] = 0.f;
-                }
-                continue;
+            for (int i = 0; i < 3; ++i) T[i] = (i != d) ? c11 * tc(qz, qy, qx, i, d) : 0.f;
+        };
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+#pragma unroll
+            for (int s = -1; s <= 1; s += 2) {
+                int dz = 0, dy = 0, dx = 0;
+                off(d, s, dz, dy, dx);
+                if (!in(dz, dy, dx)) continue;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) h[i] = fmaf(i == d ? gd[d] : go[d], P(i, dz, dy, dx) - pa[i], h[i]);
             }
-            float p[3], h[3] = {0.f, 0.f, 0.f};
+        }
+        if (!cross) return;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) p[c] = V.p(c, 1, py, x);
-            const float *cm = s_coef + m * NCOEF;
-            if (MODE == MODE_ENERGY) {
-                if (S.terms & TERM_LANDAU) {
-                    const float x2 = p[0] * p[0], y2 = p[1] * p[1], z2 = p[2] * p[2];
-                    const float f = cm[0] * x2 + cm[1] * y2 + cm[2] * z2 + cm[3] * (x2 * x2 + y2 * y2 + z2 * z2) +
-                                    cm[4] * (x2 * y2 + y2 * z2 + z2 * x2) +
-                                    cm[5] * (x2 * x2 * x2 + y2 * y2 * y2 + z2 * z2 * z2) +
-                                    cm[6] * (x2 * x2 * (y2 + z2) + y2 * y2 * (x2 + z2) + z2 * z2 * (x2 + y2)) +
-                                    cm[7] * x2 * y2 * z2;
-                    e_land += (double)f;
-                }
-                if (S.terms & TERM_GRAD) e_grad += (double)tgrad_energy(V, S, s_coef, py, x, m, p);
-                float el = 0.f, ex = 0.f;
+        for (int d = 0; d < 3; ++d) {
+            float Sa, Ta[3], Sp, Tp[3], Sm, Tm[3];
+            fl(0, 0, 0, d, Sa, Ta);
+            int az = 0, ay = 0, ax = 0, bz = 0, by = 0, bx = 0;
+            off(d, 1, az, ay, ax);
+            off(d, -1, bz, by, bx);
+            if (in(az, ay, ax)) fl(az, ay, ax, d, Sp, Tp);
+            else { Sp = -Sa; Tp[0] = -Ta[0]; Tp[1] = -Ta[1]; Tp[2] = -Ta[2]; }
+            if (in(bz, by, bx)) fl(bz, by, bx, d, Sm, Tm);
+            else { Sm = -Sa; Tm[0] = -Ta[0]; Tm[1] = -Ta[1]; Tm[2] = -Ta[2]; }
+            const float w = inv2d[d];
+            h[d] = fmaf(Sp - Sm, w, h[d]);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    if (elec) el = fmaf(-0.5f * Eb[(c * TYmax + r) * nx + x], p[c], el);
-                    if (S.terms & TERM_EXT) ex = fmaf(-eext[c], p[c], ex);
-                }
-                e_elec += (double)el;
-                e_ext += (double)ex;
-                continue;
+            for (int i = 0; i < 3; ++i)
+                if (i != d) h[i] = fmaf(Tp[i] - Tm[i], w, h[i]);
+        }
+    };
+    // the rest of a cell once its Landau and gradient fields are in h: E_el, E_ext, then the mode's
+    // output (field, dP/dt) or update
+    auto finish = [&](const int r, const int x, const float *p, float *h) {
+        const long id = ((long)z * ny + y0 + r) * nx + x;
+        if (elec) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) h[c] += Eb[(c * TYmax + r) * nx + x];
+        }
+        if (terms & TERM_EXT) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) h[c] += eext[c];
+        }
+        if (MODE == MODE_FIELD) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) outp[c * ncell + id] = h[c] * oscale;
+            return;
+        }
+        if (MODE == MODE_DERIV) {   // dP/dt of Eq. 1 (L = 1, normalized) for a multi-stage integrator
+#pragma unroll
+            for (int c = 0; c < 3; ++c) hbuf[c * ncell + id] = h[c];
+            return;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float pn, p0 = p[c];
+            if (MODE == MODE_HEUN2) {
+                p0 = Pn[c * ncell + id];
+                pn = fmaf(0.5f * dtc, hbuf[c * ncell + id] + h[c], p0);
+            } else {
+                pn = fmaf(dtc, h[c], p0);
+                if (MODE == MODE_HEUN1) hbuf[c * ncell + id] = h[c];
             }
-            if (S.terms & TERM_LANDAU) landau_field(p, cm, h);
-            if (S.terms & TERM_GRAD) tgrad_field(V, S, s_coef, py, x, m, p, h, tile_bulk && x > 0 && x < nx - 1);
-            if (elec) {
+            if (MODE != MODE_HEUN1) lmax = fmaxf(lmax, fabsf(pn - p0));
+            bad |= !(fabsf(pn) <= pmax);
+            Pn[c * ncell + id] = pn;
+            Eb[(c * TYmax + r) * nx + x] = pn;      // the cell's own slot: E read above, new P kept
+        }
+    };
+    // one cell (r, x); BULK: known bulk cell of material m0 (no vacuum, ghost or interface rule)
+    auto cell = [&](const int r, const int x, const auto kind_tag) {
+        constexpr int KIND = decltype(kind_tag)::value;   // 0 general, 1 bulk, 2 box boundary
+        constexpr bool BULK = KIND == 1, KNOWN = KIND != 0;
+        const int py = r + 1;
+        const long id = ((long)z * ny + y0 + r) * nx + x;
+        const int m = KNOWN ? m0 : V.m(1, py, x);
+        if (!KNOWN && m == 0) {
+            if (mode_updates(MODE)) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) h[c] += Eb[(c * TYmax + r) * nx + x];
-            }
-            if (S.terms & TERM_EXT) {
+                for (int c = 0; c < 3; ++c) { Pn[c * ncell + id] = 0.f; Eb[(c * TYmax + r) * nx + x] = 0.f; }
+            } else if (MODE == MODE_FIELD) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) h[c] += eext[c];
-            }
-            if (MODE == MODE_FIELD) {
+                for (int c = 0; c < 3; ++c) outp[c * ncell + id] = 0.f;
+            } else if (MODE == MODE_DERIV) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) S.out[c * S.ncell + id] = h[c] * S.out_scale;
-                continue;
+                for (int c = 0; c < 3; ++c) hbuf[c * ncell + id] = 0.f;
             }
-            if (MODE == MODE_DERIV) {   // dP/dt of Eq. 1 (L = 1, normalized) for a multi-stage integrator
+            return;
+        }
+        float p[3], h[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-                for (int c = 0; c < 3; ++c) S.hbuf[c * S.ncell + id] = h[c];
-                continue;
+        for (int c = 0; c < 3; ++c) p[c] = Pt[(c * TYH + py) * nx + x];
+        const float *cm = s_coef + m * NCOEF;
+        if (MODE == MODE_ENERGY) {
+            if (terms & TERM_LANDAU) {
+                const float x2 = p[0] * p[0], y2 = p[1] * p[1], z2 = p[2] * p[2];
+                const float f = cm[0] * x2 + cm[1] * y2 + cm[2] * z2 + cm[3] * (x2 * x2 + y2 * y2 + z2 * z2) +
+                                cm[4] * (x2 * y2 + y2 * z2 + z2 * x2) +
+                                cm[5] * (x2 * x2 * x2 + y2 * y2 * y2 + z2 * z2 * z2) +
+                                cm[6] * (x2 * x2 * (y2 + z2) + y2 * y2 * (x2 + z2) + z2 * z2 * (x2 + y2)) +
+                                cm[7] * x2 * y2 * z2;
+                e_land += (double)f;
             }
+            if (terms & TERM_GRAD) e_grad += (double)tgrad_energy(V, S, s_coef, py, x, m, p);
+            float el = 0.f, ex = 0.f;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                float pn, p0 = p[c];
-                if (MODE == MODE_HEUN2) {
-                    p0 = Pn[c * S.ncell + id];
-                    pn = fmaf(0.5f * S.dt, S.hbuf[c * S.ncell + id] + h[c], p0);
-                } else {
-                    pn = fmaf(S.dt, h[c], p0);
-                    if (MODE == MODE_HEUN1) S.hbuf[c * S.ncell + id] = h[c];
-                }
-                if (MODE != MODE_HEUN1) lmax = fmaxf(lmax, fabsf(pn - p0));
-                bad |= !(fabsf(pn) <= S.pmax);
-                Pn[c * S.ncell + id] = pn;
-                Eb[(c * TYmax + r) * nx + x] = pn;      // the cell's own slot: E read above, new P kept
+                if (elec) el = fmaf(-0.5f * Eb[(c * TYmax + r) * nx + x], p[c], el);
+                if (terms & TERM_EXT) ex = fmaf(-eext[c], p[c], ex);
+            }
+            e_elec += (double)el;
+            e_ext += (double)ex;
+            return;
+        }
+        if (terms & TERM_LANDAU) {
+            if constexpr (KNOWN) landau_field(p, land0, h);
+            else landau_field(p, cm, h);
+        }
+        if (terms & TERM_GRAD) {
+            if constexpr (BULK) bulk_grad(py, x, p, h);
+            else if constexpr (KIND == 2) box_grad(py, x, p, h);
+            else tgrad_field(V, S, s_coef, py, x, m, p, h, false);
+        }
+        finish(r, x, p, h);
+    };
+    if (MODE != MODE_XFWD) {
+        // bulk pass: cells 1 .. nx - 2 of the bulk rows, warp-uniform fast path
+        const int nb = __popc(bulk_rows);
+        for (int w = tid; w < nb * (nx - 2); w += nthr) {
+            const int j = w / (nx - 2), x = 1 + w - j * (nx - 2);
+            cell((int)s_rowidx[0][j], x, std::integral_constant<int, 1>{});
+        }
+        // general pass: every cell of the other rows, then the two end cells of each bulk row
+        const int nrest = (TY - nb) * nx;
+        for (int w = tid; w < nrest + 2 * nb; w += nthr) {
+            if (w < nrest) {
+                const int j = w / nx, x = w - j * nx;
+                const int r = (int)s_rowidx[1][j];
+                if ((box_rows >> r) & 1u) cell(r, x, std::integral_constant<int, 2>{});
+                else cell(r, x, std::integral_constant<int, 0>{});
+            } else {
+                const int k = w - nrest;
+                cell((int)s_rowidx[0][k >> 1], (k & 1) ? nx - 1 : 0, std::integral_constant<int, 2>{});
             }
         }
     }
