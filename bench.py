@@ -228,7 +228,7 @@ def gpu_arm(args, rank, world):
     ctx = tdgl.Context(dev, stream=stream.cuda_stream)
     if args.zpass_variant >= 0:   # profiling runs: a profiler distorts the autotuner's trial timings
         for n in (128, 256, 512):
-            if args.zpass_variant < (2 if n == 512 else 3):
+            if args.zpass_variant < (2 if n == 512 else 4):
                 ctx.set_zpass_variant(n, args.zpass_variant)
     wl = workload(args.workload)
     s, dt = make_sim(ctx, wl)

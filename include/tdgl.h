@@ -157,14 +157,16 @@ int tdgl_get_dt(tdgl_sim *sim, double *dt);
  * inverse transform) for 128-, 256- and 512-point lines.  Variants: 0, 16 elements per thread
  * (radices 16 x 8, 16 x 16, 16 x 16 x 2); 1, 8 elements per thread (8 x 8 x 2, 8 x 8 x 4,
  * 8 x 8 x 8) with twice the warps per SM; 2 (128 and 256 only), variant 1 with the block's rows of
- * the tensor spectrum copied into shared memory at the start, overlapping the forward transforms.
+ * the tensor spectrum copied into shared memory at the start, overlapping the forward transforms;
+ * 3 (128 and 256 only), variant 2 with the three components' transforms run together (one
+ * shared-memory exchange serves all three) and the tensor multiply on registers.
  * The first time a context prepares a sim with such lines it times every variant of the length on
  * that sim's buffers (no state changes) and keeps the fastest.  tdgl_zpass_variant reads the
  * choice (-1 = not tuned yet) and, if us is not NULL, writes TDGL_ZPASS_VARIANTS doubles: the
  * measured microseconds per launch of each variant (0 for a variant the length does not have);
  * tdgl_set_zpass_variant forces one (-1 tunes again).  All variants compute the same field up to
  * FP32 rounding. */
-#define TDGL_ZPASS_VARIANTS 3
+#define TDGL_ZPASS_VARIANTS 4
 int tdgl_zpass_variant(tdgl_ctx *ctx, int length, int *variant, double *us);
 int tdgl_set_zpass_variant(tdgl_ctx *ctx, int length, int variant);
 /* Simulated time t (s) of the sim: 0 at creation, advanced by n dt by every step call. */

@@ -121,6 +121,51 @@ __device__ __forceinline__ void fft(float2 (&v)[S::E], int t, float2 *X, Idx idx
 template <class S>
 __device__ __forceinline__ int final_pos(int t, int i) { return out_pos<S, S::NP - 1>(t, i); }
 
+// Three transforms of shape S at once (three independent vectors held by the same threads, each
+// with its own exchange buffer): the passes run back to back on the three vectors and every
+// exchange serves all three, so a block waits at a third of the barriers and each thread has three
+// independent butterflies in flight per pass.  Same results as three calls of fft.
+template <class S, int P, class Idx>
+__device__ __forceinline__ void exchange3(float2 (&a)[S::E], float2 (&b)[S::E], float2 (&c)[S::E], int t,
+                                          float2 *Xa, float2 *Xb, float2 *Xc, Idx idx) {
+#pragma unroll
+    for (int i = 0; i < S::E; ++i) {
+        const int q = idx(out_pos<S, P>(t, i));
+        Xa[q] = a[i];
+        Xb[q] = b[i];
+        Xc[q] = c[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < S::E; ++i) {
+        const int q = idx(in_pos<S, P + 1>(t, i));
+        a[i] = Xa[q];
+        b[i] = Xb[q];
+        c[i] = Xc[q];
+    }
+    __syncthreads();
+}
+
+template <class S, bool INV, class Idx>
+__device__ __forceinline__ void fft3(float2 (&a)[S::E], float2 (&b)[S::E], float2 (&c)[S::E], int t, float2 *Xa,
+                                     float2 *Xb, float2 *Xc, Idx idx, const float2 *__restrict__ tw) {
+    pass_regs<S, 0, INV>(a, t, tw);
+    pass_regs<S, 0, INV>(b, t, tw);
+    pass_regs<S, 0, INV>(c, t, tw);
+    if constexpr (S::NP > 1) {
+        exchange3<S, 0>(a, b, c, t, Xa, Xb, Xc, idx);
+        pass_regs<S, 1, INV>(a, t, tw);
+        pass_regs<S, 1, INV>(b, t, tw);
+        pass_regs<S, 1, INV>(c, t, tw);
+    }
+    if constexpr (S::NP > 2) {
+        exchange3<S, 1>(a, b, c, t, Xa, Xb, Xc, idx);
+        pass_regs<S, 2, INV>(a, t, tw);
+        pass_regs<S, 2, INV>(b, t, tw);
+        pass_regs<S, 2, INV>(c, t, tw);
+    }
+}
+
 // Zero padding to at least twice the data length (N >= 2n): the input registers m >= E/2 hold
 // positions t + T m >= N/2 >= n, which are zero, and the output registers i whose last-pass index
 // q = i mod R (R the last radix) is >= R/2 hold positions (b - j) R + j + q N/R >= N/2, which are

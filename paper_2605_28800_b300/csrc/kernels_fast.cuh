@@ -29,6 +29,10 @@ template <int N> __host__ __device__ constexpr int lines_per_block() {
 //          in shared memory by one TMA copy per component pair at the start, so that their
 //          latency overlaps the forward transforms instead of stalling the multiply (three
 //          blocks per SM instead of four).
+//   V = 3: V = 2 with the three components transformed together (k_zpass3): each pass runs on the
+//          three components back to back and each exchange serves all three (a third of the
+//          barriers, three independent butterflies per thread), and the 3x3 multiply works on
+//          registers only.
 // All variants give every length the same lines per block, hence the same work items.
 template <int N, int V> struct ZCfg : rf::Cfg<N> {};
 template <> struct ZCfg<128, 1> : rf::Shape<128, 8, 8, 8, 2> {};
@@ -36,8 +40,10 @@ template <> struct ZCfg<128, 2> : ZCfg<128, 1> {};
 template <> struct ZCfg<256, 1> : rf::Shape<256, 8, 8, 8, 4> {};
 template <> struct ZCfg<512, 1> : rf::Shape<512, 8, 8, 8, 8> {};
 template <> struct ZCfg<256, 2> : ZCfg<256, 1> {};
+template <> struct ZCfg<128, 3> : ZCfg<128, 1> {};
+template <> struct ZCfg<256, 3> : ZCfg<256, 1> {};
 // variant V stages the tensor rows in shared memory
-template <int V> __host__ __device__ constexpr bool zstaged() { return V == 2; }
+template <int V> __host__ __device__ constexpr bool zstaged() { return V == 2 || V == 3; }
 template <int N, int V> __host__ __device__ constexpr int zthreads() { return ZCfg<N, V>::E == 8 ? 256 : 128; }
 template <int N, int V> __host__ __device__ constexpr int zlines_per_block() {
     return (zthreads<N, V>() / ZCfg<N, V>::T) < 16 ? (zthreads<N, V>() / ZCfg<N, V>::T) : 16;
@@ -306,6 +312,159 @@ __global__ void __launch_bounds__(zthreads<N, V>(), zstaged<V>() ? 3 : 4)
         store(c, v);
     }
     if (tma && threadIdx.x == 0) tc::bulk_wait_read_all();   // the boxes read before shared memory goes
+}
+
+
+// Variant 3 of the z pass: the three components' transforms run together (rf::fft3).  Work items,
+// input and output layouts, the staged tensor rows and the Nyquist items are those of k_zpass<N, 2>.
+template <int N>
+__global__ void __launch_bounds__(zthreads<N, 3>(), 2)
+    k_zpass3(const SimDev *__restrict__ sims, const int4 *__restrict__ items) {
+    using S = ZCfg<N, 3>;
+    constexpr int E = S::E, T = S::T, KX = zlines_per_block<N, 3>(), NR = ztile_rows<N, KX>();
+    extern __shared__ float4 smem4[];
+    float2 *A = reinterpret_cast<float2 *>((reinterpret_cast<uintptr_t>(smem4) + 127) & ~uintptr_t(127));   // [3][N][KX]
+    float2 *tw = A + 3 * N * KX;                          // [N]
+    float2 *Nt = tw + N;                                  // [3][NR][KX] staged tensor rows
+    float2 *A0 = A, *A1 = A + N * KX, *A2 = A + 2 * N * KX;
+    const int4 it = items[blockIdx.x];
+    const SimDev &D = sims[it.x];
+    const bool across = (it.w & kAcross) != 0;
+    const int cnt = it.w & (kAcross - 1);
+    const int l = threadIdx.x % KX, t = threadIdx.x / KX;
+    const int ky = across ? it.y + l : it.y, kx = across ? it.z : it.z + l;   // this lane's line
+    const bool ok = l < cnt;
+    const int nz = D.nz, My = D.My, kxp = D.kxp;
+    const long zs = (long)My * kxp, cs = (long)nz * zs;
+    const float2 *src = D.Y + (long)ky * kxp + kx;
+    int *const flag = D.flag;
+    auto idx = [&](int pos) { return zrow<N, 3, KX>(pos) * KX + l; };
+    const int kyr = (ky <= My / 2) ? ky : My - ky;
+    const float sy = (ky <= My / 2) ? 1.f : -1.f;
+    auto at = [&](int z) { return z * KX + l; };
+    __shared__ uint64_t zbar[4];
+    const bool tma = D.has_ymap && !across && (tc::saddr(A) & 127u) == 0u;
+    const bool staged = tma && D.has_nmap;
+    if (tma) {
+        if (threadIdx.x == 0) {
+            for (int c = 0; c < 4; ++c) tc::mbar_init(&zbar[c], 1);
+            tc::mbar_fence_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int c = 0; c < 3; ++c) {
+                tc::mbar_expect_tx(&zbar[c], (uint32_t)(nz * KX * sizeof(float2)));
+                tc::tma_load_4d(tc::saddr(A + c * N * KX), &D.ymap, &zbar[c], 2 * it.z, ky, 0, c);
+            }
+            if (staged) {
+                tc::mbar_expect_tx(&zbar[3], (uint32_t)(3 * (N / 2 + 1) * KX * sizeof(float2)));
+                for (int p = 0; p < 3; ++p) tc::tma_load_4d(tc::saddr(Nt + p * NR * KX), &D.nmap, &zbar[3], 2 * it.z, kyr, 0, p);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (ok) {
+#pragma unroll
+                for (int m = 0; m < E; ++m) {
+                    const int z = t + T * m;
+                    if (z < nz) {
+                        const unsigned dst = (unsigned)__cvta_generic_to_shared(A + c * N * KX + at(z));
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src + c * cs + z * zs));
+                    }
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = D.tw[D.pz.tw + i];
+    if (tma) {
+        for (int c = 0; c < 3; ++c)
+            if (!tc::mbar_wait(&zbar[c], 0u, 1L << 24) && threadIdx.x == 0) atomicOr(flag, 2);
+    } else {
+        asm volatile("cp.async.wait_group 0;\n" ::);
+    }
+    // forward transforms of the three components from this thread's own input slots
+    float2 a[E], b[E], c[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        const int z = t + T * m;
+        const bool in = rf::padded_in<S>(m) && ok && z < nz;
+        a[m] = in ? A0[at(z)] : make_float2(0.f, 0.f);
+        b[m] = in ? A1[at(z)] : make_float2(0.f, 0.f);
+        c[m] = in ? A2[at(z)] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();   // inputs (and the twiddles) read before the exchanges overwrite them
+    rf::fft3<S, false>(a, b, c, t, A0, A1, A2, idx, tw);
+    if (staged && !tc::mbar_wait(&zbar[3], 0u, 1L << 24) && threadIdx.x == 0) atomicOr(flag, 2);
+    // E-hat(k) = escale * N-hat(k) P-hat(k) in registers, then the inverse transforms' input order
+    const float es = D.escale;
+    const long ns = (long)D.kzh * D.kyh * kxp;
+    const float2 *Nb = D.Nhat + (long)kyr * kxp + kx;
+    const long rowN = (long)D.kyh * kxp;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int kz = rf::final_pos<S>(t, i);
+        const int kzr = (kz <= N / 2) ? kz : N - kz;
+        const float sz = (kz <= N / 2) ? 1.f : -1.f;
+        float nxx = 0.f, nyy = 0.f, nzz = 0.f, nxy = 0.f, nxz = 0.f, nyz = 0.f;
+        if (staged) {
+            const float2 *Nl = Nt + kzr * KX + l;
+            const float2 n0 = Nl[0], n1 = Nl[NR * KX], n2 = Nl[2 * NR * KX];
+            nxx = n0.x; nyy = n0.y; nzz = n1.x;
+            nxy = sy * n1.y; nxz = sz * n2.x; nyz = sy * sz * n2.y;
+        } else if (ok) {
+            const float2 *Np = Nb + kzr * rowN;
+            const float2 n0 = __ldg(Np), n1 = __ldg(Np + ns), n2 = __ldg(Np + 2 * ns);
+            nxx = n0.x; nyy = n0.y; nzz = n1.x;
+            nxy = sy * n1.y; nxz = sz * n2.x; nyz = sy * sz * n2.y;
+        }
+        const float2 px = a[i], py = b[i], pz = c[i];
+        a[i] = make_float2(es * (nxx * px.x + nxy * py.x + nxz * pz.x), es * (nxx * px.y + nxy * py.y + nxz * pz.y));
+        b[i] = make_float2(es * (nxy * px.x + nyy * py.x + nyz * pz.x), es * (nxy * px.y + nyy * py.y + nyz * pz.y));
+        c[i] = make_float2(es * (nxz * px.x + nyz * py.x + nzz * pz.x), es * (nxz * px.y + nyz * py.y + nzz * pz.y));
+    }
+    float2 ia[E], ib[E], ic[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+        ia[m] = a[rf::final_reg<S>(m)];
+        ib[m] = b[rf::final_reg<S>(m)];
+        ic[m] = c[rf::final_reg<S>(m)];
+    }
+    // the exchange buffers are free: the last forward exchange's reads finished at its barrier
+    rf::fft3<S, true>(ia, ib, ic, t, A0, A1, A2, idx, tw);
+    // the first nz outputs back into Y: regular items through the input boxes and one TMA store per
+    // component, Nyquist items with 8-byte stores from each lane
+    if (tma) {
+        // (every lane's reads of the last exchange finished at its closing barrier)
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int z = rf::final_pos<S>(t, i);
+            if (rf::kept_out<S>(i) && z < nz) {
+                A0[at(z)] = ia[i];
+                A1[at(z)] = ib[i];
+                A2[at(z)] = ic[i];
+            }
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < 3; ++q) tc::tma_store_4d(&D.ymap, tc::saddr(A + q * N * KX), 2 * it.z, ky, 0, q);
+            tc::bulk_commit();
+            tc::bulk_wait_read_all();   // the boxes read before shared memory goes
+        }
+    } else if (ok) {
+        float2 *dst = D.Y + (long)ky * kxp + kx;
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int z = rf::final_pos<S>(t, i);
+            if (rf::kept_out<S>(i) && z < nz) {
+                dst[z * zs] = ia[i];
+                dst[cs + z * zs] = ib[i];
+                dst[2 * cs + z * zs] = ic[i];
+            }
+        }
+    }
 }
 
 }  // namespace tdgl

@@ -41,7 +41,7 @@ struct tdgl_ctx {
     std::vector<tdgl_batch *> batches;
     std::vector<tdgl_unet *> nets;
     // z-pass radix-schedule autotuning for 256-, 512- and 128-point lines (in that index order): chosen variant (-1 = not
-    // yet tuned) and the measured microseconds per launch of variants 0 and 1
+    // yet tuned) and the measured microseconds per launch of each variant
     int zvar[3] = {-1, -1, -1};
     double zus[3][TDGL_ZPASS_VARIANTS] = {};
 };

@@ -627,20 +627,25 @@ void ypass(const Group &g, const SimDev *d, cudaStream_t st) {
 }
 
 int zvar_index(int N) { return N == 256 ? 0 : (N == 512 ? 1 : (N == 128 ? 2 : -1)); }
-// radix-schedule variants of the z pass per length: 256 has three (V = 2 stages the tensor rows),
-// 512 two (its staged tile would not fit beside the spectra)
-int zvar_count(int N) { return (N == 128 || N == 256) ? 3 : (N == 512 ? 2 : 0); }
+// radix-schedule variants of the z pass per length: 128 and 256 have four (V = 2 stages the tensor
+// rows, V = 3 also transforms the three components together), 512 two (its staged tile would not
+// fit beside the spectra)
+int zvar_count(int N) { return (N == 128 || N == 256) ? 4 : (N == 512 ? 2 : 0); }
 
 template <int N, int V>
 void zpass_v(const Group &g, const SimDev *d, cudaStream_t st) {
-    k_zpass<N, V><<<g.n, ZCfg<N, V>::T * zlines_per_block<N, V>(), zpass_smem<N, V>(), st>>>(d, g.items);
+    if constexpr (V == 3)
+        k_zpass3<N><<<g.n, ZCfg<N, V>::T * zlines_per_block<N, V>(), zpass_smem<N, V>(), st>>>(d, g.items);
+    else
+        k_zpass<N, V><<<g.n, ZCfg<N, V>::T * zlines_per_block<N, V>(), zpass_smem<N, V>(), st>>>(d, g.items);
 }
 
 // variant v of the z pass for LEN-point lines (a template, so the lengths without variants
 // instantiate only variant 0)
 template <int LEN> void zpass_len(int v, const Group &g, const SimDev *d, cudaStream_t st) {
     if constexpr (LEN == 128 || LEN == 256) {
-        if (v == 2) zpass_v<LEN, 2>(g, d, st);
+        if (v == 3) zpass_v<LEN, 3>(g, d, st);
+        else if (v == 2) zpass_v<LEN, 2>(g, d, st);
         else if (v == 1) zpass_v<LEN, 1>(g, d, st);
         else zpass_v<LEN, 0>(g, d, st);
     } else if constexpr (LEN == 512) {
@@ -654,7 +659,10 @@ template <int LEN> void zpass_attrs(int smem) {
     cudaFuncSetAttribute(k_zpass<LEN, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if constexpr (LEN == 128 || LEN == 256 || LEN == 512)
         cudaFuncSetAttribute(k_zpass<LEN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if constexpr (LEN == 128 || LEN == 256) cudaFuncSetAttribute(k_zpass<LEN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if constexpr (LEN == 128 || LEN == 256) {
+        cudaFuncSetAttribute(k_zpass<LEN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_zpass3<LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
 }
 
 // the z pass of one group with the context's radix-schedule variant (forced >= 0, else tuned)

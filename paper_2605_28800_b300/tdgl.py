@@ -23,7 +23,7 @@ KERNEL_NAMES = {K_STEP: "k_rows<STEP>", K_YFWD: "k_yfwd", K_ZCONV: "k_zconv", K_
                 K_XFWD: "k_rows<XFWD>", K_OTHER: "other", K_UNET: "unet"}
 MAX_MATERIALS, MAX_DIM = 16, 1024
 EULER, HEUN, RK45, AB3M2 = 0, 1, 2, 3
-ZPASS_VARIANTS = 3
+ZPASS_VARIANTS = 4
 
 _CODES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EDIVERGED: "EDIVERGED",
           ENOTCONVERGED: "ENOTCONVERGED", ESTATE: "ESTATE", ETOOBIG: "ETOOBIG"}

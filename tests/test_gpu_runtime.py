@@ -303,7 +303,7 @@ def test_launch_counter_counts_kernels(ctx):
 
 @pytest.mark.parametrize("nz,length", [(128, 256), (64, 128)])
 def test_zpass_autotuner_picks_a_variant_and_every_variant_agrees_with_the_oracle(nz, length):
-    # 16 x 16 x 128 pads z to 256 points, 16 x 16 x 64 to 128: the context times the three
+    # 16 x 16 x 128 pads z to 256 points, 16 x 16 x 64 to 128: the context times the four
     # variants of the z pass on first use and keeps the fastest; forcing any of them gives the
     # same trajectory as the oracle
     from paper_2605_28800_b300 import tdgl
@@ -318,15 +318,15 @@ def test_zpass_autotuner_picks_a_variant_and_every_variant_agrees_with_the_oracl
     try:
         assert ctx.zpass_variant(length)[0] == -1
         finals = []
-        for forced in (None, 0, 1, 2):
+        for forced in (None, 0, 1, 2, 3):
             g = gpu_sim(ctx, shape, CELL, mat, MATS, 300.0, 45.0, P=P)
             if forced is not None:
                 ctx.set_zpass_variant(length, forced)
             g.step(3, dt)
             if forced is None:
                 v, us = ctx.zpass_variant(length)
-                assert len(us) == tdgl.ZPASS_VARIANTS == 3
-                assert v in (0, 1, 2) and min(us) > 0 and us[v] == min(us)
+                assert len(us) == tdgl.ZPASS_VARIANTS == 4
+                assert v in (0, 1, 2, 3) and min(us) > 0 and us[v] == min(us)
             else:
                 assert ctx.zpass_variant(length)[0] == forced
             finals.append(g.get_P())
@@ -338,7 +338,7 @@ def test_zpass_autotuner_picks_a_variant_and_every_variant_agrees_with_the_oracl
         with pytest.raises(tdgl.TdglError):
             ctx.set_zpass_variant(64, 1)           # 64-point lines have one shape
         with pytest.raises(tdgl.TdglError):
-            ctx.set_zpass_variant(512, 2)          # the staged variant exists for 128 and 256 only
+            ctx.set_zpass_variant(512, 2)          # the staged variants exist for 128 and 256 only
         ctx.set_zpass_variant(512, 1)
     finally:
         ctx.close()
