@@ -501,6 +501,37 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
                 if (i != d) h[i] = fmaf(Tp[i] - Tm[i], w, h[i]);
         }
     };
+    // Gradient energy density of a bulk cell of material m0: tgrad_energy's faces towards +x, +y, +z
+    // and cross terms, whose ghost rules never apply here, with m0's coefficients in registers
+    // (the same operations in the same order, so both give the same result bit for bit).
+    auto bulk_genergy = [&](const int py, const int x, const float *pa) {
+        constexpr int TS = TYH * nx;
+        const float *c = Pt + py * nx + x;
+        const float *hi = zhi + py * nx + x, *lo = zlo + py * nx + x;
+        float e = 0.f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float g = 0.5f * ((i == d) ? gd[d] + gd[d] : go[d] + go[d]);
+                const float nb = d == 0 ? c[i * TS + 1] : (d == 1 ? c[i * TS + nx] : __ldg(hi + i * ncell));
+                const float df = nb - pa[i];
+                e = fmaf(0.5f * g * df, df, e);
+            }
+        }
+        if (cross) {
+            float D[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                D[i][0] = (c[i * TS + 1] - c[i * TS - 1]) * inv2d[0];
+                D[i][1] = (c[i * TS + nx] - c[i * TS - nx]) * inv2d[1];
+                D[i][2] = (__ldg(hi + i * ncell) - __ldg(lo + i * ncell)) * inv2d[2];
+            }
+            e += c10 * (D[0][0] * D[1][1] + D[1][1] * D[2][2] + D[2][2] * D[0][0]) +
+                 c11 * (D[0][1] * D[1][0] + D[1][2] * D[2][1] + D[0][2] * D[2][0]);
+        }
+        return e;
+    };
     // the rest of a cell once its Landau and gradient fields are in h: E_el, E_ext, then the mode's
     // output (field, dP/dt) or update
     auto finish = [&](const int r, const int x, const float *p, float *h) {
@@ -573,7 +604,10 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
                                 cm[7] * x2 * y2 * z2;
                 e_land += (double)f;
             }
-            if (terms & TERM_GRAD) e_grad += (double)tgrad_energy(V, S, s_coef, py, x, m, p);
+            if (terms & TERM_GRAD) {
+                if constexpr (BULK) e_grad += (double)bulk_genergy(py, x, p);
+                else e_grad += (double)tgrad_energy(V, S, s_coef, py, x, m, p);
+            }
             float el = 0.f, ex = 0.f;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
