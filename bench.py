@@ -397,9 +397,27 @@ def relax_compare(args):
     print(json.dumps(line))
 
 
+def phase_fractions(P, floor=0.05, ratio=0.35):
+    """Per-cell phase of a BaTiO3 texture (3, nz, ny, nx) in C/m^2: C where |P| < floor, else by the
+    sorted absolute components a0 >= a1 >= a2: T (a1 < ratio a0, one dominant axis, <100>),
+    O (a2 < ratio a0 <= a1, <110>), R (a2 >= ratio a0, <111>).  Returns the fractions of all cells."""
+    a = np.sort(np.abs(P.reshape(3, -1).astype(np.float64)), axis=0)[::-1]
+    mag = np.sqrt((a ** 2).sum(axis=0))
+    c = mag < floor
+    t = ~c & (a[1] < ratio * a[0])
+    o = ~c & ~t & (a[2] < ratio * a[0])
+    r = ~c & ~t & ~o
+    n = float(a.shape[1])
+    return {"C": c.sum() / n, "T": t.sum() / n, "O": o.sum() / n, "R": r.sum() / n}
+
+
 def temperature_sweep(args):
-    """Relaxation sweep of the 128^3 cube, 450 -> 200 K in 25 K steps (adiabatic continuation:
-    each temperature starts from the previous relaxed state), relaxed to args.tol per step."""
+    """Relaxation sweep of the 128^3 cube, 450 -> 200 K in 25 K steps, relaxed to args.tol per step
+    at each temperature.  Each temperature starts from the state relaxed at the one before plus a
+    fresh seeded perturbation uniform in +-args.reseed_amp C/m^2 (the random start of the workload,
+    repeated per temperature: without it, below the transition the cubic state P = 0 left by the
+    previous temperature is a stationary point of Eq. 1 and passes the per-step criterion at once).
+    Reports steps, convergence, time, mean |P|, the per-cell phase fractions and the majority phase."""
     import torch
     from paper_2605_28800_b300 import tdgl
     dev = int(os.environ.get("LOCAL_RANK", 0))
@@ -408,8 +426,10 @@ def temperature_sweep(args):
     wl = workload("bto_cube_128")
     s, dt = make_sim(ctx, wl)
     rows = []
-    for T in synth.CONFIG2["temperatures"]:
+    for i, T in enumerate(synth.CONFIG2["temperatures"]):
         s.set_temperature(T)
+        if i > 0 and args.reseed_amp > 0:
+            s.set_P(s.get_P() + synth.uniform_P(wl["shape"], args.reseed_amp, 1000 + i))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         n, ok = s.relax(dt, args.tol, args.max_relax_steps, CHECK_EVERY, raise_on_cap=False)
@@ -418,13 +438,17 @@ def temperature_sweep(args):
         P = s.get_P()
         a = np.sort(np.abs(P.reshape(3, -1).mean(axis=1)))[::-1]
         mag = float(np.sqrt((P.astype(np.float64) ** 2).sum(axis=0)).mean())
+        fr = phase_fractions(P)
+        polar = {k: v for k, v in fr.items() if k != "C"}
+        major = "C" if fr["C"] > 0.5 else max(polar, key=polar.get)
         e = s.energy()
         rows.append(dict(T=T, steps=n, converged=ok, seconds=el, mean_abs_P=mag,
-                         mean_P_sorted=[float(v) for v in a], F_total=e["total"],
-                         cell_updates_per_s=n * wl["P"][0].size / el if el > 0 else None))
+                         mean_P_sorted=[float(v) for v in a], F_total=e["total"], phase_fractions=fr,
+                         phase=major, cell_updates_per_s=n * wl["P"][0].size / el if el > 0 else None))
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     print(json.dumps({"metric": "time-to-relax per temperature", "workload": "bto_cube_128_T_sweep",
                       "tol": args.tol, "max_steps": args.max_relax_steps, "dt_star": wl["dt_star"],
-                      "points": rows}))
+                      "reseed_amp": args.reseed_amp, "points": rows}))
 
 
 def warm_start(args):
@@ -692,6 +716,8 @@ def main():
     ap.add_argument("--zpass-variant", type=int, default=-1,
                     help="force the z-pass variant for 256/512-point lines instead of autotuning (for profiler runs)")
     ap.add_argument("--max-relax-steps", type=int, default=20000)
+    ap.add_argument("--reseed-amp", type=float, default=0.01,
+                    help="--temperature-sweep: fresh random perturbation (C/m^2) added at each new temperature")
     ap.add_argument("--size-sweep", action="store_true",
                     help="step time of single sims from 32x32x8 to 128^3 run alone (device relaxation loop)")
     ap.add_argument("--ensemble", action="store_true",
