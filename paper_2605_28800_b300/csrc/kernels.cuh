@@ -58,6 +58,8 @@ struct SimDev {
     float *out;               // field readback [3][ncell]
     float *hbuf;              // Heun: field of the predictor's starting point [3][ncell]
     float out_scale;          // alpha_ref P0
+    int skip;                 // nonzero: every step kernel returns at once for this sim (a batch
+                              // member the device relaxation loop has retired)
     int has_ymap;             // ymap below is valid (the z pass then loads its lines with TMA)
     // Y viewed as float32 (2 kxp, My, nz, 3), box (2 x lines per block, 1, nz, 1): the z lines of
     // one ky and one group of kx, one component per copy
@@ -276,6 +278,7 @@ __global__ void __launch_bounds__(NTHREADS) k_rows(const SimDev *__restrict__ si
     __shared__ float s_max;
     const int4 it = items[blockIdx.x];
     const SimDev &S = sims[it.x];
+    if (S.skip) return;   // a batch member that has left the relaxation
     const int z = it.y, y0 = it.z, cnt = it.w;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int ld = row_ld(S);
@@ -453,6 +456,7 @@ __global__ void __launch_bounds__(NTHREADS) k_yfwd(const SimDev *__restrict__ si
     extern __shared__ float4 smem4[];
     const int4 it = items[blockIdx.x];
     const SimDev &S = sims[it.x];
+    if (S.skip) return;   // a batch member that has left the relaxation
     const int cz = it.y, kx0 = it.z, cnt = it.w;
     const int tid = threadIdx.x, nthr = blockDim.x, ld = yld(S);
     float2 *A = reinterpret_cast<float2 *>(smem4), *B = A + cnt * ld;
@@ -474,6 +478,7 @@ __global__ void __launch_bounds__(NTHREADS) k_yinv(const SimDev *__restrict__ si
     extern __shared__ float4 smem4[];
     const int4 it = items[blockIdx.x];
     const SimDev &S = sims[it.x];
+    if (S.skip) return;   // a batch member that has left the relaxation
     const int cz = it.y, kx0 = it.z, cnt = it.w;
     const int tid = threadIdx.x, nthr = blockDim.x, ld = yld(S);
     float2 *A = reinterpret_cast<float2 *>(smem4), *B = A + cnt * ld;
@@ -496,6 +501,7 @@ __global__ void __launch_bounds__(NTHREADS) k_zconv(const SimDev *__restrict__ s
     extern __shared__ float4 smem4[];
     const int4 it = items[blockIdx.x];
     const SimDev &S = sims[it.x];
+    if (S.skip) return;   // a batch member that has left the relaxation
     const int ky = it.y, kx0 = it.z, cnt = it.w;
     const int tid = threadIdx.x, nthr = blockDim.x, ld = zld(S);
     const int nl = 3 * cnt;

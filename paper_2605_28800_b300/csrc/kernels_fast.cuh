@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(256) k_ypass(const SimDev *__restrict__ sims, 
     __shared__ float2 tw[N];
     const int4 it = items[blockIdx.x];
     const SimDev &D = sims[it.x];
+    if (D.skip) return;   // a batch member that has left the relaxation
     const bool across = (it.w & kAcross) != 0;
     const int cnt = it.w & (kAcross - 1);
     const int l = threadIdx.x % KX, t = threadIdx.x / KX;
@@ -140,6 +141,7 @@ __global__ void __launch_bounds__(zthreads<N, V>(), zstaged<V>() ? 3 : 4)
     static_assert(!zstaged<V>() || ((3 * N * KX + N) * sizeof(float2)) % 128 == 0, "staged tile must start on 128 bytes");
     const int4 it = items[blockIdx.x];
     const SimDev &D = sims[it.x];
+    if (D.skip) return;   // a batch member that has left the relaxation
     const bool across = (it.w & kAcross) != 0;
     const int cnt = it.w & (kAcross - 1);
     const int l = threadIdx.x % KX, t = threadIdx.x / KX;
@@ -329,6 +331,7 @@ __global__ void __launch_bounds__(zthreads<N, 3>(), 2)
     float2 *A0 = A, *A1 = A + N * KX, *A2 = A + 2 * N * KX;
     const int4 it = items[blockIdx.x];
     const SimDev &D = sims[it.x];
+    if (D.skip) return;   // a batch member that has left the relaxation
     const bool across = (it.w & kAcross) != 0;
     const int cnt = it.w & (kAcross - 1);
     const int l = threadIdx.x % KX, t = threadIdx.x / KX;

@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
     __shared__ unsigned char s_rowidx[2][16];   // the block's bulk rows, then its other rows, in order
     const int4 it = items[blockIdx.x];
     const SimDev &S = sims[it.x];
+    if (S.skip) return;   // a batch member that has left the relaxation
     const int z = it.y, y0 = it.z, TY = it.w;     // TY rows of this block (<= tile)
     const int ny = S.ny, nz = S.nz;
     const int tid = threadIdx.x;

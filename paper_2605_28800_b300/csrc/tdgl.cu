@@ -99,6 +99,16 @@ struct tdgl_sim {
     tdgl_batch *batch = nullptr;
 };
 
+// loop state of a batch's device relaxation: steps done in this launch's loop, the cap, the
+// tolerance, steps per body, batch size, and the cells retired so far against the cells after which
+// the loop hands back to the host (which then drops the retired sims from the work lists)
+struct BatchRelaxState {
+    long done, max_steps;
+    double tol;
+    int k, n;
+    long cells_retired, cells_stop;
+};
+
 struct tdgl_batch {
     tdgl_ctx *ctx = nullptr;
     std::vector<tdgl_sim *> sims;
@@ -109,6 +119,11 @@ struct tdgl_batch {
     std::vector<int> w_active;
     struct Cached;
     Cached *cache = nullptr;
+    // device relaxation loop state: loop counters, membership of the current active set, steps
+    // taken and status (0 running, 1 converged, 2 diverged or timed out) per sim
+    struct BatchRelaxState *drelax = nullptr;
+    int *dmember = nullptr, *dstatus = nullptr;
+    long *dsteps = nullptr;
 };
 
 // frees a batch's cached work lists and graphs (defined once the cache type is complete)
@@ -1691,8 +1706,14 @@ struct tdgl_batch::Cached {
         long kernels;
     };
     std::vector<G> graphs;
+    // the device relaxation loop over this active set (k steps per body, integrator)
+    cudaGraphExec_t relax_exec = nullptr;
+    int relax_k = 0;
+    bool relax_heun = false;
+    long relax_kernels = 0;
     ~Cached() {
         for (auto &g : graphs) cudaGraphExecDestroy(g.exec);
+        if (relax_exec) cudaGraphExecDestroy(relax_exec);
     }
 };
 
@@ -1713,6 +1734,10 @@ void tdgl_batch_destroy(tdgl_batch *b) {
     drop_cache(b);
     cudaFree(b->ddescs);
     cudaFree(b->d_items);
+    cudaFree(b->drelax);
+    cudaFree(b->dmember);
+    cudaFree(b->dstatus);
+    cudaFree(b->dsteps);
     delete b;
 }
 
@@ -1777,7 +1802,10 @@ int build_batch_work(tdgl_batch *b, const std::vector<int> &active, Work &w) {
 }
 
 // n steps of every active sim of a batch (one launch per kernel family and length class)
-int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const double *dt) {
+// Descriptors of the active sims (the others zeroed), work lists of the active set, the x-forward
+// prologue of sims whose x-spectrum is not P-hat of their P, cleared flags: the state every
+// step sequence of the batch starts from.
+int batch_setup(tdgl_batch *b, const std::vector<int> &active, const double *dt) {
     tdgl_ctx *ctx = b->ctx;
     std::vector<SimDev> descs(b->sims.size());
     memset(descs.data(), 0, descs.size() * sizeof(SimDev));
@@ -1825,20 +1853,33 @@ int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const doub
         }
     }
     for (int idx : active) CK(ctx, cudaMemsetAsync(b->sims[idx]->dflag, 0, sizeof(int), ctx->stream));
+    return TDGL_OK;
+}
+
+// the launches of n steps of the active set (one per kernel family and length class)
+int record_batch_steps(tdgl_batch *b, const std::vector<int> &active, int n) {
+    tdgl_ctx *ctx = b->ctx;
+    const Work &w = b->cache->w;
     const bool heun = b->sims[active[0]]->integrator == TDGL_HEUN;
-    auto record = [&]() -> int {
-        for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < n; ++i) {
+        TRY(launch_conv(ctx, w));
+        if (heun) {
+            TRY(launch_rows(ctx, MODE_HEUN1, w, 2 * i));
             TRY(launch_conv(ctx, w));
-            if (heun) {
-                TRY(launch_rows(ctx, MODE_HEUN1, w, 2 * i));
-                TRY(launch_conv(ctx, w));
-            }
-            if (i == n - 1)
-                for (int idx : active) CK(ctx, cudaMemsetAsync(b->sims[idx]->dmaxdp, 0, sizeof(unsigned), ctx->stream));
-            TRY(launch_rows(ctx, heun ? MODE_HEUN2 : MODE_STEP, w, heun ? 2 * i + 2 : i));
         }
-        return TDGL_OK;
-    };
+        if (i == n - 1)
+            for (int idx : active) CK(ctx, cudaMemsetAsync(b->sims[idx]->dmaxdp, 0, sizeof(unsigned), ctx->stream));
+        TRY(launch_rows(ctx, heun ? MODE_HEUN2 : MODE_STEP, w, heun ? 2 * i + 2 : i));
+    }
+    return TDGL_OK;
+}
+
+// n steps of every active sim of a batch
+int batch_steps(tdgl_batch *b, const std::vector<int> &active, int n, const double *dt) {
+    tdgl_ctx *ctx = b->ctx;
+    TRY(batch_setup(b, active, dt));
+    const bool heun = b->sims[active[0]]->integrator == TDGL_HEUN;
+    auto record = [&]() -> int { return record_batch_steps(b, active, n); };
     if (n >= 2 && !(n & 1) && !ctx->profiling && ctx->stream) {
         tdgl_batch::Cached::G *G = nullptr;
         for (auto &g : b->cache->graphs)
@@ -1898,6 +1939,146 @@ int tdgl_batch_step(tdgl_batch *b, int n, const double *dt) {
     return rc;
 }
 
+// Batch relaxation with its convergence loop on the device.  One CUDA graph per active set: a
+// conditional WHILE node repeats a body of k steps of the whole active set followed by
+// k_batch_check, which retires each running member whose last step's max |dP*| is below tol (or
+// whose flag is raised) by setting skip in its descriptor: from the next body on, every kernel's
+// blocks of that member return at once.  The loop hands back to the host when no member runs, when
+// another body would pass the cap, or when the retired members hold a quarter of the active cells
+// (the host then builds work lists without them).  Members stop at the same step as in the
+// host-checked loop, so the results are identical.
+__global__ void k_batch_check(cudaGraphConditionalHandle h, BatchRelaxState *st, SimDev *descs, const int *member,
+                              long *steps, int *status) {
+    __shared__ int s_running;
+    __shared__ unsigned long long s_retired;
+    const long done = st->done + st->k;
+    if (threadIdx.x == 0) { s_running = 0; s_retired = 0ull; }
+    __syncthreads();
+    for (int i = threadIdx.x; i < st->n; i += blockDim.x) {
+        if (!member[i] || descs[i].skip) continue;
+        const unsigned u = *descs[i].maxdp;
+        const int f = *descs[i].flag;
+        const bool conv = u < 0x7f800000u && (double)__uint_as_float(u) < st->tol;
+        if (f != 0 || conv) {
+            descs[i].skip = 1;
+            status[i] = f != 0 ? 2 : 1;
+            steps[i] = done;
+            steps[st->n + i] = (long)u;     // the last step's max |dP*| (later bodies clear maxdp)
+            atomicAdd(&s_retired, (unsigned long long)descs[i].ncell);
+        } else {
+            atomicAdd(&s_running, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->done = done;
+        st->cells_retired += (long)s_retired;
+        const bool more = s_running > 0 && done + st->k <= st->max_steps && st->cells_retired < st->cells_stop;
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+}
+
+bool batch_relax_on_device_ok(const tdgl_batch *b, const std::vector<int> &active, int k) {
+    if (b->ctx->profiling || !b->ctx->stream) return false;
+    for (int idx : active)
+        if (!relax_on_device_ok(b->sims[idx], k)) return false;
+    return true;
+}
+
+// One launch of the device loop over the active set, at most max_more steps.  On return: *done =
+// steps the loop ran; for every member status[i], and for retired members steps[i] (steps run) and
+// steps[n + i] (float bits of their last step's max |dP*|).
+int batch_relax_on_device(tdgl_batch *b, const std::vector<int> &active, const double *dt, double tol, long max_more,
+                          int k, long *done, std::vector<int> &status, std::vector<long> &steps) {
+    tdgl_ctx *ctx = b->ctx;
+    const int n = (int)b->sims.size();
+    TRY(batch_setup(b, active, dt));
+    const bool heun = b->sims[active[0]]->integrator == TDGL_HEUN;
+    if (!b->drelax) {
+        CK(ctx, cudaMalloc(&b->drelax, sizeof(BatchRelaxState)));
+        CK(ctx, cudaMalloc(&b->dmember, n * sizeof(int)));
+        CK(ctx, cudaMalloc(&b->dstatus, n * sizeof(int)));
+        CK(ctx, cudaMalloc(&b->dsteps, 2ull * n * sizeof(long)));
+    }
+    tdgl_batch::Cached &C = *b->cache;
+    if (!C.relax_exec || C.relax_k != k || C.relax_heun != heun) {
+        if (C.relax_exec) cudaGraphExecDestroy(C.relax_exec);
+        C.relax_exec = nullptr;
+        cudaGraph_t g = nullptr;
+        CK(ctx, cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle h;
+        cudaGraphNodeParams np = {};
+        cudaGraphNode_t node;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) {
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+        }
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            CK(ctx, e);
+        }
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        const long l0 = ctx->launches;
+        CK(ctx, cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        int rc = record_batch_steps(b, active, k);
+        if (rc == TDGL_OK)
+            rc = launch(ctx, TDGL_K_OTHER, [&] {
+                k_batch_check<<<1, 256, 0, ctx->stream>>>(h, b->drelax, b->ddescs, b->dmember, b->dsteps, b->dstatus);
+            });
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(ctx->stream, &captured);
+        C.relax_kernels = ctx->launches - l0;
+        ctx->launches = l0;
+        cudaGraphExec_t exec = nullptr;
+        if (rc == TDGL_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (rc != TDGL_OK) return rc;
+        CK(ctx, e);
+        C.relax_exec = exec;
+        C.relax_k = k;
+        C.relax_heun = heun;
+    }
+    std::vector<int> member(n, 0);
+    long cells = 0;
+    for (int idx : active) {
+        member[idx] = 1;
+        cells += b->sims[idx]->ncell;
+    }
+    status.assign(n, 0);
+    steps.assign(2 * n, 0);
+    BatchRelaxState st{0, max_more, tol, k, n, 0, std::max(1L, cells / 4)};
+    CK(ctx, cudaMemcpyAsync(b->drelax, &st, sizeof st, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(b->dmember, member.data(), n * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemsetAsync(b->dstatus, 0, n * sizeof(int), ctx->stream));
+    CK(ctx, cudaMemsetAsync(b->dsteps, 0, 2ull * n * sizeof(long), ctx->stream));
+    CK(ctx, cudaGraphLaunch(C.relax_exec, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(&st, b->drelax, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(status.data(), b->dstatus, n * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(steps.data(), b->dsteps, 2ull * n * sizeof(long), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    *done = st.done;
+    ctx->launches += (st.done / k) * C.relax_kernels;
+    std::vector<unsigned> us(n, 0u);
+    for (int idx : active)
+        CK(ctx, cudaMemcpyAsync(&us[idx], b->sims[idx]->dmaxdp, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int idx : active) {
+        tdgl_sim *s = b->sims[idx];
+        const long ran = status[idx] ? steps[idx] : st.done;
+        s->time += ran * dt[idx];
+        s->xstate = (s->terms & TDGL_TERM_ELEC) ? XS_PHAT : XS_NONE;
+        const unsigned u = status[idx] ? (unsigned)steps[n + idx] : us[idx];
+        float v;
+        memcpy(&v, &u, sizeof v);
+        s->last_maxdp = (u >= 0x7f800000u) ? INFINITY : (double)v;
+    }
+    return TDGL_OK;
+}
+
 int tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_steps, int check_every,
                      long *steps_taken) {
     if (!b || !dt || !(tol > 0) || max_steps < 0 || check_every < 1) return TDGL_EINVAL;
@@ -1915,6 +2096,27 @@ int tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_steps
     }
     long done = 0;
     int rc = TDGL_OK;
+    // the device loop while whole check intervals remain, then host-checked chunks
+    if (batch_relax_on_device_ok(b, active, check_every)) {
+        while (!active.empty() && max_steps - done >= check_every) {
+            long ran = 0;
+            std::vector<int> status;
+            std::vector<long> steps;
+            TRY(batch_relax_on_device(b, active, dt, tol, max_steps - done, check_every, &ran, status, steps));
+            std::vector<int> keep;
+            for (int idx : active) {
+                if (status[idx] == 0) {
+                    taken[idx] = done + ran;
+                    keep.push_back(idx);
+                    continue;
+                }
+                taken[idx] = done + steps[idx];
+                if (status[idx] == 2) rc = fail(ctx, TDGL_EDIVERGED, "sim %d diverged", idx);
+            }
+            done += ran;
+            active.swap(keep);
+        }
+    }
     while (!active.empty() && done < max_steps) {
         const int k = (int)std::min<long>(check_every, max_steps - done);
         TRY(batch_steps(b, active, k, dt));

@@ -102,6 +102,33 @@ def test_batch_relax_converged_sims_leave_the_work_list(ctx):
     B.close()
 
 
+@pytest.mark.parametrize("max_steps", [4000, 1208])
+def test_batch_device_relax_equals_single_relaxations(ctx, max_steps):
+    # the batch's device loop retires members as they converge (their kernels' blocks return at
+    # once) and hands back to the host to rebuild the work lists; every member must stop at the
+    # same step, in the same state, as its own relaxation (1208: a cap that is not a multiple of the
+    # check interval, finished by host-checked chunks)
+    from paper_2605_28800_b300 import tdgl
+    shapes = [(16, 16, 16), (12, 20, 8), (24, 24, 24), (9, 7, 5), (32, 16, 8)]
+    temps = [420.0, 300.0, 440.0, 410.0, 300.0]
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    singles, members = [], []
+    for i, (sh, T) in enumerate(zip(shapes, temps)):
+        a, _ = _bto(ctx, sh, T, seed=60 + i)
+        b, _ = _bto(ctx, sh, T, seed=60 + i)
+        singles.append(a)
+        members.append(b)
+    want = [s.relax(dt, 1e-6, max_steps, check_every=16, raise_on_cap=False)[0] for s in singles]
+    B = tdgl.Batch(ctx, members)
+    got, _ = B.relax(dt, 1e-6, max_steps, check_every=16, raise_on_cap=False)
+    assert list(got) == list(want)
+    assert min(want) < max_steps and max(want) <= max_steps
+    for a, b in zip(singles, members):
+        assert np.array_equal(a.get_P(), b.get_P())
+        assert b.last_max_dP() == a.last_max_dP()
+    B.close()
+
+
 def test_relax_reaches_oracle_state(ctx):
     shape = (6, 6, 4)
     nx, ny, nz = shape
