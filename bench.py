@@ -290,10 +290,12 @@ def gpu_arm(args, rank, world):
     if not np.isfinite(Pout.numpy()).all():
         raise RuntimeError("end-to-end run returned a non-finite P")
     zvar = {n: ctx.zpass_variant(n) for n in (128, 256, 512)}
+    row_tile = s.row_tile()
     fma_peak = ctx.fp32_fma_peak()      # after the timed region
     return dict(ms=ms, launches=launches, prof=prof, clocks=clk.summary(), ncell=ncell, wl=wl, warm=warm, fma=fma_peak,
                 e2e=aggregate_rate(ncell * e2e_steps, world, e2e_s), e2e_h2d=Ph.numel() * 4,
                 e2e_d2h=Pout.numel() * 4 + 8,
+                row_tuning={"rows_per_block": row_tile[0], "candidates_us": {str(c): round(u, 2) for c, u in row_tile[1]}},
                 zpass_tuning={str(n): {"variant": v, "us": [round(u, 2) for u in us]}
                               for n, (v, us) in zvar.items() if v >= 0})
 
@@ -811,7 +813,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
             "hbm_frac_of_fused_floor": value / world * B_ALG_FUSED / (hbm * 1e9),
-            "fft_pad": list(M), "zpass_tuning": r["zpass_tuning"], "roofline": roof, "alu_roofline": alu_roof,
+            "fft_pad": list(M), "zpass_tuning": r["zpass_tuning"], "row_tuning": r["row_tuning"], "roofline": roof, "alu_roofline": alu_roof,
             "kernels": kernels,
             "clocks": r["clocks"], "gpu_launches": r["launches"], "warmup_steps_run": r["warm"],
             "timing": "timed steps replay the library's step graphs (profiling off); per-kernel times "

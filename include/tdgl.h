@@ -169,6 +169,17 @@ int tdgl_get_dt(tdgl_sim *sim, double *dt);
 #define TDGL_ZPASS_VARIANTS 4
 int tdgl_zpass_variant(tdgl_ctx *ctx, int length, int *variant, double *us);
 int tdgl_set_zpass_variant(tdgl_ctx *ctx, int length, int variant);
+/* Row-tile autotuning of the fused step kernel (the x-rows kernel: x transforms, Landau, gradient,
+ * update) for a sim run alone.  A block takes a tile of consecutive rows of one z plane; up to
+ * TDGL_ROW_CANDIDATES tile heights (the kernel's maximum, its half and quarter, and the height that
+ * gives about one block per SM) are timed the first time a context prepares a sim of that shape
+ * (x half-length, ny, nz, electrostatics on or off), three step launches each on scratch copies of
+ * the sim's buffers (no state changes), and the fastest is kept for the context.  Sims of the
+ * generic (any-length) row kernel keep one row per block group as before.  Batch members use the
+ * kernel's maximum tile.  tdgl_row_tile reports the sim's tile (0 = not tuned) and, if not NULL,
+ * the candidates and their microseconds per launch (0 for unused slots). */
+#define TDGL_ROW_CANDIDATES 4
+int tdgl_row_tile(tdgl_sim *sim, int *rows, int *candidates, double *us);
 /* Simulated time t (s) of the sim: 0 at creation, advanced by n dt by every step call. */
 int tdgl_set_time(tdgl_sim *sim, double t);
 int tdgl_get_time(tdgl_sim *sim, double *t);

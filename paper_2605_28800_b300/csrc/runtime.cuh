@@ -44,6 +44,14 @@ struct tdgl_ctx {
     // yet tuned) and the measured microseconds per launch of each variant
     int zvar[3] = {-1, -1, -1};
     double zus[3][TDGL_ZPASS_VARIANTS] = {};
+    // row-tile autotuning of sims run alone, per (x half-length, ny, nz, electrostatics on): the
+    // chosen rows per block and the candidates' timings
+    struct RowTune {
+        int hx, ny, nz, elec, tile;
+        int cand[TDGL_ROW_CANDIDATES];
+        double us[TDGL_ROW_CANDIDATES];
+    };
+    std::vector<RowTune> rowtune;
 };
 
 namespace tdgl_rt {

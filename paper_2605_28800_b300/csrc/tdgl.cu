@@ -85,6 +85,12 @@ struct tdgl_sim {
     std::vector<int4> it_rows_full;   // row items of full tiles (batches)
     int rows_cnt_max = 1, ky_cnt_max = 1, kz_cnt_max = 1;
     int xN = 0, yN = 0, zN = 0;   // specialized x / y / z transform length (0 = generic kernels)
+    // rows per block of the tiled row kernel when the sim runs alone: 0 = the size heuristic,
+    // else the autotuner's choice; the candidates it timed and their microseconds per launch
+    int row_tile = 0;
+    bool rows_tuned = false;
+    int row_cand[TDGL_ROW_CANDIDATES] = {0};
+    double row_us[TDGL_ROW_CANDIDATES] = {0.0};
     int4 *d_rows = nullptr, *d_y = nullptr, *d_z = nullptr;
     int cur = 0;
     int xstate = XS_NONE;
@@ -280,7 +286,8 @@ void build_items(tdgl_sim *s) {
     // about one block per SM (such a small grid is bound by each block's latency, not by the
     // tile's halo overhead); in a batch the members' full tiles already fill the GPU.
     const long rows = (long)s->ny * s->nz;
-    const int RB1 = s->xN ? (int)std::min<long>(RB, std::max<long>(1, (rows + s->ctx->nsm - 1) / s->ctx->nsm)) : RB;
+    const int RB1 = s->row_tile > 0 ? std::min(s->row_tile, RB)
+                    : (s->xN ? (int)std::min<long>(RB, std::max<long>(1, (rows + s->ctx->nsm - 1) / s->ctx->nsm)) : RB);
     for (int z = 0; z < s->nz; ++z) {
         for (int y0 = 0; y0 < s->ny; y0 += RB1) s->it_rows.push_back(make_int4(0, z, y0, std::min(RB1, s->ny - y0)));
         for (int y0 = 0; y0 < s->ny; y0 += RB) s->it_rows_full.push_back(make_int4(0, z, y0, std::min(RB, s->ny - y0)));
@@ -553,6 +560,7 @@ void fill_desc(tdgl_sim *s, double dt, unsigned terms) {
 }
 
 int autotune_z(tdgl_sim *s);
+int autotune_rows(tdgl_sim *s);
 
 int prepare(tdgl_sim *s, unsigned need_terms) {
     tdgl_ctx *ctx = s->ctx;
@@ -573,6 +581,7 @@ int prepare(tdgl_sim *s, unsigned need_terms) {
         if (!s->tensor_ready) TRY(build_tensor(s));
         TRY(autotune_z(s));
     }
+    TRY(autotune_rows(s));
     return TDGL_OK;
 }
 
@@ -753,6 +762,104 @@ int autotune_z(tdgl_sim *s) {
     }
     ctx->zvar[vi] = best;
     return TDGL_OK;
+}
+
+// Row-tile autotuner (sims run alone): each candidate tile height runs the step kernel on scratch
+// copies of the x-spectrum and of the P buffer it writes (and on scratch status slots), so the
+// trial launches change no state; one launch warms up, three are timed with CUDA events.  The
+// choice is kept per (x half-length, ny, nz, electrostatics) in the context.  Runs before the sim
+// has captured any graph (its first preparation), since it rebuilds the sim's row items.
+int autotune_rows(tdgl_sim *s) {
+    if (s->rows_tuned) return TDGL_OK;
+    tdgl_ctx *ctx = s->ctx;
+    const int elec = (s->terms & TDGL_TERM_ELEC) ? 1 : 0;
+    if (elec && !s->spectra_alloc) return TDGL_OK;   // tuned once the spectra exist
+    s->rows_tuned = true;
+    if (!s->xN || ctx->profiling || !s->d_rows) return TDGL_OK;
+    for (const auto &r : ctx->rowtune)
+        if (r.hx == s->hx && r.ny == s->ny && r.nz == s->nz && r.elec == elec) {
+            s->row_tile = r.tile;
+            memcpy(s->row_cand, r.cand, sizeof r.cand);
+            memcpy(s->row_us, r.us, sizeof r.us);
+            build_items(s);
+            return upload_items(s);
+        }
+    // candidates: the kernel's tile, its half and quarter, the one-block-per-SM height
+    const int full = s->rows_cnt_max;
+    const long rows = (long)s->ny * s->nz;
+    const int spread = (int)std::min<long>(full, std::max<long>(1, (rows + ctx->nsm - 1) / ctx->nsm));
+    int cand[TDGL_ROW_CANDIDATES] = {0};
+    int nc = 0;
+    for (int c : {full, full / 2, full / 4, spread}) {
+        bool seen = c < 1;
+        for (int i = 0; i < nc; ++i) seen = seen || cand[i] == c;
+        if (!seen && nc < TDGL_ROW_CANDIDATES) cand[nc++] = c;
+    }
+    double us[TDGL_ROW_CANDIDATES] = {0.0};
+    float2 *xs = nullptr;
+    float *ps = nullptr;
+    unsigned *slots = nullptr;
+    int4 *items = nullptr;
+    SimDev *dd = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = TDGL_OK;
+    auto ck = [&](cudaError_t e) {
+        if (e != cudaSuccess && rc == TDGL_OK)
+            rc = fail(ctx, e == cudaErrorMemoryAllocation ? TDGL_ENOMEM : TDGL_ECUDA, "row tuner: %s", cudaGetErrorString(e));
+        return rc == TDGL_OK;
+    };
+    const size_t xbytes = elec ? 3ull * s->nz * s->ny * s->kxp * sizeof(float2) : 0;
+    if (elec) ck(cudaMalloc(&xs, xbytes)) && ck(cudaMemcpyAsync(xs, s->dX, xbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    ck(cudaMalloc(&ps, 3ull * s->ncell * sizeof(float))) && ck(cudaMalloc(&slots, 64)) &&
+        ck(cudaMemsetAsync(slots, 0, 64, ctx->stream)) && ck(cudaMalloc(&dd, sizeof(SimDev))) &&
+        ck(cudaMalloc(&items, ((rows + 0) * sizeof(int4)))) && ck(cudaEventCreate(&e0)) && ck(cudaEventCreate(&e1));
+    if (rc == TDGL_OK) {
+        fill_desc(s, 0.0, s->terms);
+        SimDev D = s->desc;
+        if (elec) D.X = xs;
+        D.P[1] = ps;
+        D.maxdp = slots;
+        D.flag = reinterpret_cast<int *>(slots + 4);
+        ck(cudaMemcpyAsync(dd, &D, sizeof D, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    for (int c = 0; c < nc && rc == TDGL_OK; ++c) {
+        std::vector<int4> it;
+        for (int z = 0; z < s->nz; ++z)
+            for (int y0 = 0; y0 < s->ny; y0 += cand[c]) it.push_back(make_int4(0, z, y0, std::min(cand[c], s->ny - y0)));
+        if (!ck(cudaMemcpyAsync(items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream))) break;
+        const Group g{s->xN, items, (int)it.size(), smem_rows(s, s->rows_cnt_max)};
+        rows_launch<MODE_STEP>(g, dd, ctx->stream, 0);
+        ck(cudaEventRecord(e0, ctx->stream));
+        for (int r = 0; r < 3; ++r) rows_launch<MODE_STEP>(g, dd, ctx->stream, 0);
+        ck(cudaEventRecord(e1, ctx->stream));
+        ck(cudaGetLastError());
+        if (ck(cudaEventSynchronize(e1))) {
+            float ms = 0.f;
+            ck(cudaEventElapsedTime(&ms, e0, e1));
+            us[c] = 1e3 * ms / 3.0;
+        }
+    }
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(xs);
+    cudaFree(ps);
+    cudaFree(slots);
+    cudaFree(items);
+    cudaFree(dd);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc != TDGL_OK) return rc;
+    int best = 0;
+    for (int c = 1; c < nc; ++c)
+        if (us[c] < us[best]) best = c;
+    tdgl_ctx::RowTune r{s->hx, s->ny, s->nz, elec, cand[best], {0}, {0.0}};
+    memcpy(r.cand, cand, sizeof cand);
+    memcpy(r.us, us, sizeof us);
+    ctx->rowtune.push_back(r);
+    s->row_tile = cand[best];
+    memcpy(s->row_cand, cand, sizeof cand);
+    memcpy(s->row_us, us, sizeof us);
+    build_items(s);
+    return upload_items(s);
 }
 
 // bring X to the E-hat state of the current P (descriptor already uploaded with P[0] = current)
@@ -1359,6 +1466,16 @@ int tdgl_set_zpass_variant(tdgl_ctx *ctx, int length, int variant) {
     ctx->zvar[vi] = variant;
     if (variant < 0)
         for (int v = 0; v < kZVariants; ++v) ctx->zus[vi][v] = 0.0;
+    return TDGL_OK;
+}
+
+int tdgl_row_tile(tdgl_sim *s, int *rows, int *candidates, double *us) {
+    if (!s || !rows) return TDGL_EINVAL;
+    *rows = s->row_tile;
+    for (int i = 0; i < TDGL_ROW_CANDIDATES; ++i) {
+        if (candidates) candidates[i] = s->row_cand[i];
+        if (us) us[i] = s->row_us[i];
+    }
     return TDGL_OK;
 }
 

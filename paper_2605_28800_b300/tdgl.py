@@ -24,6 +24,7 @@ KERNEL_NAMES = {K_STEP: "k_rows<STEP>", K_YFWD: "k_yfwd", K_ZCONV: "k_zconv", K_
 MAX_MATERIALS, MAX_DIM = 16, 1024
 EULER, HEUN, RK45, AB3M2 = 0, 1, 2, 3
 ZPASS_VARIANTS = 4
+ROW_CANDIDATES = 4
 
 _CODES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", EDIVERGED: "EDIVERGED",
           ENOTCONVERGED: "ENOTCONVERGED", ESTATE: "ESTATE", ETOOBIG: "ETOOBIG"}
@@ -68,6 +69,7 @@ _SIGS = {
     "tdgl_set_adaptive": (_I, [_VP, _D, _D, _D]),
     "tdgl_get_dt": (_I, [_VP, ctypes.POINTER(_D)]),
     "tdgl_zpass_variant": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "tdgl_row_tile": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "tdgl_fp32_fma_peak": (_I, [_VP, ctypes.POINTER(_D)]),
     "tdgl_set_zpass_variant": (_I, [_VP, _I, _I]),
     "tdgl_set_time": (_I, [_VP, _D]),
@@ -298,6 +300,13 @@ class Sim:
 
     def step(self, n: int, dt: float):
         self._c(self.lib.tdgl_step(self.h, int(n), float(dt)))
+
+    def row_tile(self):
+        """(rows per block chosen by the row-tile autotuner, 0 = not tuned, and the list of
+        (candidate, microseconds per launch) it timed)"""
+        r, c, us = _I(), (_I * ROW_CANDIDATES)(), (_D * ROW_CANDIDATES)()
+        self._c(self.lib.tdgl_row_tile(self.h, ctypes.byref(r), c, us))
+        return r.value, [(int(a), float(b)) for a, b in zip(c, us) if a > 0]
 
     def last_max_dP(self) -> float:
         v = _D()

@@ -54,7 +54,7 @@ def test_binding_constants_match_the_header():
     # every #define of the header that the binding mirrors has the same value there
     from paper_2605_28800_b300 import tdgl
     defs = dict(re.findall(r"#define\s+TDGL_([A-Z0-9_]+)\s+\(?(-?\d+)", open(HEADER).read()))
-    pairs = {"ZPASS_VARIANTS": tdgl.ZPASS_VARIANTS, "EULER": tdgl.EULER, "HEUN": tdgl.HEUN, "RK45": tdgl.RK45,
+    pairs = {"ZPASS_VARIANTS": tdgl.ZPASS_VARIANTS, "ROW_CANDIDATES": tdgl.ROW_CANDIDATES, "EULER": tdgl.EULER, "HEUN": tdgl.HEUN, "RK45": tdgl.RK45,
              "AB3M2": tdgl.AB3M2, "K_STEP": tdgl.K_STEP, "K_ZCONV": tdgl.K_ZCONV, "K_UNET": tdgl.K_UNET,
              "EINVAL": tdgl.EINVAL, "ECUDA": tdgl.ECUDA, "EDIVERGED": tdgl.EDIVERGED}
     for name, value in pairs.items():

@@ -129,6 +129,32 @@ def test_batch_device_relax_equals_single_relaxations(ctx, max_steps):
     B.close()
 
 
+def test_row_tile_autotuner_times_candidates_and_reuses_the_choice():
+    # the first preparation of a sim shape times each candidate tile of the step kernel on scratch
+    # buffers (state unchanged) and keeps the fastest for the context; a second sim of the shape
+    # reuses it, and both step like the oracle
+    from paper_2605_28800_b300 import tdgl
+    c = tdgl.Context(0)
+    try:
+        shape = (32, 32, 16)
+        dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+        a, P = _bto(c, shape, seed=71)
+        assert a.row_tile()[0] == 0
+        a.step(2, dt)
+        tile, cands = a.row_tile()
+        assert len(cands) >= 2 and all(us > 0 for _, us in cands)
+        assert tile == min(cands, key=lambda cu: cu[1])[0]
+        b, _ = _bto(c, shape, seed=71)
+        b.step(2, dt)
+        assert b.row_tile() == (tile, cands)
+        assert np.array_equal(a.get_P(), b.get_P())
+        nx, ny, nz = shape
+        o = oracle_sys(shape, (1e-9,) * 3, np.ones((nz, ny, nx), np.uint8), {1: synth.BTO}, 300.0, 45.0)
+        assert np.abs(a.get_P() - o.run(P.astype(np.float64), dt, 2)).max() / a.scales()[0] <= 1e-5
+    finally:
+        c.close()
+
+
 def test_relax_reaches_oracle_state(ctx):
     shape = (6, 6, 4)
     nx, ny, nz = shape
