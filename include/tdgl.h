@@ -41,6 +41,8 @@ extern "C" {
 #define TDGL_ENOTCONVERGED  -5   /* relaxation hit its step cap before reaching the tolerance   */
 #define TDGL_ESTATE         -6   /* call not valid in the current state (e.g. no material)      */
 #define TDGL_ETOOBIG        -7   /* grid too large for tdgl_elec_field_static's fixed scratch   */
+#define TDGL_ETIMEOUT       -8   /* a bounded device wait (a pipeline barrier of a tensor copy)
+                                    gave up; the kernel returned and the device stays usable     */
 
 #define TDGL_HOST   0
 #define TDGL_DEVICE 1
@@ -279,6 +281,15 @@ int tdgl_elec_field_static(int nx, int ny, int nz, double dx, double dy, double 
 int tdgl_profile(tdgl_ctx *ctx, int enable);
 int tdgl_profile_read(tdgl_ctx *ctx, int kind, double *total_ms, long *launches);
 
+/* Timeout path check.  Every wait of the library's kernels on an mbarrier (the arrival of a tensor
+ * copy, a tensor-core commit) is bounded: after its poll limit the waiting thread sets a status flag,
+ * the kernel finishes and the call returns TDGL_ETIMEOUT, with the context still usable.
+ * tdgl_wait_probe runs that path on purpose and safely: one thread of a one-block kernel waits for
+ * an mbarrier on which nothing is pending and nothing will arrive (no copy in flight), for at most
+ * `polls` polls (1 .. 2^24), then records the timeout.  Returns TDGL_ETIMEOUT (the expected result),
+ * TDGL_EINVAL for a bad count, TDGL_ECUDA if the launch failed. */
+int tdgl_wait_probe(tdgl_ctx *ctx, long polls);
+
 /* Measurement helper (it computes nothing of the paper's method): the device's FP32 fused
  * multiply-add throughput, the denominator of the FP32-ALU roofline of the transform kernels.  One
  * launch of 8 independent FMA chains per thread on every SM (a warm-up launch, then three timed with
@@ -313,7 +324,7 @@ int tdgl_fp32_fma_peak(tdgl_ctx *ctx, double *tflops);
  *   respect to every parameter (grads: caller-owned, param_count floats, same order), no update.
  * tdgl_unet_train_step: forward, loss, backward and one Adam step (lr; beta1 0.9, beta2 0.999,
  *   eps 1e-8, bias-corrected with the net's own step counter).  *loss receives the loss before the
- *   update.  Returns TDGL_ECUDA if a tensor-core pipeline wait timed out (the device stays usable).
+ *   update.  Returns TDGL_ETIMEOUT if a tensor-core pipeline wait timed out (the device stays usable).
  * All calls are ordered on the context's stream and return after the results are in place. */
 int  tdgl_unet_create(tdgl_ctx *ctx, int cin, int cout, int levels, const int *chans, int nx, int ny, int nz,
                       int max_batch, uint64_t seed, tdgl_unet **out);

@@ -126,7 +126,7 @@ struct tdgl_batch {
     struct Cached;
     Cached *cache = nullptr;
     // device relaxation loop state: loop counters, membership of the current active set, steps
-    // taken and status (0 running, 1 converged, 2 diverged or timed out) per sim
+    // taken and status (0 running, 1 converged, 2 diverged, 3 a bounded wait timed out) per sim
     struct BatchRelaxState *drelax = nullptr;
     int *dmember = nullptr, *dstatus = nullptr;
     long *dsteps = nullptr;
@@ -1231,6 +1231,39 @@ __global__ void __launch_bounds__(256) k_fma_peak(float *sink, int iters, float 
     if (s == -1.2345f) sink[0] = s;
 }
 
+// Timeout probe: thread 0 waits for phase 0 of an mbarrier that expects one arrival nobody makes (no
+// copy is in flight, so giving up leaves nothing outstanding), at most `polls` polls, and records
+// the timeout in flag bit 1 as the pipelined kernels do.
+__global__ void k_wait_probe(int *flag, long polls) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::mbar_fence_init();
+        if (!tc::mbar_wait(&bar, 0u, polls)) atomicOr(flag, 2);
+    }
+}
+
+int tdgl_wait_probe(tdgl_ctx *ctx, long polls) {
+    if (!ctx) return TDGL_EINVAL;
+    if (polls < 1 || polls > (1L << 24)) return fail(ctx, TDGL_EINVAL, "poll count %ld", polls);
+    ctx_set(ctx);
+    int *dflag = nullptr;
+    CK(ctx, cudaMalloc(&dflag, sizeof(int)));
+    int h = 0;
+    cudaError_t e = cudaMemsetAsync(dflag, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) {
+        k_wait_probe<<<1, 32, 0, ctx->stream>>>(dflag, polls);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, dflag, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(dflag);
+    if (e != cudaSuccess) return fail(ctx, TDGL_ECUDA, "wait probe: %s", cudaGetErrorString(e));
+    ctx->launches++;
+    if (h & 2) return fail(ctx, TDGL_ETIMEOUT, "the probe's bounded wait gave up after %ld polls", polls);
+    return TDGL_OK;
+}
+
 int tdgl_fp32_fma_peak(tdgl_ctx *ctx, double *tflops) {
     if (!ctx || !tflops) return TDGL_EINVAL;
     ctx_set(ctx);
@@ -1612,7 +1645,7 @@ int tdgl_step(tdgl_sim *s, int n, double dt) {
     TRY(read_status(s, &m, &f));
     if (f) {
         CK(s->ctx, cudaMemsetAsync(s->dflag, 0, sizeof(int), s->ctx->stream));
-        if (f & 2) return fail(s->ctx, TDGL_ECUDA, "a bounded wait for a tensor copy timed out");
+        if (f & 2) return fail(s->ctx, TDGL_ETIMEOUT, "a bounded wait for a tensor copy timed out");
         return fail(s->ctx, TDGL_EDIVERGED, "P diverged (NaN or |P| > 1e3 P0)");
     }
     return TDGL_OK;
@@ -1734,7 +1767,7 @@ int tdgl_relax(tdgl_sim *s, double dt, double tol, long max_steps, int check_eve
     }
     auto flagged = [&](int f) {
         CK(s->ctx, cudaMemsetAsync(s->dflag, 0, sizeof(int), s->ctx->stream));
-        if (f & 2) return fail(s->ctx, TDGL_ECUDA, "a bounded wait for a tensor copy timed out");
+        if (f & 2) return fail(s->ctx, TDGL_ETIMEOUT, "a bounded wait for a tensor copy timed out");
         return fail(s->ctx, TDGL_EDIVERGED, "P diverged after %ld steps", done);
     };
     const bool elec = (s->terms & TDGL_TERM_ELEC) != 0;
@@ -2051,7 +2084,8 @@ int tdgl_batch_step(tdgl_batch *b, int n, const double *dt) {
         double m;
         int f;
         TRY(read_status(b->sims[idx], &m, &f));
-        if (f) rc = fail(ctx, TDGL_EDIVERGED, "sim %d diverged", idx);
+        if (f) rc = (f & 2) ? fail(ctx, TDGL_ETIMEOUT, "sim %d: a bounded wait timed out", idx)
+                      : fail(ctx, TDGL_EDIVERGED, "sim %d diverged", idx);
     }
     return rc;
 }
@@ -2078,7 +2112,7 @@ __global__ void k_batch_check(cudaGraphConditionalHandle h, BatchRelaxState *st,
         const bool conv = u < 0x7f800000u && (double)__uint_as_float(u) < st->tol;
         if (f != 0 || conv) {
             descs[i].skip = 1;
-            status[i] = f != 0 ? 2 : 1;
+            status[i] = (f & 2) ? 3 : (f != 0 ? 2 : 1);
             steps[i] = done;
             steps[st->n + i] = (long)u;     // the last step's max |dP*| (later bodies clear maxdp)
             atomicAdd(&s_retired, (unsigned long long)descs[i].ncell);
@@ -2229,6 +2263,7 @@ int tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_steps
                 }
                 taken[idx] = done + steps[idx];
                 if (status[idx] == 2) rc = fail(ctx, TDGL_EDIVERGED, "sim %d diverged", idx);
+                if (status[idx] == 3) rc = fail(ctx, TDGL_ETIMEOUT, "sim %d: a bounded wait timed out", idx);
             }
             done += ran;
             active.swap(keep);
@@ -2245,7 +2280,8 @@ int tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_steps
             TRY(read_status(b->sims[idx], &m, &f));
             taken[idx] = done;
             if (f) {
-                rc = fail(ctx, TDGL_EDIVERGED, "sim %d diverged", idx);
+                rc = (f & 2) ? fail(ctx, TDGL_ETIMEOUT, "sim %d: a bounded wait timed out", idx)
+                             : fail(ctx, TDGL_EDIVERGED, "sim %d diverged", idx);
                 continue;
             }
             if (!(m < tol)) keep.push_back(idx);

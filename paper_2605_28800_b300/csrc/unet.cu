@@ -195,7 +195,7 @@ int check_err(tdgl_ctx *ctx, int *derr) {
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     if (h) {
         cudaMemsetAsync(derr, 0, sizeof(int), ctx->stream);
-        return fail(ctx, TDGL_ECUDA, "tensor-core pipeline wait timed out");
+        return fail(ctx, TDGL_ETIMEOUT, "tensor-core pipeline wait timed out");
     }
     return TDGL_OK;
 }

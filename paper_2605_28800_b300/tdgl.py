@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtdgl.so")
 
-OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ENOTCONVERGED, ESTATE, ETOOBIG = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ENOTCONVERGED, ESTATE, ETOOBIG, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7, -8
 HOST, DEVICE = 0, 1
 TERM_LANDAU, TERM_GRAD, TERM_ELEC, TERM_EXT, TERM_ALL = 1, 2, 4, 8, 15
 K_STEP, K_YFWD, K_ZCONV, K_YINV, K_XFWD, K_OTHER, K_UNET = range(7)
@@ -71,6 +71,7 @@ _SIGS = {
     "tdgl_zpass_variant": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "tdgl_row_tile": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "tdgl_fp32_fma_peak": (_I, [_VP, ctypes.POINTER(_D)]),
+    "tdgl_wait_probe": (_I, [_VP, _L]),
     "tdgl_set_zpass_variant": (_I, [_VP, _I, _I]),
     "tdgl_set_time": (_I, [_VP, _D]),
     "tdgl_get_time": (_I, [_VP, ctypes.POINTER(_D)]),
@@ -155,6 +156,10 @@ class Context:
     def _adopt(self, obj):
         self._children.add(obj)
 
+    def last_error(self) -> str:
+        """message of the last failed call on this context"""
+        return self.lib.tdgl_last_error(self.h).decode()
+
     def check(self, rc):
         if rc != OK:
             raise TdglError(rc, self.lib.tdgl_last_error(self.h).decode())
@@ -172,6 +177,11 @@ class Context:
         v = _D()
         self.check(self.lib.tdgl_fp32_fma_peak(self.h, ctypes.byref(v)))
         return v.value
+
+    def wait_probe(self, polls: int) -> int:
+        """run one bounded mbarrier wait that nothing satisfies (nothing pending) for at most polls
+        polls; returns the library's status code (ETIMEOUT expected) without raising"""
+        return int(self.lib.tdgl_wait_probe(self.h, int(polls)))
 
     def set_zpass_variant(self, length, variant):
         self.check(self.lib.tdgl_set_zpass_variant(self.h, int(length), int(variant)))

@@ -56,7 +56,7 @@ def test_binding_constants_match_the_header():
     defs = dict(re.findall(r"#define\s+TDGL_([A-Z0-9_]+)\s+\(?(-?\d+)", open(HEADER).read()))
     pairs = {"ZPASS_VARIANTS": tdgl.ZPASS_VARIANTS, "ROW_CANDIDATES": tdgl.ROW_CANDIDATES, "EULER": tdgl.EULER, "HEUN": tdgl.HEUN, "RK45": tdgl.RK45,
              "AB3M2": tdgl.AB3M2, "K_STEP": tdgl.K_STEP, "K_ZCONV": tdgl.K_ZCONV, "K_UNET": tdgl.K_UNET,
-             "EINVAL": tdgl.EINVAL, "ECUDA": tdgl.ECUDA, "EDIVERGED": tdgl.EDIVERGED}
+             "EINVAL": tdgl.EINVAL, "ECUDA": tdgl.ECUDA, "EDIVERGED": tdgl.EDIVERGED, "ETIMEOUT": tdgl.ETIMEOUT}
     for name, value in pairs.items():
         assert name in defs, name
         assert int(defs[name]) == value, name

@@ -155,6 +155,20 @@ def test_row_tile_autotuner_times_candidates_and_reuses_the_choice():
         c.close()
 
 
+def test_bounded_wait_times_out_and_the_context_stays_usable(ctx):
+    # a wait on an mbarrier that nothing will complete (no copy in flight) gives up after its poll
+    # limit; the library reports ETIMEOUT and the same context keeps stepping correctly
+    from paper_2605_28800_b300 import tdgl
+    assert ctx.wait_probe(1000) == tdgl.ETIMEOUT
+    assert "gave up" in ctx.last_error()
+    assert ctx.wait_probe(0) == tdgl.EINVAL
+    s, P = _bto(ctx, (8, 8, 4), seed=81)
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    s.step(3, dt)
+    o = oracle_sys((8, 8, 4), (1e-9,) * 3, np.ones((4, 8, 8), np.uint8), {1: synth.BTO}, 300.0, 45.0)
+    assert np.abs(s.get_P() - o.run(P.astype(np.float64), dt, 3)).max() / s.scales()[0] <= 1e-5
+
+
 def test_relax_reaches_oracle_state(ctx):
     shape = (6, 6, 4)
     nx, ny, nz = shape
