@@ -484,6 +484,8 @@ def hysteresis(args):
     torch.cuda.set_device(dev)
     ctx = tdgl.Context(dev)
     wl = workload("pto_sto_bilayer_256x256x64")
+    if args.loop_dt_star > 0:
+        wl["dt_star"] = args.loop_dt_star
     s, dt = make_sim(ctx, wl)
     s.energy()                      # one-off tensor build, outside the timed loop
     pto = wl["mat"] == 1
@@ -497,14 +499,217 @@ def hysteresis(args):
         n, ok = s.relax(dt, args.tol, args.loop_steps, CHECK_EVERY, raise_on_cap=False)
         t_relax += time.perf_counter() - ta
         P = s.get_P()
-        points.append({"Ez_MV_per_m": E / 1e6, "steps": n, "converged": ok, "mean_Pz_PTO": float(P[2][pto].mean())})
+        points.append({"Ez_MV_per_m": E / 1e6, "steps": n, "converged": ok, "residual": s.last_max_dP(),
+                       "mean_Pz_PTO": float(P[2][pto].mean())})
     wall = time.perf_counter() - t0
     steps = sum(p["steps"] for p in points)
     line = {"metric": "DC hysteresis loop time", "unit": "s", "workload": "pto_sto_bilayer_256x256x64",
             "points": len(points), "tol": args.tol, "max_steps_per_point": args.loop_steps,
-            "relax_seconds": t_relax, "loop_seconds": wall, "total_steps": steps,
+            "dt_star": wl["dt_star"], "relax_seconds": t_relax, "loop_seconds": wall, "total_steps": steps,
             "cell_updates_per_s": steps * ncell / t_relax, "converged_points": sum(p["converged"] for p in points),
+            "max_residual": max(p["residual"] for p in points),
+            "loop_area_kJ_per_m3": loop_area([p["Ez_MV_per_m"] * 1e6 for p in points],
+                                             [p["mean_Pz_PTO"] for p in points]) / 1e3,
             "per_point": points}
+    print(json.dumps(line))
+
+
+# ---- analysis of recorded textures and loops (host side, on results read back) ------------------
+def loop_area(E, P):
+    """Area enclosed by the closed polygon (E_i, P_i) (shoelace formula; the last point joins the
+    first).  For a P-E hysteresis loop, in V/m times C/m^2, it is the energy dissipated per cycle
+    and unit volume, J/m^3 (Sec. 4.4, Fig. 3(c))."""
+    E = np.asarray(E, np.float64)
+    P = np.asarray(P, np.float64)
+    return 0.5 * abs(float(np.dot(E, np.roll(P, -1)) - np.dot(np.roll(E, -1), P)))
+
+
+def topological_charge(p):
+    """Skyrmion number of a planar texture p (3, ny, nx): the signed solid angles of the unit
+    vectors over the two triangles of every plaquette (Berg-Luscher lattice form), summed and
+    divided by 4 pi.  An integer whenever the texture is uniform along the plane's border."""
+    n = np.asarray(p, np.float64)
+    n = n / np.maximum(np.linalg.norm(n, axis=0, keepdims=True), 1e-300)
+
+    def omega(a, b, c):
+        triple = np.sum(a * np.cross(b, c, axis=0), axis=0)
+        den = 1.0 + np.sum(a * b, axis=0) + np.sum(b * c, axis=0) + np.sum(c * a, axis=0)
+        return 2.0 * np.arctan2(triple, den)
+
+    n00, n10, n11, n01 = n[:, :-1, :-1], n[:, :-1, 1:], n[:, 1:, 1:], n[:, 1:, :-1]
+    return float((omega(n00, n10, n11) + omega(n00, n11, n01)).sum() / (4.0 * np.pi))
+
+
+def plane_texture(p):
+    """Descriptors of a planar cut p (3, ny, nx) of P, C/m^2: topological charge, fraction with
+    P_z > 0, mean |P_z| and in-plane |P|, the mean curl of the in-plane part (units of P per cell;
+    a vortex tube along z has a large one) and the number of connected P_z-sign domains."""
+    from scipy import ndimage
+    px, py, pz = (np.asarray(c, np.float64) for c in p)
+    curl = np.gradient(py, axis=1) - np.gradient(px, axis=0)
+    ndom = ndimage.label(pz > 0)[1] + ndimage.label(pz <= 0)[1]
+    return {"Q": topological_charge(p), "frac_up": float((pz > 0).mean()), "mean_abs_Pz": float(np.abs(pz).mean()),
+            "mean_inplane": float(np.hypot(px, py).mean()), "mean_curl": float(curl.mean()), "domains": int(ndom)}
+
+
+def ac_loop(args):
+    """P-E loops of the Sec. 4.4 sample (synth.CONFIG_AC: 20 nm PbTiO3 on 12 nm SrTiO3, 128 x 128 nm,
+    eps_B = 649, 300 K) under E_z(t) = E0 cos(2 pi f t) at each frequency of --ac-freqs (MHz; one full
+    period from the state relaxed at +E0, mean P_z of the PbTiO3 layers sampled --ac-samples times),
+    and the quasi-static DC loop of the same sample (81 points, +-400 MV/m, each relaxed to --tol or
+    --dc-steps steps).  Reports each loop's area (the hysteresis energy of Fig. 3(c)), the coercive
+    fields and the time per loop."""
+    import math
+    import torch
+    from paper_2605_28800_b300 import tdgl
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    ctx = tdgl.Context(dev)
+    c = synth.CONFIG_AC
+    shape = c["shape"]
+    mat = synth.layer_map(shape, c["layers"])
+    pto = mat == 1
+    P = synth.uniform_P(shape, c["amp"], c["seed"])
+    P[2][pto] += np.float32(c["p_up"])
+    s = tdgl.Sim(ctx, shape, c["cell"])
+    s.define_material(1, synth.PTO)
+    s.define_material(2, synth.STO)
+    s.set_material_map(mat)
+    s.set_temperature(c["T"])
+    s.set_eps_b(c["eps_b"])
+    s.set_P(P)
+    P0, a = s.scales()
+    dt = args.ac_dt_star / a
+    ncell = int(np.prod(shape))
+    E0 = c["E0"]
+    mean_pz = lambda: float(s.get_P()[2][pto].mean())
+
+    def coercive(E, Pz):
+        """fields where the sampled mean P_z changes sign (linear interpolation)"""
+        out = []
+        for i in range(len(E) - 1):
+            if Pz[i] * Pz[i + 1] < 0:
+                out.append((E[i] + (E[i + 1] - E[i]) * Pz[i] / (Pz[i] - Pz[i + 1])) / 1e6)
+        return out
+
+    s.set_field((0.0, 0.0, E0))
+    n_sat, ok_sat = s.relax(dt, args.tol, args.dc_steps, CHECK_EVERY, raise_on_cap=False)
+    Psat = s.get_P()
+    # quasi-static loop
+    dc, t0 = [], time.perf_counter()
+    for E in c["dc_fields"]:
+        s.set_field((0.0, 0.0, E))
+        n, ok = s.relax(dt, args.tol, args.dc_steps, CHECK_EVERY, raise_on_cap=False)
+        dc.append({"Ez_MV_per_m": E / 1e6, "steps": n, "converged": ok, "residual": s.last_max_dP(),
+                   "mean_Pz_PTO": mean_pz()})
+    t_dc = time.perf_counter() - t0
+    Edc = [p["Ez_MV_per_m"] * 1e6 for p in dc]
+    Pdc = [p["mean_Pz_PTO"] for p in dc]
+    dc_rec = {"points": len(dc), "converged_points": sum(p["converged"] for p in dc),
+              "max_residual": max(p["residual"] for p in dc), "steps": sum(p["steps"] for p in dc),
+              "seconds": t_dc, "area_kJ_per_m3": loop_area(Edc, Pdc) / 1e3,
+              "coercive_MV_per_m": coercive(Edc, Pdc), "per_point": dc}
+    # AC loops, one period each from the state relaxed at +E0
+    ac = []
+    s.set_field((0.0, 0.0, 0.0))
+    for f_mhz in args.ac_freqs:
+        f = f_mhz * 1e6
+        s.set_P(Psat)
+        s.set_time(0.0)
+        s.set_field_ac((0.0, 0.0, E0), f, math.pi / 2)
+        nper = int(round(1.0 / (f * dt)))
+        chunk = max(1, nper // args.ac_samples)
+        E_s, P_s = [E0], [mean_pz()]
+        done, t0 = 0, time.perf_counter()
+        while done < nper:
+            k = min(chunk, nper - done)
+            s.step(k, dt)
+            done += k
+            E_s.append(E0 * math.cos(2.0 * math.pi * f * s.time()))
+            P_s.append(mean_pz())
+        el = time.perf_counter() - t0
+        ac.append({"f_MHz": f_mhz, "steps_per_period": nper, "seconds": el,
+                   "cell_updates_per_s": nper * ncell / el, "area_kJ_per_m3": loop_area(E_s, P_s) / 1e3,
+                   "coercive_MV_per_m": coercive(E_s, P_s), "Pz_min": min(P_s), "Pz_max": max(P_s),
+                   "E_MV_per_m": [e / 1e6 for e in E_s], "mean_Pz_PTO": P_s})
+    s.set_field_ac((0.0, 0.0, 0.0), 0.0, 0.0)
+    line = {"metric": "P-E loop area vs AC frequency", "unit": "kJ/m^3", "sample": "128x128x32, 12 nm SrTiO3 + 20 nm PbTiO3",
+            "dt_star": args.ac_dt_star, "dt_s": dt, "tol": args.tol, "E0_MV_per_m": E0 / 1e6,
+            "saturation": {"steps": n_sat, "converged": ok_sat, "mean_Pz_PTO": float(Psat[2][pto].mean())},
+            "dc": dc_rec, "ac": ac}
+    if args.out:
+        with open(args.out, "w") as fh:
+            json.dump(line, fh)
+    summary = dict(line, dc={k: v for k, v in dc_rec.items() if k != "per_point"},
+                   ac=[{k: v for k, v in r.items() if k not in ("E_MV_per_m", "mean_Pz_PTO")} for r in ac])
+    print(json.dumps(summary))
+
+
+def skyrmion(args):
+    """Strain sweep of Sec. 4.4 (Fig. 4; synth.CONFIG_SKX): 40 x 40 x 32 nm PbTiO3 on 8 nm SrTiO3,
+    0.5 nm cells, r_s = 1.0 ... 1.8 on the PbTiO3 z quadratic term, each r_s relaxed (to --tol or
+    --skx-steps steps) from the state of the one before plus a seeded +-(--skx-kick) perturbation,
+    the first from the seeded random start.
+    Reports per r_s the steps, the energy density, and the texture of the PbTiO3 mid-plane
+    (topological charge, P_z-sign domains, in-plane curl) with a classification."""
+    import torch
+    from paper_2605_28800_b300 import tdgl
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    ctx = tdgl.Context(dev)
+    c = synth.CONFIG_SKX
+    shape = c["shape"]
+    nx, ny, nz = shape
+    mat = synth.layer_map(shape, c["layers"])
+    z_pto = [z for z in range(nz) if mat[z].any() and (mat[z] == 1).all()]
+    mid = z_pto[len(z_pto) // 2]
+    vol = float((mat > 0).sum()) * float(np.prod(c["cell"]))
+    s = tdgl.Sim(ctx, shape, c["cell"])
+    s.define_material(1, synth.PTO_SKX)
+    s.define_material(2, synth.STO_SKX)
+    s.set_material_map(mat)
+    s.set_temperature(c["T"])
+    s.set_eps_b(args.skx_eps_b if args.skx_eps_b > 0 else c["eps_b"])
+    s.set_P(synth.uniform_P(shape, c["amp"], c["seed"]))
+    P0, a = s.scales()
+    dt = args.skx_dt_star / a
+    rows, t_all = [], time.perf_counter()
+    for i, rs in enumerate(c["r_s"]):
+        s.define_material(1, dict(synth.PTO_SKX, r_s=float(rs)))
+        if i > 0 and args.skx_kick > 0:
+            # the state relaxed at the previous r_s plus a fresh seeded perturbation: a texture with
+            # P_z = 0 in its bulk (the r_s = 1 vortex tube) is a stationary point of Eq. 1 at any
+            # r_s, and left alone it passes the per-step tolerance before its instability shows
+            Pk = s.get_P() + synth.uniform_P(shape, args.skx_kick, c["seed"] + i) * (mat > 0)
+            s.set_P(Pk.astype(np.float32))
+        t0 = time.perf_counter()
+        n, ok = s.relax(dt, args.tol, args.skx_steps, CHECK_EVERY, raise_on_cap=False)
+        el = time.perf_counter() - t0
+        e = s.energy()
+        P = s.get_P()
+        tex = plane_texture(P[:, mid])
+        pz = P[2][mat == 1]
+        if tex["mean_inplane"] > tex["mean_abs_Pz"] and abs(tex["mean_curl"]) > 0.01:
+            kind = "vortex tube"        # in-plane polarization circulating about the z axis
+        elif abs(tex["Q"]) > 0.8:
+            kind = "skyrmion"
+        elif tex["domains"] > 2:
+            kind = "multidomain"
+        else:
+            kind = "single domain" if tex["domains"] <= 1 else "two domains"
+        rows.append({"r_s": round(float(rs), 3), "steps": n, "converged": ok, "residual": s.last_max_dP(),
+                     "seconds": el, "energy_density_MJ_per_m3": e["total"] / vol / 1e6,
+                     "energy_terms_MJ_per_m3": {k: v / vol / 1e6 for k, v in e.items() if k != "total"},
+                     "mean_Pz_PTO": float(pz.mean()), "mid_plane_z": mid, "mid_plane": tex, "texture": kind})
+    line = {"metric": "strain sweep of the PbTiO3/SrTiO3 skyrmion sample", "unit": "s",
+            "grid": list(shape), "cell_nm": [x * 1e9 for x in c["cell"]], "eps_b": args.skx_eps_b if args.skx_eps_b > 0 else c["eps_b"],
+            "dt_star": args.skx_dt_star, "tol": args.tol, "max_steps_per_r_s": args.skx_steps,
+            "kick_C_per_m2": args.skx_kick,
+            "seconds": time.perf_counter() - t_all, "per_r_s": rows}
+    if args.out:
+        with open(args.out, "w") as fh:
+            json.dump(line, fh)
+        np.save(os.path.splitext(args.out)[0] + "_P.npy", P)
     print(json.dumps(line))
 
 
@@ -727,11 +932,29 @@ def main():
     ap.add_argument("--hysteresis", action="store_true",
                     help="DC field loop of the 256x256x64 bilayer (81 points, relaxed from point to point)")
     ap.add_argument("--loop-steps", type=int, default=400, help="step cap per field point of --hysteresis")
+    ap.add_argument("--loop-dt-star", type=float, default=0.0, help="dt* of --hysteresis (0: the workload's 0.004)")
+    ap.add_argument("--ac-loop", action="store_true",
+                    help="P-E loops of the Sec. 4.4 sample at the --ac-freqs frequencies and its quasi-static DC loop")
+    ap.add_argument("--ac-freqs", type=float, nargs="+", default=synth.CONFIG_AC["freqs_mhz"][:4], help="MHz")
+    ap.add_argument("--ac-samples", type=int, default=400, help="samples of mean P_z per AC period")
+    ap.add_argument("--ac-dt-star", type=float, default=0.04)
+    ap.add_argument("--dc-steps", type=int, default=4000, help="step cap per DC point of --ac-loop")
+    ap.add_argument("--skyrmion", action="store_true", help="the r_s strain sweep of the Sec. 4.4 skyrmion sample")
+    ap.add_argument("--skx-steps", type=int, default=100000, help="step cap per r_s of --skyrmion")
+    ap.add_argument("--skx-kick", type=float, default=0.01,
+                    help="amplitude (C/m^2) of the seeded perturbation added at each r_s after the first")
+    ap.add_argument("--skx-dt-star", type=float, default=0.015)
+    ap.add_argument("--skx-eps-b", type=float, default=0.0, help="eps_B of --skyrmion (0: the recipe's 45)")
+    ap.add_argument("--out", default="", help="full JSON record of --ac-loop / --skyrmion")
     ap.add_argument("--cufft-compare", action="store_true",
                     help="electrostatic field of the bench cube: this library vs a cuFFT (torch.fft) convolution")
     args = ap.parse_args()
     if args.cufft_compare:
         return cufft_compare(args)
+    if args.ac_loop:
+        return ac_loop(args)
+    if args.skyrmion:
+        return skyrmion(args)
     if args.hysteresis:
         return hysteresis(args)
     if args.ensemble:

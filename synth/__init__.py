@@ -174,3 +174,27 @@ def bilayer_map(shape_xyz, t_pto) -> np.ndarray:
     """SrTiO3 (id 2) below, PbTiO3 (id 1) in the top t_pto layers."""
     nz = shape_xyz[2]
     return layer_map(shape_xyz, [(0, nz - t_pto, 2), (nz - t_pto, nz, 1)])
+
+
+#: The AC hysteresis sample of Sec. 4.4 (Fig. 3): 128 nm x 128 nm, 12 nm SrTiO3 below 20 nm
+#: PbTiO3, 1 nm cells, eps_B = 649, 300 K.  The 4 nm vacuum cap of the paper's sample is the open
+#: boundary above the grid (P = 0 outside).  Start: +0.7 C/m^2 along z in PbTiO3 plus +-0.01 C/m^2
+#: noise (seed 6).  Out-of-plane field of amplitude 400 MV/m (the DC loop spans about +-400 MV/m);
+#: the AC frequencies span the paper's 0.0017 - 0.174 MHz; the DC loop steps 20 MV/m.
+CONFIG_AC = dict(shape=(128, 128, 32), cell=(1e-9, 1e-9, 1e-9), seed=6, amp=0.01, p_up=0.7, eps_b=649.0,
+                 T=300.0, layers=[(0, 12, 2), (12, 32, 1)], E0=4e8,
+                 freqs_mhz=[0.174, 0.0552, 0.0174, 0.0055, 0.0017],
+                 dc_fields=[4e8 - 2e7 * i for i in range(41)] + [-3.8e8 + 2e7 * i for i in range(40)])
+
+#: PbTiO3 with the gradient coefficients of the strain-skyrmion study (Sec. 4.4, Ref. [36]):
+#: G11 = 3.46e-10, G12 = 0, G44 = G'44 = 1.73e-10 N m^4 C^-2; Landau terms of Table 1.
+PTO_SKX = dict(PTO, G11=3.46e-10, G12=0.0, G44=1.73e-10, G44p=1.73e-10)
+#: SrTiO3 of Table 1 with the same gradient coefficients (its Table 1 entries are blank).
+STO_SKX = dict(STO, G11=3.46e-10, G12=0.0, G44=1.73e-10, G44p=1.73e-10)
+
+#: The strain-skyrmion sample of Sec. 4.4 (Fig. 4): 40 x 40 x 32 nm^3 PbTiO3 on a 40 x 40 x 8 nm^3
+#: SrTiO3 layer in vacuum, 0.5 nm cells (80 x 80 x 80), 300 K, eps_B = 45 (the paper gives none for
+#: this sample; 45 is its PbTiO3 cube value), r_s = 1.0 ... 1.8 applied to PbTiO3, each r_s starting
+#: from the state relaxed at the one before, the first from a +-0.01 C/m^2 random start (seed 7).
+CONFIG_SKX = dict(shape=(80, 80, 80), cell=(0.5e-9, 0.5e-9, 0.5e-9), seed=7, amp=0.01, eps_b=45.0, T=300.0,
+                  layers=[(0, 16, 2), (16, 80, 1)], r_s=[1.0 + 0.1 * i for i in range(9)])
