@@ -232,6 +232,8 @@ def gpu_arm(args, rank, world):
                 ctx.set_zpass_variant(n, args.zpass_variant)
     wl = workload(args.workload)
     s, dt = make_sim(ctx, wl)
+    if args.row_tile > 0:   # profiling runs: as for the z pass, the tuner's trial timings are distorted
+        s.set_row_tile(args.row_tile)
     ncell = int(np.prod(wl["shape"]))
     # warm-up (includes the one-off FP64 tensor build): the timed region's own chunk pattern (every
     # chunk length it uses, so that each step graph and relaxation graph it replays is captured and
@@ -920,6 +922,8 @@ def main():
     ap.add_argument("--ws-lr", type=float, default=2e-3)
     ap.add_argument("--sweep-sims", type=int, default=48)
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--row-tile", type=int, default=0,
+                    help="rows per block of the step kernel (profiling runs; 0 = autotuned)")
     ap.add_argument("--zpass-variant", type=int, default=-1,
                     help="force the z-pass variant for 256/512-point lines instead of autotuning (for profiler runs)")
     ap.add_argument("--max-relax-steps", type=int, default=20000)

@@ -182,6 +182,12 @@ int tdgl_set_zpass_variant(tdgl_ctx *ctx, int length, int variant);
  * the candidates and their microseconds per launch (0 for unused slots). */
 #define TDGL_ROW_CANDIDATES 4
 int tdgl_row_tile(tdgl_sim *sim, int *rows, int *candidates, double *us);
+/* Forces the sim's row tile to `rows` rows per block (clamped to the kernel's maximum; the
+ * autotuner then leaves the sim alone), or with rows = 0 returns it to the autotuner.  For runs
+ * whose timings cannot be trusted, e.g. under a profiler that serializes launches.  Waits for the
+ * context's stream and drops the sim's captured step graphs (they are captured again on the next
+ * use).  TDGL_EINVAL for rows < 0. */
+int tdgl_set_row_tile(tdgl_sim *sim, int rows);
 /* Simulated time t (s) of the sim: 0 at creation, advanced by n dt by every step call. */
 int tdgl_set_time(tdgl_sim *sim, double t);
 int tdgl_get_time(tdgl_sim *sim, double *t);

@@ -1512,6 +1512,28 @@ int tdgl_row_tile(tdgl_sim *s, int *rows, int *candidates, double *us) {
     return TDGL_OK;
 }
 
+int tdgl_set_row_tile(tdgl_sim *s, int rows) {
+    if (!s || rows < 0) return s ? fail(s->ctx, TDGL_EINVAL, "row tile %d", rows) : TDGL_EINVAL;
+    tdgl_ctx *ctx = s->ctx;
+    ctx_set(ctx);
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    // the captured step sequences hold the old row items: drop them (recaptured on the next use)
+    for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto &g : s->relax_graphs) cudaGraphExecDestroy(g.exec);
+    s->graphs.clear();
+    s->relax_graphs.clear();
+    s->row_tile = rows;
+    s->rows_tuned = rows > 0;   // 0: tuned (or taken from the context's record) at the next preparation
+    if (rows > 0)
+        for (int i = 0; i < TDGL_ROW_CANDIDATES; ++i) {
+            s->row_cand[i] = 0;
+            s->row_us[i] = 0.0;
+        }
+    build_items(s);
+    if (rows > 0) s->row_tile = std::min(rows, s->rows_cnt_max);
+    return upload_items(s);
+}
+
 int tdgl_set_adaptive(tdgl_sim *s, double err_tol, double dt_min, double dt_max) {
     if (!s || !(err_tol >= 0) || !(dt_min >= 0) || !(dt_max >= 0) || !std::isfinite(err_tol) || !std::isfinite(dt_min) ||
         !std::isfinite(dt_max) || (dt_max > 0 && dt_max < dt_min))

@@ -70,6 +70,7 @@ _SIGS = {
     "tdgl_get_dt": (_I, [_VP, ctypes.POINTER(_D)]),
     "tdgl_zpass_variant": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "tdgl_row_tile": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "tdgl_set_row_tile": (_I, [_VP, _I]),
     "tdgl_fp32_fma_peak": (_I, [_VP, ctypes.POINTER(_D)]),
     "tdgl_wait_probe": (_I, [_VP, _L]),
     "tdgl_set_zpass_variant": (_I, [_VP, _I, _I]),
@@ -317,6 +318,10 @@ class Sim:
         r, c, us = _I(), (_I * ROW_CANDIDATES)(), (_D * ROW_CANDIDATES)()
         self._c(self.lib.tdgl_row_tile(self.h, ctypes.byref(r), c, us))
         return r.value, [(int(a), float(b)) for a, b in zip(c, us) if a > 0]
+
+    def set_row_tile(self, rows: int):
+        """Force rows per block of the step kernel (0: back to the autotuner)."""
+        self._c(self.lib.tdgl_set_row_tile(self.h, int(rows)))
 
     def last_max_dP(self) -> float:
         v = _D()

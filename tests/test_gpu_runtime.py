@@ -155,6 +155,34 @@ def test_row_tile_autotuner_times_candidates_and_reuses_the_choice():
         c.close()
 
 
+def test_forced_row_tile_steps_like_the_tuned_one():
+    # a sim whose row tile is forced (before its first step, and again after its step graphs were
+    # captured) reports that tile, clamped to the kernel's maximum, and steps like the tuned sim
+    from paper_2605_28800_b300 import tdgl
+    c = tdgl.Context(0)
+    try:
+        shape = (32, 32, 16)
+        dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+        a, P = _bto(c, shape, seed=73)
+        a.step(40, dt)
+        f, _ = _bto(c, shape, seed=73)
+        f.set_row_tile(2)
+        f.step(20, dt)
+        assert f.row_tile() == (2, [])
+        f.set_row_tile(1000)                  # after the step graphs were captured
+        assert f.row_tile()[0] < 1000 and f.row_tile()[0] >= 2
+        f.step(20, dt)
+        assert np.abs(f.get_P() - a.get_P()).max() / a.scales()[0] <= 1e-6
+        with pytest.raises(tdgl.TdglError):
+            f.set_row_tile(-1)
+        f.set_row_tile(0)                     # back to the tuner (its record for this shape)
+        f.step(2, dt)
+        a.step(2, dt)
+        assert f.row_tile()[0] == a.row_tile()[0]
+    finally:
+        c.close()
+
+
 def test_bounded_wait_times_out_and_the_context_stays_usable(ctx):
     # a wait on an mbarrier that nothing will complete (no copy in flight) gives up after its poll
     # limit; the library reports ETIMEOUT and the same context keeps stepping correctly
