@@ -203,6 +203,27 @@ int tdgl_get_scales(tdgl_sim *sim, double *P0, double *alpha_ref);
 /* P in C/m^2, float32 [3][nz][ny][nx].  set_P zeroes vacuum cells. */
 int tdgl_set_P(tdgl_sim *sim, const float *P, int where);
 int tdgl_get_P(tdgl_sim *sim, float *out, int where);
+
+/* Pipelined host I/O (Sec. 3: the solver records P at user-chosen intervals while it runs).  These
+ * calls queue work and return without waiting for it:
+ *  - tdgl_set_P_async copies P (C/m^2, float32 [3][nz][ny][nx] in host memory) into the sim on the
+ *    context's upload stream; the sim's later work waits for it.
+ *  - tdgl_step_async queues n steps like tdgl_step (forward Euler or Heun; TDGL_EINVAL for RK45 and
+ *    AB3M2, which read their error estimates on the host) without reading their status.
+ *  - tdgl_get_P_async queues the copy of the sim's P at that point of its work into `out` (host
+ *    memory, same layout) on the context's download stream.
+ *  - tdgl_sync waits until every call above on this sim has completed, then reports the status of
+ *    the steps queued since the last check: TDGL_EDIVERGED or TDGL_ETIMEOUT as tdgl_step would.
+ * Each upload and download goes through a staging buffer of its own (allocated on first use, 2 x
+ * 12 bytes per cell), so consecutive set / step / get calls overlap: the next input's upload and
+ * the last result's download run while the current steps compute.  Host buffers must be
+ * page-locked for the copies to overlap (pageable memory works, with the copies staged by the
+ * driver); a buffer passed to tdgl_set_P_async must not change, and one passed to tdgl_get_P_async
+ * must not be read, until tdgl_sync returns.  Not for use inside a stream capture. */
+int tdgl_set_P_async(tdgl_sim *sim, const float *P);
+int tdgl_step_async(tdgl_sim *sim, int n, double dt);
+int tdgl_get_P_async(tdgl_sim *sim, float *out);
+int tdgl_sync(tdgl_sim *sim);
 /* Fill P with independent uniform values in [-amp, amp] C/m^2 from a Philox4x32-10 stream:
  * value (c, cell) uses counter (cell, c, 0, 0) and key (seed & 0xffffffff, seed >> 32); the
  * first 32-bit output u maps to amp * (2 (u + 0.5) / 2^32 - 1).  Vacuum cells stay 0. */

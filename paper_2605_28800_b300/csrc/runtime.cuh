@@ -30,6 +30,8 @@ struct tdgl_ctx {
     int nsm = 148;                      // streaming multiprocessors of the device
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // copy streams of the asynchronous host I/O calls (created on first use): uploads, downloads
+    cudaStream_t up = nullptr, down = nullptr;
     std::string err;
     long launches = 0;
     bool profiling = false;

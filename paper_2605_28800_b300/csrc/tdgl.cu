@@ -103,6 +103,12 @@ struct tdgl_sim {
     RelaxState *drelax = nullptr;         // their loop state
     double last_maxdp = 0.0;
     tdgl_batch *batch = nullptr;
+    // asynchronous host I/O: staging buffers of uploads and downloads and the events that order
+    // them (input landed, input consumed, output staged, output read out); status of steps that
+    // tdgl_step_async enqueued and nobody has read yet
+    float *din_a = nullptr, *dout_a = nullptr;
+    cudaEvent_t ev_in_ready = nullptr, ev_in_free = nullptr, ev_out_ready = nullptr, ev_out_free = nullptr;
+    bool status_pending = false;
 };
 
 // loop state of a batch's device relaxation: steps done in this launch's loop, the cap, the
@@ -1207,6 +1213,8 @@ void tdgl_ctx_destroy(tdgl_ctx *ctx) {
     for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->up) cudaStreamDestroy(ctx->up);
+    if (ctx->down) cudaStreamDestroy(ctx->down);
     delete ctx;
 }
 
@@ -1364,6 +1372,11 @@ void tdgl_sim_destroy(tdgl_sim *s) {
     if (!s) return;
     ctx_set(s->ctx);
     cudaStreamSynchronize(s->ctx->stream);
+    if (s->ev_out_free) cudaEventSynchronize(s->ev_out_free);   // a download still reading dout_a
+    for (cudaEvent_t e : {s->ev_in_ready, s->ev_in_free, s->ev_out_ready, s->ev_out_free})
+        if (e) cudaEventDestroy(e);
+    cudaFree(s->din_a);
+    cudaFree(s->dout_a);
     auto &v = s->ctx->sims;
     v.erase(std::remove(v.begin(), v.end(), s), v.end());
     if (s->batch) {   // leave the batch rather than dangle in it
@@ -1618,6 +1631,98 @@ int tdgl_get_P(tdgl_sim *s, float *out, int where) {
         k_scale_out<<<grid_for(3 * s->ncell), 256, 0, ctx->stream>>>(s->dout, s->dP[s->cur], 3 * s->ncell, f);
     }));
     return copy_out(ctx, out, s->dout, 3ull * s->ncell * sizeof(float), where);
+}
+
+// ---- asynchronous host I/O -------------------------------------------------------------------
+// Uploads run on the context's `up` stream into din_a, downloads on its `down` stream from dout_a;
+// the scale kernels and the steps run on the context's stream.  Events order each staging buffer's
+// writer after its previous reader, so consecutive upload / step / download calls overlap: the
+// upload of the next input and the download of the previous result run during the current steps.
+int io_setup(tdgl_sim *s) {
+    tdgl_ctx *ctx = s->ctx;
+    if (!ctx->up) CK(ctx, cudaStreamCreateWithFlags(&ctx->up, cudaStreamNonBlocking));
+    if (!ctx->down) CK(ctx, cudaStreamCreateWithFlags(&ctx->down, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&s->ev_in_ready, &s->ev_in_free, &s->ev_out_ready, &s->ev_out_free})
+        if (!*e) CK(ctx, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    return TDGL_OK;
+}
+
+int tdgl_set_P_async(tdgl_sim *s, const float *P) {
+    if (!s || !P) return TDGL_EINVAL;
+    tdgl_ctx *ctx = s->ctx;
+    ctx_set(ctx);
+    if (lowest_material(s)) fix_scales(s);
+    TRY(io_setup(s));
+    const size_t bytes = 3ull * s->ncell * sizeof(float);
+    if (!s->din_a) CK(ctx, cudaMalloc(&s->din_a, bytes));
+    // din_a is free once the previous upload's scale kernel has read it (an event never recorded
+    // counts as complete)
+    CK(ctx, cudaStreamWaitEvent(ctx->up, s->ev_in_free, 0));
+    CK(ctx, cudaMemcpyAsync(s->din_a, P, bytes, cudaMemcpyHostToDevice, ctx->up));
+    CK(ctx, cudaEventRecord(s->ev_in_ready, ctx->up));
+    CK(ctx, cudaStreamWaitEvent(ctx->stream, s->ev_in_ready, 0));
+    const float f = (float)(1.0 / s->P0);
+    TRY(launch(ctx, TDGL_K_OTHER, [&] {
+        k_scale_in<<<grid_for(3 * s->ncell), 256, 0, ctx->stream>>>(s->dP[s->cur], s->din_a, s->dmat, s->ncell, f);
+    }));
+    CK(ctx, cudaEventRecord(s->ev_in_free, ctx->stream));
+    s->ab_hist = 0;
+    s->xstate = XS_NONE;
+    return TDGL_OK;
+}
+
+int tdgl_get_P_async(tdgl_sim *s, float *out) {
+    if (!s || !out) return TDGL_EINVAL;
+    tdgl_ctx *ctx = s->ctx;
+    ctx_set(ctx);
+    if (lowest_material(s)) fix_scales(s);
+    TRY(io_setup(s));
+    const size_t bytes = 3ull * s->ncell * sizeof(float);
+    if (!s->dout_a) CK(ctx, cudaMalloc(&s->dout_a, bytes));
+    // dout_a is free once the previous download has read it
+    CK(ctx, cudaStreamWaitEvent(ctx->stream, s->ev_out_free, 0));
+    const float f = (float)s->P0;
+    TRY(launch(ctx, TDGL_K_OTHER, [&] {
+        k_scale_out<<<grid_for(3 * s->ncell), 256, 0, ctx->stream>>>(s->dout_a, s->dP[s->cur], 3 * s->ncell, f);
+    }));
+    CK(ctx, cudaEventRecord(s->ev_out_ready, ctx->stream));
+    CK(ctx, cudaStreamWaitEvent(ctx->down, s->ev_out_ready, 0));
+    CK(ctx, cudaMemcpyAsync(out, s->dout_a, bytes, cudaMemcpyDeviceToHost, ctx->down));
+    CK(ctx, cudaEventRecord(s->ev_out_free, ctx->down));
+    return TDGL_OK;
+}
+
+int tdgl_step_async(tdgl_sim *s, int n, double dt) {
+    if (!s || n < 0 || !(dt > 0) || !std::isfinite(dt)) return s ? fail(s->ctx, TDGL_EINVAL, "bad n or dt") : TDGL_EINVAL;
+    ctx_set(s->ctx);
+    if (s->integrator >= TDGL_RK45)
+        return fail(s->ctx, TDGL_EINVAL, "RK45 and AB3M2 read their error estimates on the host: use tdgl_step");
+    if (n == 0) return TDGL_OK;
+    TRY(prepare(s, s->terms));
+    TRY(steps_nosync(s, n, dt));
+    s->status_pending = true;
+    return TDGL_OK;
+}
+
+int tdgl_sync(tdgl_sim *s) {
+    if (!s) return TDGL_EINVAL;
+    tdgl_ctx *ctx = s->ctx;
+    ctx_set(ctx);
+    // the context's stream holds every upload's scale kernel (after its copy) and every step;
+    // the last download's event covers the downloads
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (s->ev_out_free) CK(ctx, cudaEventSynchronize(s->ev_out_free));
+    if (!s->status_pending) return TDGL_OK;
+    s->status_pending = false;
+    double m;
+    int f;
+    TRY(read_status(s, &m, &f));
+    if (f) {
+        CK(ctx, cudaMemsetAsync(s->dflag, 0, sizeof(int), ctx->stream));
+        if (f & 2) return fail(ctx, TDGL_ETIMEOUT, "a bounded wait for a tensor copy timed out");
+        return fail(ctx, TDGL_EDIVERGED, "P diverged (NaN or |P| > 1e3 P0)");
+    }
+    return TDGL_OK;
 }
 
 int tdgl_init_random(tdgl_sim *s, uint64_t seed, double amp) {

@@ -80,6 +80,10 @@ _SIGS = {
     "tdgl_get_scales": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "tdgl_set_P": (_I, [_VP, _VP, _I]),
     "tdgl_get_P": (_I, [_VP, _VP, _I]),
+    "tdgl_set_P_async": (_I, [_VP, _VP]),
+    "tdgl_get_P_async": (_I, [_VP, _VP]),
+    "tdgl_step_async": (_I, [_VP, _I, _D]),
+    "tdgl_sync": (_I, [_VP]),
     "tdgl_init_random": (_I, [_VP, ctypes.c_uint64, _D]),
     "tdgl_get_field": (_I, [_VP, _U, _VP, _I]),
     "tdgl_step": (_I, [_VP, _I, _D]),
@@ -297,6 +301,32 @@ class Sim:
         p, where = _ptr(out)
         self._c(self.lib.tdgl_get_P(self.h, p, where))
         return out
+
+    def _host_ptr(self, a):
+        p, where = _ptr(a)
+        if where != HOST:
+            raise ValueError("the asynchronous I/O calls take host buffers")
+        if (a.numel() if hasattr(a, "numel") else a.size) != 3 * self.ncell:
+            raise ValueError("P must have 3*nx*ny*nz elements")
+        if (a.dtype != np.float32) if isinstance(a, np.ndarray) else (str(a.dtype) != "torch.float32"):
+            raise ValueError("P must be float32")
+        return p
+
+    def set_P_async(self, P):
+        """Queue the upload of P (host, float32, page-locked to overlap); P must not change until sync()."""
+        self._c(self.lib.tdgl_set_P_async(self.h, self._host_ptr(P)))
+
+    def step_async(self, n: int, dt: float):
+        """Queue n steps without reading their status (sync() reports it)."""
+        self._c(self.lib.tdgl_step_async(self.h, int(n), float(dt)))
+
+    def get_P_async(self, out):
+        """Queue the download of the current P into out (host, float32); read it after sync()."""
+        self._c(self.lib.tdgl_get_P_async(self.h, self._host_ptr(out)))
+
+    def sync(self):
+        """Wait for the queued uploads, steps and downloads; raises on divergence or a timeout."""
+        self._c(self.lib.tdgl_sync(self.h))
 
     def init_random(self, seed: int, amp: float):
         self._c(self.lib.tdgl_init_random(self.h, ctypes.c_uint64(seed), float(amp)))

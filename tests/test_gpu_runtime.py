@@ -183,6 +183,56 @@ def test_forced_row_tile_steps_like_the_tuned_one():
         c.close()
 
 
+def test_async_host_io_pipeline_equals_synchronous_calls(ctx):
+    # a queue of independent problems through the pipelined calls (upload, steps, download, no host
+    # wait until sync) gives each problem the same P, bit for bit, as set_P / step / get_P; the
+    # results match the oracle; sync reports divergence; RK45 is refused
+    import torch
+    from paper_2605_28800_b300 import tdgl
+    shape = (32, 32, 16)
+    nx, ny, nz = shape
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    s, _ = _bto(ctx, shape, seed=91)
+    inputs = [torch.from_numpy(synth.uniform_P(shape, 0.05, 200 + k)).pin_memory() for k in range(5)]
+    outs = [torch.full((3, nz, ny, nx), float("nan")).pin_memory() for _ in inputs]
+    for Pin, Pout in zip(inputs, outs):
+        s.set_P_async(Pin)
+        s.step_async(3, dt)
+        s.get_P_async(Pout)
+    s.sync()
+    for Pin, Pout in zip(inputs, outs):
+        s.set_P(Pin.numpy())
+        s.step(3, dt)
+        assert np.array_equal(Pout.numpy(), s.get_P())
+    o = oracle_sys(shape, (1e-9,) * 3, np.ones((nz, ny, nx), np.uint8), {1: synth.BTO}, 300.0, 45.0)
+    want = o.run(inputs[-1].numpy().astype(np.float64), dt, 3)
+    assert np.abs(outs[-1].numpy() - want).max() / s.scales()[0] <= 1e-5
+    # continuing a sim: snapshots taken between queued steps
+    s.set_P(inputs[0].numpy())
+    snaps = [torch.empty(3, nz, ny, nx).pin_memory() for _ in range(3)]
+    for snap in snaps:
+        s.step_async(2, dt)
+        s.get_P_async(snap)
+    s.sync()
+    s.set_P(inputs[0].numpy())
+    for snap in snaps:
+        s.step(2, dt)
+        assert np.array_equal(snap.numpy(), s.get_P())
+    # divergence of queued steps is reported by sync, and the sim is usable afterwards
+    s.set_P_async(inputs[1])
+    s.step_async(50, 1e-6)                  # far beyond the explicit stability bound
+    with pytest.raises(tdgl.TdglError) as e:
+        s.sync()
+    assert e.value.code == tdgl.EDIVERGED
+    s.set_P(inputs[1].numpy())
+    s.step(3, dt)
+    s.set_integrator(tdgl.RK45)
+    with pytest.raises(tdgl.TdglError):
+        s.step_async(1, dt)
+    with pytest.raises(ValueError):
+        s.get_P_async(torch.empty(3, nz, ny, nx, device="cuda"))
+
+
 def test_bounded_wait_times_out_and_the_context_stays_usable(ctx):
     # a wait on an mbarrier that nothing will complete (no copy in flight) gives up after its poll
     # limit; the library reports ETIMEOUT and the same context keeps stepping correctly
