@@ -775,7 +775,7 @@ def size_sweep(args):
     torch.cuda.set_device(dev)
     ctx = tdgl.Context(dev)
     rows = []
-    for shape in [(32, 32, 8), (32, 32, 32), (64, 64, 64), (96, 96, 96), (128, 128, 128)]:
+    for shape in [(32, 32, 8), (32, 32, 32), (48, 48, 48), (64, 64, 64), (96, 96, 96), (128, 128, 128)]:
         nx, ny, nz = shape
         s = tdgl.Sim(ctx, shape, (1e-9,) * 3)
         s.define_material(1, synth.BTO)
@@ -791,8 +791,19 @@ def size_sweep(args):
         t0 = time.perf_counter()
         k, _ = s.relax(dt, 1e-30, n, CHECK_EVERY, raise_on_cap=False)
         el = time.perf_counter() - t0
+        # per-kernel device time of the same steps, launched one by one with CUDA events
+        ctx.profile(True)
+        for kind in range(6):
+            ctx.profile_read(kind)
+        s.relax(dt, 1e-30, 64, CHECK_EVERY, raise_on_cap=False)
+        torch.cuda.synchronize()
+        prof = {tdgl.KERNEL_NAMES[kind]: ctx.profile_read(kind) for kind in range(6)}
+        ctx.profile(False)
         rows.append({"grid": list(shape), "steps": int(k), "us_per_step": 1e6 * el / k,
-                     "cell_updates_per_s": nx * ny * nz * k / el})
+                     "cell_updates_per_s": nx * ny * nz * k / el, "fft_pad": list(s.fft_pad()),
+                     "zpass_variant": ctx.zpass_variant(s.fft_pad()[2])[0] if s.fft_pad()[2] in (128, 256, 512) else None,
+                     "row_tile": s.row_tile()[0],
+                     "us_per_launch": {kn: round(1e3 * v[0] / v[1], 2) for kn, v in prof.items() if v[1] > 0}})
         s.close()
     print(json.dumps({"metric": "step time of single sims run alone", "unit": "us per step", "per_grid": rows}))
 

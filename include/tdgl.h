@@ -106,6 +106,17 @@ int  tdgl_sim_create(tdgl_ctx *ctx, int nx, int ny, int nz, double dx, double dy
                      tdgl_sim **out);
 void tdgl_sim_destroy(tdgl_sim *sim);
 
+/* Padded transform lengths of the open-boundary convolution (Eqs. 5-6; any length >= 2n - 1 gives
+ * the same linear convolution).  Defaults: the smallest 2^a 3^b >= 2n - 1 along x (even) and y;
+ * along z the same, except that a length with a factor 3 gives way to the next power of two when
+ * that is 128, 256 or 512 and at most 4/3 of it (96 -> 128, 192 -> 256, 384 -> 512), whose tuned
+ * z pass finishes first.  tdgl_fft_pad reports them; tdgl_set_fft_pad sets them (0 = the default
+ * for that axis): each must be 2^a 3^b, >= 2n - 1 and <= 4 TDGL_MAX_DIM, Mx even, else TDGL_EINVAL.
+ * Setting new lengths waits for the context's stream, frees the sim's spectra and tensor spectrum
+ * (rebuilt on the next call that needs the field) and drops its captured step graphs. */
+int tdgl_fft_pad(tdgl_sim *sim, int *Mx, int *My, int *Mz);
+int tdgl_set_fft_pad(tdgl_sim *sim, int Mx, int My, int Mz);
+
 /* Define (or redefine) material `id` (1..15) from Table 1-style coefficients (Sec. 3:
  * spatially varying material parameters at the cell level). */
 int tdgl_material_define(tdgl_sim *sim, int id, const tdgl_material *m);

@@ -93,12 +93,54 @@ template <bool INV> __device__ __forceinline__ void dft16(float2 *a) {
     for (int k = 0; k < 8; ++k) { a[k] = cadd(e[k], o[k]); a[k + 8] = csub(e[k], o[k]); }
 }
 
+template <int R, bool INV> __device__ __forceinline__ void dft(float2 *a);
+
+// x with (a x) mod m = 1 (m > 1, a and m coprime)
+__host__ __device__ constexpr int inv_mod(int a, int m) {
+    for (int x = 1; x < m; ++x)
+        if ((a * x) % m == 1) return x;
+    return 1;
+}
+
+// Radices 6 and 12 as prime-factor (Good-Thomas) transforms of coprime lengths N1 N2 (2 x 3,
+// 3 x 4).  With the input index n = (N2 n1 + N1 n2) mod N and the output index
+// k = (N2 q1 k1 + N1 q2 k2) mod N, q1 = N2^-1 mod N1, q2 = N1^-1 mod N2, the length-N DFT
+// factors into N2-point DFTs over n2 followed by N1-point DFTs over n1 with no twiddle factors
+// between them (W_N^(nk) = W_N1^(n1 k1) W_N2^(n2 k2) for these index maps).
+template <int N1, int N2, bool INV> __device__ __forceinline__ void dft_pfa(float2 *a) {
+    constexpr int N = N1 * N2, q1 = inv_mod(N2 % N1, N1), q2 = inv_mod(N1 % N2, N2);
+    float2 y[N1][N2];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) {
+        float2 b[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) b[n2] = a[(N2 * n1 + N1 * n2) % N];
+        dft<N2, INV>(b);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) y[n1][k2] = b[k2];
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) {
+        float2 c[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) c[n1] = y[n1][k2];
+        dft<N1, INV>(c);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) a[(N2 * q1 * k1 + N1 * q2 * k2) % N] = c[k1];
+    }
+}
+
 template <int R, bool INV> __device__ __forceinline__ void dft(float2 *a) {
     if constexpr (R == 2) dft2<INV>(a[0], a[1]);
     else if constexpr (R == 3) dft3<INV>(a[0], a[1], a[2]);
     else if constexpr (R == 4) dft4<INV>(a[0], a[1], a[2], a[3]);
+    else if constexpr (R == 6) dft_pfa<2, 3, INV>(a);
     else if constexpr (R == 8) dft8<INV>(a);
-    else dft16<INV>(a);
+    else if constexpr (R == 12) dft_pfa<3, 4, INV>(a);
+    else {
+        static_assert(R == 16, "radices 2, 3, 4, 6, 8, 12, 16");
+        dft16<INV>(a);
+    }
 }
 
 // One Stockham pass of radix R over `lines` lines (stride ld) from src to dst.

@@ -24,7 +24,8 @@ template <int N_, int E_, int R0_, int R1_ = 1, int R2_ = 1> struct Shape {
     static_assert(N_ % E_ == 0, "E must divide N");
 };
 
-// default shapes: 16 elements per thread for the power-of-two lengths, 12 or 24 for 3 * 2^k
+// default shapes: 16 elements per thread for the power-of-two lengths, 12 for 3 * 2^k (radix 6 or
+// 12 first: a prime-factor butterfly, so the first pass has no twiddle factors at all)
 template <int N> struct Cfg;
 template <> struct Cfg<16>  : Shape<16, 16, 16> {};
 template <> struct Cfg<32>  : Shape<32, 16, 16, 2> {};
@@ -33,8 +34,8 @@ template <> struct Cfg<128> : Shape<128, 16, 16, 8> {};
 template <> struct Cfg<256> : Shape<256, 16, 16, 16> {};
 template <> struct Cfg<512> : Shape<512, 16, 16, 16, 2> {};
 template <> struct Cfg<48>  : Shape<48, 12, 4, 4, 3> {};
-template <> struct Cfg<96>  : Shape<96, 24, 8, 4, 3> {};
-template <> struct Cfg<192> : Shape<192, 24, 8, 8, 3> {};
+template <> struct Cfg<96>  : Shape<96, 12, 6, 4, 4> {};
+template <> struct Cfg<192> : Shape<192, 12, 12, 4, 4> {};
 
 template <int N> __host__ __device__ constexpr int threads_per_line() { return Cfg<N>::T; }
 

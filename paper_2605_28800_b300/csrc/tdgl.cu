@@ -158,6 +158,27 @@ int smooth_at_least(int m, bool even) {
     return best;
 }
 
+bool is_smooth(int m) {   // m = 2^a 3^b
+    if (m < 1) return false;
+    while (m % 2 == 0) m /= 2;
+    while (m % 3 == 0) m /= 3;
+    return m == 1;
+}
+
+// Default padded length along z: the smallest 2^a 3^b >= 2 nz - 1, except that a length with a
+// factor 3 gives way to the next power of two when that is one of the z pass's tuned lengths (128,
+// 256, 512) and at most 4/3 of it (96 -> 128, 192 -> 256, 384 -> 512).  Any length >= 2 nz - 1
+// gives the same linear convolution; on a B300 the tuned 256-point z pass takes 15 ps per point
+// against 29 ps for the generic 192-point shape, so the longer lines finish first (96^3 cube:
+// 104 -> about 73 us per z pass).
+int default_z_length(int nz) {
+    const int m = smooth_at_least(2 * nz - 1, false);
+    if (m % 3 != 0) return m;
+    int p2 = 1;
+    while (p2 < m) p2 *= 2;
+    return ((p2 == 128 || p2 == 256 || p2 == 512) && 3 * p2 <= 4 * m) ? p2 : m;
+}
+
 Plan make_plan(int n, std::vector<float2> &tw) {
     Plan p;
     memset(&p, 0, sizeof p);
@@ -1299,6 +1320,28 @@ int tdgl_fp32_fma_peak(tdgl_ctx *ctx, double *tflops) {
     return TDGL_OK;
 }
 
+// padded transform lengths of a sim: plans, the twiddle table (returned for upload) and work items
+void set_lengths(tdgl_sim *s, int Mx, int My, int Mz, std::vector<float2> &tw) {
+    s->Mx = Mx;
+    s->My = My;
+    s->Mz = Mz;
+    s->hx = s->Mx / 2;
+    s->Kx = s->hx + 1;
+    s->kxp = (s->Kx + 3) & ~3;
+    s->kyh = s->My / 2 + 1;
+    s->kzh = s->Mz / 2 + 1;
+    tw.clear();
+    s->px = make_plan(s->hx, tw);
+    s->py = make_plan(s->My, tw);
+    s->pz = make_plan(s->Mz, tw);
+    s->twr = (int)tw.size();
+    for (int k = 0; k <= s->hx; ++k) {
+        const double a = -2.0 * M_PI * (double)k / (double)s->Mx;
+        tw.push_back(make_float2((float)cos(a), (float)sin(a)));
+    }
+    build_items(s);
+}
+
 int tdgl_sim_create(tdgl_ctx *ctx, int nx, int ny, int nz, double dx, double dy, double dz, tdgl_sim **out) {
     if (!ctx || !out) return TDGL_EINVAL;
     *out = nullptr;
@@ -1315,24 +1358,8 @@ int tdgl_sim_create(tdgl_ctx *ctx, int nx, int ny, int nz, double dx, double dy,
     s->ncell = (long)nx * ny * nz;
     memset(s->mats, 0, sizeof s->mats);
     s->map.assign(s->ncell, 0);
-    s->Mx = smooth_at_least(2 * nx - 1, true);
-    s->My = smooth_at_least(2 * ny - 1, false);
-    s->Mz = smooth_at_least(2 * nz - 1, false);
-    s->hx = s->Mx / 2;
-    s->Kx = s->hx + 1;
-    s->kxp = (s->Kx + 3) & ~3;
-    s->kyh = s->My / 2 + 1;
-    s->kzh = s->Mz / 2 + 1;
     std::vector<float2> tw;
-    s->px = make_plan(s->hx, tw);
-    s->py = make_plan(s->My, tw);
-    s->pz = make_plan(s->Mz, tw);
-    s->twr = (int)tw.size();
-    for (int k = 0; k <= s->hx; ++k) {
-        const double a = -2.0 * M_PI * (double)k / (double)s->Mx;
-        tw.push_back(make_float2((float)cos(a), (float)sin(a)));
-    }
-    build_items(s);
+    set_lengths(s, smooth_at_least(2 * nx - 1, true), smooth_at_least(2 * ny - 1, false), default_z_length(nz), tw);
     int rc = TDGL_OK;
     auto al = [&](void **p, size_t b) {
         if (rc != TDGL_OK) return;
@@ -1523,6 +1550,52 @@ int tdgl_row_tile(tdgl_sim *s, int *rows, int *candidates, double *us) {
         if (us) us[i] = s->row_us[i];
     }
     return TDGL_OK;
+}
+
+int tdgl_fft_pad(tdgl_sim *s, int *Mx, int *My, int *Mz) {
+    if (!s || !Mx || !My || !Mz) return TDGL_EINVAL;
+    *Mx = s->Mx;
+    *My = s->My;
+    *Mz = s->Mz;
+    return TDGL_OK;
+}
+
+int tdgl_set_fft_pad(tdgl_sim *s, int Mx, int My, int Mz) {
+    if (!s) return TDGL_EINVAL;
+    tdgl_ctx *ctx = s->ctx;
+    if (Mx == 0) Mx = smooth_at_least(2 * s->nx - 1, true);
+    if (My == 0) My = smooth_at_least(2 * s->ny - 1, false);
+    if (Mz == 0) Mz = default_z_length(s->nz);
+    if (Mx < 2 * s->nx - 1 || My < 2 * s->ny - 1 || Mz < 2 * s->nz - 1 || Mx % 2 != 0 || !is_smooth(Mx) ||
+        !is_smooth(My) || !is_smooth(Mz) || Mx > 4 * TDGL_MAX_DIM || My > 4 * TDGL_MAX_DIM || Mz > 4 * TDGL_MAX_DIM)
+        return fail(ctx, TDGL_EINVAL, "padded lengths %d %d %d: each must be 2^a 3^b, at least 2n - 1 and at most %d "
+                                      "(x even)", Mx, My, Mz, 4 * TDGL_MAX_DIM);
+    if (Mx == s->Mx && My == s->My && Mz == s->Mz) return TDGL_OK;
+    ctx_set(ctx);
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto &g : s->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto &g : s->relax_graphs) cudaGraphExecDestroy(g.exec);
+    s->graphs.clear();
+    s->relax_graphs.clear();
+    if (s->batch) drop_cache(s->batch);   // its work lists hold this sim's items
+    // spectra and the tensor spectrum are sized by the padded lengths: rebuilt on the next use
+    cudaFree(s->dX); cudaFree(s->dY); cudaFree(s->dNhat);
+    s->dX = s->dY = nullptr;
+    s->dNhat = nullptr;
+    s->spectra_alloc = false;
+    s->tensor_ready = false;
+    s->has_ymap = s->has_nmap = false;
+    s->xstate = XS_NONE;
+    s->ab_hist = 0;
+    s->rows_tuned = false;
+    s->row_tile = 0;
+    std::vector<float2> tw;
+    set_lengths(s, Mx, My, Mz, tw);
+    cudaFree(s->dtw);
+    s->dtw = nullptr;
+    CK(ctx, cudaMalloc(&s->dtw, tw.size() * sizeof(float2)));
+    CK(ctx, cudaMemcpy(s->dtw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    return upload_items(s);
 }
 
 int tdgl_set_row_tile(tdgl_sim *s, int rows) {

@@ -71,6 +71,8 @@ _SIGS = {
     "tdgl_zpass_variant": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "tdgl_row_tile": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "tdgl_set_row_tile": (_I, [_VP, _I]),
+    "tdgl_fft_pad": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "tdgl_set_fft_pad": (_I, [_VP, _I, _I, _I]),
     "tdgl_fp32_fma_peak": (_I, [_VP, ctypes.POINTER(_D)]),
     "tdgl_wait_probe": (_I, [_VP, _L]),
     "tdgl_set_zpass_variant": (_I, [_VP, _I, _I]),
@@ -348,6 +350,16 @@ class Sim:
         r, c, us = _I(), (_I * ROW_CANDIDATES)(), (_D * ROW_CANDIDATES)()
         self._c(self.lib.tdgl_row_tile(self.h, ctypes.byref(r), c, us))
         return r.value, [(int(a), float(b)) for a, b in zip(c, us) if a > 0]
+
+    def fft_pad(self):
+        """(Mx, My, Mz): the padded transform lengths of the electrostatic convolution."""
+        a, b, c = _I(), _I(), _I()
+        self._c(self.lib.tdgl_fft_pad(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def set_fft_pad(self, Mx=0, My=0, Mz=0):
+        """Set the padded lengths (0 = the default for that axis)."""
+        self._c(self.lib.tdgl_set_fft_pad(self.h, int(Mx), int(My), int(Mz)))
 
     def set_row_tile(self, rows: int):
         """Force rows per block of the step kernel (0: back to the autotuner)."""

@@ -47,6 +47,23 @@ def test_each_field_term_matches_oracle(ctx, shape, term, tol):
     assert np.all(got[:, mat == 0] == 0)
 
 
+@pytest.mark.parametrize("shape,Mz", [((8, 8, 48), 96), ((8, 8, 96), 192), ((17, 9, 40), 81)])
+def test_electrostatic_field_with_forced_z_padding_matches_oracle(ctx, shape, Mz):
+    # by default z lengths 96 and 192 give way to the tuned 128 and 256; forcing the smallest
+    # 2^a 3^b keeps the radix-3 z passes (and a generic 81-point one) pinned against the oracle,
+    # and both paddings give the same field
+    mat, P = mixed_case(shape, seed=sum(shape) + 1)
+    g = gpu_sim(ctx, shape, CELL, mat, MATS, 280.0, 30.0, P=P)
+    default = g.get_field(4)
+    g.set_fft_pad(0, 0, Mz)
+    assert g.fft_pad()[2] == Mz
+    got = g.get_field(4)
+    o = oracle_sys(shape, CELL, mat, MATS, 280.0, 30.0)
+    want = np.where(mat > 0, o.fields(P.astype(np.float64))["elec"], 0.0)
+    assert rel_err(got, want) <= 2e-5
+    assert rel_err(default, want) <= 2e-5
+
+
 def test_electrostatic_field_of_uniform_slab(ctx):
     # closed form as well: uniform Pz film -> E_z ~ -Pz/(eps0 epsB) in the middle
     shape = (64, 64, 2)
@@ -152,8 +169,10 @@ def _sample_cells(shape, n, seed):
 
 
 @pytest.mark.parametrize("workload", ["bto_cube_128", "pto_sto_bilayer_256x256x64", "bto_cube_48", "bto_cube_64",
-                                      "bto_cube_96"])
+                                      "bto_cube_96", "bto_cube_96_z192"])
 def test_full_size_field_and_step_at_sampled_cells(ctx, workload):
+    z192 = workload.endswith("_z192")     # the 96^3 cube with its z axis padded to 192, not 256
+    workload = workload.replace("_z192", "")
     if workload.startswith("bto_cube"):
         c = synth.CONFIG2
         L = int(workload.rsplit("_", 1)[1])
@@ -175,6 +194,8 @@ def test_full_size_field_and_step_at_sampled_cells(ctx, workload):
     cell = c["cell"]
     E = (0.0, 0.0, 1e8)
     g = gpu_sim(ctx, shape, cell, mat, mats, T, eps_b, E=E, P=P)
+    if z192:
+        g.set_fft_pad(0, 0, 192)
     octant = otensor.octant(shape, cell)
     cells = _sample_cells(shape, 20, 5)
     h_o = _oracle_field_at(shape, cell, mat, mats, T, eps_b, P, octant, cells) + np.array(E)[None, :]

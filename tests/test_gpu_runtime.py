@@ -183,6 +183,35 @@ def test_forced_row_tile_steps_like_the_tuned_one():
         c.close()
 
 
+def test_fft_padding_defaults_and_forced_lengths(ctx):
+    # defaults: smallest 2^a 3^b >= 2n - 1 (x even), z giving way to 128 / 256 / 512 within 4/3;
+    # forced lengths are validated, and a sim re-padded between steps follows the same trajectory
+    from paper_2605_28800_b300 import tdgl
+    cases = {(96, 96, 96): (192, 192, 256), (48, 48, 48): (96, 96, 128), (17, 9, 5): (36, 18, 9),
+             (32, 32, 8): (64, 64, 16), (128, 128, 128): (256, 256, 256),
+             (40, 40, 81): (96, 81, 162)}   # x: 81 is odd, so 96; z: 256 > 4/3 of 162
+    for shape, want in cases.items():
+        s = tdgl.Sim(ctx, shape, (1e-9,) * 3)
+        assert s.fft_pad() == want, shape
+        s.close()
+    a, P = _bto(ctx, (24, 20, 48), seed=97)
+    b, _ = _bto(ctx, (24, 20, 48), seed=97)
+    assert a.fft_pad()[2] == 128
+    for bad in ((47, 0, 0), (48, 38, 0), (0, 0, 100), (0, 0, 64)):
+        with pytest.raises(tdgl.TdglError) as e:
+            b.set_fft_pad(*bad)
+        assert e.value.code == tdgl.EINVAL
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    a.step(12, dt)
+    b.step(6, dt)
+    b.set_fft_pad(54, 0, 96)
+    assert b.fft_pad() == (54, 48, 96)
+    b.step(6, dt)
+    b.set_fft_pad(0, 0, 0)
+    assert b.fft_pad() == a.fft_pad()
+    assert np.abs(a.get_P() - b.get_P()).max() / a.scales()[0] <= 1e-6
+
+
 def test_async_host_io_pipeline_equals_synchronous_calls(ctx):
     # a queue of independent problems through the pipelined calls (upload, steps, download, no host
     # wait until sync) gives each problem the same P, bit for bit, as set_P / step / get_P; the
