@@ -32,6 +32,10 @@ struct tdgl_ctx {
     bool own_stream = false;
     // copy streams of the asynchronous host I/O calls (created on first use): uploads, downloads
     cudaStream_t up = nullptr, down = nullptr;
+    // split-K partial sums of the network's small convolutions (grown on demand, reused by every
+    // convolution of the context: its work is ordered on the one stream)
+    float *splitk = nullptr;
+    size_t splitk_n = 0;
     std::string err;
     long launches = 0;
     bool profiling = false;

@@ -1234,6 +1234,7 @@ void tdgl_ctx_destroy(tdgl_ctx *ctx) {
     for (auto &r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    cudaFree(ctx->splitk);
     if (ctx->up) cudaStreamDestroy(ctx->up);
     if (ctx->down) cudaStreamDestroy(ctx->down);
     delete ctx;

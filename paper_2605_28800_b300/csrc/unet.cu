@@ -94,7 +94,7 @@ bool wgt_map(CUtensorMap *m, const void *w, int Ci, int Co, int bn) {
 // wb: the same weights as [27][Co][Ci] for the brick kernel (null: gather kernel only)
 int launch_conv(tdgl_ctx *ctx, const __nv_bfloat16 *x, const __nv_bfloat16 *w, const __nv_bfloat16 *wb, const float *b,
                 void *y, long nvox, Dims d, int Ci, int Co, int ntap, int Kp, bool relu, bool f32out, int *err) {
-    ConvP p{x, w, b, y, nvox, d.Z, d.Y, d.X, Ci, Co, ntap, Kp / 8, relu ? 1 : 0, f32out ? 1 : 0, err};
+    ConvP p{x, w, b, y, nvox, d.Z, d.Y, d.X, Ci, Co, ntap, Kp / 8, relu ? 1 : 0, f32out ? 1 : 0, err, 1, nullptr};
     // the brick kernel: 3x3x3, 16-channel input chunks, 8 x 16 voxel bricks, output tiles up to 64
     if (wb && ntap == 27 && Ci % 16 == 0 && d.X % 8 == 0 && d.Y % 16 == 0) {
         const int bn = Co % 64 == 0 ? 64 : (Co % 32 == 0 ? 32 : 16);
@@ -116,14 +116,40 @@ int launch_conv(tdgl_ctx *ctx, const __nv_bfloat16 *x, const __nv_bfloat16 *w, c
         });
     }
     const int bn = conv_bn(Co);
-    const dim3 grid((unsigned)((nvox + 127) / 128), (unsigned)((Co + bn - 1) / bn));
-    return launch(ctx, TDGL_K_UNET, [&] {
+    dim3 grid((unsigned)((nvox + 127) / 128), (unsigned)((Co + bn - 1) / bn));
+    // layers with fewer CTAs than half the SMs (the deepest levels) split their K range so that
+    // about one CTA per SM works; at least four sub-chunks per split, and no split left empty
+    const int nsub = p.G / 2;
+    const long ctas = (long)grid.x * grid.y;
+    if (2 * ctas < ctx->nsm && nsub >= 8) {
+        int S = (int)std::min<long>((ctx->nsm + ctas - 1) / ctas, nsub / 4);
+        const int per = (nsub + S - 1) / S;
+        S = (nsub + per - 1) / per;
+        if (S > 1) {
+            const size_t need = (size_t)S * nvox * Co;
+            if (need > ctx->splitk_n) {
+                cudaFree(ctx->splitk);
+                ctx->splitk = nullptr;
+                ctx->splitk_n = 0;
+                CK(ctx, cudaMalloc(&ctx->splitk, need * sizeof(float)));
+                ctx->splitk_n = need;
+            }
+            p.ksplit = S;
+            p.part = ctx->splitk;
+            grid.z = (unsigned)S;
+        }
+    }
+    TRY(launch(ctx, TDGL_K_UNET, [&] {
         switch (bn) {
             case 128: k_conv<128><<<grid, 128, gemm_smem<128>(), ctx->stream>>>(p); break;
             case 64: k_conv<64><<<grid, 128, gemm_smem<64>(), ctx->stream>>>(p); break;
             case 32: k_conv<32><<<grid, 128, gemm_smem<32>(), ctx->stream>>>(p); break;
             default: k_conv<16><<<grid, 128, gemm_smem<16>(), ctx->stream>>>(p); break;
         }
+    }));
+    if (p.ksplit == 1) return TDGL_OK;
+    return launch(ctx, TDGL_K_UNET, [&] {
+        k_splitk_sum<<<grid_n(nvox * Co), 256, 0, ctx->stream>>>(p.part, p.ksplit, nvox, Co, b, p.relu, p.f32out, y);
     });
 }
 
@@ -405,7 +431,8 @@ int conv_backward(tdgl_unet *n, Layer &ly, int B) {
     const __nv_bfloat16 *out = ly.relu ? reinterpret_cast<const __nv_bfloat16 *>(ly.out) : nullptr;
     TRY(launch_relu_bwd(ctx, ly.g_out, out, n->dpre, n->dpret, gb, n->bpart, V, ly.Co));
     TRY(launch(ctx, TDGL_K_UNET, [&] {
-        k_xshift<<<(unsigned)((V + 31) / 32), 256, 0, ctx->stream>>>(ly.in, n->xs, V, ly.Ci, d.X, ly.ntap == 27 ? 3 : 1);
+        k_xshift<<<(unsigned)((V + xshift_vb(ly.Ci) - 1) / xshift_vb(ly.Ci)), 256, xshift_smem(ly.Ci), ctx->stream>>>(
+            ly.in, n->xs, V, ly.Ci, d.X, ly.ntap == 27 ? 3 : 1, xshift_vb(ly.Ci));
     }));
     TRY(launch_wgrad(ctx, n->dpret, n->xs, gw, n->wpart, V, d, ly.Ci, ly.Co, ly.ntap, ly.Kp, n->derr));
     if (ly.need_dx)
@@ -806,7 +833,8 @@ int tdgl_conv3d_backward(tdgl_ctx *ctx, const float *x, const float *w, const fl
     TRY(launch(ctx, TDGL_K_UNET, [&] { k_to_ndhwc_f32<<<grid_n(V * co), 256, 0, ctx->stream>>>(gy, gyn, V, co, co, d.vps()); }));
     TRY(launch_relu_bwd(ctx, gyn, nullptr, dpre, dpret, gb, bpart, V, co));
     TRY(launch(ctx, TDGL_K_UNET, [&] {
-        k_xshift<<<(unsigned)((V + 31) / 32), 256, 0, ctx->stream>>>(xb, xs, V, ci, d.X, ntap == 27 ? 3 : 1);
+        k_xshift<<<(unsigned)((V + xshift_vb(ci) - 1) / xshift_vb(ci)), 256, xshift_smem(ci), ctx->stream>>>(
+            xb, xs, V, ci, d.X, ntap == 27 ? 3 : 1, xshift_vb(ci));
     }));
     TRY(launch_wgrad(ctx, dpret, xs, gw, wpart, V, d, ci, co, ntap, Kp, derr));
     TRY(launch_conv(ctx, dpre, wt, wtb, nullptr, gx, V, d, co, ci, ntap, Kpt, false, true, derr));

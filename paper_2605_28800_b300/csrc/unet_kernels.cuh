@@ -130,9 +130,14 @@ struct ConvP {
     long nvox;
     int Z, Y, X, Ci, Co, ntap, G, relu, f32out;
     int *err;
+    int ksplit;               // > 1: the K range is split over gridDim.z CTAs, each writing its partial
+    float *part;              // [ksplit][nvox][Co] FP32 partial sums (ksplit > 1), added by k_splitk_sum
 };
 
-// Y = act(bias + conv(X, W)) for a 3x3x3 (ntap 27) or 1x1x1 (ntap 1) kernel, zero padding
+// Y = act(bias + conv(X, W)) for a 3x3x3 (ntap 27) or 1x1x1 (ntap 1) kernel, zero padding.  With
+// p.ksplit > 1 CTA (x, y, z) sums only the z-th of ksplit equal ranges of K sub-chunks and stores
+// that partial sum; k_splitk_sum adds the partials in split order and applies bias and activation
+// (for layers with too few voxel tiles to fill the GPU)
 template <int BN>
 __global__ void __launch_bounds__(128) k_conv(ConvP p) {
     extern __shared__ uint8_t smem_raw[];
@@ -152,8 +157,11 @@ __global__ void __launch_bounds__(128) k_conv(ConvP p) {
         vz = (int)(q % p.Z); vb = q / p.Z;
     }
     const int cg = p.Ci >> 3;
+    const int nsub_all = p.G / 2, per = (nsub_all + p.ksplit - 1) / p.ksplit, j0 = (int)blockIdx.z * per;
+    const int nsub = nsub_all - j0 < per ? nsub_all - j0 : per;   // >= 1: the host leaves no split empty
     const uint32_t tmem = prologue<BN>(bar, tslot);
-    auto load = [&](int c, uint32_t a_s, uint32_t b_s) {
+    auto load = [&](int cl, uint32_t a_s, uint32_t b_s) {
+        const int c = cl + j0;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int g = 2 * c + h;
@@ -174,7 +182,7 @@ __global__ void __launch_bounds__(128) k_conv(ConvP p) {
         }
     };
     int issued;
-    const bool ok = mainloop<BN>(load, p.G / 2, tiles, bar, tmem, &issued);   // sub-chunk j: groups 2j, 2j+1
+    const bool ok = mainloop<BN>(load, nsub, tiles, bar, tmem, &issued);   // sub-chunk j: groups 2j, 2j+1
     if (!ok) {
         if (tid == 0) atomicOr(p.err, 1);
     } else {
@@ -183,6 +191,13 @@ __global__ void __launch_bounds__(128) k_conv(ConvP p) {
             float r[16];
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
             if (!vok) continue;
+            if (p.ksplit > 1) {
+                float *dst = p.part + ((long)blockIdx.z * p.nvox + v) * p.Co;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (n0 + c0 + j < p.Co) dst[n0 + c0 + j] = r[j];
+                continue;
+            }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
                 const int co = n0 + c0 + j;
@@ -195,6 +210,20 @@ __global__ void __launch_bounds__(128) k_conv(ConvP p) {
         }
     }
     epilogue_free<BN>(tmem);
+}
+
+// y[v][o] = act(bias[o] + sum over splits s = 0, 1, ... of part[s][v][o]), in that order
+__global__ void k_splitk_sum(const float *__restrict__ part, int nsplit, long nvox, int Co, const float *__restrict__ bias,
+                             int relu, int f32out, void *__restrict__ y) {
+    const long n = nvox * Co;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        float a = 0.f;
+        for (int s = 0; s < nsplit; ++s) a += part[(long)s * n + i];
+        a += bias ? bias[i % Co] : 0.f;
+        if (relu) a = fmaxf(a, 0.f);
+        if (f32out) reinterpret_cast<float *>(y)[i] = a;
+        else reinterpret_cast<__nv_bfloat16 *>(y)[i] = __float2bfloat16_rn(a);
+    }
 }
 
 // ---- brick convolution: the input brick staged once, the 27 taps as descriptor offsets -----------
@@ -374,17 +403,38 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradP p) {
     }
     const __nv_bfloat16 *xrow = p.xs + ((long)(dx + 1) * p.Ci + ci) * p.nvox + dz * YX + (long)dy * p.X;
     const uint32_t tmem = prologue<BN>(bar, tslot);
+    // (x, y, z) of voxel vbase + 16 nextc, the first voxel of the next sub-chunk to load: the main
+    // loop loads the sub-chunks in increasing order, so the coordinates advance by 16 voxels per
+    // load instead of being divided out of the voxel index each time (X is a multiple of 8, so an
+    // 8-voxel half never leaves its x-row)
+    int xq, yq, zq, nextc = 0;
+    {
+        const long row = vbase / p.X;
+        xq = (int)(vbase - row * p.X);
+        yq = (int)(row % p.Y);
+        zq = (int)((row / p.Y) % p.Z);
+    }
+    auto next_row = [&](int &y, int &z) {
+        if (++y == p.Y) {
+            y = 0;
+            if (++z == p.Z) z = 0;
+        }
+    };
     auto load = [&](int c, uint32_t a_s, uint32_t b_s) {
+        for (; nextc < c; ++nextc) {
+            xq += 16;
+            while (xq >= p.X) {
+                xq -= p.X;
+                next_row(yq, zq);
+            }
+        }
         const long k0 = vbase + 16L * c;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {   // A: row (tap, i), voxels k0 + 8h .. + 7 (one x-row)
             const long kv = k0 + 8 * h;
-            bool ok = rok && kv < vend;
-            if (ok) {
-                const long row = kv / p.X;
-                const int y = (int)(row % p.Y), zz = (int)((row / p.Y) % p.Z);
-                ok = (unsigned)(zz + dz) < (unsigned)p.Z && (unsigned)(y + dy) < (unsigned)p.Y;
-            }
+            int y = yq, zz = zq;
+            if (h == 1 && xq + 8 >= p.X) next_row(y, zz);
+            const bool ok = rok && kv < vend && (unsigned)(zz + dz) < (unsigned)p.Z && (unsigned)(y + dy) < (unsigned)p.Y;
             tc::cp16(a_s + tc::tile_off(tid, h), ok ? xrow + kv : p.xs, ok);
         }
         for (int i = tid; i < 2 * BN; i += 128) {   // B: row o, voxels k0 + 8h .. + 7
@@ -587,29 +637,57 @@ __global__ void k_relu_bwd(const float *__restrict__ g, const __nv_bfloat16 *__r
     }
 }
 
-// layer input transposed and shifted along x: xs[j][c][v] = x[v + (j - 1)][c] when x + j - 1 is
-// inside the row, else 0 (j = 0, 1, 2; only j = 1 for a 1x1x1 kernel)
-__global__ void k_xshift(const __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ xs, long V, int C, int X,
-                         int nshift) {
-    __shared__ __nv_bfloat16 tile[34][193];
-    const long v0 = (long)blockIdx.x * 32;
-    for (int i = threadIdx.x; i < 34 * C; i += blockDim.x) {
-        const int r = i / C, c = i - r * C;
-        const long v = v0 + r - 1;
-        tile[r][c] = (v >= 0 && v < V) ? x[v * C + c] : __float2bfloat16_rn(0.f);
+// x [V][C] (channels last, BF16) -> xs [j][C][V] with xs[j][c][v] = x[v + j - 1][c] when the x
+// coordinate of v plus j - 1 stays in [0, X), else 0 (j = 0, 1, 2; nshift = 1 writes j = 1 only):
+// the weight gradient's input transposed to [channel][voxel], in three copies shifted along x so
+// that every 8-voxel run it loads starts on 16 bytes.  A block takes VB voxels (a multiple of 16,
+// (VB + 2) C elements of shared memory): the input around them is one contiguous range, copied with
+// 16-byte loads; each thread then assembles 16 consecutive voxels of one (j, c) row and writes them
+// with two 16-byte stores.  C and X are multiples of 8 (the network's shapes).
+__global__ void __launch_bounds__(256) k_xshift(const __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ xs,
+                                                long V, int C, int X, int nshift, int VB) {
+    extern __shared__ uint4 xsm[];
+    const __nv_bfloat16 *tile = reinterpret_cast<const __nv_bfloat16 *>(xsm);   // [VB + 2][C], row r = voxel v0 - 1 + r
+    const long v0 = (long)blockIdx.x * VB;
+    const int cq = C / 8;                                   // 16-byte pieces per voxel
+    const int n16 = (VB + 2) * cq;
+    const uint4 *src = reinterpret_cast<const uint4 *>(x);
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) {
+        const long v = v0 - 1 + i / cq;
+        xsm[i] = (v >= 0 && v < V) ? src[(v0 - 1) * cq + i] : make_uint4(0u, 0u, 0u, 0u);
     }
     __syncthreads();
     const int j0 = nshift == 3 ? 0 : 1;
-    for (int i = threadIdx.x; i < nshift * 32 * C; i += blockDim.x) {
-        const int jj = i / (32 * C), rem = i - jj * 32 * C;
-        const int c = rem / 32, r = rem - c * 32;
-        const long v = v0 + r;
-        if (v >= V) continue;
-        const int j = j0 + jj, xx = (int)(v % X) + j - 1;
-        const __nv_bfloat16 val = ((unsigned)xx < (unsigned)X) ? tile[r + j][c] : __float2bfloat16_rn(0.f);
-        xs[((long)j * C + c) * V + v] = val;
+    const int ng = VB / 16;
+    for (int w = threadIdx.x; w < nshift * C * ng; w += blockDim.x) {
+        const int c = w % C, rest = w / C;
+        const int g = rest % ng, j = j0 + rest / ng;
+        const long vs = v0 + 16L * g;                       // first voxel of this run
+        if (vs >= V) continue;
+        alignas(16) __nv_bfloat16 val[16];
+        int xv = (int)(vs % X);                             // x coordinate of voxel vs + k
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const bool in = vs + k < V && (unsigned)(xv + j - 1) < (unsigned)X;
+            val[k] = in ? tile[(16 * g + k + j) * C + c] : __float2bfloat16_rn(0.f);
+            if (++xv == X) xv = 0;
+        }
+        __nv_bfloat16 *dst = xs + ((long)j * C + c) * V + vs;
+        if (vs + 16 <= V && V % 8 == 0) {                   // 16-byte aligned: V, vs multiples of 8
+            reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(val)[0];
+            reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(val)[1];
+        } else {
+            for (int k = 0; k < 16 && vs + k < V; ++k) dst[k] = val[k];
+        }
     }
 }
+// voxels per block of k_xshift for C channels, and its shared memory
+inline int xshift_vb(int C) {
+    int vb = 8192 / C;
+    vb = vb > 256 ? 256 : (vb < 16 ? 16 : vb);
+    return vb / 16 * 16;
+}
+inline size_t xshift_smem(int C) { return (size_t)(xshift_vb(C) + 2) * C * sizeof(__nv_bfloat16); }
 
 // squared error of y [n] against t divided by denom (the number of real elements; padded channels
 // hold 0 in both), one partial sum per block (k_dsum adds them in order), and its gradient
