@@ -487,6 +487,68 @@ def warm_start(args):
                       "workload": "pto_sto_bilayer_64x64x32_config5", **rep}))
 
 
+def integrator_compare(args):
+    """Time to relax the config-5 bilayer points (64x64x32 PbTiO3/SrTiO3, the first --ic-points of
+    the seeded list, random starts) alone with each integrator of Sec. 3, all stopping at the same
+    rate |dP/dt| (1e-6 P0 per reference step of dt* = 0.004): forward Euler at the reference step
+    (the baseline) and at dt* = --ic-dt-star, Heun and AB3M2 at --ic-dt-star (their per-step
+    tolerance is the reference one times dt / dt_ref), RK45 with adaptive steps from the reference
+    step (its check scales max |dP| by dt_ref / dt itself).  Reports per method the steps, field
+    evaluations, wall time, and the final states' free-energy and texture differences to the
+    baseline's."""
+    import torch
+    from paper_2605_28800_b300 import tdgl, warmstart
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    ctx = tdgl.Context(dev)
+    cfg = synth.CONFIG5
+    pts = synth.bilayer_points(args.ic_points, cfg["seed"], cfg["T"], cfg["Ez"], cfg["ratio"], cfg["shape"][2])
+    big = args.ic_dt_star
+    # (name, integrator, dt*, evaluations per step, adaptive error tolerance)
+    methods = [("euler dt*=0.004", tdgl.EULER, cfg["dt_star"], 1, 0.0),
+               (f"euler dt*={big}", tdgl.EULER, big, 1, 0.0),
+               (f"heun dt*={big}", tdgl.HEUN, big, 2, 0.0),
+               (f"ab3m2 dt*={big}", tdgl.AB3M2, big, 2, 0.0),
+               ("rk45 adaptive", tdgl.RK45, cfg["dt_star"], 6, args.ic_err_tol)]
+    rows, ref = [], None
+    for name, integ, dts, evals, err_tol in methods:
+        steps, conv, secs, F, Ps = [], [], 0.0, [], []
+        for p in pts:
+            s = warmstart.make_sim(ctx, cfg["shape"], cfg["cell"], p, cfg["eps_b"],
+                                   synth.uniform_P(cfg["shape"], cfg["amp"], p["seed"]))
+            s.set_integrator(integ)
+            if err_tol > 0:
+                s.set_adaptive(err_tol)
+            a = s.scales()[1]
+            dt, dt_ref = dts / a, cfg["dt_star"] / a
+            tol = cfg["tol"] * (dt / dt_ref if err_tol == 0 else 1.0)
+            s.energy()                      # one-off tensor build, outside the timing
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            n, ok = s.relax(dt, tol, args.max_relax_steps, CHECK_EVERY, raise_on_cap=False)
+            torch.cuda.synchronize()
+            secs += time.perf_counter() - t0
+            steps.append(n)
+            conv.append(ok)
+            F.append(s.energy()["total"])
+            Ps.append(s.get_P())
+            s.close()
+        rec = {"method": name, "dt_star": dts, "seconds": secs, "steps": int(sum(steps)),
+               "field_evaluations_min": int(sum(steps) * evals), "converged": int(sum(conv)), "points": len(pts)}
+        if ref is None:
+            ref = (F, Ps)
+        else:
+            dF = [abs(f - g) / abs(g) for f, g in zip(F, ref[0])]
+            dP = [float(np.sqrt(np.mean((P - Q) ** 2)) / np.sqrt(np.mean(Q ** 2))) for P, Q in zip(Ps, ref[1])]
+            rec.update(dF_rel_median=float(np.median(dF)), dF_rel_max=float(max(dF)),
+                       texture_rms_rel_median=float(np.median(dP)), texture_rms_rel_max=float(max(dP)),
+                       speedup_vs_baseline=rows[0]["seconds"] / secs)
+        rows.append(rec)
+    print(json.dumps({"metric": "time-to-relax per integrator at equal rate tolerance", "unit": "s",
+                      "workload": "pto_sto_bilayer_64x64x32_config5", "tol_rate": cfg["tol"],
+                      "max_steps": args.max_relax_steps, "per_method": rows}))
+
+
 def hysteresis(args):
     """The DC field loop of the bilayer workload (256x256x64 PbTiO3 on SrTiO3, 81 out-of-plane field
     points from +200 to -200 MV/m and back): at each point the state relaxes from the previous one
@@ -973,11 +1035,18 @@ def main():
     ap.add_argument("--skx-dt-star", type=float, default=0.015)
     ap.add_argument("--skx-eps-b", type=float, default=0.0, help="eps_B of --skyrmion (0: the recipe's 45)")
     ap.add_argument("--out", default="", help="full JSON record of --ac-loop / --skyrmion")
+    ap.add_argument("--integrator-compare", action="store_true",
+                    help="time to relax config-5 bilayer points with Euler, Heun, AB3M2 and adaptive RK45")
+    ap.add_argument("--ic-points", type=int, default=16)
+    ap.add_argument("--ic-dt-star", type=float, default=0.04)
+    ap.add_argument("--ic-err-tol", type=float, default=1e-5)
     ap.add_argument("--cufft-compare", action="store_true",
                     help="electrostatic field of the bench cube: this library vs a cuFFT (torch.fft) convolution")
     args = ap.parse_args()
     if args.cufft_compare:
         return cufft_compare(args)
+    if args.integrator_compare:
+        return integrator_compare(args)
     if args.ac_loop:
         return ac_loop(args)
     if args.skyrmion:
