@@ -400,12 +400,15 @@ def relax_compare(args):
         for s, _ in sims:
             s.close()
     cells = sum(m["L"] ** 3 for m in members)
+    updates = sum(n * m["L"] ** 3 for n, m in zip(res["plain"]["steps"], members))   # cell-updates of the sweep
     same = all(abs(a - b) <= 1e-6 * max(abs(a), 1e-30) for a, b in zip(res["plain"]["energies"], res["batched"]["energies"]))
     line = {"metric": "time-to-relax, batched vs plain at equal tol", "unit": "s",
             "workload": f"bto_sweep_{len(members)}", "sims": len(members), "cells": cells, "tol": args.tol,
             "check_every": CHECK_EVERY, "max_steps": args.max_relax_steps,
             "plain_s": res["plain"]["seconds"], "batched_s": res["batched"]["seconds"],
             "speedup": res["plain"]["seconds"] / res["batched"]["seconds"],
+            "aggregate_cell_updates_per_s": {"plain": updates / res["plain"]["seconds"],
+                                             "batched": updates / res["batched"]["seconds"]},
             "converged": [res["plain"]["converged"], res["batched"]["converged"]],
             "total_steps": sum(res["plain"]["steps"]), "same_final_energies": same,
             "sizes": [m["L"] for m in members], "temperatures": [m["T"] for m in members],
