@@ -840,7 +840,8 @@ def size_sweep(args):
     torch.cuda.set_device(dev)
     ctx = tdgl.Context(dev)
     rows = []
-    for shape in [(32, 32, 8), (32, 32, 32), (48, 48, 48), (64, 64, 64), (96, 96, 96), (128, 128, 128)]:
+    for shape in [(32, 32, 8), (32, 32, 32), (40, 40, 40), (48, 48, 48), (64, 64, 64), (80, 80, 80), (96, 96, 96),
+                  (128, 128, 128)]:
         nx, ny, nz = shape
         s = tdgl.Sim(ctx, shape, (1e-9,) * 3)
         s.define_material(1, synth.BTO)

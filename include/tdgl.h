@@ -107,10 +107,12 @@ int  tdgl_sim_create(tdgl_ctx *ctx, int nx, int ny, int nz, double dx, double dy
 void tdgl_sim_destroy(tdgl_sim *sim);
 
 /* Padded transform lengths of the open-boundary convolution (Eqs. 5-6; any length >= 2n - 1 gives
- * the same linear convolution).  Defaults: the smallest 2^a 3^b >= 2n - 1 along x (even) and y;
- * along z the same, except that a length with a factor 3 gives way to the next power of two when
- * that is 128, 256 or 512 and at most 4/3 of it (96 -> 128, 192 -> 256, 384 -> 512), whose tuned
- * z pass finishes first.  tdgl_fft_pad reports them; tdgl_set_fft_pad sets them (0 = the default
+ * the same linear convolution).  Defaults: the smallest 2^a 3^b >= 2n - 1 along x (even), y and z,
+ * except that along z a length with a factor 3 gives way to the next power of two when that is 128,
+ * 256 or 512 and at most 4/3 of it (96 -> 128, 192 -> 256, 384 -> 512), whose tuned z pass finishes
+ * first, and along y and z a length the specialized transforms (16, 32, 48, 64, 96, 128, 192, 256,
+ * 512) do not cover gives way to the smallest one they cover within 4/3 (81 -> 96, 162 -> 192).
+ * tdgl_fft_pad reports them; tdgl_set_fft_pad sets them (0 = the default
  * for that axis): each must be 2^a 3^b, >= 2n - 1 and <= 4 TDGL_MAX_DIM, Mx even, else TDGL_EINVAL.
  * Setting new lengths waits for the context's stream, frees the sim's spectra and tensor spectrum
  * (rebuilt on the next call that needs the field) and drops its captured step graphs. */

@@ -165,19 +165,34 @@ bool is_smooth(int m) {   // m = 2^a 3^b
     return m == 1;
 }
 
-// Default padded length along z: the smallest 2^a 3^b >= 2 nz - 1, except that a length with a
-// factor 3 gives way to the next power of two when that is one of the z pass's tuned lengths (128,
-// 256, 512) and at most 4/3 of it (96 -> 128, 192 -> 256, 384 -> 512).  Any length >= 2 nz - 1
-// gives the same linear convolution; on a B300 the tuned 256-point z pass takes 15 ps per point
-// against 29 ps for the generic 192-point shape, so the longer lines finish first (96^3 cube:
-// 104 -> about 73 us per z pass).
-int default_z_length(int nz) {
-    const int m = smooth_at_least(2 * nz - 1, false);
-    if (m % 3 != 0) return m;
-    int p2 = 1;
-    while (p2 < m) p2 *= 2;
-    return ((p2 == 128 || p2 == 256 || p2 == 512) && 3 * p2 <= 4 * m) ? p2 : m;
+// smallest length >= m that the specialized (register) transforms cover, 0 if none
+int fast_at_least(int m) {
+    static const int L[] = {16, 32, 48, 64, 96, 128, 192, 256, 512};
+    for (int v : L)
+        if (v >= m) return v;
+    return 0;
 }
+
+// Default padded length of the y or z axis of n cells: the smallest 2^a 3^b >= 2n - 1, except
+//  - along z, a length with a factor 3 gives way to the next power of two when that is one of the
+//    z pass's tuned lengths (128, 256, 512) and at most 4/3 of it (96 -> 128, 192 -> 256, 384 ->
+//    512): the tuned 256-point z pass takes 15 ps per point against 29 ps for the 192-point shape;
+//  - a length the specialized transforms do not cover gives way to the smallest one they cover
+//    when that is at most 4/3 of it (81 -> 96, 162 -> 192): the generic shared-memory kernels take
+//    2-3 times as long per point (80^3 cube: 407 -> 221 us per step).
+// Any length >= 2n - 1 gives the same linear convolution.
+int default_yz_length(int n, bool z) {
+    const int m = smooth_at_least(2 * n - 1, false);
+    if (z && m % 3 == 0) {
+        int p2 = 1;
+        while (p2 < m) p2 *= 2;
+        if ((p2 == 128 || p2 == 256 || p2 == 512) && 3 * p2 <= 4 * m) return p2;
+    }
+    const int f = fast_at_least(2 * n - 1);
+    return (f && f != m && 3 * f <= 4 * m && fast_at_least(m) != m) ? f : m;
+}
+int default_z_length(int nz) { return default_yz_length(nz, true); }
+int default_y_length(int ny) { return default_yz_length(ny, false); }
 
 Plan make_plan(int n, std::vector<float2> &tw) {
     Plan p;
@@ -1360,7 +1375,7 @@ int tdgl_sim_create(tdgl_ctx *ctx, int nx, int ny, int nz, double dx, double dy,
     memset(s->mats, 0, sizeof s->mats);
     s->map.assign(s->ncell, 0);
     std::vector<float2> tw;
-    set_lengths(s, smooth_at_least(2 * nx - 1, true), smooth_at_least(2 * ny - 1, false), default_z_length(nz), tw);
+    set_lengths(s, smooth_at_least(2 * nx - 1, true), default_y_length(ny), default_z_length(nz), tw);
     int rc = TDGL_OK;
     auto al = [&](void **p, size_t b) {
         if (rc != TDGL_OK) return;
@@ -1565,7 +1580,7 @@ int tdgl_set_fft_pad(tdgl_sim *s, int Mx, int My, int Mz) {
     if (!s) return TDGL_EINVAL;
     tdgl_ctx *ctx = s->ctx;
     if (Mx == 0) Mx = smooth_at_least(2 * s->nx - 1, true);
-    if (My == 0) My = smooth_at_least(2 * s->ny - 1, false);
+    if (My == 0) My = default_y_length(s->ny);
     if (Mz == 0) Mz = default_z_length(s->nz);
     if (Mx < 2 * s->nx - 1 || My < 2 * s->ny - 1 || Mz < 2 * s->nz - 1 || Mx % 2 != 0 || !is_smooth(Mx) ||
         !is_smooth(My) || !is_smooth(Mz) || Mx > 4 * TDGL_MAX_DIM || My > 4 * TDGL_MAX_DIM || Mz > 4 * TDGL_MAX_DIM)

@@ -184,12 +184,14 @@ def test_forced_row_tile_steps_like_the_tuned_one():
 
 
 def test_fft_padding_defaults_and_forced_lengths(ctx):
-    # defaults: smallest 2^a 3^b >= 2n - 1 (x even), z giving way to 128 / 256 / 512 within 4/3;
+    # defaults: smallest 2^a 3^b >= 2n - 1 (x even); z gives way to 128 / 256 / 512 within 4/3, and
+    # y and z to the smallest specialized transform length within 4/3;
     # forced lengths are validated, and a sim re-padded between steps follows the same trajectory
     from paper_2605_28800_b300 import tdgl
     cases = {(96, 96, 96): (192, 192, 256), (48, 48, 48): (96, 96, 128), (17, 9, 5): (36, 18, 9),
              (32, 32, 8): (64, 64, 16), (128, 128, 128): (256, 256, 256),
-             (40, 40, 81): (96, 81, 162)}   # x: 81 is odd, so 96; z: 256 > 4/3 of 162
+             (40, 40, 81): (96, 96, 192),   # x: 81 is odd, so 96; y 81 and z 162 give way to 96 and 192
+             (80, 80, 80): (162, 192, 192), (40, 40, 40): (96, 96, 96), (3, 5, 7): (6, 9, 16)}
     for shape, want in cases.items():
         s = tdgl.Sim(ctx, shape, (1e-9,) * 3)
         assert s.fft_pad() == want, shape
