@@ -112,6 +112,9 @@ void tdgl_sim_destroy(tdgl_sim *sim);
  * 256 or 512 and at most 4/3 of it (96 -> 128, 192 -> 256, 384 -> 512), whose tuned z pass finishes
  * first, and along y and z a length the specialized transforms (16, 32, 48, 64, 96, 128, 192, 256,
  * 512) do not cover gives way to the smallest one they cover within 4/3 (81 -> 96, 162 -> 192).
+ * Along x, for rows a multiple of 4 cells long whose half-length is not specialized, twice the
+ * smallest specialized half-length >= nx within 4/3 (80 cells: 162 -> 192): such rows, and any rows
+ * of nx <= Mx / 2 cells with nx a multiple of 4, run in the tiled step kernel.
  * tdgl_fft_pad reports them; tdgl_set_fft_pad sets them (0 = the default
  * for that axis): each must be 2^a 3^b, >= 2n - 1 and <= 4 TDGL_MAX_DIM, Mx even, else TDGL_EINVAL.
  * Setting new lengths waits for the context's stream, frees the sim's spectra and tensor spectrum

@@ -47,20 +47,26 @@ template <int HX> __host__ __device__ constexpr size_t xrows_smem() {
 // Neighbourhood of a block's cells: materials of planes z-1, z, z+1 (rows y0-1 .. y0+TY, all x,
 // out-of-grid cells vacuum) and P of the centre plane in shared memory; P of planes z-1 and z+1
 // is read through the L1 cache from global memory.  Every caller reads P only at material cells
-// (checked on the material tile first), which are inside the grid.
-template <int NX, int TYH>
+// (checked on the material tile first), which are inside the grid.  Tile rows are LX apart in
+// shared memory (the x half-length); a grid row holds nx <= LX cells.
+template <int LX, int TYH, bool SHORT>
 struct TileView {
-    const float *P;       // centre plane [3 comps][TYH rows][NX], shared memory
+    const float *P;       // centre plane [3 comps][TYH rows][LX], shared memory
     const float *G;       // the sim's P (global), component stride ncell
     long ncell;
     long row0[2];         // index of (plane z-1 / z+1, row y0-1, x 0) in one component of G
-    const uint8_t *M;     // [3 planes][TYH][NX]
+    const uint8_t *M;     // [3 planes][TYH][LX]
+    int nxr;              // cells per row when SHORT (else LX)
+    __device__ __forceinline__ int nx() const {
+        if constexpr (SHORT) return nxr;
+        else return LX;
+    }
     __device__ __forceinline__ int m(int pz, int py, int x) const {
-        return (unsigned)x < (unsigned)NX ? (int)M[(pz * TYH + py) * NX + x] : 0;
+        return (unsigned)x < (unsigned)nx() ? (int)M[(pz * TYH + py) * LX + x] : 0;
     }
     __device__ __forceinline__ float p(int c, int pz, int py, int x) const {
-        if (pz == 1) return P[(c * TYH + py) * NX + x];
-        return __ldg(G + c * ncell + row0[pz >> 1] + py * NX + x);
+        if (pz == 1) return P[(c * TYH + py) * LX + x];
+        return __ldg(G + c * ncell + row0[pz >> 1] + py * nx() + x);
     }
 };
 
@@ -209,11 +215,13 @@ __device__ __forceinline__ float tgrad_energy(const TV &V, const SimDev &S, cons
     return e;
 }
 
-template <int MODE, int HX>
+template <int MODE, int HX, bool SHORT = false>
 __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sims, const int4 *__restrict__ items,
                                                int istep) {
     constexpr int E = rf::Cfg<HX>::E, T = HX / E, LDP = xrows_ldp<HX>();
-    constexpr int nx = HX, TYmax = xrows_tile<HX>(), TYH = TYmax + 2, nthr = xrows_threads<HX>();
+    // LX: row stride of the shared tiles (the x half-length); nx: cells per grid row, LX itself
+    // unless SHORT (then nx <= LX, a multiple of 4; the x transforms zero-pad the rest of the row)
+    constexpr int LX = HX, TYmax = xrows_tile<HX>(), TYH = TYmax + 2, nthr = xrows_threads<HX>();
     extern __shared__ float4 smem4[];
     __shared__ float s_coef[MAXMAT * NCOEF];
     __shared__ float2 s_tw[HX];          // W_HX^t for the complex transform
@@ -227,16 +235,20 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
     const SimDev &S = sims[it.x];
     if (S.skip) return;   // a batch member that has left the relaxation
     const int z = it.y, y0 = it.z, TY = it.w;     // TY rows of this block (<= tile)
+    const int nx = [&] {
+        if constexpr (SHORT) return S.nx;
+        else return LX;
+    }();
     const int ny = S.ny, nz = S.nz;
     const int tid = threadIdx.x;
-    // layout (xrows_smem): region R = max(P tile [3][3][TYH][nx] floats, x-transform exchange
+    // layout (xrows_smem): region R = max(P tile [3][3][TYH][LX] floats, x-transform exchange
     // [nthr/T][LDP] float2; the exchange is only live while the tile is not), then the E / new-P
-    // rows [3][TYmax][nx] and the material tile [3][TYH][nx]
+    // rows [3][TYmax][LX] and the material tile [3][TYH][LX]
     float *Pt = reinterpret_cast<float *>(smem4);
     float2 *X2 = reinterpret_cast<float2 *>(smem4);
     constexpr int rf_ = xrows_region<HX>();                     // floats, multiple of 4
     float *Eb = Pt + rf_;
-    uint8_t *Mt = reinterpret_cast<uint8_t *>(Eb + 3 * TYmax * nx);
+    uint8_t *Mt = reinterpret_cast<uint8_t *>(Eb + 3 * TYmax * LX);
     const int parity = istep & 1;      // istep: step index within the call
     // HEUN2 evaluates the field on the predictor (other buffer) and updates P in place
     const float *Pc = (MODE == MODE_HEUN2) ? S.P[parity ^ 1] : S.P[parity];
@@ -248,7 +260,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
     // copies issued now, zero (vacuum) outside the grid, waited for before the cells
     const unsigned m0x4 = 0x01010101u * (unsigned)__ldg(S.mat + ((long)z * ny + y0) * nx);
     const int mrow = ((MODE == MODE_XFWD) ? 1 : 3) * TYH;
-    static_assert(nx % 4 == 0, "row length must be a multiple of 4");
+    static_assert(LX % 4 == 0, "tile rows must be a multiple of 4 long");
     for (int w = tid; w < mrow * (nx / 4); w += nthr) {
         const int q = w % (nx / 4), rr = w / (nx / 4);
         const int py = rr % TYH;
@@ -256,7 +268,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
         const int gy = y0 - 1 + py, gz = z - 1 + pz;
         const bool in = (unsigned)gy < (unsigned)ny && (unsigned)gz < (unsigned)nz && py <= TY + 1;
         const uint8_t *g = in ? S.mat + ((long)gz * ny + gy) * nx + 4 * q : S.mat;
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(Mt + (pz * TYH + py) * nx + 4 * q);
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(Mt + (pz * TYH + py) * LX + 4 * q);
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(g), "r"(in ? 4 : 0));
     }
     asm volatile("cp.async.commit_group;\n" ::);
@@ -298,7 +310,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
             for (int i = 0; i < E; ++i) {
                 const int j = rf::final_pos<rf::Cfg<HX>>(t, i);
                 const int x0 = 2 * j;
-                float *er = Eb + (lc * TYmax + lr) * nx;
+                float *er = Eb + (lc * TYmax + lr) * LX;
                 if (rf::kept_out<rf::Cfg<HX>>(i) && x0 < nx) er[x0] = v[i].x;
                 if (rf::kept_out<rf::Cfg<HX>>(i) && x0 + 1 < nx) er[x0 + 1] = v[i].y;
             }
@@ -317,7 +329,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
             const int q = w % (nx / 4), rr = w / (nx / 4);
             const int py = rr % TYH;
             const int pz = (MODE == MODE_XFWD) ? 1 : rr / TYH;
-            const unsigned v = reinterpret_cast<const unsigned *>(Mt + (pz * TYH + py) * nx)[q];
+            const unsigned v = reinterpret_cast<const unsigned *>(Mt + (pz * TYH + py) * LX)[q];
             if (MODE != MODE_XFWD && py <= TY + 1 && v != m0x4) {
                 const int gy = y0 - 1 + py, gz = z - 1 + pz;
                 atomicOr(&s_bad, 1u << py);
@@ -334,7 +346,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
                 const bool in = (unsigned)gy < (unsigned)ny && py <= TY + 1;
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (in) v = __ldg(reinterpret_cast<const float4 *>(Pc + c * S.ncell + ((long)z * ny + gy) * nx) + q);
-                reinterpret_cast<float4 *>(Pt + (c * TYH + py) * nx)[q] = v;
+                reinterpret_cast<float4 *>(Pt + (c * TYH + py) * LX)[q] = v;
             }
         } else {
             for (int w = tid; w < 3 * TYH * nx; w += nthr) {
@@ -342,7 +354,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
                 const int py = rr % TYH, c = rr / TYH;
                 const int gy = y0 - 1 + py;
                 const bool in = (unsigned)gy < (unsigned)ny && py <= TY + 1;
-                Pt[(c * TYH + py) * nx + x] = in ? __ldg(&Pc[c * S.ncell + ((long)z * ny + gy) * nx + x]) : 0.f;
+                Pt[(c * TYH + py) * LX + x] = in ? __ldg(&Pc[c * S.ncell + ((long)z * ny + gy) * nx + x]) : 0.f;
             }
         }
     }
@@ -363,7 +375,8 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
     }
     __syncthreads();
     // ---- cells
-    const TileView<nx, TYH> V{Pt, Pc, S.ncell, {((long)(z - 1) * ny + y0 - 1) * nx, ((long)(z + 1) * ny + y0 - 1) * nx}, Mt};
+    const TileView<LX, TYH, SHORT> V{Pt, Pc, S.ncell, {((long)(z - 1) * ny + y0 - 1) * nx, ((long)(z + 1) * ny + y0 - 1) * nx},
+                                     Mt, nx};
     // The sim's scalars and material m0's coefficients in registers: the cell loops store to global
     // memory, after which every field of the descriptor (itself in global memory) would be reloaded.
     const long ncell = S.ncell;
@@ -398,13 +411,13 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
     // the discrete Eq. 4 reduces to G (P(+) + P(-) - 2P) / dx^2 per face pair plus
     // (G12 + G44 - G'44) times the four-corner mixed differences d_e d_f P_f (tgrad_field's bulk form).
     auto bulk_grad = [&](const int py, const int x, const float *p, float *h) {
-        constexpr int TS = TYH * nx;                  // component stride of the shared tile
-        const float *c = Pt + py * nx + x;            // centre plane, component 0
+        constexpr int TS = TYH * LX;                  // component stride of the shared tile
+        const float *c = Pt + py * LX + x;            // centre plane, component 0
         const float *lo = zlo + py * nx + x, *hi = zhi + py * nx + x;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const float lx = c[i * TS - 1] + c[i * TS + 1] - 2.f * p[i];
-            const float ly = c[i * TS - nx] + c[i * TS + nx] - 2.f * p[i];
+            const float ly = c[i * TS - LX] + c[i * TS + LX] - 2.f * p[i];
             const float lz = __ldg(lo + i * ncell) + __ldg(hi + i * ncell) - 2.f * p[i];
             h[i] = fmaf(i == 0 ? gd[0] : go[0], lx, fmaf(i == 1 ? gd[1] : go[1], ly, fmaf(i == 2 ? gd[2] : go[2], lz, h[i])));
         }
@@ -412,7 +425,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
             // (x+,y+) - (x+,y-) - (x-,y+) + (x-,y-) and the xz / yz analogues
             auto cxy = [&](int f) {
                 const float *q = c + f * TS;
-                return q[nx + 1] - q[-nx + 1] - q[nx - 1] + q[-nx - 1];
+                return q[LX + 1] - q[-LX + 1] - q[LX - 1] + q[-LX - 1];
             };
             auto cxz = [&](int f) {
                 const float *a = hi + f * ncell, *b = lo + f * ncell;
@@ -506,8 +519,8 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
     // and cross terms, whose ghost rules never apply here, with m0's coefficients in registers
     // (the same operations in the same order, so both give the same result bit for bit).
     auto bulk_genergy = [&](const int py, const int x, const float *pa) {
-        constexpr int TS = TYH * nx;
-        const float *c = Pt + py * nx + x;
+        constexpr int TS = TYH * LX;
+        const float *c = Pt + py * LX + x;
         const float *hi = zhi + py * nx + x, *lo = zlo + py * nx + x;
         float e = 0.f;
 #pragma unroll
@@ -515,7 +528,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const float g = 0.5f * ((i == d) ? gd[d] + gd[d] : go[d] + go[d]);
-                const float nb = d == 0 ? c[i * TS + 1] : (d == 1 ? c[i * TS + nx] : __ldg(hi + i * ncell));
+                const float nb = d == 0 ? c[i * TS + 1] : (d == 1 ? c[i * TS + LX] : __ldg(hi + i * ncell));
                 const float df = nb - pa[i];
                 e = fmaf(0.5f * g * df, df, e);
             }
@@ -525,7 +538,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 D[i][0] = (c[i * TS + 1] - c[i * TS - 1]) * inv2d[0];
-                D[i][1] = (c[i * TS + nx] - c[i * TS - nx]) * inv2d[1];
+                D[i][1] = (c[i * TS + LX] - c[i * TS - LX]) * inv2d[1];
                 D[i][2] = (__ldg(hi + i * ncell) - __ldg(lo + i * ncell)) * inv2d[2];
             }
             e += c10 * (D[0][0] * D[1][1] + D[1][1] * D[2][2] + D[2][2] * D[0][0]) +
@@ -539,7 +552,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
         const long id = ((long)z * ny + y0 + r) * nx + x;
         if (elec) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) h[c] += Eb[(c * TYmax + r) * nx + x];
+            for (int c = 0; c < 3; ++c) h[c] += Eb[(c * TYmax + r) * LX + x];
         }
         if (terms & TERM_EXT) {
 #pragma unroll
@@ -568,7 +581,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
             if (MODE != MODE_HEUN1) lmax = fmaxf(lmax, fabsf(pn - p0));
             bad |= !(fabsf(pn) <= pmax);
             Pn[c * ncell + id] = pn;
-            Eb[(c * TYmax + r) * nx + x] = pn;      // the cell's own slot: E read above, new P kept
+            Eb[(c * TYmax + r) * LX + x] = pn;      // the cell's own slot: E read above, new P kept
         }
     };
     // one cell (r, x); BULK: known bulk cell of material m0 (no vacuum, ghost or interface rule)
@@ -581,7 +594,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
         if (!KNOWN && m == 0) {
             if (mode_updates(MODE)) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) { Pn[c * ncell + id] = 0.f; Eb[(c * TYmax + r) * nx + x] = 0.f; }
+                for (int c = 0; c < 3; ++c) { Pn[c * ncell + id] = 0.f; Eb[(c * TYmax + r) * LX + x] = 0.f; }
             } else if (MODE == MODE_FIELD) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) outp[c * ncell + id] = 0.f;
@@ -593,7 +606,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
         }
         float p[3], h[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) p[c] = Pt[(c * TYH + py) * nx + x];
+        for (int c = 0; c < 3; ++c) p[c] = Pt[(c * TYH + py) * LX + x];
         const float *cm = s_coef + m * NCOEF;
         if (MODE == MODE_ENERGY) {
             if (terms & TERM_LANDAU) {
@@ -612,7 +625,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
             float el = 0.f, ex = 0.f;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                if (elec) el = fmaf(-0.5f * Eb[(c * TYmax + r) * nx + x], p[c], el);
+                if (elec) el = fmaf(-0.5f * Eb[(c * TYmax + r) * LX + x], p[c], el);
                 if (terms & TERM_EXT) ex = fmaf(-eext[c], p[c], ex);
             }
             e_elec += (double)el;
@@ -672,7 +685,7 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
     // ---- x-forward of the new (STEP) or current (XFWD) rows: z_j = (x_2j, x_2j+1), zero padded
     {
         float2 v[E];
-        const float *src = (MODE == MODE_XFWD) ? Pt + (lc * TYH + lr + 1) * nx : Eb + (lc * TYmax + lr) * nx;
+        const float *src = (MODE == MODE_XFWD) ? Pt + (lc * TYH + lr + 1) * LX : Eb + (lc * TYmax + lr) * LX;
 #pragma unroll
         for (int m = 0; m < E; ++m) {
             const int j = t + T * m;

@@ -194,6 +194,18 @@ int default_yz_length(int n, bool z) {
 int default_z_length(int nz) { return default_yz_length(nz, true); }
 int default_y_length(int ny) { return default_yz_length(ny, false); }
 
+// Default padded length of the x axis of nx cells: the smallest even 2^a 3^b >= 2 nx - 1, except
+// that when its half is not a specialized length and nx is a multiple of 4 it gives way to twice the
+// smallest specialized half-length >= nx within 4/3 (80 cells: 162 -> 192), so the rows run in the
+// tiled step kernel (which takes rows of nx <= Mx / 2 cells, nx a multiple of 4) instead of the
+// generic one.
+int default_x_length(int nx) {
+    const int m = smooth_at_least(2 * nx - 1, true);
+    if (nx % 4 != 0 || fast_at_least(m / 2) == m / 2) return m;
+    const int h = fast_at_least(nx);
+    return (h && 3 * (2 * h) <= 4 * m) ? 2 * h : m;
+}
+
 Plan make_plan(int n, std::vector<float2> &tw) {
     Plan p;
     memset(&p, 0, sizeof p);
@@ -319,8 +331,9 @@ void build_items(tdgl_sim *s) {
     s->it_rows_full.clear();
     s->it_y.clear();
     s->it_z.clear();
-    // the tiled row kernel needs the row length to equal the x half-length (2 nx smooth)
-    s->xN = (fast_len(s->hx) && s->nx == s->hx) ? s->hx : 0;
+    // the tiled row kernel takes rows of nx <= hx cells, nx a multiple of 4 (a shorter row is zero
+    // padded inside its x transforms)
+    s->xN = (fast_len(s->hx) && s->nx <= s->hx && s->nx % 4 == 0) ? s->hx : 0;
     const int RB = s->xN ? fast_rowtile(s->hx)
                          : std::max(1, std::min(s->ny, std::max(1, 512 / s->nx)));
     s->rows_cnt_max = RB;
@@ -634,11 +647,15 @@ int upload_desc(tdgl_sim *s) {
 
 // -- kernel sequences (over a descriptor table and item lists) ---------------------------------------
 struct Group {
-    int N;              // specialized transform length, 0 = generic kernel
+    int N;              // specialized transform length, 0 = generic kernel; for row groups -N marks
+                        // rows shorter than the x half-length N (the step kernel's SHORT form)
     const int4 *items;
     int n;
     size_t smem;        // dynamic shared memory (generic kernels only)
 };
+
+// row-group length of a sim: its x half-length, negative when its rows are shorter (SHORT kernel)
+int row_group_len(const tdgl_sim *s) { return (s->xN && s->nx < s->xN) ? -s->xN : s->xN; }
 
 struct Work {
     const SimDev *descs;
@@ -651,8 +668,13 @@ void rows_launch(const Group &g, const SimDev *d, cudaStream_t st, int parity) {
         k_rows<MODE><<<g.n, NTHREADS, g.smem, st>>>(d, g.items, parity);
         return;
     }
-    switch (g.N) {
-#define TDGL_R(LEN) case LEN: k_xrows<MODE, LEN><<<g.n, xrows_threads<LEN>(), g.smem, st>>>(d, g.items, parity); break;
+    const bool sh = g.N < 0;
+    switch (sh ? -g.N : g.N) {
+#define TDGL_R(LEN)                                                                               \
+    case LEN:                                                                                     \
+        if (sh) k_xrows<MODE, LEN, true><<<g.n, xrows_threads<LEN>(), g.smem, st>>>(d, g.items, parity); \
+        else k_xrows<MODE, LEN><<<g.n, xrows_threads<LEN>(), g.smem, st>>>(d, g.items, parity);   \
+        break;
         TDGL_FAST_LENGTHS(TDGL_R)
 #undef TDGL_R
     }
@@ -760,7 +782,7 @@ int launch_conv(tdgl_ctx *ctx, const Work &w) {
 Work sim_work(tdgl_sim *s, bool elec) {
     Work w;
     w.descs = s->ddesc;
-    w.rg.push_back(Group{s->xN, s->d_rows, (int)s->it_rows.size(), smem_rows(s, s->rows_cnt_max)});
+    w.rg.push_back(Group{row_group_len(s), s->d_rows, (int)s->it_rows.size(), smem_rows(s, s->rows_cnt_max)});
     if (elec) {
         w.yg.push_back(Group{s->yN, s->d_y, (int)s->it_y.size(), s->yN ? 0 : smem_y(s, s->ky_cnt_max)});
         w.zg.push_back(Group{s->zN, s->d_z, (int)s->it_z.size(), s->zN ? 0 : smem_z(s, s->kz_cnt_max)});
@@ -869,7 +891,7 @@ int autotune_rows(tdgl_sim *s) {
         for (int z = 0; z < s->nz; ++z)
             for (int y0 = 0; y0 < s->ny; y0 += cand[c]) it.push_back(make_int4(0, z, y0, std::min(cand[c], s->ny - y0)));
         if (!ck(cudaMemcpyAsync(items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream))) break;
-        const Group g{s->xN, items, (int)it.size(), smem_rows(s, s->rows_cnt_max)};
+        const Group g{row_group_len(s), items, (int)it.size(), smem_rows(s, s->rows_cnt_max)};
         rows_launch<MODE_STEP>(g, dd, ctx->stream, 0);
         ck(cudaEventRecord(e0, ctx->stream));
         for (int r = 0; r < 3; ++r) rows_launch<MODE_STEP>(g, dd, ctx->stream, 0);
@@ -1225,7 +1247,14 @@ int tdgl_ctx_create(tdgl_ctx **out, int device, void *stream) {
     cudaFuncSetAttribute(k_xrows<MODE_XFWD, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);   \
     cudaFuncSetAttribute(k_xrows<MODE_HEUN1, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);  \
     cudaFuncSetAttribute(k_xrows<MODE_HEUN2, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);  \
-    cudaFuncSetAttribute(k_xrows<MODE_DERIV, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaFuncSetAttribute(k_xrows<MODE_DERIV, LEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);  \
+    cudaFuncSetAttribute(k_xrows<MODE_STEP, LEN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);   \
+    cudaFuncSetAttribute(k_xrows<MODE_FIELD, LEN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);  \
+    cudaFuncSetAttribute(k_xrows<MODE_ENERGY, LEN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem); \
+    cudaFuncSetAttribute(k_xrows<MODE_XFWD, LEN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);   \
+    cudaFuncSetAttribute(k_xrows<MODE_HEUN1, LEN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);  \
+    cudaFuncSetAttribute(k_xrows<MODE_HEUN2, LEN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);  \
+    cudaFuncSetAttribute(k_xrows<MODE_DERIV, LEN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     TDGL_FAST_LENGTHS(TDGL_XA)
 #undef TDGL_XA
 #define TDGL_ZA(LEN) zpass_attrs<LEN>(kMaxSmem);
@@ -1375,7 +1404,7 @@ int tdgl_sim_create(tdgl_ctx *ctx, int nx, int ny, int nz, double dx, double dy,
     memset(s->mats, 0, sizeof s->mats);
     s->map.assign(s->ncell, 0);
     std::vector<float2> tw;
-    set_lengths(s, smooth_at_least(2 * nx - 1, true), default_y_length(ny), default_z_length(nz), tw);
+    set_lengths(s, default_x_length(nx), default_y_length(ny), default_z_length(nz), tw);
     int rc = TDGL_OK;
     auto al = [&](void **p, size_t b) {
         if (rc != TDGL_OK) return;
@@ -1579,7 +1608,7 @@ int tdgl_fft_pad(tdgl_sim *s, int *Mx, int *My, int *Mz) {
 int tdgl_set_fft_pad(tdgl_sim *s, int Mx, int My, int Mz) {
     if (!s) return TDGL_EINVAL;
     tdgl_ctx *ctx = s->ctx;
-    if (Mx == 0) Mx = smooth_at_least(2 * s->nx - 1, true);
+    if (Mx == 0) Mx = default_x_length(s->nx);
     if (My == 0) My = default_y_length(s->ny);
     if (Mz == 0) Mz = default_z_length(s->nz);
     if (Mx < 2 * s->nx - 1 || My < 2 * s->ny - 1 || Mz < 2 * s->nz - 1 || Mx % 2 != 0 || !is_smooth(Mx) ||
@@ -2128,7 +2157,7 @@ int build_batch_work(tdgl_batch *b, const std::vector<int> &active, Work &w) {
     for (int idx : active) {
         tdgl_sim *s = b->sims[idx];
         const bool elec = (s->terms & TDGL_TERM_ELEC) != 0;
-        const size_t gr = group_of(rgr, rsm, s->xN);
+        const size_t gr = group_of(rgr, rsm, row_group_len(s));
         for (auto it : s->it_rows_full) rgr[gr].second.push_back(make_int4(idx, it.y, it.z, it.w));
         rsm[gr] = std::max(rsm[gr], smem_rows(s, s->rows_cnt_max));
         if (elec) {
@@ -2195,7 +2224,7 @@ int batch_setup(tdgl_batch *b, const std::vector<int> &active, const double *dt)
         for (int idx : active) {
             tdgl_sim *s = b->sims[idx];
             if ((s->terms & TDGL_TERM_ELEC) && s->xstate != XS_PHAT) {
-                const size_t g = group_of(pgr, psm, s->xN);
+                const size_t g = group_of(pgr, psm, row_group_len(s));
                 for (auto it : s->it_rows_full) pgr[g].second.push_back(make_int4(idx, it.y, it.z, it.w));
                 psm[g] = std::max(psm[g], smem_rows(s, s->rows_cnt_max));
                 npro += s->it_rows_full.size();

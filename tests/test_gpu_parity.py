@@ -19,7 +19,10 @@ MATS = {1: synth.BTO, 2: dict(synth.PTO, G12=3e-11, G44=7e-11, G44p=2e-11, r_s=1
 SHAPES = [(1, 1, 1), (1, 1, 6), (5, 1, 1), (3, 5, 7), (8, 8, 4), (17, 9, 5), (32, 32, 8), (24, 12, 20),
           # the transform lengths of the uneven sweep's 48^3 and 96^3 members, one axis at a time:
           # x half-lengths 96 / 48 and y lengths 96 / 192, z lengths 96 / 192 (radix-3 register FFTs)
-          (96, 48, 8), (48, 96, 8), (8, 8, 48), (8, 8, 96)]
+          (96, 48, 8), (48, 96, 8), (8, 8, 48), (8, 8, 96),
+          # rows shorter than the x half-length in the tiled step kernel (x padded beyond 2 nx):
+          # 20 of 32, 40 and 44 of 48, 80 of 96
+          (20, 8, 6), (40, 12, 8), (44, 10, 6), (80, 8, 4)]
 
 
 @pytest.fixture(scope="module")
@@ -62,6 +65,24 @@ def test_electrostatic_field_with_forced_z_padding_matches_oracle(ctx, shape, Mz
     want = np.where(mat > 0, o.fields(P.astype(np.float64))["elec"], 0.0)
     assert rel_err(got, want) <= 2e-5
     assert rel_err(default, want) <= 2e-5
+
+
+@pytest.mark.parametrize("shape", [(40, 12, 8), (20, 16, 12)])
+def test_trajectory_with_rows_shorter_than_the_half_length(ctx, shape):
+    # the tiled step kernel on rows of nx < Mx / 2 cells (mixed materials, vacuum holes, cross
+    # terms): 24 steps, graph replays included, against the oracle trajectory
+    mat, P = mixed_case(shape, seed=sum(shape) + 7)
+    P *= 0.3
+    g = gpu_sim(ctx, shape, CELL, mat, MATS, 290.0, 40.0, E=(0.0, 1e7, 2e7), P=P)
+    Mx = g.fft_pad()[0]
+    assert shape[0] < Mx // 2
+    o = oracle_sys(shape, CELL, mat, MATS, 290.0, 40.0, E=(0.0, 1e7, 2e7))
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    g.step(8, dt)
+    g.energy()
+    g.step(16, dt)
+    want = o.run(P.astype(np.float64), dt, 24)
+    assert np.abs(g.get_P() - want).max() / g.scales()[0] <= 1e-5
 
 
 def test_electrostatic_field_of_uniform_slab(ctx):

@@ -58,7 +58,7 @@ def test_batch_members_match_oracle(ctx):
     # energy call on each member (it leaves the field spectrum for the next step), 8 more steps
     from paper_2605_28800_b300 import tdgl
     members = [((16, 16, 16), 300.0, 1.0), ((12, 20, 8), 250.0, 0.8), ((48, 48, 48), 300.0, 1.0),
-               ((96, 24, 8), 200.0, 0.5), ((9, 7, 5), 350.0, 1.2)]
+               ((96, 24, 8), 200.0, 0.5), ((9, 7, 5), 350.0, 1.2), ((40, 16, 8), 300.0, 1.0)]
     a1 = abs(coefficients(synth.BTO, 300.0)["a1x"])
     sims, starts, dts = [], [], []
     for i, (sh, T, f) in enumerate(members):
@@ -184,14 +184,16 @@ def test_forced_row_tile_steps_like_the_tuned_one():
 
 
 def test_fft_padding_defaults_and_forced_lengths(ctx):
-    # defaults: smallest 2^a 3^b >= 2n - 1 (x even); z gives way to 128 / 256 / 512 within 4/3, and
-    # y and z to the smallest specialized transform length within 4/3;
+    # defaults: smallest 2^a 3^b >= 2n - 1 (x even); z gives way to 128 / 256 / 512 within 4/3, y and z
+    # to the smallest specialized length within 4/3, and x (rows a multiple of 4 long) to twice the
+    # smallest specialized half-length >= nx within 4/3;
     # forced lengths are validated, and a sim re-padded between steps follows the same trajectory
     from paper_2605_28800_b300 import tdgl
     cases = {(96, 96, 96): (192, 192, 256), (48, 48, 48): (96, 96, 128), (17, 9, 5): (36, 18, 9),
              (32, 32, 8): (64, 64, 16), (128, 128, 128): (256, 256, 256),
              (40, 40, 81): (96, 96, 192),   # x: 81 is odd, so 96; y 81 and z 162 give way to 96 and 192
-             (80, 80, 80): (162, 192, 192), (40, 40, 40): (96, 96, 96), (3, 5, 7): (6, 9, 16)}
+             (80, 80, 80): (192, 192, 192), (40, 40, 40): (96, 96, 96), (3, 5, 7): (6, 9, 16),
+             (24, 20, 48): (64, 48, 128), (12, 20, 8): (32, 48, 16)}
     for shape, want in cases.items():
         s = tdgl.Sim(ctx, shape, (1e-9,) * 3)
         assert s.fft_pad() == want, shape
