@@ -192,10 +192,18 @@ int launch_wgrad(tdgl_ctx *ctx, const __nv_bfloat16 *dyt, const __nv_bfloat16 *x
 
 // ReLU mask of the upstream gradient (BF16 copies in both layouts) and db += its sum over voxels:
 // per-block partials into part, summed in block order
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 int launch_relu_bwd(tdgl_ctx *ctx, const float *g, const __nv_bfloat16 *out, __nv_bfloat16 *d, __nv_bfloat16 *dt,
                     float *db, float *part, long V, int C) {
-    const long nb = (V + 31) / 32;
-    TRY(launch(ctx, TDGL_K_UNET, [&] { k_relu_bwd<<<(unsigned)nb, 256, 0, ctx->stream>>>(g, out, d, dt, part, V, C); }));
+    // the vector form for 8-channel groups and aligned buffers (the network's), else 32 voxels per block
+    const bool vec = C % 8 == 0 && aligned16(g) && aligned16(d) && aligned16(dt) && (!out || aligned16(out));
+    const int vb = vec ? relu_bwd_vb(C) : 32;
+    const long nb = (V + vb - 1) / vb;      // <= (V + 31) / 32: the partial buffer's size
+    TRY(launch(ctx, TDGL_K_UNET, [&] {
+        if (vec) k_relu_bwd_v<<<(unsigned)nb, 256, relu_bwd_smem(C), ctx->stream>>>(g, out, d, dt, part, V, C, vb);
+        else k_relu_bwd<<<(unsigned)nb, 256, 0, ctx->stream>>>(g, out, d, dt, part, V, C);
+    }));
     return launch(ctx, TDGL_K_UNET, [&] { k_colsum<<<(unsigned)C, 256, 0, ctx->stream>>>(db, part, nb, C); });
 }
 
@@ -407,9 +415,14 @@ int forward(tdgl_unet *n, const float *x, int B) {
         const Layer &skip = n->L[2 * l + 1];
         const Dims &d = n->dims[l];
         TRY(launch(ctx, TDGL_K_UNET, [&] {
-            k_upcat<<<grid_n(V * (deep.Co + skip.Co)), 256, 0, ctx->stream>>>(
-                reinterpret_cast<const __nv_bfloat16 *>(deep.out), reinterpret_cast<const __nv_bfloat16 *>(skip.out),
-                n->L[li].in, V, deep.Co, skip.Co, d.Z, d.Y, d.X);
+            const auto *dpo = reinterpret_cast<const __nv_bfloat16 *>(deep.out);
+            const auto *spo = reinterpret_cast<const __nv_bfloat16 *>(skip.out);
+            if (deep.Co % 8 == 0 && skip.Co % 8 == 0 && aligned16(dpo) && aligned16(spo) && aligned16(n->L[li].in))
+                k_upcat_v<<<grid_n(V * (deep.Co + skip.Co) / 8), 256, 0, ctx->stream>>>(dpo, spo, n->L[li].in, V, deep.Co,
+                                                                                        skip.Co, d.Z, d.Y, d.X);
+            else
+                k_upcat<<<grid_n(V * (deep.Co + skip.Co)), 256, 0, ctx->stream>>>(dpo, spo, n->L[li].in, V, deep.Co, skip.Co,
+                                                                                   d.Z, d.Y, d.X);
         }));
         for (int s = 0; s < 2; ++s, ++li) {
             Layer &ly = n->L[li];

@@ -637,6 +637,93 @@ __global__ void k_relu_bwd(const float *__restrict__ g, const __nv_bfloat16 *__r
     }
 }
 
+// k_relu_bwd for C a multiple of 8 and 16-byte aligned buffers: a block takes VB voxels (a multiple
+// of 16, VB C <= 8192), reads g and out with 16- and 8-byte loads, writes d with 8-byte stores and
+// the transpose dt as 32-byte runs of 16 voxels, and leaves one per-channel partial sum of the
+// block's (BF16-rounded) gradient in dbp; same values as k_relu_bwd, partial sums over VB voxels.
+__global__ void __launch_bounds__(256) k_relu_bwd_v(const float *__restrict__ g, const __nv_bfloat16 *__restrict__ out,
+                                                    __nv_bfloat16 *__restrict__ d, __nv_bfloat16 *__restrict__ dt,
+                                                    float *__restrict__ dbp, long V, int C, int VB) {
+    extern __shared__ float rtile[];                 // [VB][C + 1]
+    const int ld = C + 1;
+    const long v0 = (long)blockIdx.x * VB;
+    const int n4 = VB * C / 4;
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+        const int e = 4 * i, r = e / C, c = e - r * C;
+        const long v = v0 + r;
+        float a[4] = {0.f, 0.f, 0.f, 0.f};
+        if (v < V) {
+            const float4 q = reinterpret_cast<const float4 *>(g + v * C + c)[0];
+            a[0] = q.x; a[1] = q.y; a[2] = q.z; a[3] = q.w;
+            if (out) {
+                alignas(8) __nv_bfloat16 o[4];
+                *reinterpret_cast<uint2 *>(o) = *reinterpret_cast<const uint2 *>(out + v * C + c);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (!(__bfloat162float(o[k]) > 0.f)) a[k] = 0.f;
+            }
+            alignas(8) __nv_bfloat16 b[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) b[k] = __float2bfloat16_rn(a[k]);
+            *reinterpret_cast<uint2 *>(d + v * C + c) = *reinterpret_cast<const uint2 *>(b);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rtile[r * ld + c + k] = __bfloat162float(__float2bfloat16_rn(a[k]));
+    }
+    __syncthreads();
+    const int ng = VB / 16;
+    for (int w = threadIdx.x; w < C * ng; w += blockDim.x) {
+        const int c = w / ng, gq = w - c * ng;
+        const long vs = v0 + 16L * gq;
+        if (vs >= V) continue;
+        alignas(16) __nv_bfloat16 val[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) val[k] = __float2bfloat16_rn(rtile[(16 * gq + k) * ld + c]);
+        __nv_bfloat16 *dst = dt + (long)c * V + vs;
+        if (vs + 16 <= V && V % 8 == 0) {
+            reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(val)[0];
+            reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(val)[1];
+        } else {
+            for (int k = 0; k < 16 && vs + k < V; ++k) dst[k] = val[k];
+        }
+    }
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float sum = 0.f;
+        for (int r = 0; r < VB; ++r) sum += rtile[r * ld + c];
+        dbp[(long)blockIdx.x * C + c] = sum;
+    }
+}
+inline int relu_bwd_vb(int C) {
+    int vb = 8192 / C;
+    vb = vb > 256 ? 256 : (vb < 16 ? 16 : vb);
+    return vb / 16 * 16;
+}
+inline size_t relu_bwd_smem(int C) { return (size_t)relu_bwd_vb(C) * (C + 1) * sizeof(float); }
+
+// k_upcat for Cd and Cs multiples of 8 and 16-byte aligned buffers: one 16-byte group of 8 channels
+// per thread and step (each group lies wholly in the deep or the skip part)
+__global__ void k_upcat_v(const __nv_bfloat16 *__restrict__ deep, const __nv_bfloat16 *__restrict__ skip,
+                          __nv_bfloat16 *__restrict__ out, long V, int Cd, int Cs, int Z, int Y, int X) {
+    const int Cdg = Cd / 8, Csg = Cs / 8, Cg = Cdg + Csg;
+    const uint4 *dp = reinterpret_cast<const uint4 *>(deep), *sp = reinterpret_cast<const uint4 *>(skip);
+    uint4 *op = reinterpret_cast<uint4 *>(out);
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V * Cg; i += (long)gridDim.x * blockDim.x) {
+        const long v = i / Cg;
+        const int gq = (int)(i - v * Cg);
+        if (gq >= Cdg) {
+            op[i] = sp[v * Csg + (gq - Cdg)];
+            continue;
+        }
+        long q = v;
+        const int x = (int)(q % X); q /= X;
+        const int y = (int)(q % Y); q /= Y;
+        const int z = (int)(q % Z);
+        const long b = q / Z;
+        const long vh = ((b * (Z / 2) + z / 2) * (Y / 2) + y / 2) * (X / 2) + x / 2;
+        op[i] = dp[vh * Cdg + gq];
+    }
+}
+
 // x [V][C] (channels last, BF16) -> xs [j][C][V] with xs[j][c][v] = x[v + j - 1][c] when the x
 // coordinate of v plus j - 1 stays in [0, X), else 0 (j = 0, 1, 2; nshift = 1 writes j = 1 only):
 // the weight gradient's input transposed to [channel][voxel], in three copies shifted along x so
