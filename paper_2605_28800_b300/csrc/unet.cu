@@ -153,13 +153,14 @@ int launch_conv(tdgl_ctx *ctx, const __nv_bfloat16 *x, const __nv_bfloat16 *w, c
     });
 }
 
-// dW[o][tap Ci + i] += sum_v xs[dx + 1][i][v + dz YX + dy X] dYt[o][v]
-// voxels per CTA of the weight gradient (about four CTAs per SM over the (tap, i) tiles) and the
-// number of voxel chunks, each leaving one partial gradient
+// dW[o][tap Ci + i] += sum_v xs[dx + 1][v + dz YX + dy X][i] dY[v][o] (both operands in 8-voxel groups)
+// voxels per CTA of the weight gradient (about four CTAs per SM over the (tap, i) tiles; a multiple
+// of the 64 voxels of a pipeline stage) and the number of voxel chunks, each leaving one partial
+// gradient
 long wgrad_vchunk(long nvox, int N) {
     const long ntile = (N + 127) / 128;
     const long v = (nvox * ntile + 591) / 592;
-    return std::min<long>(std::max<long>((v + 15) / 16 * 16, 256), 16384);
+    return std::min<long>(std::max<long>((v + 63) / 64 * 64, 256), 16384);
 }
 long wgrad_chunks(long nvox, int N) { return (nvox + wgrad_vchunk(nvox, N) - 1) / wgrad_vchunk(nvox, N); }
 // floats of the partial-gradient workspace of one convolution (weights, then biases)
@@ -172,6 +173,8 @@ size_t bias_part_floats(long nvox, int Co) { return (size_t)((nvox + 31) / 32) *
 int launch_wgrad(tdgl_ctx *ctx, const __nv_bfloat16 *dyt, const __nv_bfloat16 *xs, float *dw, float *part, long nvox,
                  Dims d, int Ci, int Co, int ntap, int ldw, int *err) {
     const int N = ntap * Ci;
+    if (nvox % 8 || d.X % 8 || Ci % 8 || Co > 128)
+        return fail(ctx, TDGL_EINVAL, "weight gradient: voxels, x extent and input channels multiples of 8, at most 128 outputs");
     const int bn = Co <= 16 ? 16 : (Co <= 32 ? 32 : (Co <= 64 ? 64 : 128));
     const long ntile = (N + 127) / 128;
     const long vchunk = wgrad_vchunk(nvox, N), nchunk = wgrad_chunks(nvox, N);
@@ -190,14 +193,14 @@ int launch_wgrad(tdgl_ctx *ctx, const __nv_bfloat16 *dyt, const __nv_bfloat16 *x
     });
 }
 
-// ReLU mask of the upstream gradient (BF16 copies in both layouts) and db += its sum over voxels:
+// ReLU mask of the upstream gradient (BF16, [voxel][C] and in 8-voxel groups) and db += its sum over voxels:
 // per-block partials into part, summed in block order
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 int launch_relu_bwd(tdgl_ctx *ctx, const float *g, const __nv_bfloat16 *out, __nv_bfloat16 *d, __nv_bfloat16 *dt,
                     float *db, float *part, long V, int C) {
     // the vector form for 8-channel groups and aligned buffers (the network's), else 32 voxels per block
-    const bool vec = C % 8 == 0 && aligned16(g) && aligned16(d) && aligned16(dt) && (!out || aligned16(out));
+    const bool vec = C % 8 == 0 && V % 8 == 0 && aligned16(g) && aligned16(d) && aligned16(dt) && (!out || aligned16(out));
     const int vb = vec ? relu_bwd_vb(C) : 32;
     const long nb = (V + vb - 1) / vb;      // <= (V + 31) / 32: the partial buffer's size
     TRY(launch(ctx, TDGL_K_UNET, [&] {

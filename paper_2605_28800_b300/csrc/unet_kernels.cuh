@@ -367,18 +367,25 @@ __global__ void __launch_bounds__(128) k_conv_brick(const __grid_constant__ Bric
     epilogue_free<BN>(tmem);
 }
 
+// Operands of the weight gradient in 8-voxel groups: for a [voxel][C] tensor, group g holds the 8
+// voxels 8g .. 8g+7 of every channel as C records of 16 bytes, [g][c][8].  X is a multiple of 8, so
+// a group lies in one x-row and a tap's shift by (dz, dy) moves whole groups; the shift by dx is
+// in the three copies of the input.
 struct WgradP {
-    const __nv_bfloat16 *dyt;   // [Co][nvox]  upstream gradient (after the ReLU mask), transposed
-    const __nv_bfloat16 *xs;    // [3][Ci][nvox]  layer input transposed, shifted by dx = -1, 0, +1
+    const __nv_bfloat16 *dyt;   // [nvox/8][Co][8]  upstream gradient (after the ReLU mask)
+    const __nv_bfloat16 *xs;    // [3][nvox/8][Ci][8]  layer input shifted by dx = -1, 0, +1
     float *part;                // [voxel chunk][Co][ldw], column tap * Ci + i: one partial sum per chunk
-    long nvox;
-    int Z, Y, X, Ci, Co, ntap, ldw, vchunk;
+    long nvox;                  // a multiple of 8
+    int Z, Y, X, Ci, Co, ntap, ldw, vchunk;   // X, Ci multiples of 8, vchunk a multiple of 16
     int *err;
 };
 
 // partial dW[o][tap, i] = sum over this CTA's voxel chunk of X[v + off(tap)][i] dY[v][o]:
-// M = 128 (tap, i) rows, N = the output channels (BN >= Co), K = voxels.  k_wsum adds the chunks'
-// partials in chunk order, so the gradient does not depend on the order the CTAs finish in.
+// M = 128 (tap, i) rows, N = the output channels (BN >= Co), K = voxels.  Each thread copies the
+// 16-byte records of its row (tap, i), one per 8-voxel group; the records of consecutive rows of a
+// tap are consecutive in memory, so a warp's copies of one group cover a few contiguous runs.
+// k_wsum adds the chunks' partials in chunk order, so the gradient does not depend on the order the
+// CTAs finish in.
 template <int BN>
 __global__ void __launch_bounds__(128) k_wgrad(WgradP p) {
     extern __shared__ uint8_t smem_raw[];
@@ -401,7 +408,9 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradP p) {
         ci = ng - tap * p.Ci;
         if (p.ntap == 27) { dz = tap / 9 - 1; dy = (tap / 3) % 3 - 1; dx = tap % 3 - 1; }
     }
-    const __nv_bfloat16 *xrow = p.xs + ((long)(dx + 1) * p.Ci + ci) * p.nvox + dz * YX + (long)dy * p.X;
+    // record of group 0 of this row's shifted input; group g's record is Ci * 8 elements further on
+    const long G = p.nvox / 8, gstride = (long)p.Ci * 8;
+    const __nv_bfloat16 *xrow = p.xs + ((long)(dx + 1) * G * p.Ci + ci) * 8 + (dz * YX + (long)dy * p.X) / 8 * gstride;
     const uint32_t tmem = prologue<BN>(bar, tslot);
     // (x, y, z) of voxel vbase + 16 nextc, the first voxel of the next sub-chunk to load: the main
     // loop loads the sub-chunks in increasing order, so the coordinates advance by 16 voxels per
@@ -435,13 +444,13 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradP p) {
             int y = yq, zz = zq;
             if (h == 1 && xq + 8 >= p.X) next_row(y, zz);
             const bool ok = rok && kv < vend && (unsigned)(zz + dz) < (unsigned)p.Z && (unsigned)(y + dy) < (unsigned)p.Y;
-            tc::cp16(a_s + tc::tile_off(tid, h), ok ? xrow + kv : p.xs, ok);
+            tc::cp16(a_s + tc::tile_off(tid, h), ok ? xrow + (kv >> 3) * gstride : p.xs, ok);
         }
         for (int i = tid; i < 2 * BN; i += 128) {   // B: row o, voxels k0 + 8h .. + 7
             const int o = i >> 1, h = i & 1;
             const long kv = k0 + 8 * h;
             const bool ok = o < p.Co && kv < vend;
-            tc::cp16(b_s + tc::tile_off(o, h), ok ? p.dyt + (long)o * p.nvox + kv : p.dyt, ok);
+            tc::cp16(b_s + tc::tile_off(o, h), ok ? p.dyt + ((kv >> 3) * p.Co + o) * 8 : p.dyt, ok);
         }
     };
     int issued;
@@ -606,7 +615,8 @@ __global__ void k_upcat_bwd(const float *__restrict__ g, float *__restrict__ gde
 }
 
 // ReLU backward and the operands of the layer's backward GEMMs:
-//   d[v][c] = g[v][c] * (out[v][c] > 0)  (out null: no ReLU)  -> BF16 [voxel][C] and [C][voxel],
+//   d[v][c] = g[v][c] * (out[v][c] > 0)  (out null: no ReLU)  -> BF16 [voxel][C] and, in 8-voxel
+//   groups for the weight gradient, dt [V/8][C][8] (V a multiple of 8),
 //   dbp[block][c] = sum over the block's 32 voxels of d[v][c] (k_colsum adds the blocks in order).
 //   Block: 32 voxels x C channels through shared memory.
 __global__ void k_relu_bwd(const float *__restrict__ g, const __nv_bfloat16 *__restrict__ out,
@@ -628,7 +638,8 @@ __global__ void k_relu_bwd(const float *__restrict__ g, const __nv_bfloat16 *__r
     __syncthreads();
     for (int i = threadIdx.x; i < 32 * C; i += blockDim.x) {
         const int c = i / 32, r = i - c * 32;
-        if (v0 + r < V) dt[(long)c * V + v0 + r] = __float2bfloat16_rn(tile[r][c]);
+        const long v = v0 + r;
+        if (v < V) dt[((v >> 3) * C + c) * 8 + (v & 7)] = __float2bfloat16_rn(tile[r][c]);
     }
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
         float s = 0.f;
@@ -639,7 +650,7 @@ __global__ void k_relu_bwd(const float *__restrict__ g, const __nv_bfloat16 *__r
 
 // k_relu_bwd for C a multiple of 8 and 16-byte aligned buffers: a block takes VB voxels (a multiple
 // of 16, VB C <= 8192), reads g and out with 16- and 8-byte loads, writes d with 8-byte stores and
-// the transpose dt as 32-byte runs of 16 voxels, and leaves one per-channel partial sum of the
+// dt as pairs of 16-byte channel records of 8 voxels, and leaves one per-channel partial sum of the
 // block's (BF16-rounded) gradient in dbp; same values as k_relu_bwd, partial sums over VB voxels.
 __global__ void __launch_bounds__(256) k_relu_bwd_v(const float *__restrict__ g, const __nv_bfloat16 *__restrict__ out,
                                                     __nv_bfloat16 *__restrict__ d, __nv_bfloat16 *__restrict__ dt,
@@ -673,19 +684,15 @@ __global__ void __launch_bounds__(256) k_relu_bwd_v(const float *__restrict__ g,
     __syncthreads();
     const int ng = VB / 16;
     for (int w = threadIdx.x; w < C * ng; w += blockDim.x) {
-        const int c = w / ng, gq = w - c * ng;
+        const int c = w % C, gq = w / C;                 // consecutive threads: consecutive records
         const long vs = v0 + 16L * gq;
         if (vs >= V) continue;
         alignas(16) __nv_bfloat16 val[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) val[k] = __float2bfloat16_rn(rtile[(16 * gq + k) * ld + c]);
-        __nv_bfloat16 *dst = dt + (long)c * V + vs;
-        if (vs + 16 <= V && V % 8 == 0) {
-            reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(val)[0];
-            reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(val)[1];
-        } else {
-            for (int k = 0; k < 16 && vs + k < V; ++k) dst[k] = val[k];
-        }
+        uint4 *dst = reinterpret_cast<uint4 *>(dt + ((vs >> 3) * C + c) * 8);
+        dst[0] = reinterpret_cast<const uint4 *>(val)[0];
+        if (vs + 16 <= V) dst[C] = reinterpret_cast<const uint4 *>(val)[1];
     }
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
         float sum = 0.f;
@@ -724,13 +731,14 @@ __global__ void k_upcat_v(const __nv_bfloat16 *__restrict__ deep, const __nv_bfl
     }
 }
 
-// x [V][C] (channels last, BF16) -> xs [j][C][V] with xs[j][c][v] = x[v + j - 1][c] when the x
-// coordinate of v plus j - 1 stays in [0, X), else 0 (j = 0, 1, 2; nshift = 1 writes j = 1 only):
-// the weight gradient's input transposed to [channel][voxel], in three copies shifted along x so
-// that every 8-voxel run it loads starts on 16 bytes.  A block takes VB voxels (a multiple of 16,
-// (VB + 2) C elements of shared memory): the input around them is one contiguous range, copied with
-// 16-byte loads; each thread then assembles 16 consecutive voxels of one (j, c) row and writes them
-// with two 16-byte stores.  C and X are multiples of 8 (the network's shapes).
+// x [V][C] (channels last, BF16) -> xs [j][V/8][C][8] with xs[j][g][c][k] = x[8g + k + j - 1][c]
+// when the x coordinate of voxel 8g + k plus j - 1 stays in [0, X), else 0 (j = 0, 1, 2; nshift = 1
+// writes j = 1 only): the weight gradient's input in 8-voxel groups (k_wgrad), in three copies
+// shifted along x so that a tap's shift along x needs no realignment.  A block takes VB voxels (a
+// multiple of 16, (VB + 2) C elements of shared memory): the input around them is one contiguous
+// range, copied with 16-byte loads; each thread then assembles 16 consecutive voxels of one (j, c)
+// row and writes them as two 16-byte channel records.  C, X and V are multiples of 8 (the
+// network's shapes).
 __global__ void __launch_bounds__(256) k_xshift(const __nv_bfloat16 *__restrict__ x, __nv_bfloat16 *__restrict__ xs,
                                                 long V, int C, int X, int nshift, int VB) {
     extern __shared__ uint4 xsm[];
@@ -759,13 +767,10 @@ __global__ void __launch_bounds__(256) k_xshift(const __nv_bfloat16 *__restrict_
             val[k] = in ? tile[(16 * g + k + j) * C + c] : __float2bfloat16_rn(0.f);
             if (++xv == X) xv = 0;
         }
-        __nv_bfloat16 *dst = xs + ((long)j * C + c) * V + vs;
-        if (vs + 16 <= V && V % 8 == 0) {                   // 16-byte aligned: V, vs multiples of 8
-            reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(val)[0];
-            reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(val)[1];
-        } else {
-            for (int k = 0; k < 16 && vs + k < V; ++k) dst[k] = val[k];
-        }
+        // groups vs / 8 and vs / 8 + 1 (the second one only inside the tensor: V is a multiple of 8)
+        uint4 *dst = reinterpret_cast<uint4 *>(xs + (((long)j * (V / 8) + vs / 8) * C + c) * 8);
+        dst[0] = reinterpret_cast<const uint4 *>(val)[0];
+        if (vs + 16 <= V) dst[C] = reinterpret_cast<const uint4 *>(val)[1];
     }
 }
 // voxels per block of k_xshift for C channels, and its shared memory
