@@ -134,6 +134,41 @@ struct ConvP {
     float *part;              // [ksplit][nvox][Co] FP32 partial sums (ksplit > 1), added by k_splitk_sum
 };
 
+// Epilogue of one output voxel v and 16 channels co0 .. co0 + 15 (the accumulator row r): bias,
+// activation, store.  With whole 8-channel groups (Co a multiple of 8, co0 + 16 <= Co, y on 16 bytes)
+// the row goes out as 16-byte vector stores (two for BF16, four for FP32), else channel by channel.
+__device__ __forceinline__ void store_row16(const ConvP &p, long v, int co0, const float (&r)[16]) {
+    float a[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int co = co0 + j < p.Co ? co0 + j : p.Co - 1;
+        a[j] = r[j] + (p.bias ? p.bias[co] : 0.f);
+        if (p.relu) a[j] = fmaxf(a[j], 0.f);
+    }
+    if (p.Co % 8 == 0 && co0 + 16 <= p.Co && (reinterpret_cast<uintptr_t>(p.y) & 15u) == 0) {
+        if (p.f32out) {
+            float4 *dst = reinterpret_cast<float4 *>(reinterpret_cast<float *>(p.y) + v * p.Co + co0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_float4(a[4 * q], a[4 * q + 1], a[4 * q + 2], a[4 * q + 3]);
+        } else {
+            alignas(16) __nv_bfloat16 b[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) b[j] = __float2bfloat16_rn(a[j]);
+            uint4 *dst = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(p.y) + v * p.Co + co0);
+            dst[0] = reinterpret_cast<const uint4 *>(b)[0];
+            dst[1] = reinterpret_cast<const uint4 *>(b)[1];
+        }
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int co = co0 + j;
+        if (co >= p.Co) break;
+        if (p.f32out) reinterpret_cast<float *>(p.y)[v * p.Co + co] = a[j];
+        else reinterpret_cast<__nv_bfloat16 *>(p.y)[v * p.Co + co] = __float2bfloat16_rn(a[j]);
+    }
+}
+
 // Y = act(bias + conv(X, W)) for a 3x3x3 (ntap 27) or 1x1x1 (ntap 1) kernel, zero padding.  With
 // p.ksplit > 1 CTA (x, y, z) sums only the z-th of ksplit equal ranges of K sub-chunks and stores
 // that partial sum; k_splitk_sum adds the partials in split order and applies bias and activation
@@ -198,15 +233,7 @@ __global__ void __launch_bounds__(128) k_conv(ConvP p) {
                     if (n0 + c0 + j < p.Co) dst[n0 + c0 + j] = r[j];
                 continue;
             }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int co = n0 + c0 + j;
-                if (co >= p.Co) break;
-                float a = r[j] + (p.bias ? p.bias[co] : 0.f);
-                if (p.relu) a = fmaxf(a, 0.f);
-                if (p.f32out) reinterpret_cast<float *>(p.y)[v * p.Co + co] = a;
-                else reinterpret_cast<__nv_bfloat16 *>(p.y)[v * p.Co + co] = __float2bfloat16_rn(a);
-            }
+            store_row16(p, v, n0 + c0, r);
         }
     }
     epilogue_free<BN>(tmem);
@@ -353,15 +380,7 @@ __global__ void __launch_bounds__(128) k_conv_brick(const __grid_constant__ Bric
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float r[16];
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int co = n0 + c0 + j;
-                if (co >= p.Co) break;
-                float a = r[j] + (p.bias ? p.bias[co] : 0.f);
-                if (p.relu) a = fmaxf(a, 0.f);
-                if (p.f32out) reinterpret_cast<float *>(p.y)[v * p.Co + co] = a;
-                else reinterpret_cast<__nv_bfloat16 *>(p.y)[v * p.Co + co] = __float2bfloat16_rn(a);
-            }
+            store_row16(p, v, n0 + c0, r);
         }
     }
     epilogue_free<BN>(tmem);

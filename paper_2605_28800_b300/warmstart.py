@@ -85,7 +85,8 @@ def relax_points(ctx, cfg, points, starts, max_steps, chunk=64, sequential=False
 
 def train(net, X, Y, epochs, batch, lr, seed=0, log=None):
     """Adam on (X, Y) pairs (lists of (4, ...) inputs and (3, ...) targets scaled by P_SCALE),
-    shuffled each epoch with a seeded generator; lr decays by a quarter over the run (cosine).
+    shuffled each epoch with a seeded generator; lr follows a cosine from lr down to lr / 20 over the
+    run, so the last epochs average out the minibatch noise instead of ending on one of its swings.
     The pairs are moved to device memory once and batches are gathered there."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -104,7 +105,7 @@ def train(net, X, Y, epochs, batch, lr, seed=0, log=None):
             xb = Xd.index_select(0, idx).contiguous()
             yb = Yd.index_select(0, idx).contiguous()
             torch.cuda.current_stream().synchronize()     # the library runs on its own stream
-            lr_k = lr * (0.75 + 0.25 * np.cos(np.pi * k / max(steps_total, 1)))
+            lr_k = lr * (0.05 + 0.475 * (1.0 + np.cos(np.pi * k / max(steps_total, 1))))
             run.append(net.train_step(xb, yb, lr_k))
             k += 1
         losses.append(float(np.mean(run)))
@@ -114,12 +115,18 @@ def train(net, X, Y, epochs, batch, lr, seed=0, log=None):
     return losses
 
 
+P_CLIP = 1.25   # largest proposed |P_i| in units of P_SCALE
+
+
 def propose(net, shape, points, batch):
-    """Warm starts (3, nz, ny, nx) float32 in C/m^2 for the points."""
+    """Warm starts (3, nz, ny, nx) float32 in C/m^2 for the points.  Each component is clipped to
+    +-P_CLIP P_SCALE: the relaxed textures of these bilayers stay below it, so a useful proposal is
+    unchanged, while an untrained or badly trained network's outliers (the explicit step is unstable
+    from polarizations far above saturation) cannot make the judging relaxation diverge."""
     out = []
     for i in range(0, len(points), batch):
         xb = np.stack([features(shape, p) for p in points[i:i + batch]])
-        y = net.forward(xb)
+        y = np.clip(net.forward(xb), -P_CLIP, P_CLIP)
         out.extend([(P_SCALE * y[j]).astype(np.float32) for j in range(y.shape[0])])
     return out
 
@@ -204,6 +211,7 @@ def run(ctx, cfg, points, random_start, n_train, n_test, epochs, max_steps, batc
         gen_seconds=t_gen, train_seconds=t_train, infer_seconds=t_inf,
         train_loss_first=losses[0], train_loss_last=losses[-1], train_losses=losses,
         train_steps_median=float(np.median(st_tr)), train_converged=float(np.mean(cv_tr)),
+        relaxed_P_abs_max=float(max(float(np.abs(P).max()) for P in P_tr)), proposal_clip=P_CLIP * P_SCALE,
         plain_steps=st_plain.tolist(), warm_steps=st_warm.tolist(),
         plain_steps_total=int(st_plain.sum()), warm_steps_total=int(st_warm.sum()),
         steps_saved_fraction=float(1.0 - st_warm.sum() / max(st_plain.sum(), 1)),
