@@ -230,9 +230,10 @@ int tdgl_get_P(tdgl_sim *sim, float *out, int where);
  *    memory, same layout) on the context's download stream.
  *  - tdgl_sync waits until every call above on this sim has completed, then reports the status of
  *    the steps queued since the last check: TDGL_EDIVERGED or TDGL_ETIMEOUT as tdgl_step would.
- * Each upload and download goes through a staging buffer of its own (allocated on first use, 2 x
- * 12 bytes per cell), so consecutive set / step / get calls overlap: the next input's upload and
- * the last result's download run while the current steps compute.  Host buffers must be
+ * Uploads and downloads go through device staging buffers, two per direction used in turn
+ * (allocated on first use, 4 x 12 bytes per cell), so consecutive set / step / get calls overlap:
+ * the next input's upload and the last result's download run while the current steps compute, and
+ * the copies of one direction follow each other back to back.  Host buffers must be
  * page-locked for the copies to overlap (pageable memory works, with the copies staged by the
  * driver); a buffer passed to tdgl_set_P_async must not change, and one passed to tdgl_get_P_async
  * must not be read, until tdgl_sync returns.  Not for use inside a stream capture. */

@@ -103,11 +103,12 @@ struct tdgl_sim {
     RelaxState *drelax = nullptr;         // their loop state
     double last_maxdp = 0.0;
     tdgl_batch *batch = nullptr;
-    // asynchronous host I/O: staging buffers of uploads and downloads and the events that order
-    // them (input landed, input consumed, output staged, output read out); status of steps that
-    // tdgl_step_async enqueued and nobody has read yet
-    float *din_a = nullptr, *dout_a = nullptr;
-    cudaEvent_t ev_in_ready = nullptr, ev_in_free = nullptr, ev_out_ready = nullptr, ev_out_free = nullptr;
+    // asynchronous host I/O: two staging buffers per direction, used in turn, and the events that
+    // order each (input landed, input consumed, output staged, output read out); status of steps
+    // that tdgl_step_async enqueued and nobody has read yet
+    float *din_a[2] = {nullptr, nullptr}, *dout_a[2] = {nullptr, nullptr};
+    cudaEvent_t ev_in_ready[2] = {}, ev_in_free[2] = {}, ev_out_ready[2] = {}, ev_out_free[2] = {};
+    int in_next = 0, out_next = 0;
     bool status_pending = false;
 };
 
@@ -1444,11 +1445,13 @@ void tdgl_sim_destroy(tdgl_sim *s) {
     if (!s) return;
     ctx_set(s->ctx);
     cudaStreamSynchronize(s->ctx->stream);
-    if (s->ev_out_free) cudaEventSynchronize(s->ev_out_free);   // a download still reading dout_a
-    for (cudaEvent_t e : {s->ev_in_ready, s->ev_in_free, s->ev_out_ready, s->ev_out_free})
-        if (e) cudaEventDestroy(e);
-    cudaFree(s->din_a);
-    cudaFree(s->dout_a);
+    for (int i = 0; i < 2; ++i) {
+        if (s->ev_out_free[i]) cudaEventSynchronize(s->ev_out_free[i]);   // a download still reading dout_a
+        for (cudaEvent_t e : {s->ev_in_ready[i], s->ev_in_free[i], s->ev_out_ready[i], s->ev_out_free[i]})
+            if (e) cudaEventDestroy(e);
+        cudaFree(s->din_a[i]);
+        cudaFree(s->dout_a[i]);
+    }
     auto &v = s->ctx->sims;
     v.erase(std::remove(v.begin(), v.end(), s), v.end());
     if (s->batch) {   // leave the batch rather than dangle in it
@@ -1756,12 +1759,16 @@ int tdgl_get_P(tdgl_sim *s, float *out, int where) {
 // the scale kernels and the steps run on the context's stream.  Events order each staging buffer's
 // writer after its previous reader, so consecutive upload / step / download calls overlap: the
 // upload of the next input and the download of the previous result run during the current steps.
+// Each direction alternates between two staging buffers, so an upload need not wait for the scale
+// kernel of the one before it (nor a scale kernel for the download before it): the copies of one
+// direction follow each other back to back.
 int io_setup(tdgl_sim *s) {
     tdgl_ctx *ctx = s->ctx;
     if (!ctx->up) CK(ctx, cudaStreamCreateWithFlags(&ctx->up, cudaStreamNonBlocking));
     if (!ctx->down) CK(ctx, cudaStreamCreateWithFlags(&ctx->down, cudaStreamNonBlocking));
-    for (cudaEvent_t *e : {&s->ev_in_ready, &s->ev_in_free, &s->ev_out_ready, &s->ev_out_free})
-        if (!*e) CK(ctx, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    for (int i = 0; i < 2; ++i)
+        for (cudaEvent_t *e : {&s->ev_in_ready[i], &s->ev_in_free[i], &s->ev_out_ready[i], &s->ev_out_free[i]})
+            if (!*e) CK(ctx, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     return TDGL_OK;
 }
 
@@ -1772,18 +1779,20 @@ int tdgl_set_P_async(tdgl_sim *s, const float *P) {
     if (lowest_material(s)) fix_scales(s);
     TRY(io_setup(s));
     const size_t bytes = 3ull * s->ncell * sizeof(float);
-    if (!s->din_a) CK(ctx, cudaMalloc(&s->din_a, bytes));
-    // din_a is free once the previous upload's scale kernel has read it (an event never recorded
-    // counts as complete)
-    CK(ctx, cudaStreamWaitEvent(ctx->up, s->ev_in_free, 0));
-    CK(ctx, cudaMemcpyAsync(s->din_a, P, bytes, cudaMemcpyHostToDevice, ctx->up));
-    CK(ctx, cudaEventRecord(s->ev_in_ready, ctx->up));
-    CK(ctx, cudaStreamWaitEvent(ctx->stream, s->ev_in_ready, 0));
+    const int i = s->in_next;
+    if (!s->din_a[i]) CK(ctx, cudaMalloc(&s->din_a[i], bytes));
+    s->in_next ^= 1;
+    // din_a[i] is free once the scale kernel of the upload before last (the one that used it) has
+    // read it (an event never recorded counts as complete)
+    CK(ctx, cudaStreamWaitEvent(ctx->up, s->ev_in_free[i], 0));
+    CK(ctx, cudaMemcpyAsync(s->din_a[i], P, bytes, cudaMemcpyHostToDevice, ctx->up));
+    CK(ctx, cudaEventRecord(s->ev_in_ready[i], ctx->up));
+    CK(ctx, cudaStreamWaitEvent(ctx->stream, s->ev_in_ready[i], 0));
     const float f = (float)(1.0 / s->P0);
     TRY(launch(ctx, TDGL_K_OTHER, [&] {
-        k_scale_in<<<grid_for(3 * s->ncell), 256, 0, ctx->stream>>>(s->dP[s->cur], s->din_a, s->dmat, s->ncell, f);
+        k_scale_in<<<grid_for(3 * s->ncell), 256, 0, ctx->stream>>>(s->dP[s->cur], s->din_a[i], s->dmat, s->ncell, f);
     }));
-    CK(ctx, cudaEventRecord(s->ev_in_free, ctx->stream));
+    CK(ctx, cudaEventRecord(s->ev_in_free[i], ctx->stream));
     s->ab_hist = 0;
     s->xstate = XS_NONE;
     return TDGL_OK;
@@ -1796,17 +1805,19 @@ int tdgl_get_P_async(tdgl_sim *s, float *out) {
     if (lowest_material(s)) fix_scales(s);
     TRY(io_setup(s));
     const size_t bytes = 3ull * s->ncell * sizeof(float);
-    if (!s->dout_a) CK(ctx, cudaMalloc(&s->dout_a, bytes));
-    // dout_a is free once the previous download has read it
-    CK(ctx, cudaStreamWaitEvent(ctx->stream, s->ev_out_free, 0));
+    const int i = s->out_next;
+    if (!s->dout_a[i]) CK(ctx, cudaMalloc(&s->dout_a[i], bytes));
+    s->out_next ^= 1;
+    // dout_a[i] is free once the download before last (the one that used it) has read it
+    CK(ctx, cudaStreamWaitEvent(ctx->stream, s->ev_out_free[i], 0));
     const float f = (float)s->P0;
     TRY(launch(ctx, TDGL_K_OTHER, [&] {
-        k_scale_out<<<grid_for(3 * s->ncell), 256, 0, ctx->stream>>>(s->dout_a, s->dP[s->cur], 3 * s->ncell, f);
+        k_scale_out<<<grid_for(3 * s->ncell), 256, 0, ctx->stream>>>(s->dout_a[i], s->dP[s->cur], 3 * s->ncell, f);
     }));
-    CK(ctx, cudaEventRecord(s->ev_out_ready, ctx->stream));
-    CK(ctx, cudaStreamWaitEvent(ctx->down, s->ev_out_ready, 0));
-    CK(ctx, cudaMemcpyAsync(out, s->dout_a, bytes, cudaMemcpyDeviceToHost, ctx->down));
-    CK(ctx, cudaEventRecord(s->ev_out_free, ctx->down));
+    CK(ctx, cudaEventRecord(s->ev_out_ready[i], ctx->stream));
+    CK(ctx, cudaStreamWaitEvent(ctx->down, s->ev_out_ready[i], 0));
+    CK(ctx, cudaMemcpyAsync(out, s->dout_a[i], bytes, cudaMemcpyDeviceToHost, ctx->down));
+    CK(ctx, cudaEventRecord(s->ev_out_free[i], ctx->down));
     return TDGL_OK;
 }
 
@@ -1829,7 +1840,8 @@ int tdgl_sync(tdgl_sim *s) {
     // the context's stream holds every upload's scale kernel (after its copy) and every step;
     // the last download's event covers the downloads
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    if (s->ev_out_free) CK(ctx, cudaEventSynchronize(s->ev_out_free));
+    for (int i = 0; i < 2; ++i)
+        if (s->ev_out_free[i]) CK(ctx, cudaEventSynchronize(s->ev_out_free[i]));
     if (!s->status_pending) return TDGL_OK;
     s->status_pending = false;
     double m;
