@@ -281,6 +281,17 @@ int  tdgl_batch_step(tdgl_batch *b, int n, const double *dt);
  * Returns TDGL_OK when all converged, else TDGL_ENOTCONVERGED / TDGL_EDIVERGED. */
 int  tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_steps,
                       int check_every, long *steps_taken);
+/* tdgl_batch_relax that also reports how each sim ended, in state[i] (may be NULL): converged,
+ * still above the tolerance after max_steps, diverged, or a bounded device wait timed out.  With
+ * it a caller can run a long relaxation in slices of max_steps (a multiple of check_every keeps
+ * the check steps of one uninterrupted call) and refill the slots of finished sims between slices:
+ * a sim that converges exactly at a slice's last check is told apart from one that did not. */
+#define TDGL_RELAX_CONVERGED 0
+#define TDGL_RELAX_AT_CAP 1
+#define TDGL_RELAX_DIVERGED 2
+#define TDGL_RELAX_TIMEOUT 3
+int  tdgl_batch_relax_state(tdgl_batch *b, const double *dt, double tol, long max_steps,
+                            int check_every, long *steps_taken, int *state);
 
 /* ---- field without allocation ------------------------------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that cannot call cudaMalloc:

@@ -2489,6 +2489,11 @@ int batch_relax_on_device(tdgl_batch *b, const std::vector<int> &active, const d
 
 int tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_steps, int check_every,
                      long *steps_taken) {
+    return tdgl_batch_relax_state(b, dt, tol, max_steps, check_every, steps_taken, nullptr);
+}
+
+int tdgl_batch_relax_state(tdgl_batch *b, const double *dt, double tol, long max_steps, int check_every,
+                           long *steps_taken, int *state) {
     if (!b || !dt || !(tol > 0) || max_steps < 0 || check_every < 1) return TDGL_EINVAL;
     tdgl_ctx *ctx = b->ctx;
     ctx_set(ctx);
@@ -2497,6 +2502,7 @@ int tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_steps
     TRY(batch_check_integrator(b));
     std::vector<int> active;
     std::vector<long> taken(n, 0);
+    std::vector<int> st(n, TDGL_RELAX_CONVERGED);
     for (int i = 0; i < n; ++i) {
         if (!(dt[i] > 0) || !std::isfinite(dt[i])) return fail(ctx, TDGL_EINVAL, "dt[%d]", i);
         TRY(prepare(b->sims[i], b->sims[i]->terms));
@@ -2519,8 +2525,14 @@ int tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_steps
                     continue;
                 }
                 taken[idx] = done + steps[idx];
-                if (status[idx] == 2) rc = fail(ctx, TDGL_EDIVERGED, "sim %d diverged", idx);
-                if (status[idx] == 3) rc = fail(ctx, TDGL_ETIMEOUT, "sim %d: a bounded wait timed out", idx);
+                if (status[idx] == 2) {
+                    st[idx] = TDGL_RELAX_DIVERGED;
+                    rc = fail(ctx, TDGL_EDIVERGED, "sim %d diverged", idx);
+                }
+                if (status[idx] == 3) {
+                    st[idx] = TDGL_RELAX_TIMEOUT;
+                    rc = fail(ctx, TDGL_ETIMEOUT, "sim %d: a bounded wait timed out", idx);
+                }
             }
             done += ran;
             active.swap(keep);
@@ -2537,6 +2549,7 @@ int tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_steps
             TRY(read_status(b->sims[idx], &m, &f));
             taken[idx] = done;
             if (f) {
+                st[idx] = (f & 2) ? TDGL_RELAX_TIMEOUT : TDGL_RELAX_DIVERGED;
                 rc = (f & 2) ? fail(ctx, TDGL_ETIMEOUT, "sim %d: a bounded wait timed out", idx)
                              : fail(ctx, TDGL_EDIVERGED, "sim %d diverged", idx);
                 continue;
@@ -2545,8 +2558,11 @@ int tdgl_batch_relax(tdgl_batch *b, const double *dt, double tol, long max_steps
         }
         active.swap(keep);
     }
+    for (int idx : active) st[idx] = TDGL_RELAX_AT_CAP;
     if (steps_taken)
         for (int i = 0; i < n; ++i) steps_taken[i] = taken[i];
+    if (state)
+        for (int i = 0; i < n; ++i) state[i] = st[i];
     if (rc != TDGL_OK) return rc;
     if (!active.empty()) return fail(ctx, TDGL_ENOTCONVERGED, "%zu sims not converged after %ld steps", active.size(), done);
     return TDGL_OK;

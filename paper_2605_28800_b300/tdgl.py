@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtdgl.so")
 
 OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ENOTCONVERGED, ESTATE, ETOOBIG, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7, -8
+RELAX_CONVERGED, RELAX_AT_CAP, RELAX_DIVERGED, RELAX_TIMEOUT = 0, 1, 2, 3   # tdgl_batch_relax_state
 HOST, DEVICE = 0, 1
 TERM_LANDAU, TERM_GRAD, TERM_ELEC, TERM_EXT, TERM_ALL = 1, 2, 4, 8, 15
 K_STEP, K_YFWD, K_ZCONV, K_YINV, K_XFWD, K_OTHER, K_UNET = range(7)
@@ -96,6 +97,7 @@ _SIGS = {
     "tdgl_batch_destroy": (None, [_VP]),
     "tdgl_batch_step": (_I, [_VP, _I, ctypes.POINTER(_D)]),
     "tdgl_batch_relax": (_I, [_VP, ctypes.POINTER(_D), _D, _L, _I, ctypes.POINTER(_L)]),
+    "tdgl_batch_relax_state": (_I, [_VP, ctypes.POINTER(_D), _D, _L, _I, ctypes.POINTER(_L), ctypes.POINTER(_I)]),
     "tdgl_elec_field_static": (_I, [_I, _I, _I, _D, _D, _D, _D, _VP, _VP, _VP, _VP]),
     "tdgl_unet_create": (_I, [_VP, _I, _I, _I, _VP, _I, _I, _I, _I, ctypes.c_uint64, ctypes.POINTER(_VP)]),
     "tdgl_unet_destroy": (None, [_VP]),
@@ -420,6 +422,18 @@ class Batch:
         if not (rc == ENOTCONVERGED and not raise_on_cap):
             self.ctx.check(rc)
         return [int(v) for v in steps], rc == OK
+
+    def relax_state(self, dt, tol, max_steps, check_every=16):
+        """relax that reports how each sim ended: (steps taken, states), a state per sim one of
+        RELAX_CONVERGED, RELAX_AT_CAP, RELAX_DIVERGED, RELAX_TIMEOUT.  Raises only for errors that
+        are not a sim's own outcome."""
+        steps = (_L * len(self.sims))()
+        state = (_I * len(self.sims))()
+        rc = self.lib.tdgl_batch_relax_state(self.h, self._dts(dt), float(tol), int(max_steps), int(check_every),
+                                             steps, state)
+        if rc not in (OK, ENOTCONVERGED, EDIVERGED, ETIMEOUT):
+            self.ctx.check(rc)
+        return [int(v) for v in steps], [int(v) for v in state]
 
     def close(self):
         if getattr(self, "h", None):

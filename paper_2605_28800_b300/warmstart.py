@@ -59,27 +59,56 @@ def make_sim(ctx, shape, cell, point, eps_b, P):
     return s
 
 
-def relax_points(ctx, cfg, points, starts, max_steps, chunk=64, sequential=False):
-    """Relax every point from its start: `chunk` sims per batch, or (sequential) each sim alone
-    on the single-simulation path.  Returns the final textures (3, nz, ny, nx) float32, the steps
-    taken, whether each converged, and the total energies."""
+def relax_points(ctx, cfg, points, starts, max_steps, chunk=64, sequential=False, slice_steps=1024):
+    """Relax every point from its start.  Returns the final textures (3, nz, ny, nx) float32, the
+    steps taken, whether each converged, and the total energies.
+
+    Batched: at most `chunk` sims at a time, relaxed in slices of `slice_steps` steps (a multiple of
+    the 16-step check interval, so each sim is checked on the same steps as in one uninterrupted
+    relaxation and stops at the same step).  Between slices the sims that finished (converged, or
+    at max_steps) leave and the next points take their slots, so the batch stays full instead of
+    waiting for its slowest member.  Sequential: each sim alone on the single-simulation path."""
     shape, cell = cfg["shape"], cfg["cell"]
-    P_out, steps, conv, F = [], [], [], []
-    for i in range(0, len(points), chunk):
-        sims = [make_sim(ctx, shape, cell, p, cfg["eps_b"], P) for p, P in zip(points[i:i + chunk], starts[i:i + chunk])]
-        dts = [cfg["dt_star"] / s.scales()[1] for s in sims]
-        if sequential:
-            n = [s.relax(dt, cfg["tol"], max_steps, raise_on_cap=False)[0] for s, dt in zip(sims, dts)]
-        else:
-            b = tdgl.Batch(ctx, sims)
-            n, _ = b.relax(dts, cfg["tol"], max_steps, raise_on_cap=False)
-            b.close()
-        for s, k in zip(sims, n):
-            P_out.append(s.get_P())
-            steps.append(int(k))
-            conv.append(int(k) < max_steps)
-            F.append(s.energy()["total"])
-            s.close()
+    n = len(points)
+    P_out, steps, conv, F = [None] * n, [0] * n, [False] * n, [None] * n
+
+    def finish(i, s, converged):
+        P_out[i] = s.get_P()
+        conv[i] = bool(converged)
+        F[i] = s.energy()["total"]
+        s.close()
+
+    if sequential:
+        for i0 in range(0, n, chunk):
+            sims = [make_sim(ctx, shape, cell, p, cfg["eps_b"], P) for p, P in zip(points[i0:i0 + chunk], starts[i0:i0 + chunk])]
+            for j, s in enumerate(sims):
+                k = s.relax(cfg["dt_star"] / s.scales()[1], cfg["tol"], max_steps, raise_on_cap=False)[0]
+                steps[i0 + j] = int(k)
+                finish(i0 + j, s, int(k) < max_steps)
+        return P_out, steps, conv, F
+    if slice_steps % 16:
+        raise ValueError("slice_steps must be a multiple of the 16-step check interval")
+    queue, active = list(range(n)), []
+    while queue or active:
+        while queue and len(active) < chunk:
+            i = queue.pop(0)
+            s = make_sim(ctx, shape, cell, points[i], cfg["eps_b"], starts[i])
+            active.append((i, s, cfg["dt_star"] / s.scales()[1]))
+        k = min(slice_steps, min(max_steps - steps[i] for i, _, _ in active))
+        b = tdgl.Batch(ctx, [s for _, s, _ in active])
+        ran, state = b.relax_state([dt for _, _, dt in active], cfg["tol"], k)
+        b.close()
+        keep = []
+        for (i, s, dt), r, st in zip(active, ran, state):
+            steps[i] += r
+            if st in (tdgl.RELAX_DIVERGED, tdgl.RELAX_TIMEOUT):
+                raise tdgl.TdglError(tdgl.EDIVERGED if st == tdgl.RELAX_DIVERGED else tdgl.ETIMEOUT,
+                                     f"point {i} did not relax")
+            if st == tdgl.RELAX_CONVERGED or steps[i] >= max_steps:
+                finish(i, s, st == tdgl.RELAX_CONVERGED)
+            else:
+                keep.append((i, s, dt))
+        active = keep
     return P_out, steps, conv, F
 
 
