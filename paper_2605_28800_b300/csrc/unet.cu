@@ -61,16 +61,16 @@ int conv_bn(int co) {
     return 16;
 }
 
-// activations [B][Z][Y][X][C] BF16 as (C, X, Y, Z, B), box (8, 10, 18, 3, 1): one 8-channel plane of
-// a brick with its halo; out-of-range voxels read as zero
-bool act_map(CUtensorMap *m, const void *x, int C, Dims d, long B) {
+// activations [B][Z][Y][X][C] BF16 as (C, X, Y, Z, B), box (8, 10, 18, zt + 2, 1): one 8-channel
+// plane of a brick with its halo for zt output planes; out-of-range voxels read as zero
+bool act_map(CUtensorMap *m, const void *x, int C, Dims d, long B, int zt) {
     auto enc = tmap_encode();
     if (!enc) return false;
     const cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)d.X, (cuuint64_t)d.Y, (cuuint64_t)d.Z, (cuuint64_t)B};
     const cuuint64_t e = 2;
     const cuuint64_t strides[4] = {C * e, (cuuint64_t)d.X * C * e, (cuuint64_t)d.Y * d.X * C * e,
                                    (cuuint64_t)d.Z * d.Y * d.X * C * e};
-    const cuuint32_t box[5] = {8, (cuuint32_t)kBX, (cuuint32_t)kBY, (cuuint32_t)kBZ, 1};
+    const cuuint32_t box[5] = {8, (cuuint32_t)kBX, (cuuint32_t)kBY, (cuuint32_t)(zt + 2), 1};
     const cuuint32_t es[5] = {1, 1, 1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(x), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -101,17 +101,23 @@ int launch_conv(tdgl_ctx *ctx, const __nv_bfloat16 *x, const __nv_bfloat16 *w, c
         BrickP bp;
         memset(&bp, 0, sizeof bp);
         bp.c = p;
-        if (!act_map(&bp.tx, x, Ci, d, nvox / d.vps()) || !wgt_map(&bp.tw, wb, Ci, Co, bn))
-            return fail(ctx, TDGL_ECUDA, "cannot encode the tensor maps of a convolution");
         const bool one = Ci == 16;
-        const dim3 grid((unsigned)(nvox / 128), (unsigned)((Co + bn - 1) / bn));
+        // CTAs of 8 x 16 voxels in zt z planes: two planes while that still gives at least one CTA
+        // per SM (they share one brick and one weight load), else one
+        const long B = nvox / d.vps(), ntile = (Co + bn - 1) / bn;
+        const int zt = (long)(d.X / 8) * (d.Y / 16) * ((d.Z + 1) / 2) * B * ntile >= ctx->nsm ? 2 : 1;
+        if (!act_map(&bp.tx, x, Ci, d, B, zt) || !wgt_map(&bp.tw, wb, Ci, Co, bn))
+            return fail(ctx, TDGL_ECUDA, "cannot encode the tensor maps of a convolution");
+        const dim3 grid((unsigned)((long)(d.X / 8) * (d.Y / 16) * ((d.Z + zt - 1) / zt) * B), (unsigned)ntile);
         return launch(ctx, TDGL_K_UNET, [&] {
-#define TDGL_BRICK(BN_, S_) k_conv_brick<BN_, S_><<<grid, 128, brick_smem<BN_, S_>(), ctx->stream>>>(bp)
+#define TDGL_BRICK(BN_, S_, ZT_) k_conv_brick<BN_, S_, ZT_><<<grid, 128, brick_smem<BN_, S_, ZT_>(), ctx->stream>>>(bp)
+#define TDGL_BRICK_Z(BN_, S_) if (zt == 2) TDGL_BRICK(BN_, S_, 2); else TDGL_BRICK(BN_, S_, 1)
             switch (bn) {
-                case 64: if (one) TDGL_BRICK(64, 1); else TDGL_BRICK(64, 2); break;
-                case 32: if (one) TDGL_BRICK(32, 1); else TDGL_BRICK(32, 2); break;
-                default: if (one) TDGL_BRICK(16, 1); else TDGL_BRICK(16, 2); break;
+                case 64: if (one) { TDGL_BRICK_Z(64, 1); } else { TDGL_BRICK_Z(64, 2); } break;
+                case 32: if (one) { TDGL_BRICK_Z(32, 1); } else { TDGL_BRICK_Z(32, 2); } break;
+                default: if (one) { TDGL_BRICK_Z(16, 1); } else { TDGL_BRICK_Z(16, 2); } break;
             }
+#undef TDGL_BRICK_Z
 #undef TDGL_BRICK
         });
     }
@@ -212,8 +218,10 @@ int launch_relu_bwd(tdgl_ctx *ctx, const float *g, const __nv_bfloat16 *out, __n
 
 template <int BN, int S>
 int set_brick_attr() {
-    return cudaFuncSetAttribute(k_conv_brick<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)brick_smem<BN, S>()) == cudaSuccess
+    return cudaFuncSetAttribute(k_conv_brick<BN, S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)brick_smem<BN, S, 1>()) == cudaSuccess &&
+                   cudaFuncSetAttribute(k_conv_brick<BN, S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)brick_smem<BN, S, 2>()) == cudaSuccess
                ? 0
                : -1;
 }

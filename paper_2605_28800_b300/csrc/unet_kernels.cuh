@@ -255,23 +255,33 @@ __global__ void k_splitk_sum(const float *__restrict__ part, int nsplit, long nv
 
 // ---- brick convolution: the input brick staged once, the 27 taps as descriptor offsets -----------
 //
-// A CTA owns 128 output voxels: x0..x0+7 (core-matrix rows) by y0..y0+15 (row groups) at one z.
-// Per 16-channel chunk of the input, two TMA loads bring the brick with its one-voxel halo,
-// 10 x 18 x 3 voxels, as two planes (channels 0-7 and 8-15 of the chunk) of 16-byte voxel records,
-// x fastest (out-of-grid voxels read as zero), and two more bring the chunk's weights for all 27
-// taps as [half][tap][output channel] records.  For a tap (dz, dy, dx) the A operand is the brick
-// read from a shifted start: row group g at ((1 + dz) * 18 + g + 1 + dy) * 10 + 1 + dx records, rows
-// 16 bytes apart, so its descriptor keeps the stride-dimension offset 160 bytes (one brick row) and
-// the leading-dimension offset one plane; the B operand of the tap is its slice of the weights.
-// One elected thread drives the pipeline: TMA into a stage, wait for its bytes, 27 MMAs, commit to
-// the stage's "empty" barrier, refill the stage once those MMAs are done.
-constexpr int kBX = 10, kBY = 18, kBZ = 3, kBrick = kBX * kBY * kBZ;     // voxel records per plane
-constexpr uint32_t kPlane = 8704u;                                        // 540 records, padded to 128 B
+// A CTA owns 128 ZT output voxels: x0..x0+7 (core-matrix rows) by y0..y0+15 (row groups) in the ZT
+// planes z0 .. z0 + ZT - 1 (ZT = 1 or 2; planes past the grid dropped).  Per 16-channel chunk of the
+// input, two TMA loads bring the brick with its one-voxel halo, 10 x 18 x (ZT + 2) voxels, as two planes
+// (channels 0-7 and 8-15 of the chunk) of 16-byte voxel records, x fastest (out-of-grid voxels read
+// as zero), and two more bring the chunk's weights for all 27 taps as [half][tap][output channel]
+// records.  For a tap (dz, dy, dx) and output plane zz the A operand is the brick read from a
+// shifted start: row group g at ((1 + zz + dz) * 18 + g + 1 + dy) * 10 + 1 + dx records, rows 16
+// bytes apart, so its descriptor keeps the stride-dimension offset 160 bytes (one brick row) and the
+// leading-dimension offset one plane; the B operand of the tap is its slice of the weights, shared
+// by the planes, whose accumulators sit side by side in tensor memory.  Two planes per CTA share
+// one brick (4 instead of 2 x 3 halo planes) and one weight load, and each copy round trip feeds 54
+// MMAs; one plane per CTA keeps twice the CTAs for grids too small to fill the GPU otherwise.  One elected thread drives the pipeline: TMA into a stage, wait for its bytes, the MMAs,
+// commit to the stage's "empty" barrier, refill the stage once those MMAs are done.
+constexpr int kBX = 10, kBY = 18;
+// ZT output planes per CTA: the brick is ZT + 2 planes deep; voxel records per 8-channel plane
+// of the brick, and its bytes padded to 128
+template <int ZT> __host__ __device__ constexpr int brick_records() { return kBX * kBY * (ZT + 2); }
+template <int ZT> __host__ __device__ constexpr uint32_t brick_plane() { return (brick_records<ZT>() * 16u + 127u) / 128u * 128u; }
+// the ZT planes' accumulators sit side by side in tensor memory
+template <int BN, int ZT> __host__ __device__ constexpr uint32_t brick_tmem_cols() { return ZT * BN < 32 ? 32u : (uint32_t)(ZT * BN); }
 template <int BN> __host__ __device__ constexpr uint32_t brick_wplane() { return 27u * BN * 16u; }
-template <int BN> __host__ __device__ constexpr uint32_t brick_stage_bytes() { return 2u * kPlane + 2u * brick_wplane<BN>(); }
+template <int BN, int ZT> __host__ __device__ constexpr uint32_t brick_stage_bytes() {
+    return 2u * brick_plane<ZT>() + 2u * brick_wplane<BN>();
+}
 // S pipeline stages: 1 when the input has a single 16-channel chunk, 2 otherwise
-template <int BN, int S> __host__ __device__ constexpr uint32_t brick_smem() {
-    return S * brick_stage_bytes<BN>() + 256u + 1024u;
+template <int BN, int S, int ZT> __host__ __device__ constexpr uint32_t brick_smem() {
+    return S * brick_stage_bytes<BN, ZT>() + 256u + 1024u;
 }
 
 // shared-memory descriptor with explicit leading / stride byte offsets
@@ -286,16 +296,17 @@ __device__ __forceinline__ uint64_t sdesc_lbo_sbo(uint32_t addr, uint32_t lbo, u
 
 struct BrickP {
     ConvP c;
-    CUtensorMap tx;   // activations [B][Z][Y][X][Ci] BF16 as (Ci, X, Y, Z, B), box (8, 10, 18, 3, 1)
+    CUtensorMap tx;   // activations [B][Z][Y][X][Ci] BF16 as (Ci, X, Y, Z, B), box (8, 10, 18, ZT + 2, 1)
     CUtensorMap tw;   // weights [27][Co][Ci] BF16 as (Ci, Co, 27), box (8, BN, 27)
 };
 
-template <int BN, int S>
+template <int BN, int S, int ZT>
 __global__ void __launch_bounds__(128) k_conv_brick(const __grid_constant__ BrickP bp) {
     const ConvP &p = bp.c;
-    constexpr uint32_t ST = brick_stage_bytes<BN>(), AB = 2u * kPlane, WP = brick_wplane<BN>();
+    constexpr uint32_t kPlane = brick_plane<ZT>();
+    constexpr uint32_t ST = brick_stage_bytes<BN, ZT>(), AB = 2u * kPlane, WP = brick_wplane<BN>();
     constexpr uint32_t idesc = tc::idesc_bf16(128, BN);
-    constexpr uint32_t kBytes = 2u * (uint32_t)kBrick * 16u + 2u * 27u * BN * 16u;   // per stage
+    constexpr uint32_t kBytes = 2u * (uint32_t)brick_records<ZT>() * 16u + 2u * 27u * BN * 16u;   // per stage
     extern __shared__ uint8_t smem_raw[];
     uint8_t *tiles = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(tiles + S * ST);
@@ -303,12 +314,12 @@ __global__ void __launch_bounds__(128) k_conv_brick(const __grid_constant__ Bric
     uint32_t *tslot = reinterpret_cast<uint32_t *>(empty + S);
     int *s_state = reinterpret_cast<int *>(tslot + 2);     // [0] MMA stages issued, [1] ok
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int nbx = p.X / 8, nby = p.Y / 16;
+    const int nbx = p.X / 8, nby = p.Y / 16, nzp = (p.Z + ZT - 1) / ZT;
     long q = blockIdx.x;
     const int bx = (int)(q % nbx); q /= nbx;
     const int by = (int)(q % nby); q /= nby;
-    const int z = (int)(q % p.Z);
-    const int b = (int)(q / p.Z);
+    const int z0 = ZT * (int)(q % nzp);           // planes z0 .. z0 + ZT - 1 (the last ones may lie past Z)
+    const int b = (int)(q / nzp);
     const int x0 = bx * 8, y0 = by * 16;
     const int n0 = blockIdx.y * BN;
     if (tid == 0) {
@@ -318,7 +329,7 @@ __global__ void __launch_bounds__(128) k_conv_brick(const __grid_constant__ Bric
         }
         tc::mbar_fence_init();
     }
-    if (tid < 32) tc::tmem_alloc(tslot, tmem_cols<BN>());
+    if (tid < 32) tc::tmem_alloc(tslot, brick_tmem_cols<BN, ZT>());
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -331,7 +342,7 @@ __global__ void __launch_bounds__(128) k_conv_brick(const __grid_constant__ Bric
             const uint32_t st = base + (uint32_t)s * ST;
             tc::mbar_expect_tx(&full[s], kBytes);
             for (int h = 0; h < 2; ++h) {
-                tc::tma_load_5d(st + (uint32_t)h * kPlane, &bp.tx, &full[s], 16 * c + 8 * h, x0 - 1, y0 - 1, z - 1, b);
+                tc::tma_load_5d(st + (uint32_t)h * kPlane, &bp.tx, &full[s], 16 * c + 8 * h, x0 - 1, y0 - 1, z0 - 1, b);
                 tc::tma_load_3d(st + AB + (uint32_t)h * WP, &bp.tw, &full[s], 16 * c + 8 * h, n0, 0);
             }
         };
@@ -347,9 +358,13 @@ __global__ void __launch_bounds__(128) k_conv_brick(const __grid_constant__ Bric
 #pragma unroll 1
             for (int t = 0; t < 27; ++t) {
                 const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-                const uint32_t a = st + (uint32_t)((((1 + dz) * kBY + 1 + dy) * kBX + 1 + dx) * 16);
-                tc::mma_bf16(tmem, sdesc_lbo_sbo(a, kPlane, kBX * 16u), sdesc_lbo_sbo(st + AB + (uint32_t)t * (BN * 16u), WP, 128u),
-                             idesc, (c > 0 || t > 0) ? 1u : 0u);
+                const uint64_t bd = sdesc_lbo_sbo(st + AB + (uint32_t)t * (BN * 16u), WP, 128u);
+#pragma unroll
+                for (int zz = 0; zz < ZT; ++zz) {   // plane z0 + zz into accumulator columns zz BN ..
+                    const uint32_t a = st + (uint32_t)((((1 + zz + dz) * kBY + 1 + dy) * kBX + 1 + dx) * 16);
+                    tc::mma_bf16(tmem + (uint32_t)(zz * BN), sdesc_lbo_sbo(a, kPlane, kBX * 16u), bd, idesc,
+                                 (c > 0 || t > 0) ? 1u : 0u);
+                }
             }
             tc::mma_commit(&empty[s]);
             issued = c + 1;
@@ -374,16 +389,24 @@ __global__ void __launch_bounds__(128) k_conv_brick(const __grid_constant__ Bric
     if (!ok) {
         if (tid == 0) atomicOr(p.err, 1);
     } else {
-        // row tid: x = x0 + tid % 8, y = y0 + tid / 8
-        const long v = (((long)b * p.Z + z) * p.Y + y0 + tid / 8) * p.X + x0 + (tid & 7);
+        // row tid: x = x0 + tid % 8, y = y0 + tid / 8, at z0 .. z0 + ZT - 1
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            float r[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-            store_row16(p, v, n0 + c0, r);
+        for (int zz = 0; zz < ZT && z0 + zz < p.Z; ++zz) {
+            const long v = (((long)b * p.Z + z0 + zz) * p.Y + y0 + tid / 8) * p.X + x0 + (tid & 7);
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                float r[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(zz * BN + c0), r);
+                store_row16(p, v, n0 + c0, r);
+            }
         }
     }
-    epilogue_free<BN>(tmem);
+    tc::fence_before();
+    __syncthreads();
+    if (tid < 32) {
+        tc::fence_after();
+        tc::tmem_free(tmem, brick_tmem_cols<BN, ZT>());
+    }
 }
 
 // Operands of the weight gradient in 8-voxel groups: for a [voxel][C] tensor, group g holds the 8
