@@ -974,8 +974,8 @@ int record_steps(tdgl_sim *s, const Work &w, int i0, int n, bool elec, bool heun
     return TDGL_OK;
 }
 
-// n steps of one sim without a status read; maxdp reset before the last step
-int steps_nosync(tdgl_sim *s, int n, double dt) {
+// n <= kStepChunk steps of one sim without a status read; maxdp reset before the last step
+int steps_chunk(tdgl_sim *s, int n, double dt) {
     tdgl_ctx *ctx = s->ctx;
     const bool elec = (s->terms & TDGL_TERM_ELEC) != 0;
     fill_desc(s, dt, s->terms);
@@ -1021,6 +1021,20 @@ int steps_nosync(tdgl_sim *s, int n, double dt) {
     if ((n & 1) && !heun) s->cur ^= 1;
     s->xstate = elec ? XS_PHAT : XS_NONE;
     s->time += n * dt;
+    return TDGL_OK;
+}
+
+// n steps of one sim without a status read; maxdp reset before the last step.  A long call runs as
+// chunks of kStepChunk steps (even, so the buffer parity repeats), each replaying the same cached
+// graph with its descriptor refreshed (the applied field's phase at the chunk's first step): the
+// graphs a sim keeps stay few and small whatever n is.
+constexpr int kStepChunk = 64;
+int steps_nosync(tdgl_sim *s, int n, double dt) {
+    for (int done = 0; done < n;) {
+        const int len = std::min(kStepChunk, n - done);
+        TRY(steps_chunk(s, len, dt));
+        done += len;
+    }
     return TDGL_OK;
 }
 
@@ -2335,7 +2349,11 @@ int tdgl_batch_step(tdgl_batch *b, int n, const double *dt) {
         active.push_back((int)i);
     }
     if (n == 0) return TDGL_OK;
-    TRY(batch_steps(b, active, n, dt));
+    for (int done = 0; done < n;) {   // chunks as for a single sim (steps_nosync)
+        const int len = std::min(kStepChunk, n - done);
+        TRY(batch_steps(b, active, len, dt));
+        done += len;
+    }
     int rc = TDGL_OK;
     for (int idx : active) {
         double m;

@@ -529,3 +529,39 @@ def test_fp32_fma_peak_is_plausible(ctx):
     nominal = p.multi_processor_count * 128 * 2 * 2.2e9 / 1e12       # 128 FP32 lanes per SM, <= 2.2 GHz
     v = ctx.fp32_fma_peak()
     assert 0.1 * nominal < v < 1.1 * nominal, (v, nominal)
+
+
+def test_long_step_calls_run_as_bounded_chunks(ctx):
+    # a step call longer than one chunk replays one cached 64-step graph per chunk (plus one for the
+    # remainder): the same states, bit for bit, as the same steps in short calls, for a sim and a
+    # batch; under an AC field (each chunk's phase from its own start time) the trajectory still
+    # matches short calls to rounding
+    from paper_2605_28800_b300 import tdgl
+    shape = (16, 16, 8)
+    dt = 0.004 / abs(coefficients(synth.BTO, 300.0)["a1x"])
+    a, _ = _bto(ctx, shape, seed=61)
+    b, _ = _bto(ctx, shape, seed=61)
+    a.step(301, dt)
+    for n in (50, 64, 1, 100, 86):
+        b.step(n, dt)
+    assert np.array_equal(a.get_P(), b.get_P())
+    c, _ = _bto(ctx, shape, seed=62)
+    d, _ = _bto(ctx, (12, 20, 8), seed=63)
+    e, _ = _bto(ctx, shape, seed=62)
+    f, _ = _bto(ctx, (12, 20, 8), seed=63)
+    B = tdgl.Batch(ctx, [c, d])
+    B.step(150, [dt, 0.8 * dt])
+    B.close()
+    for n in (40, 40, 40, 30):
+        e.step(n, dt)
+        f.step(n, 0.8 * dt)
+    assert np.array_equal(c.get_P(), e.get_P()) and np.array_equal(d.get_P(), f.get_P())
+    g, _ = _bto(ctx, shape, seed=64)
+    h, _ = _bto(ctx, shape, seed=64)
+    for s in (g, h):
+        s.set_field_ac((0.0, 0.0, 5e7), 2e9)
+    g.step(200, dt)
+    for _ in range(10):
+        h.step(20, dt)
+    assert np.abs(g.get_P() - h.get_P()).max() <= 1e-6 * np.abs(h.get_P()).max()
+    assert g.time() == pytest.approx(h.time(), rel=1e-12)
