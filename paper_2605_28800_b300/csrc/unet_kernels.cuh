@@ -471,6 +471,24 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradP p) {
             if (++z == p.Z) z = 0;
         }
     };
+    // this thread's records of the next sub-chunk's first group (A row, and B row o = tid / 2 of
+    // half tid % 2 for the threads that load B), advanced with the coordinates
+    const int ngroups = (int)((vend - vbase) >> 3);
+    const __nv_bfloat16 *acur = xrow + (vbase >> 3) * gstride;
+    constexpr int NB = (2 * BN + 127) / 128;      // B copies per thread and sub-chunk
+    const __nv_bfloat16 *bcur[NB];
+    uint32_t b_off[NB];
+    int bh[NB];
+    bool bload[NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {                // B entry i = tid + 128 r: row o = i / 2, half i % 2
+        const int i = tid + 128 * r, o = i >> 1;
+        bh[r] = i & 1;
+        bload[r] = i < 2 * BN && o < p.Co;
+        bcur[r] = p.dyt + (((vbase >> 3) + bh[r]) * p.Co + (o < p.Co ? o : 0)) * 8;
+        b_off[r] = tc::tile_off(o, bh[r]);
+    }
+    const uint32_t a_off0 = tc::tile_off(tid, 0), a_off1 = tc::tile_off(tid, 1);
     auto load = [&](int c, uint32_t a_s, uint32_t b_s) {
         for (; nextc < c; ++nextc) {
             xq += 16;
@@ -478,22 +496,25 @@ __global__ void __launch_bounds__(128) k_wgrad(WgradP p) {
                 xq -= p.X;
                 next_row(yq, zq);
             }
-        }
-        const long k0 = vbase + 16L * c;
+            acur += 2 * gstride;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {   // A: row (tap, i), voxels k0 + 8h .. + 7 (one x-row)
-            const long kv = k0 + 8 * h;
-            int y = yq, zz = zq;
-            if (h == 1 && xq + 8 >= p.X) next_row(y, zz);
-            const bool ok = rok && kv < vend && (unsigned)(zz + dz) < (unsigned)p.Z && (unsigned)(y + dy) < (unsigned)p.Y;
-            tc::cp16(a_s + tc::tile_off(tid, h), ok ? xrow + (kv >> 3) * gstride : p.xs, ok);
+            for (int r = 0; r < NB; ++r) bcur[r] += 16 * p.Co;
         }
-        for (int i = tid; i < 2 * BN; i += 128) {   // B: row o, voxels k0 + 8h .. + 7
-            const int o = i >> 1, h = i & 1;
-            const long kv = k0 + 8 * h;
-            const bool ok = o < p.Co && kv < vend;
-            tc::cp16(b_s + tc::tile_off(o, h), ok ? p.dyt + ((kv >> 3) * p.Co + o) * 8 : p.dyt, ok);
-        }
+        const int g = 2 * c;            // the sub-chunk's first group within the chunk
+        // A: row (tap, i), groups g and g + 1 (each one x-row)
+        bool ok = rok && g < ngroups && (unsigned)(zq + dz) < (unsigned)p.Z && (unsigned)(yq + dy) < (unsigned)p.Y;
+        tc::cp16(a_s + a_off0, ok ? acur : p.xs, ok);
+        int y = yq, zz = zq;
+        if (xq + 8 >= p.X) next_row(y, zz);
+        ok = rok && g + 1 < ngroups && (unsigned)(zz + dz) < (unsigned)p.Z && (unsigned)(y + dy) < (unsigned)p.Y;
+        tc::cp16(a_s + a_off1, ok ? acur + gstride : p.xs, ok);
+        // B: row o, group g + half
+#pragma unroll
+        for (int r = 0; r < NB; ++r)
+            if (tid + 128 * r < 2 * BN) {
+                const bool okb = bload[r] && g + bh[r] < ngroups;
+                tc::cp16(b_s + b_off[r], okb ? bcur[r] : p.dyt, okb);
+            }
     };
     int issued;
     const bool ok = mainloop<BN>(load, nch, tiles, bar, tmem, &issued);
