@@ -406,7 +406,10 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
     const float *const zhi = Pc + V.row0[1];   // plane z + 1
     float lmax = 0.f;
     bool bad = false;
-    double e_land = 0.0, e_grad = 0.0, e_elec = 0.0, e_ext = 0.0;
+    // energy sums of this thread's few cells in float32 (their densities are float32), widened to
+    // float64 once for the block and grid sums: one conversion per thread and term instead of a
+    // float64 add per cell, which this part's FP64 rate would make the energy pass's bottleneck
+    float e_land = 0.f, e_grad = 0.f, e_elec = 0.f, e_ext = 0.f;
     // Gradient field of a bulk cell of material m0 (all 18 neighbours inside the grid and of m0):
     // the discrete Eq. 4 reduces to G (P(+) + P(-) - 2P) / dx^2 per face pair plus
     // (G12 + G44 - G'44) times the four-corner mixed differences d_e d_f P_f (tgrad_field's bulk form).
@@ -616,11 +619,11 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
                                 cm[5] * (x2 * x2 * x2 + y2 * y2 * y2 + z2 * z2 * z2) +
                                 cm[6] * (x2 * x2 * (y2 + z2) + y2 * y2 * (x2 + z2) + z2 * z2 * (x2 + y2)) +
                                 cm[7] * x2 * y2 * z2;
-                e_land += (double)f;
+                e_land += f;
             }
             if (terms & TERM_GRAD) {
-                if constexpr (BULK) e_grad += (double)bulk_genergy(py, x, p);
-                else e_grad += (double)tgrad_energy(V, S, s_coef, py, x, m, p);
+                if constexpr (BULK) e_grad += bulk_genergy(py, x, p);
+                else e_grad += tgrad_energy(V, S, s_coef, py, x, m, p);
             }
             float el = 0.f, ex = 0.f;
 #pragma unroll
@@ -628,8 +631,8 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
                 if (elec) el = fmaf(-0.5f * Eb[(c * TYmax + r) * LX + x], p[c], el);
                 if (terms & TERM_EXT) ex = fmaf(-eext[c], p[c], ex);
             }
-            e_elec += (double)el;
-            e_ext += (double)ex;
+            e_elec += el;
+            e_ext += ex;
             return;
         }
         if (terms & TERM_LANDAU) {
@@ -666,10 +669,10 @@ __global__ void __launch_bounds__(192, 4) k_xrows(const SimDev *__restrict__ sim
     }
     if (MODE == MODE_ENERGY) {
         double v;
-        v = block_sum(e_land, s_red); if (tid == 0) atomicAdd(&S.energy[0], v);
-        v = block_sum(e_grad, s_red); if (tid == 0) atomicAdd(&S.energy[1], v);
-        v = block_sum(e_elec, s_red); if (tid == 0) atomicAdd(&S.energy[2], v);
-        v = block_sum(e_ext, s_red); if (tid == 0) atomicAdd(&S.energy[3], v);
+        v = block_sum((double)e_land, s_red); if (tid == 0) atomicAdd(&S.energy[0], v);
+        v = block_sum((double)e_grad, s_red); if (tid == 0) atomicAdd(&S.energy[1], v);
+        v = block_sum((double)e_elec, s_red); if (tid == 0) atomicAdd(&S.energy[2], v);
+        v = block_sum((double)e_ext, s_red); if (tid == 0) atomicAdd(&S.energy[3], v);
         return;
     }
     if (MODE == MODE_FIELD || MODE == MODE_DERIV) return;
